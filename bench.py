@@ -1,0 +1,375 @@
+"""Benchmark: full FMM data-structure rebuild throughput (Mpoints/s).
+
+Workload (one "step"): one fmm_build of N = M = 2^24 float32 points drawn
+i.i.d. uniform in the unit cube (sources and receivers independent), L = 7:
+Morton keys, sort, boxes of levels 0..7, E2 and E4 lists of levels 2..7.
+Inputs (402 MB) are larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle
+instead, on bounded samples of the same workload (see ``reference_arm``).
+Multi-GPU (torchrun): every rank builds its own replica (the path has no
+exchange step); value = all points of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpts/s full FMM-structure rebuild at N=M=2^24 L=7; batched vs plain; p99 ms"
+N_PTS = 1 << 24
+LEVEL = 7
+SEEDS = (3, 4)
+WORKLOAD = "plain build N=M=2^24 uniform [0,1)^3 float32, L=7, lists at levels 2..7"
+
+# Readback of one build: status word + box counts (first read) and status
+# word + list totals (second read), see api.cu.
+D2H_BYTES = 16 + 2 * (2 * 22 * 4) + 16 + 22 * 2 * 8
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _algorithmic_bytes(tree) -> dict:
+    """Compulsory traffic of one build: inputs read once, outputs written once."""
+    n, m = tree.src.n, tree.recv.n
+    b = {"xyz": 12 * (n + m), "perm": 4 * (n + m), "boxes": 0, "e2": 0, "e4": 0}
+    for sd in (tree.src, tree.recv):
+        for l in range(tree.L + 1):
+            nb = sd.nbox[l]
+            b["boxes"] += 8 * nb + 4 * (nb + 1) + 4 * nb
+    for l in range(2, tree.L + 1):
+        nr = tree.recv.nbox[l]
+        b["e2"] += 4 * (nr + 1) + 4 * tree.nnz_e2[l]
+        b["e4"] += 4 * (nr + 1) + 4 * tree.nnz_e4[l]
+    b["total"] = sum(v for k, v in b.items())
+    return b
+
+
+def _kernel_alg_bytes(name: str, tree) -> tuple:
+    """Algorithmic bytes of ALL launches of one kernel in one build, and the unit."""
+    n, m = tree.src.n, tree.recv.n
+    if name == "list_fill":  # writes the E2 and E4 index lists (offsets come from the scans)
+        return 4 * sum(tree.nnz_e2[l] + tree.nnz_e4[l] for l in range(2, tree.L + 1)), "list entries"
+    if name == "onesweep":  # one LSD pass reads and writes (u64 key, u32 index)
+        return None, "pass"
+    if name == "segment_finish":  # reads (key, index), writes the permutation
+        return 16 * (n + m), "points"
+    if name == "upfront_hist":
+        return 12 * (n + m), "points"
+    if name == "boxes":
+        bx = 0
+        for sd in (tree.src, tree.recv):
+            for l in range(tree.L + 1):
+                nb = sd.nbox[l]
+                bx += 8 * nb + 4 * (nb + 1) + 4 * nb + (4 * (nb + 1) if l < tree.L else 0)
+        return 8 * (n + m) + bx, "points"
+    return None, ""
+
+
+def _src_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1301_1704_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel: str):
+    """ncu DRAM bytes per launch of `kernel`, if captured from the current source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("src_hash") != _src_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(sub: int = 2) -> dict:
+    """The oracle (single thread) on the points of the workload that fall in
+    the sub-cube [0, 1/sub)^3: same level, same density, 1/sub^3 of the work."""
+    from oracle import oracle
+    from paper_1301_1704_gb300 import workloads
+    src = workloads.uniform(N_PTS, SEEDS[0])
+    recv = workloads.uniform(N_PTS, SEEDS[1])
+    lim = np.float32(1.0 / sub)
+    s = np.ascontiguousarray(src[np.all(src < lim, axis=1)])
+    r = np.ascontiguousarray(recv[np.all(recv < lim, axis=1)])
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.build_tree(s, r, L=LEVEL, mode=oracle.MODE_STENCIL)
+    dt = time.perf_counter() - t0
+    pts = len(s) + len(r)
+    return {"value": pts / dt / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+            "sample": f"points of the benchmark inputs inside [0,1/{sub})^3 ({len(s)} src + {len(r)} recv),"
+                      f" L={LEVEL}, stencil lists; one single-threaded run of {dt:.1f} s"}
+
+
+def reference_arm(args) -> None:
+    """`--impl reference`: the CPU oracle, each step one bounded sample of the
+    workload (points inside one of the 64 sub-cubes of side 1/4, in turn)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_1301_1704_gb300 import workloads
+    oracle.build()
+    src = workloads.uniform(N_PTS, SEEDS[0])
+    recv = workloads.uniform(N_PTS, SEEDS[1])
+    cs, cr = (src * 4).astype(np.int64).clip(0, 3), (recv * 4).astype(np.int64).clip(0, 3)
+    ids = cs[:, 0] + 4 * cs[:, 1] + 16 * cs[:, 2]
+    idr = cr[:, 0] + 4 * cr[:, 1] + 16 * cr[:, 2]
+    times, pts = [], []
+    for step in range(args.warmup + args.steps):
+        sub = step % 64
+        s = np.ascontiguousarray(src[ids == sub])
+        r = np.ascontiguousarray(recv[idr == sub])
+        t0 = time.perf_counter()
+        oracle.build_tree(s, r, L=LEVEL, mode=oracle.MODE_STENCIL)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            pts.append(len(s) + len(r))
+    total = sum(times)
+    val = sum(pts) / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Mpts/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "one 1/64 sub-cube of the inputs per step"},
+        "cpu_baseline": {"value": val, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: the points of the benchmark inputs inside one of the"
+                                   " 64 sub-cubes of side 1/4 (about 2^18 per set), L=7"},
+        "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    if args.warmup < 3:
+        raise SystemExit("warmup must be >= 3")
+
+    import torch
+    from paper_1301_1704_gb300 import fmmds, workloads
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    src_h = workloads.uniform(N_PTS, SEEDS[0])
+    recv_h = workloads.uniform(N_PTS, SEEDS[1])
+    src = torch.from_numpy(src_h).cuda()
+    recv = torch.from_numpy(recv_h).cuda()
+    ctx = fmmds.Context(local)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        tree = ctx.build(src, recv, L=LEVEL, stream=stream)
+    torch.cuda.synchronize()
+
+    # Timed region: K builds, kernel timing on (events on the build's stream).
+    ctx.reset_timing()
+    ctx.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    barrier()
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        tree = ctx.build(src, recv, L=LEVEL, stream=stream)
+        ends[i].record(stream)
+        launches += ctx.last_launch_count()
+    t_all1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ctx.set_timing(False)
+    total_ms = t_all0.elapsed_time(t_all1)
+    step_ms = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ktimes = ctx.timing()
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    pts_per_step = N_PTS * 2
+    value = pts_per_step * args.steps * ws / (total_ms / 1e3) / 1e6
+    p50 = step_ms[len(step_ms) // 2]
+    p99 = step_ms[min(len(step_ms) - 1, int(np.ceil(0.99 * len(step_ms))) - 1)]
+
+    # Roofline of the dominant kernel (largest summed time in the timed region).
+    peak, peak_kind = _peaks()
+    alg = _algorithmic_bytes(tree)
+    dom = max(ktimes.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom
+    per_build_launches = dom_launches / args.steps
+    kb, unit = _kernel_alg_bytes(dom_name, tree)
+    if kb is None and dom_name == "onesweep":
+        kb = 24 * pts_per_step * 3  # three passes per set, (8 + 4) B read + written per point
+    avg_ms = dom_ms / dom_launches
+    bytes_per_launch = kb / per_build_launches
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _traffic_for(dom_name),
+                "kernel": dom_name, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms}
+    build_frac = alg["total"] / (p50 / 1e3) / 1e9 / peak
+
+    # End to end through the C ABI: pinned host inputs, copies inside the call.
+    hs = torch.from_numpy(src_h).pin_memory()
+    hr = torch.from_numpy(recv_h).pin_memory()
+    for _ in range(2):
+        ctx.build(hs, hr, L=LEVEL, flags=fmmds.FMM_FLAG_HOST_INPUT, stream=stream)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        ctx.build(hs, hr, L=LEVEL, flags=fmmds.FMM_FLAG_HOST_INPUT, stream=stream)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = pts_per_step * args.e2e_steps * ws / (e2e_ms / 1e3) / 1e6
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N_PTS, "M": N_PTS, "L": LEVEL,
+                       "seeds": list(SEEDS), "l2": "inputs larger than L2 (402 MB of xyz)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "p50_ms": p50, "p99_ms": p99,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "roofline": roofline,
+            "build_roofline": {"alg_bytes": alg, "frac_of_peak": build_frac, "peak": peak,
+                               "note": "whole build, compulsory bytes / p50 step time"},
+            "kernel_ms_per_step": {k: v[1] / args.steps for k, v in sorted(ktimes.items())},
+            "nnz": {"e2": int(sum(tree.nnz_e2)), "e4": int(sum(tree.nnz_e4))},
+            "e2e": {"value": e2e_val, "unit": "Mpts/s", "h2d_bytes_per_step": 12 * pts_per_step,
+                    "d2h_bytes_per_step": D2H_BYTES, "steps": args.e2e_steps},
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -191,18 +191,26 @@ uint32_t max_occupancy(const Side& s, int l) {
   return m;
 }
 
+// Ascending level-l keys of the non-empty source boxes (not owned).
+struct KeyView {
+  const uint64_t* p;
+  size_t n;
+};
+
+KeyView view_of(const std::vector<uint64_t>& v) { return KeyView{v.data(), v.size()}; }
+
 // Rank of a level-l key among the non-empty source boxes, or -1.
-int64_t find_rank(const std::vector<uint64_t>& keys, uint64_t k) {
-  auto it = std::lower_bound(keys.begin(), keys.end(), k);
-  if (it == keys.end() || *it != k) return -1;
-  return (int64_t)(it - keys.begin());
+int64_t find_rank(KeyView keys, uint64_t k) {
+  const uint64_t* it = std::lower_bound(keys.p, keys.p + keys.n, k);
+  if (it == keys.p + keys.n || *it != k) return -1;
+  return (int64_t)(it - keys.p);
 }
 
 // Stencil route for one receiver box (key rk at level l >= 2).
 //   E2: the 27 cells at Chebyshev distance <= 1 inside the cube.
 //   E4: the children of the 27 cells around the parent (Sec. 1.4 item 4),
 //       minus E2.
-void stencil_lists(const std::vector<uint64_t>& src_keys, int l, uint64_t rk,
+void stencil_lists(KeyView src_keys, int l, uint64_t rk,
                    std::vector<uint32_t>* e2, std::vector<uint32_t>* e4) {
   e2->clear();
   e4->clear();
@@ -239,16 +247,16 @@ void stencil_lists(const std::vector<uint64_t>& src_keys, int l, uint64_t rk,
 
 // Brute-force route for one receiver box: every source box of the level is
 // tested against the definitions of E2 and E4.
-void brute_lists(const std::vector<uint64_t>& src_keys, int l, uint64_t rk,
+void brute_lists(KeyView src_keys, int l, uint64_t rk,
                  std::vector<uint32_t>* e2, std::vector<uint32_t>* e4) {
   e2->clear();
   e4->clear();
   int64_t c[3], pc[3];
   deinterleave(rk, l, c);
   for (int d = 0; d < 3; ++d) pc[d] = c[d] >> 1;
-  for (uint32_t t = 0; t < (uint32_t)src_keys.size(); ++t) {
+  for (uint32_t t = 0; t < (uint32_t)src_keys.n; ++t) {
     int64_t s[3], ps[3];
-    deinterleave(src_keys[t], l, s);
+    deinterleave(src_keys.p[t], l, s);
     for (int d = 0; d < 3; ++d) ps[d] = s[d] >> 1;
     if (cheb(c, s) <= 1)
       e2->push_back(t);
@@ -271,9 +279,9 @@ void make_lists(Tree* t, int mode) {
     t->e4_off[l].push_back(0);
     for (uint64_t rk : recv.key[l]) {
       if (mode == 1)
-        brute_lists(src.key[l], l, rk, &e2, &e4);
+        brute_lists(view_of(src.key[l]), l, rk, &e2, &e4);
       else
-        stencil_lists(src.key[l], l, rk, &e2, &e4);
+        stencil_lists(view_of(src.key[l]), l, rk, &e2, &e4);
       t->e2_idx[l].insert(t->e2_idx[l].end(), e2.begin(), e2.end());
       t->e4_idx[l].insert(t->e4_idx[l].end(), e4.begin(), e4.end());
       t->e2_off[l].push_back((uint32_t)t->e2_idx[l].size());
@@ -404,7 +412,7 @@ const uint32_t* orc_list_idx(void* h, int which, int l) {
 int orc_box_lists(const uint64_t* src_keys, uint32_t nsrc, int l, uint64_t rkey, int mode,
                   uint32_t* e2, uint32_t* n2, uint32_t* e4, uint32_t* n4) {
   if (l < 2 || l > kMaxLevel || (nsrc && !src_keys)) return ORC_ERR_ARG;
-  std::vector<uint64_t> keys(src_keys, src_keys + nsrc);
+  const KeyView keys{src_keys, nsrc};
   std::vector<uint32_t> a, b;
   if (mode == 1)
     brute_lists(keys, l, rkey, &a, &b);

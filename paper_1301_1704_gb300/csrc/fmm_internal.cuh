@@ -1,0 +1,257 @@
+// fmm_internal.cuh -- device helpers and kernel launchers shared by the
+// library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fmmds.h"
+
+namespace fmm {
+
+constexpr int kMaxLevel = FMM_MAX_LEVEL;
+constexpr int kLevels = FMM_LEVELS;
+
+// ---------------------------------------------------------------------------
+// Device status word.  `code` keeps the first error (fmm_status); `seg_long`
+// records that a box was too long for the in-tile finishing sort.
+struct DevStatus {
+  uint32_t code;
+  uint32_t seg_long;
+  uint32_t abort;  // set by the first wait that gives up, seen by the others
+  uint32_t pad;
+};
+
+__device__ __forceinline__ void set_error(DevStatus* st, uint32_t code) {
+  atomicCAS(&st->code, 0u, code);
+}
+
+// True once an earlier kernel (or an earlier block) has recorded an error;
+// later kernels then leave their outputs alone.
+__device__ __forceinline__ bool failed(const DevStatus* st) {
+  return *(volatile const uint32_t*)&st->code != 0u;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Morton code.  The 21 bits of a cell coordinate are spread three apart with
+// the usual shift-and-mask ladder (each step doubles the gap between groups
+// of bits: 16 -> 8 -> 4 -> 2 -> 1 bit groups); compact3 undoes it.
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | (x << 32)) & 0x001f00000000ffffull;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x001f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x001f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x1fffffull;
+  return (uint32_t)x;
+}
+
+// Cell of one coordinate at level 21; false if outside [0, 1] or NaN.
+__device__ __forceinline__ bool quantize21(float x, uint32_t* q) {
+  bool ok = (x >= 0.0f) && (x <= 1.0f);
+  float t = ok ? x * 2097152.0f : 0.0f;  // exact: power-of-two scale
+  uint32_t v = (uint32_t)t;
+  *q = v > 0x1fffffu ? 0x1fffffu : v;
+  return ok;
+}
+
+__device__ __forceinline__ uint64_t morton_key(float x, float y, float z, bool* ok) {
+  uint32_t qx, qy, qz;
+  bool a = quantize21(x, &qx), b = quantize21(y, &qy), c = quantize21(z, &qz);
+  *ok = a && b && c;
+  return spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+}
+
+// ---------------------------------------------------------------------------
+// Decoupled look-back words: 2 flag bits over a 62-bit value.
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagIncl = 2ull << 62;
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Exclusive prefix of tile `tile` for one counter, looking back over the
+// words status[j * stride] of the tiles j < tile.  Every wait is bounded:
+// after `wait_ns` (or once another thread has given up) it records
+// FMM_ERR_TIMEOUT and returns what it has.
+__device__ __forceinline__ uint64_t lookback(const uint64_t* status, uint32_t tile, uint32_t stride,
+                                             DevStatus* st, uint64_t wait_ns) {
+  uint64_t excl = 0;
+  int64_t j = (int64_t)tile - 1;
+  uint64_t t0 = 0;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    uint64_t w = ld_relaxed(status + (uint64_t)j * stride);
+    uint64_t f = w & ~kValMask;
+    if (f == kFlagIncl) {
+      excl += w & kValMask;
+      break;
+    }
+    if (f == kFlagAgg) {
+      excl += w & kValMask;
+      --j;
+      spins = 0;
+      continue;
+    }
+    // not yet published
+    ++spins;
+    if (spins > 64) {
+      if (t0 == 0) t0 = global_timer_ns();
+      __nanosleep(spins > 1024 ? 1000 : 64);
+      if ((spins & 63) == 0) {
+        if (ld_relaxed_u32(&st->abort) != 0) break;
+        if (global_timer_ns() - t0 > wait_ns) {
+          set_error(st, FMM_ERR_TIMEOUT);
+          atomicExch(&st->abort, 1u);
+          break;
+        }
+      }
+    }
+  }
+  return excl;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// Tunables of the kernels.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
+constexpr int kRadixMax = 256;
+
+constexpr int kSegThreads = 256;
+constexpr int kSegTile = 2048;
+constexpr int kSegHalo = 1024;  // longest box the finishing sort handles
+
+constexpr int kBoxThreads = 256;
+constexpr int kBoxItems = 8;
+constexpr int kBoxTile = kBoxThreads * kBoxItems;  // 2048
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+constexpr int kListThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Per-level device views handed to the kernels.
+struct LevelArrays {
+  uint32_t cap[kLevels];  // allocated boxes per level (writes are bounded by it)
+  uint64_t* key[kLevels];
+  uint32_t* off[kLevels];
+  uint32_t* parent[kLevels];
+  uint32_t* child[kLevels];
+  uint8_t* occ[kLevels];
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (host side).  All asynchronous on `s`.
+struct SortPlan {
+  int Ls;        // sort by the level-Ls key (top 3*Ls bits)
+  int passes;    // onesweep passes
+  int bits;      // digit width
+  int lo;        // lowest sorted bit
+  uint32_t ntiles;
+};
+SortPlan make_sort_plan(uint32_t n, int Ls);
+
+// Upfront digit histograms of every pass (keys computed from xyz), domain
+// check, then the exclusive digit offsets.  hist: [passes][256] zeroed.
+void launch_upfront_hist(const float* xyz, uint32_t n, const SortPlan& p, uint32_t* hist,
+                         DevStatus* st, cudaStream_t s);
+void launch_digit_scan(const SortPlan& p, uint32_t* hist, cudaStream_t s);
+// One onesweep pass.  pass 0 reads xyz (values = point index), later passes
+// read keys_in/vals_in.  status: [ntiles][256] zeroed; counter: zeroed.
+void launch_onesweep_pass(int pass, const float* xyz, const uint64_t* keys_in,
+                          const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                          uint32_t n, const SortPlan& p, const uint32_t* digit_base,
+                          uint64_t* status, uint32_t* counter, DevStatus* st, uint64_t wait_ns,
+                          int stall_tile, cudaStream_t s);
+// Finishing sort inside each level-Ls box by (full key, index) -> perm.
+void launch_segment_finish(const uint64_t* keys, const uint32_t* vals, uint32_t n, int Ls,
+                           uint32_t* perm, DevStatus* st, cudaStream_t s);
+
+// Boxes of levels 0..Lb from keys sorted by their top 3*Lb bits.
+// status: [ntiles][kLevels] zeroed; counter zeroed; nbox: [kLevels].
+void launch_boxes(const uint64_t* keys, uint32_t n, int Lb, LevelArrays lv, uint64_t* status,
+                  uint32_t* counter, uint32_t* nbox, DevStatus* st, uint64_t wait_ns,
+                  cudaStream_t s);
+uint32_t boxes_tiles(uint32_t n);
+// Child-occupancy masks of the boxes of levels 0..Lb-1.
+void launch_occupancy(int Lb, LevelArrays lv, const uint32_t* nbox, uint32_t n,
+                      const DevStatus* st, cudaStream_t s);
+// Largest box occupancy per level -> maxocc[kLevels] (zeroed).
+void launch_max_occupancy(int Lb, LevelArrays lv, const uint32_t* nbox, uint32_t n,
+                          uint32_t* maxocc, const DevStatus* st, cudaStream_t s);
+
+// Exclusive scan of u32 counts in place (count entries at data[0..count)),
+// writes data[count] = total (low 32 bits) and total64; flags
+// FMM_ERR_CAPACITY if the total needs more than 32 bits.  `count` is read
+// from device memory (*count_dev) and bounded by cap.
+void launch_scan_u32(uint32_t* data, const uint32_t* count_dev, uint32_t cap, uint64_t* status,
+                     uint32_t* counter, uint64_t* total64, DevStatus* st, uint64_t wait_ns,
+                     cudaStream_t s);
+uint32_t scan_tiles(uint32_t cap);
+
+struct ListArgs {
+  int l;
+  // receivers: parents at level l-1, boxes at level l
+  const uint32_t* nbox_recv;  // device [kLevels]
+  const uint32_t* nbox_src;
+  const uint64_t* rkey_up;    // key_recv[l-1]
+  const uint32_t* rchild_up;  // child_recv[l-1]
+  const uint64_t* rkey;       // key_recv[l]
+  // parent's E2 list at l-1 (l >= 3)
+  const uint32_t* e2_off_up;
+  const uint32_t* e2_idx_up;
+  // sources at level l-1
+  const uint64_t* skey_up;
+  const uint32_t* schild_up;
+  const uint8_t* socc_up;
+  // outputs
+  uint32_t* e2_off;
+  uint32_t* e4_off;
+  uint32_t* e2_idx;
+  uint32_t* e4_idx;
+  const uint64_t* nnz;  // device [2]: E2, E4 totals of this level (fill)
+};
+void launch_list_count(const ListArgs& a, uint32_t nparents_cap, cudaStream_t s);
+void launch_list_fill(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s);
+
+// Morton keys of n points (public fmm_morton_keys).
+void launch_keys(const float* xyz, uint32_t n, uint64_t* keys, DevStatus* st, cudaStream_t s);
+
+}  // namespace fmm

@@ -1,0 +1,231 @@
+// lists.cu -- E2 neighbour lists and E4 (M2L) interaction lists, levels 2..L.
+//
+// Alg. 4 builds E2 by a search of the 27 cells around each receiver box.  Here
+// both lists come from the level above, with no search: the children of the
+// source boxes in E2(parent(r), l-1) are exactly E2(r, l) + E4(r, l) (Sec. 1.4
+// item 4, E4 = E2(parent) minus E2).  The level-2 case uses the fact that all
+// level-1 boxes touch, so E2 at level 1 is "every non-empty source box".
+//
+// For a parent-level neighbour Q at offset delta (per axis -1, 0, +1) from
+// parent(r), and r in octant rho of its parent, a child of Q in octant o is in
+// E2(r) iff on every axis |2 delta + o - rho| <= 1, i.e.
+//     delta = 0: any child bit;  delta = +1: bit 0, only if rho = 1;
+//     delta = -1: bit 1, only if rho = 0.
+// So E2 children of Q = occ(Q) & mask(delta, rho) and the E4 children are the
+// rest of occ(Q), where occ(Q) is Q's child-occupancy byte.  A child's rank is
+// child(Q) + popc(occ(Q) below its octant), so neither list reads child keys,
+// and walking Q in ascending rank, children in ascending octant, yields
+// ascending ranks.
+//
+// One warp handles one parent box p: lane k takes the k-th entry Q_k of
+// E2(p) (at most 27), and the warp serves every receiver child r of p.
+// Counting and filling are two kernels around a prefix sum of the counts.
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+__device__ __forceinline__ uint32_t axis_mask(int delta, uint32_t rho_bit, uint32_t lo_oct,
+                                              uint32_t hi_oct) {
+  // lo_oct / hi_oct: octants with child bit 0 / 1 on this axis.
+  if (delta == 0) return lo_oct | hi_oct;
+  if (delta == 1) return rho_bit ? lo_oct : 0u;
+  return rho_bit ? 0u : hi_oct;  // delta == -1
+}
+
+__device__ __forceinline__ uint32_t e2_child_mask(int dx, int dy, int dz, uint32_t rho) {
+  return axis_mask(dx, rho & 1u, 0x55u, 0xaau) & axis_mask(dy, (rho >> 1) & 1u, 0x33u, 0xccu) &
+         axis_mask(dz, (rho >> 2) & 1u, 0x0fu, 0xf0u);
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint32_t warp_excl(uint32_t v, int lane) {
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x - v;
+}
+
+// Per-lane view of one parent-level neighbour.
+struct Neighbour {
+  int dx, dy, dz;
+  uint32_t occ;
+  uint32_t child;
+};
+
+__device__ __forceinline__ Neighbour load_neighbour(const ListArgs& a, uint32_t p, int lane) {
+  Neighbour q{0, 0, 0, 0u, 0u};
+  uint32_t m, first;
+  if (a.l == 2) {
+    first = 0;
+    m = a.nbox_src[1];
+  } else {
+    first = a.e2_off_up[p];
+    m = a.e2_off_up[p + 1] - first;
+  }
+  if ((uint32_t)lane < m) {
+    const uint32_t Q = (a.l == 2) ? (uint32_t)lane : a.e2_idx_up[first + lane];
+    const uint64_t pk = a.rkey_up[p];
+    const uint64_t qk = a.skey_up[Q];
+    q.dx = (int)compact3(qk) - (int)compact3(pk);
+    q.dy = (int)compact3(qk >> 1) - (int)compact3(pk >> 1);
+    q.dz = (int)compact3(qk >> 2) - (int)compact3(pk >> 2);
+    q.occ = a.socc_up[Q];
+    q.child = a.schild_up[Q];
+  }
+  return q;
+}
+
+__global__ void __launch_bounds__(kListThreads) list_count_kernel(ListArgs a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t np = a.nbox_recv[a.l - 1];
+  for (uint32_t p = gw; p < np; p += nw) {
+    const Neighbour q = load_neighbour(a, p, lane);
+    const uint32_t tot = warp_sum(__popc(q.occ));
+    const uint32_t c1 = a.rchild_up[p + 1];
+    for (uint32_t r = a.rchild_up[p]; r < c1; ++r) {
+      const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
+      const uint32_t n2 = warp_sum(__popc(q.occ & e2_child_mask(q.dx, q.dy, q.dz, rho)));
+      if (lane == 0) {
+        a.e2_off[r] = n2;
+        a.e4_off[r] = tot - n2;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kListThreads) list_fill_kernel(ListArgs a, DevStatus* st) {
+  if ((a.nnz[0] >> 32) != 0 || (a.nnz[1] >> 32) != 0) return;  // capacity error already set
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t np = a.nbox_recv[a.l - 1];
+  for (uint32_t p = gw; p < np; p += nw) {
+    const Neighbour q = load_neighbour(a, p, lane);
+    const uint32_t c1 = a.rchild_up[p + 1];
+    for (uint32_t r = a.rchild_up[p]; r < c1; ++r) {
+      const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
+      const uint32_t m2 = q.occ & e2_child_mask(q.dx, q.dy, q.dz, rho);
+      const uint32_t m4 = q.occ & ~m2;
+      uint32_t o2 = a.e2_off[r] + warp_excl(__popc(m2), lane);
+      uint32_t o4 = a.e4_off[r] + warp_excl(__popc(m4), lane);
+      uint32_t bits = q.occ;
+      uint32_t rank = q.child;
+      while (bits) {
+        const uint32_t o = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if ((m2 >> o) & 1u)
+          a.e2_idx[o2++] = rank;
+        else
+          a.e4_idx[o4++] = rank;
+        ++rank;
+      }
+    }
+  }
+}
+
+void launch_list_count(const ListArgs& a, uint32_t nparents_cap, cudaStream_t s) {
+  uint32_t blocks = (uint32_t)(((uint64_t)nparents_cap * 32 + kListThreads - 1) / kListThreads);
+  if (blocks > 152u * 8u) blocks = 152u * 8u;
+  if (blocks == 0) blocks = 1;
+  list_count_kernel<<<blocks, kListThreads, 0, s>>>(a);
+}
+
+void launch_list_fill(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s) {
+  uint32_t blocks = (uint32_t)(((uint64_t)nparents_cap * 32 + kListThreads - 1) / kListThreads);
+  if (blocks > 152u * 8u) blocks = 152u * 8u;
+  if (blocks == 0) blocks = 1;
+  list_fill_kernel<<<blocks, kListThreads, 0, s>>>(a, st);
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive prefix sum of u32 counts in place, single pass with decoupled
+// look-back (the CSR row starts NeighborBookmark of Alg. 4).
+__host__ __device__ inline uint32_t scan_tiles_of(uint32_t cap) {
+  const uint64_t t = ((uint64_t)cap + kScanTile - 1) / kScanTile;
+  return t == 0 ? 1u : (uint32_t)t;
+}
+
+uint32_t scan_tiles(uint32_t cap) { return scan_tiles_of(cap); }
+
+__global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(uint32_t* data,
+                                                               const uint32_t* count_dev,
+                                                               uint32_t cap, uint64_t* status,
+                                                               uint32_t* counter, uint64_t* total64,
+                                                               DevStatus* st, uint64_t wait_ns) {
+  constexpr int W = kScanThreads / 32;
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_wsum[W];
+  __shared__ uint64_t s_prev;
+  const uint32_t count = *count_dev < cap ? *count_dev : cap;
+  const uint32_t need = scan_tiles_of(count);
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile >= need) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t i0 = (uint64_t)tile * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (i0 + k < count) ? data[i0 + k] : 0u;
+    sum += v[k];
+  }
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wsum[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < W; ++w) {
+      const uint32_t c = s_wsum[w];
+      s_wsum[w] = run;
+      run += c;
+    }
+    uint64_t prev = 0;
+    if (tile == 0) {
+      st_relaxed(status, kFlagIncl | run);
+    } else {
+      st_relaxed(status + tile, kFlagAgg | run);
+      prev = lookback(status, tile, 1, st, wait_ns);
+      st_relaxed(status + tile, kFlagIncl | (prev + run));
+    }
+    s_prev = prev;
+    if (tile == need - 1) {
+      const uint64_t total = prev + run;
+      *total64 = total;
+      data[count] = (uint32_t)total;
+      if (total >> 32) set_error(st, FMM_ERR_CAPACITY);
+    }
+  }
+  __syncthreads();
+  uint64_t off = s_prev + s_wsum[warp] + (x - sum);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (i0 + k < count) data[i0 + k] = (uint32_t)off;
+    off += v[k];
+  }
+}
+
+void launch_scan_u32(uint32_t* data, const uint32_t* count_dev, uint32_t cap, uint64_t* status,
+                     uint32_t* counter, uint64_t* total64, DevStatus* st, uint64_t wait_ns,
+                     cudaStream_t s) {
+  scan_u32_kernel<<<scan_tiles(cap), kScanThreads, 0, s>>>(data, count_dev, cap, status, counter,
+                                                           total64, st, wait_ns);
+}
+
+}  // namespace fmm

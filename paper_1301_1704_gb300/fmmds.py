@@ -1,0 +1,310 @@
+"""ctypes binding of ``libfmmds.so`` (the C ABI in ``include/fmmds.h``).
+
+Argument marshalling only: every step of the build runs in the library's
+CUDA kernels.  PyTorch supplies device memory (its caching allocator backs
+the context's arena) and streams.  If the shared library is missing this
+module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfmmds.so")
+
+FMM_LEVELS = 22
+FMM_MAX_LEVEL = 21
+
+FMM_OK, FMM_ERR_ARG, FMM_ERR_DOMAIN, FMM_ERR_LEVEL = 0, 1, 2, 3
+FMM_ERR_OOM, FMM_ERR_TIMEOUT, FMM_ERR_CUDA, FMM_ERR_CAPACITY = 4, 5, 6, 7
+
+FMM_FLAG_HOST_INPUT = 0x1
+FMM_FLAG_TEST_STALL = 0x80000000
+
+_u32p = C.POINTER(C.c_uint32)
+_u64p = C.POINTER(C.c_uint64)
+_L = FMM_LEVELS
+
+
+class Params(C.Structure):
+    _fields_ = [("L", C.c_int), ("s", C.c_uint32), ("flags", C.c_uint32), ("wait_ms", C.c_uint32)]
+
+
+class TreeC(C.Structure):
+    _fields_ = [
+        ("L", C.c_int), ("s_unmet", C.c_uint32), ("n_src", C.c_uint32), ("n_recv", C.c_uint32),
+        ("perm_src", C.c_void_p), ("perm_recv", C.c_void_p),
+        ("nbox_src", C.c_uint32 * _L), ("nbox_recv", C.c_uint32 * _L),
+        ("key_src", C.c_void_p * _L), ("key_recv", C.c_void_p * _L),
+        ("off_src", C.c_void_p * _L), ("off_recv", C.c_void_p * _L),
+        ("parent_src", C.c_void_p * _L), ("parent_recv", C.c_void_p * _L),
+        ("child_src", C.c_void_p * _L), ("child_recv", C.c_void_p * _L),
+        ("nnz_e2", C.c_uint64 * _L), ("nnz_e4", C.c_uint64 * _L),
+        ("e2_off", C.c_void_p * _L), ("e2_idx", C.c_void_p * _L),
+        ("e4_off", C.c_void_p * _L), ("e4_idx", C.c_void_p * _L),
+    ]
+
+
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+# Every function declared in include/fmmds.h.
+EXPORTS = (
+    "fmm_create", "fmm_destroy", "fmm_build", "fmm_morton_keys", "fmm_query_workspace",
+    "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing", "fmm_last_launch_count",
+    "fmm_status_string",
+)
+
+_lib = None
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = _load().fmm_status_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} (status {code})")
+        self.code = code
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1301_1704_gb300.build`"
+                           " (or __graft_entry__.build()); there is no fallback path")
+    lib = C.CDLL(LIB_PATH)
+    lib.fmm_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, ALLOC_FN, FREE_FN, C.c_void_p]
+    lib.fmm_create.restype = C.c_int
+    lib.fmm_destroy.argtypes = [C.c_void_p]
+    lib.fmm_destroy.restype = C.c_int
+    lib.fmm_build.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, Params,
+                              C.POINTER(TreeC), C.c_void_p]
+    lib.fmm_build.restype = C.c_int
+    lib.fmm_morton_keys.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]
+    lib.fmm_morton_keys.restype = C.c_int
+    lib.fmm_query_workspace.argtypes = [C.c_uint32, C.c_uint32, Params, _u64p]
+    lib.fmm_query_workspace.restype = C.c_int
+    lib.fmm_set_timing.argtypes = [C.c_void_p, C.c_int]
+    lib.fmm_set_timing.restype = C.c_int
+    lib.fmm_reset_timing.argtypes = [C.c_void_p]
+    lib.fmm_reset_timing.restype = C.c_int
+    lib.fmm_get_timing.argtypes = [C.c_void_p, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)]
+    lib.fmm_get_timing.restype = C.c_int
+    lib.fmm_last_launch_count.argtypes = [C.c_void_p, _u64p]
+    lib.fmm_last_launch_count.restype = C.c_int
+    lib.fmm_status_string.argtypes = [C.c_int]
+    lib.fmm_status_string.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def library():
+    return _load()
+
+
+class _DevArray:
+    """Zero-copy view of a device array for torch.as_tensor."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {
+            "shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False), "version": 3,
+        }
+
+
+def _view(ptr, n: int, typestr: str):
+    import torch
+    if n == 0 or not ptr:
+        return torch.zeros(0, dtype=torch.int64 if typestr.endswith("8") else torch.int32,
+                           device="cuda")
+    return torch.as_tensor(_DevArray(ptr, n, typestr), device="cuda")
+
+
+@dataclass
+class Side:
+    """Per-set arrays of a build (device tensors; int32/int64 carry the uint32/uint64 bits)."""
+    n: int
+    perm: object
+    nbox: list
+    key: list = field(default_factory=list)
+    off: list = field(default_factory=list)
+    parent: list = field(default_factory=list)
+    child: list = field(default_factory=list)
+
+
+@dataclass
+class Tree:
+    """Result of :meth:`Context.build`; valid until the context's next build."""
+    L: int
+    s_unmet: int
+    src: Side
+    recv: Side
+    nnz_e2: list
+    nnz_e4: list
+    e2_off: dict
+    e2_idx: dict
+    e4_off: dict
+    e4_idx: dict
+
+    def numpy(self) -> dict:
+        """Host copy with the oracle's layout (uint32 / uint64 numpy arrays)."""
+        def u32(t):
+            return t.cpu().numpy().view(np.uint32).copy()
+
+        def u64(t):
+            return t.cpu().numpy().view(np.uint64).copy()
+
+        out = {"L": self.L, "s_unmet": self.s_unmet}
+        for name, sd in (("src", self.src), ("recv", self.recv)):
+            out[name] = {
+                "n": sd.n, "perm": u32(sd.perm),
+                "key": [u64(k) for k in sd.key], "off": [u32(o) for o in sd.off],
+                "parent": [u32(p) for p in sd.parent], "child": [u32(c) for c in sd.child],
+            }
+        for nm in ("e2_off", "e2_idx", "e4_off", "e4_idx"):
+            out[nm] = {l: u32(t) for l, t in getattr(self, nm).items()}
+        return out
+
+
+def _side(tc: TreeC, which: str, L: int, n: int) -> Side:
+    nbox = [int(v) for v in getattr(tc, "nbox_" + which)]
+    sd = Side(n=n, perm=_view(getattr(tc, "perm_" + which), n, "<i4"), nbox=nbox)
+    for l in range(L + 1):
+        nb = nbox[l]
+        sd.key.append(_view(getattr(tc, "key_" + which)[l], nb, "<i8"))
+        sd.off.append(_view(getattr(tc, "off_" + which)[l], nb + 1, "<i4"))
+        sd.parent.append(_view(getattr(tc, "parent_" + which)[l], nb if l >= 1 else 0, "<i4"))
+        sd.child.append(_view(getattr(tc, "child_" + which)[l], nb + 1 if l < L else 0, "<i4"))
+    return sd
+
+
+class Context:
+    """One fmm_ctx on one CUDA device, its arena backed by torch's allocator."""
+
+    def __init__(self, device: int = 0, torch_allocator: bool = True):
+        import torch
+        lib = _load()
+        self.device = device
+        self._h = C.c_void_p()
+        if torch_allocator:
+            def _alloc(nbytes, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, stream, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb = ALLOC_FN(_alloc)
+            self._free_cb = FREE_FN(_free)
+        else:
+            self._alloc_cb = C.cast(None, ALLOC_FN)
+            self._free_cb = C.cast(None, FREE_FN)
+        st = lib.fmm_create(C.byref(self._h), device, self._alloc_cb, self._free_cb, None)
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_create")
+
+    def close(self):
+        if self._h:
+            _load().fmm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream) -> int:
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+    def build(self, src, recv, L: int | None = None, s: int | None = None, stream=None,
+              flags: int = 0, wait_ms: int = 0, raw: bool = False):
+        """fmm_build.  ``src``/``recv``: float32 [n, 3] CUDA tensors (or pinned
+        CPU tensors with ``flags=FMM_FLAG_HOST_INPUT``).  Give ``L`` (0..21) or
+        ``s`` (cluster size).  Returns a :class:`Tree` (or the raw ``TreeC``)."""
+        lib = _load()
+        if (L is None) == (s is None):
+            raise ValueError("give exactly one of L or s")
+        p = Params(L if L is not None else -1, s if s is not None else 0, flags, wait_ms)
+        for t in (src, recv):
+            if t.dtype.itemsize != 4 or (t.numel() and not t.is_contiguous()):
+                raise ValueError("points must be contiguous float32 [n, 3]")
+        tc = TreeC()
+        n, m = src.shape[0], recv.shape[0]
+        st = lib.fmm_build(self._h, C.c_void_p(src.data_ptr() if n else 0), n,
+                           C.c_void_p(recv.data_ptr() if m else 0), m, p, C.byref(tc),
+                           C.c_void_p(self._stream(stream)))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_build")
+        if raw:
+            return tc
+        Lr = tc.L
+        tree = Tree(L=Lr, s_unmet=tc.s_unmet, src=_side(tc, "src", Lr, n),
+                    recv=_side(tc, "recv", Lr, m), nnz_e2=list(tc.nnz_e2), nnz_e4=list(tc.nnz_e4),
+                    e2_off={}, e2_idx={}, e4_off={}, e4_idx={})
+        for l in range(2, Lr + 1):
+            nr = tc.nbox_recv[l]
+            tree.e2_off[l] = _view(tc.e2_off[l], nr + 1, "<i4")
+            tree.e4_off[l] = _view(tc.e4_off[l], nr + 1, "<i4")
+            tree.e2_idx[l] = _view(tc.e2_idx[l], tc.nnz_e2[l], "<i4")
+            tree.e4_idx[l] = _view(tc.e4_idx[l], tc.nnz_e4[l], "<i4")
+        return tree
+
+    def morton_keys(self, xyz, out=None, stream=None):
+        """fmm_morton_keys: int64 CUDA tensor carrying the uint64 keys."""
+        import torch
+        lib = _load()
+        n = xyz.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.int64, device=xyz.device)
+        st = lib.fmm_morton_keys(self._h, C.c_void_p(xyz.data_ptr() if n else 0), n,
+                                 C.c_void_p(out.data_ptr() if n else 0),
+                                 C.c_void_p(self._stream(stream)))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_morton_keys")
+        return out
+
+    def set_timing(self, on: bool):
+        _load().fmm_set_timing(self._h, 1 if on else 0)
+
+    def reset_timing(self):
+        _load().fmm_reset_timing(self._h)
+
+    def timing(self) -> dict:
+        lib = _load()
+        n = C.c_int()
+        buf = (KernelTime * 64)()
+        lib.fmm_get_timing(self._h, buf, 64, C.byref(n))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+                for i in range(min(n.value, 64))}
+
+    def last_launch_count(self) -> int:
+        v = C.c_uint64()
+        _load().fmm_last_launch_count(self._h, C.byref(v))
+        return int(v.value)
+
+
+def query_workspace(N: int, M: int, L: int | None = None, s: int | None = None, flags: int = 0) -> int:
+    v = C.c_uint64()
+    p = Params(L if L is not None else -1, s if s is not None else 0, flags, 0)
+    st = _load().fmm_query_workspace(N, M, p, C.byref(v))
+    if st != FMM_OK:
+        raise FmmError(st, "fmm_query_workspace")
+    return int(v.value)
+
+
+def status_string(code: int) -> str:
+    return _load().fmm_status_string(code).decode()

@@ -1,0 +1,217 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+All of this is integer and index work, so the bar is bit-exact equality of
+every output array.  Small and medium cases compare whole trees (several
+sort, box and scan tiles plus ragged tails); the full-size workloads compare
+keys, permutations and boxes in full and the lists on sampled receiver boxes
+that the oracle computes one by one.
+"""
+import numpy as np
+import pytest
+
+from paper_1301_1704_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1301_1704_gb300 import build, fmmds
+    build.build()
+    c = fmmds.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def compare_full(got, want, L):
+    assert got["L"] == want["L"] == L
+    for side in ("src", "recv"):
+        assert np.array_equal(got[side]["perm"], want[side]["perm"]), f"{side} perm"
+        for l in range(L + 1):
+            for nm in ("key", "off", "parent", "child"):
+                g, w = got[side][nm][l], want[side][nm][l]
+                assert np.array_equal(g, w), f"{side} {nm} level {l}: {g[:8]} vs {w[:8]}"
+    for l in range(2, L + 1):
+        for nm in ("e2_off", "e2_idx", "e4_off", "e4_idx"):
+            assert np.array_equal(got[nm][l], want[nm][l]), f"{nm} level {l}"
+
+
+def run_both(ctx, orc, src, recv, L, mode=None, aliased=False):
+    s = _dev(src)
+    r = s if aliased else _dev(recv)
+    got = ctx.build(s, r, L=L).numpy()
+    want = orc.build_tree(src, src if aliased else recv, L=L,
+                          mode=orc.MODE_STENCIL if mode is None else mode)
+    return got, want
+
+
+def test_morton_keys_match_oracle(ctx, orc):
+    rng = np.random.default_rng(3)
+    pts = [rng.random((100003, 3)).astype(np.float32),
+           np.array([[0, 0, 0], [1, 1, 1], [0.5, 0.25, 1.0], [1 - 2 ** -21, 2 ** -21, 0.75]],
+                    np.float32)]
+    for p in pts:
+        got = ctx.morton_keys(_dev(p)).cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, orc.keys(p))
+
+
+def test_config1_full_tree_brute(ctx, orc):
+    src, recv, L = workloads.config_inputs(1)
+    got, want = run_both(ctx, orc, src, recv, L, mode=orc.MODE_BRUTE)
+    compare_full(got, want, L)
+
+
+@pytest.mark.parametrize("N,M,L", [
+    (1, 1, 3), (2, 7, 2), (31, 1000, 4), (4095, 4097, 5), (4096, 8191, 3), (12345, 23456, 6),
+    (100000, 77777, 5), (70001, 50000, 8),
+])
+def test_uniform_ragged_sizes(ctx, orc, N, M, L):
+    src = workloads.uniform(N, 100 + N)
+    recv = workloads.uniform(M, 200 + M)
+    got, want = run_both(ctx, orc, src, recv, L)
+    compare_full(got, want, L)
+
+
+@pytest.mark.parametrize("L", [0, 1, 2, 3, 9, 10, 12, 21])
+def test_levels_edge(ctx, orc, L):
+    src = workloads.clumps(20000, 7, nclumps=5, sigma=0.02)
+    recv = workloads.sphere(15000, 8)
+    got, want = run_both(ctx, orc, src, recv, L)
+    compare_full(got, want, L)
+
+
+def test_empty_sets(ctx, orc):
+    z = np.zeros((0, 3), np.float32)
+    p = workloads.uniform(5000, 9)
+    for src, recv in ((z, p), (p, z), (z, z)):
+        got, want = run_both(ctx, orc, src, recv, 4)
+        compare_full(got, want, 4)
+
+
+def test_identical_points(ctx, orc):
+    same = np.repeat(np.array([[0.3, 0.7, 0.1]], np.float32), 5000, axis=0)
+    got, want = run_both(ctx, orc, same, workloads.uniform(3000, 4), 5)
+    compare_full(got, want, 5)
+
+
+def test_long_boxes_take_the_full_sort(ctx, orc):
+    # 60000 points in 2 boxes at the sort depth: boxes far longer than the
+    # finishing sort's window, distinct full keys inside them.
+    rng = np.random.default_rng(5)
+    p = (0.25 + 0.01 * rng.random((60000, 3))).astype(np.float32)
+    p[:30000, 0] += 0.5
+    got, want = run_both(ctx, orc, p, p[::-1].copy(), 3)
+    compare_full(got, want, 3)
+
+
+def test_faces_and_corners(ctx, orc):
+    vals = np.array([0.0, 1.0, 0.5, 0.25, 0.75, 2.0 ** -21, 1 - 2.0 ** -24], np.float32)
+    rng = np.random.default_rng(12)
+    p = vals[rng.integers(0, len(vals), size=(9000, 3))]
+    got, want = run_both(ctx, orc, p, workloads.uniform(4000, 13), 6)
+    compare_full(got, want, 6)
+
+
+def test_aliased_sets(ctx, orc):
+    p = workloads.clumps(30000, 14, nclumps=6, sigma=0.03)
+    got, want = run_both(ctx, orc, p, p, 6, aliased=True)
+    compare_full(got, want, 6)
+    assert np.array_equal(got["src"]["perm"], got["recv"]["perm"])
+
+
+def test_host_input_flag(ctx, orc):
+    from paper_1301_1704_gb300 import fmmds
+    src = workloads.uniform(20000, 15)
+    recv = workloads.sphere(17000, 16)
+    hs = torch.from_numpy(src).pin_memory()
+    hr = torch.from_numpy(recv).pin_memory()
+    got = ctx.build(hs, hr, L=5, flags=fmmds.FMM_FLAG_HOST_INPUT).numpy()
+    compare_full(got, orc.build_tree(src, recv, L=5), 5)
+
+
+@pytest.mark.parametrize("s", [1, 8, 64, 300])
+def test_cluster_size_mode(ctx, orc, s):
+    src = workloads.clumps(40000, 17, nclumps=8, sigma=0.02)
+    recv = workloads.uniform(30000, 18)
+    got = ctx.build(_dev(src), _dev(recv), s=s).numpy()
+    want = orc.build_tree(src, recv, L=-1, s=s)
+    assert (got["L"], got["s_unmet"]) == (want["L"], want["s_unmet"])
+    compare_full(got, want, want["L"])
+
+
+def test_domain_error_then_recovery(ctx, orc):
+    from paper_1301_1704_gb300 import fmmds
+    p = workloads.uniform(10000, 19)
+    for bad in (np.nan, -0.5, 1.5):
+        q = p.copy()
+        q[1234, 1] = bad
+        with pytest.raises(fmmds.FmmError) as e:
+            ctx.build(_dev(q), _dev(p), L=4)
+        assert e.value.code == fmmds.FMM_ERR_DOMAIN
+    got, want = run_both(ctx, orc, p, p[:777].copy(), 4)
+    compare_full(got, want, 4)
+
+
+def test_bounded_wait_reports_timeout(ctx, orc):
+    """One sort tile never publishes (test flag): the bounded look-back must
+    give up with FMM_ERR_TIMEOUT, and the context must stay usable."""
+    from paper_1301_1704_gb300 import fmmds
+    p = workloads.uniform(200000, 20)
+    with pytest.raises(fmmds.FmmError) as e:
+        ctx.build(_dev(p), _dev(p[:1000].copy()), L=5, flags=fmmds.FMM_FLAG_TEST_STALL, wait_ms=100)
+    assert e.value.code == fmmds.FMM_ERR_TIMEOUT
+    got, want = run_both(ctx, orc, p[:50000].copy(), p[:1000].copy(), 5)
+    compare_full(got, want, 5)
+
+
+def test_bad_arguments(ctx):
+    from paper_1301_1704_gb300 import fmmds
+    p = _dev(workloads.uniform(10, 1))
+    with pytest.raises(fmmds.FmmError) as e:
+        ctx.build(p, p, L=22)
+    assert e.value.code == fmmds.FMM_ERR_LEVEL
+    with pytest.raises(ValueError):
+        ctx.build(p, p)
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads, in the launch configuration the benchmark times.
+
+def _sampled_lists(ctx, orc, got, want, L, per_level=400, seed=0):
+    rng = np.random.default_rng(seed)
+    for l in range(2, L + 1):
+        rk = got["recv"]["key"][l]
+        sk = got["src"]["key"][l]
+        nr = len(rk)
+        pick = np.unique(np.concatenate([[0, nr - 1], rng.integers(0, nr, size=per_level)]))
+        e2o, e2i = got["e2_off"][l].astype(np.int64), got["e2_idx"][l]
+        e4o, e4i = got["e4_off"][l].astype(np.int64), got["e4_idx"][l]
+        assert e2o[0] == 0 and e4o[0] == 0 and np.all(np.diff(e2o) >= 0) and np.all(np.diff(e4o) >= 0)
+        assert e2o[-1] == len(e2i) and e4o[-1] == len(e4i)
+        assert np.diff(e2o).max() <= 27 and np.diff(e4o).max() <= 189
+        for r in pick:
+            w2, w4 = orc.box_lists(sk, l, int(rk[r]))
+            assert np.array_equal(e2i[e2o[r]:e2o[r + 1]], w2), (l, r)
+            assert np.array_equal(e4i[e4o[r]:e4o[r + 1]], w4), (l, r)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_full_size_configs(ctx, orc, cfg):
+    src, recv, L = workloads.config_inputs(cfg)
+    got = ctx.build(_dev(src), _dev(recv), L=L).numpy()
+    want = orc.build_tree(src, recv, L=L, mode=orc.MODE_NOLISTS)
+    for side in ("src", "recv"):
+        assert np.array_equal(got[side]["perm"], want[side]["perm"]), side
+        for l in range(L + 1):
+            for nm in ("key", "off", "parent", "child"):
+                assert np.array_equal(got[side][nm][l], want[side][nm][l]), (side, nm, l)
+    _sampled_lists(ctx, orc, got, want, L, seed=cfg)
