@@ -239,6 +239,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--points", type=int, default=N_PTS,
+                    help="points per set (default 2^24; smaller values only for profiling)")
+    ap.add_argument("--level", type=int, default=LEVEL)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -261,15 +264,16 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    src_h = workloads.uniform(N_PTS, SEEDS[0])
-    recv_h = workloads.uniform(N_PTS, SEEDS[1])
+    npts, level = args.points, args.level
+    src_h = workloads.uniform(npts, SEEDS[0])
+    recv_h = workloads.uniform(npts, SEEDS[1])
     src = torch.from_numpy(src_h).cuda()
     recv = torch.from_numpy(recv_h).cuda()
     ctx = fmmds.Context(local)
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
-        tree = ctx.build(src, recv, L=LEVEL, stream=stream)
+        tree = ctx.build(src, recv, L=level, stream=stream)
     torch.cuda.synchronize()
 
     # Timed region: K builds, kernel timing on (events on the build's stream).
@@ -286,7 +290,7 @@ def main():
     t_all0.record(stream)
     for i in range(args.steps):
         starts[i].record(stream)
-        tree = ctx.build(src, recv, L=LEVEL, stream=stream)
+        tree = ctx.build(src, recv, L=level, stream=stream)
         ends[i].record(stream)
         launches += ctx.last_launch_count()
     t_all1.record(stream)
@@ -301,7 +305,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
 
-    pts_per_step = N_PTS * 2
+    pts_per_step = npts * 2
     value = pts_per_step * args.steps * ws / (total_ms / 1e3) / 1e6
     p50 = step_ms[len(step_ms) // 2]
     p99 = step_ms[min(len(step_ms) - 1, int(np.ceil(0.99 * len(step_ms))) - 1)]
@@ -327,29 +331,30 @@ def main():
     # End to end through the C ABI: pinned host inputs, copies inside the call.
     hs = torch.from_numpy(src_h).pin_memory()
     hr = torch.from_numpy(recv_h).pin_memory()
-    for _ in range(2):
-        ctx.build(hs, hr, L=LEVEL, flags=fmmds.FMM_FLAG_HOST_INPUT, stream=stream)
+    for _ in range(min(2, args.e2e_steps)):
+        ctx.build(hs, hr, L=level, flags=fmmds.FMM_FLAG_HOST_INPUT, stream=stream)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.e2e_steps):
-        ctx.build(hs, hr, L=LEVEL, flags=fmmds.FMM_FLAG_HOST_INPUT, stream=stream)
+        ctx.build(hs, hr, L=level, flags=fmmds.FMM_FLAG_HOST_INPUT, stream=stream)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms = max(e0.elapsed_time(e1), 1e-9)
     if dist is not None:
         t = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e_val = pts_per_step * args.e2e_steps * ws / (e2e_ms / 1e3) / 1e6
+    e2e_val = pts_per_step * args.e2e_steps * ws / (e2e_ms / 1e3) / 1e6 if args.e2e_steps else None
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N_PTS, "M": N_PTS, "L": LEVEL,
+            "config": {"workload": WORKLOAD if (npts, level) == (N_PTS, LEVEL) else
+                       f"profiling case N=M={npts} uniform, L={level}", "N": npts, "M": npts, "L": level,
                        "seeds": list(SEEDS), "l2": "inputs larger than L2 (402 MB of xyz)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "p50_ms": p50, "p99_ms": p99,
@@ -363,7 +368,7 @@ def main():
             "e2e": {"value": e2e_val, "unit": "Mpts/s", "h2d_bytes_per_step": 12 * pts_per_step,
                     "d2h_bytes_per_step": D2H_BYTES, "steps": args.e2e_steps},
         }
-        if not args.no_cpu_baseline and ws == 1:
+        if not args.no_cpu_baseline and ws == 1 and (npts, level) == (N_PTS, LEVEL):
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
     ctx.close()
