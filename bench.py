@@ -125,25 +125,26 @@ def _algorithmic_bytes(tree) -> dict:
     return b
 
 
-def _kernel_alg_bytes(name: str, tree) -> tuple:
-    """Algorithmic bytes of ALL launches of one kernel in one build, and the unit."""
+def _kernel_alg_bytes(name: str, tree) -> float | None:
+    """Algorithmic bytes of ALL launches of one kernel in one build (None if
+    the kernel has no compulsory traffic of its own)."""
     n, m = tree.src.n, tree.recv.n
     if name == "list_fill":  # writes the E2 and E4 index lists (offsets come from the scans)
-        return 4 * sum(tree.nnz_e2[l] + tree.nnz_e4[l] for l in range(2, tree.L + 1)), "list entries"
-    if name == "onesweep":  # one LSD pass reads and writes (u64 key, u32 index)
-        return None, "pass"
+        return 4 * sum(tree.nnz_e2[l] + tree.nnz_e4[l] for l in range(2, tree.L + 1))
+    if name == "onesweep":  # one LSD pass reads and writes (u64 key, u32 index) per point
+        return None  # filled in by the caller from the pass count
     if name == "segment_finish":  # reads (key, index), writes the permutation
-        return 16 * (n + m), "points"
-    if name == "upfront_hist":
-        return 12 * (n + m), "points"
-    if name == "boxes":
+        return 16 * (n + m)
+    if name == "upfront_hist":  # reads the coordinates
+        return 12 * (n + m)
+    if name == "boxes":  # reads the sorted keys, writes keys/offsets/parents/children
         bx = 0
         for sd in (tree.src, tree.recv):
             for l in range(tree.L + 1):
                 nb = sd.nbox[l]
                 bx += 8 * nb + 4 * (nb + 1) + 4 * nb + (4 * (nb + 1) if l < tree.L else 0)
-        return 8 * (n + m) + bx, "points"
-    return None, ""
+        return 8 * (n + m) + bx
+    return None
 
 
 def _src_hash() -> str:
@@ -313,19 +314,23 @@ def main():
     # Roofline of the dominant kernel (largest summed time in the timed region).
     peak, peak_kind = _peaks()
     alg = _algorithmic_bytes(tree)
-    dom = max(ktimes.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_launches, dom_ms) = dom
+    def alg_of(name):
+        if name == "onesweep":
+            return 24 * pts_per_step * (ktimes[name][0] / args.steps) / 2
+        return _kernel_alg_bytes(name, tree)
+
+    measured = {k: v for k, v in ktimes.items() if alg_of(k) is not None}
+    dom_name, (dom_launches, dom_ms) = max(measured.items(), key=lambda kv: kv[1][1])
     per_build_launches = dom_launches / args.steps
-    kb, unit = _kernel_alg_bytes(dom_name, tree)
-    if kb is None and dom_name == "onesweep":
-        kb = 24 * pts_per_step * 3  # three passes per set, (8 + 4) B read + written per point
     avg_ms = dom_ms / dom_launches
-    bytes_per_launch = kb / per_build_launches
+    bytes_per_launch = alg_of(dom_name) / per_build_launches
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": _traffic_for(dom_name),
                 "kernel": dom_name, "peak_kind": peak_kind,
                 "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms}
+    kernel_frac = {k: alg_of(k) / (v[1] / args.steps / 1e3) / 1e9 / peak
+                   for k, v in measured.items()}
     build_frac = alg["total"] / (p50 / 1e3) / 1e9 / peak
 
     # End to end through the C ABI: pinned host inputs, copies inside the call.
@@ -364,6 +369,7 @@ def main():
             "build_roofline": {"alg_bytes": alg, "frac_of_peak": build_frac, "peak": peak,
                                "note": "whole build, compulsory bytes / p50 step time"},
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in sorted(ktimes.items())},
+            "kernel_hbm_frac": kernel_frac,
             "nnz": {"e2": int(sum(tree.nnz_e2)), "e4": int(sum(tree.nnz_e4))},
             "e2e": {"value": e2e_val, "unit": "Mpts/s", "h2d_bytes_per_step": 12 * pts_per_step,
                     "d2h_bytes_per_step": D2H_BYTES, "steps": args.e2e_steps},
