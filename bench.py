@@ -131,19 +131,19 @@ def _kernel_alg_bytes(name: str, tree) -> float | None:
     n, m = tree.src.n, tree.recv.n
     if name == "list_fill":  # writes the E2 and E4 index lists (offsets come from the scans)
         return 4 * sum(tree.nnz_e2[l] + tree.nnz_e4[l] for l in range(2, tree.L + 1))
-    if name == "onesweep":  # one LSD pass reads and writes (u64 key, u32 index) per point
+    if name in ("onesweep", "rts_scatter"):  # one LSD pass reads and writes (u64 key, u32 index)
         return None  # filled in by the caller from the pass count
-    if name == "segment_finish":  # reads (key, index), writes the permutation
-        return 16 * (n + m)
-    if name == "upfront_hist":  # reads the coordinates
-        return 12 * (n + m)
-    if name == "boxes":  # reads the sorted keys, writes keys/offsets/parents/children
+    if name == "tile_hist":  # reads the keys (or the coordinates in the first pass)
+        return None
+    if name == "finish_boxes":  # reads (key, index), writes the permutation and every box level
         bx = 0
         for sd in (tree.src, tree.recv):
             for l in range(tree.L + 1):
                 nb = sd.nbox[l]
                 bx += 8 * nb + 4 * (nb + 1) + 4 * nb + (4 * (nb + 1) if l < tree.L else 0)
-        return 8 * (n + m) + bx
+        return 16 * (n + m) + bx
+    if name == "upfront_hist":  # reads the coordinates
+        return 12 * (n + m)
     return None
 
 
@@ -243,6 +243,7 @@ def main():
     ap.add_argument("--points", type=int, default=N_PTS,
                     help="points per set (default 2^24; smaller values only for profiling)")
     ap.add_argument("--level", type=int, default=LEVEL)
+    ap.add_argument("--sort-kind", type=int, default=None, help="0 reduce-then-scan, 1 onesweep")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -271,6 +272,8 @@ def main():
     src = torch.from_numpy(src_h).cuda()
     recv = torch.from_numpy(recv_h).cuda()
     ctx = fmmds.Context(local)
+    if args.sort_kind is not None:
+        ctx.set_tuning(args.sort_kind)
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
@@ -315,7 +318,7 @@ def main():
     peak, peak_kind = _peaks()
     alg = _algorithmic_bytes(tree)
     def alg_of(name):
-        if name == "onesweep":
+        if name in ("onesweep", "rts_scatter"):
             return 24 * pts_per_step * (ktimes[name][0] / args.steps) / 2
         return _kernel_alg_bytes(name, tree)
 
@@ -358,6 +361,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "tuning": ctx.tuning(),
             "config": {"workload": WORKLOAD if (npts, level) == (N_PTS, LEVEL) else
                        f"profiling case N=M={npts} uniform, L={level}", "N": npts, "M": npts, "L": level,
                        "seeds": list(SEEDS), "l2": "inputs larger than L2 (402 MB of xyz)",

@@ -153,6 +153,22 @@ int fmm_morton_keys(fmm_ctx* ctx, const float* xyz, uint32_t n, uint64_t* keys, 
 /* Upper bound of the arena bytes one build of this size needs. */
 int fmm_query_workspace(uint32_t N, uint32_t M, fmm_params params, uint64_t* bytes);
 
+/* Tuning of a context (the autotuner's knobs).  sort_kind selects how each
+ * radix pass finds its output positions:
+ *   FMM_SORT_RTS       per-tile digit histograms, one prefix sum, then a
+ *                      scatter with no waiting between tiles (default);
+ *   FMM_SORT_ONESWEEP  one kernel per pass, each tile finds its offsets by
+ *                      decoupled look-back over the earlier tiles.
+ * Both give the same result.  FMM_ERR_ARG for an unknown kind. */
+#define FMM_SORT_RTS 0u
+#define FMM_SORT_ONESWEEP 1u
+typedef struct fmm_tuning {
+  uint32_t sort_kind;
+} fmm_tuning;
+
+int fmm_set_tuning(fmm_ctx* ctx, const fmm_tuning* tuning);
+int fmm_get_tuning(fmm_ctx* ctx, fmm_tuning* tuning);
+
 /* Per-kernel timing with CUDA events on the build's stream (off by
  * default).  Each entry: kernel name, launches and summed milliseconds since
  * the last reset. */

@@ -4,7 +4,8 @@
 // Per set (sources, then receivers; once if both are the same array):
 //   upfront digit histograms -> digit offsets -> onesweep passes (the first
 //   one forms the Morton keys from the coordinates) -> finishing sort inside
-//   boxes (permutation) -> boxes of all levels -> child occupancy.
+//   boxes (permutation) fused with the boxes of all levels -> child
+//   occupancy.
 // Then, after one read-back of the box counts (for list capacities and the
 // cluster-size level), for l = 2..L: list counts -> two prefix sums -> fill.
 // A final read-back returns sizes and the device status word.
@@ -69,6 +70,7 @@ struct fmm_ctx {
   std::vector<TimeAcc> acc;
   uint64_t launches = 0;
   uint64_t last_launches = 0;
+  fmm_tuning tuning{FMM_SORT_RTS};
 };
 
 namespace {
@@ -232,6 +234,88 @@ uint64_t wait_ns_of(const fmm_params& p) {
   return (uint64_t)(p.wait_ms ? p.wait_ms : 2000u) * 1000000ull;
 }
 
+// Radix passes over the (key, index) pairs of one set: the first pass forms
+// the keys from the coordinates.  Output in (*kout, *vout); with
+// vals_last != null the last pass writes its values there instead.
+int sort_pairs(fmm_ctx* c, const SortPlan& plan, const float* xyz, uint32_t n, bool stall,
+               uint64_t wait_ns, uint64_t* ka, uint32_t* va, uint64_t* kb, uint32_t* vb,
+               uint32_t* vals_last, uint64_t** kout, uint32_t** vout) {
+  cudaStream_t s = c->stream;
+  int err = FMM_OK;
+  *kout = nullptr;
+  *vout = nullptr;
+  if (n == 0 || plan.passes == 0) return FMM_OK;
+  const uint32_t radix = 1u << plan.bits;
+  // The bounded-wait test needs a look-back pass: it always takes onesweep.
+  const bool onesweep = stall || c->tuning.sort_kind == FMM_SORT_ONESWEEP;
+  uint32_t* hist = nullptr;
+  uint64_t* sstatus = nullptr;
+  uint32_t* counters = nullptr;
+  size_t per_pass = 0;
+  if (onesweep) {
+    per_pass = (size_t)plan.ntiles * radix;
+    const size_t zb = align_up(sizeof(uint32_t) * 8 * kRadixMax) +
+                      align_up(sizeof(uint64_t) * per_pass * plan.passes) +
+                      align_up(sizeof(uint32_t) * 16);
+    char* z = arena_get<char>(c, zb, &err);
+    if (err) return err;
+    FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
+    hist = reinterpret_cast<uint32_t*>(z);
+    sstatus = reinterpret_cast<uint64_t*>(z + align_up(sizeof(uint32_t) * 8 * kRadixMax));
+    counters = reinterpret_cast<uint32_t*>(z + align_up(sizeof(uint32_t) * 8 * kRadixMax) +
+                                           align_up(sizeof(uint64_t) * per_pass * plan.passes));
+    {
+      Launch L(c, "upfront_hist");
+      launch_upfront_hist(xyz, n, plan, hist, c->st, s);
+    }
+    Launch L(c, "digit_scan");
+    launch_digit_scan(plan, hist, s);
+  } else {
+    per_pass = (size_t)radix * plan.ntiles;  // digit-major tile histogram
+    const uint32_t stiles = scan_tiles((uint32_t)per_pass);
+    const size_t zb = align_up(sizeof(uint64_t) * stiles) * plan.passes +
+                      align_up(sizeof(uint32_t) * 16);
+    char* z = arena_get<char>(c, zb, &err);
+    hist = arena_get<uint32_t>(c, (per_pass + 1) * plan.passes, &err);
+    if (err) return err;
+    FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
+    sstatus = reinterpret_cast<uint64_t*>(z);
+    counters = reinterpret_cast<uint32_t*>(z + align_up(sizeof(uint64_t) * stiles) * plan.passes);
+  }
+  uint64_t* kin = nullptr;
+  uint32_t* vin = nullptr;
+  for (int p = 0; p < plan.passes; ++p) {
+    uint64_t* ko = (p & 1) ? kb : ka;
+    uint32_t* vo = (p & 1) ? vb : va;
+    if (vals_last && p == plan.passes - 1) vo = vals_last;
+    if (onesweep) {
+      Launch L(c, "onesweep");
+      launch_onesweep_pass(p, xyz, kin, vin, ko, vo, n, plan, hist + p * kRadixMax,
+                           sstatus + (size_t)p * per_pass, counters + p, c->st, wait_ns,
+                           (stall && p == 0 && plan.ntiles > 2) ? 1 : -1, s);
+    } else {
+      uint32_t* h = hist + (per_pass + 1) * p;
+      const uint32_t stiles = scan_tiles((uint32_t)per_pass);
+      {
+        Launch L(c, "tile_hist");
+        launch_tile_hist(p, xyz, kin, n, plan, h, c->st, s);
+      }
+      {
+        Launch L(c, "scan");
+        launch_scan_u32(h, nullptr, (uint32_t)per_pass, sstatus + (size_t)stiles * p,
+                        counters + p, nullptr, c->st, wait_ns, s);
+      }
+      Launch L(c, "rts_scatter");
+      launch_rts_scatter(p, xyz, kin, vin, ko, vo, n, plan, h, c->st, s);
+    }
+    kin = ko;
+    vin = vo;
+  }
+  *kout = kin;
+  *vout = vin;
+  return FMM_OK;
+}
+
 // Keys, order, boxes of levels 0..Lb and (sources) occupancy for one set.
 int build_set(fmm_ctx* c, SetArrays* S, int Lb, bool need_occ, bool stall, uint64_t wait_ns,
               bool full_sort) {
@@ -240,27 +324,20 @@ int build_set(fmm_ctx* c, SetArrays* S, int Lb, bool need_occ, bool stall, uint6
   const uint32_t n = S->n;
   S->Ls = full_sort ? kMaxLevel : std::max(sort_level(n, Lb), Lb);
   const SortPlan plan = make_sort_plan(n, S->Ls);
-  const uint32_t radix = 1u << plan.bits;
 
-  // Zero-initialised scratch: histograms, look-back words, tile counters.
-  const size_t sort_status = (size_t)plan.passes * plan.ntiles * radix;
+  // Zero-initialised scratch of the box pass: look-back words, tile counter,
+  // box counts.
   const uint32_t btiles = boxes_tiles(n);
-  const size_t zero_bytes = align_up(sizeof(uint32_t) * 8 * kRadixMax) +
-                            align_up(sizeof(uint64_t) * std::max<size_t>(sort_status, 1)) +
+  const size_t zero_bytes = align_up(sizeof(uint64_t) * (size_t)btiles * kLevels) +
                             align_up(sizeof(uint32_t) * 16) +
-                            align_up(sizeof(uint64_t) * (size_t)btiles * kLevels) +
                             align_up(sizeof(uint32_t) * kLevels * 2);
   char* z = arena_get<char>(c, zero_bytes, &err);
   if (!z) return err;
   FMM_CUDA(cudaMemsetAsync(z, 0, zero_bytes, s));
-  uint32_t* hist = reinterpret_cast<uint32_t*>(z);
-  z += align_up(sizeof(uint32_t) * 8 * kRadixMax);
-  uint64_t* sstatus = reinterpret_cast<uint64_t*>(z);
-  z += align_up(sizeof(uint64_t) * std::max<size_t>(sort_status, 1));
-  uint32_t* counters = reinterpret_cast<uint32_t*>(z);
-  z += align_up(sizeof(uint32_t) * 16);
   uint64_t* bstatus = reinterpret_cast<uint64_t*>(z);
   z += align_up(sizeof(uint64_t) * (size_t)btiles * kLevels);
+  uint32_t* counters = reinterpret_cast<uint32_t*>(z);
+  z += align_up(sizeof(uint32_t) * 16);
   S->nbox_dev = reinterpret_cast<uint32_t*>(z);
   S->maxocc_dev = S->nbox_dev + kLevels;
 
@@ -270,37 +347,13 @@ int build_set(fmm_ctx* c, SetArrays* S, int Lb, bool need_occ, bool stall, uint6
   uint32_t* vb = arena_get<uint32_t>(c, n, &err);
   if (!S->perm) S->perm = arena_get<uint32_t>(c, n, &err);
   if (err) return err;
-
-  if (n && plan.passes) {
-    {
-      Launch L(c, "upfront_hist");
-      launch_upfront_hist(S->xyz, n, plan, hist, c->st, s);
-    }
-    Launch L(c, "digit_scan");
-    launch_digit_scan(plan, hist, s);
-  }
   uint64_t* kin = nullptr;
   uint32_t* vin = nullptr;
-  for (int p = 0; p < plan.passes; ++p) {
-    uint64_t* ko = (p & 1) ? kb : ka;
-    uint32_t* vo = (p & 1) ? vb : va;
-    if (n) {
-      Launch L(c, "onesweep");
-      launch_onesweep_pass(p, S->xyz, kin, vin, ko, vo, n, plan, hist + p * kRadixMax,
-                           sstatus + (size_t)p * plan.ntiles * radix, counters + p, c->st,
-                           wait_ns, (stall && p == 0 && plan.ntiles > 2) ? 1 : -1, s);
-    }
-    kin = ko;
-    vin = vo;
-  }
+  FMM_TRY(sort_pairs(c, plan, S->xyz, n, stall, wait_ns, ka, va, kb, vb, nullptr, &kin, &vin));
   S->skeys = kin;
   S->svals = vin;
-  if (n) {
-    Launch L(c, "segment_finish");
-    launch_segment_finish(kin, vin, n, S->Ls, S->perm, c->st, s);
-  }
 
-  // Boxes of levels 0..Lb.
+  // Boxes of levels 0..Lb, fused with the finishing sort (permutation).
   for (int l = 0; l <= Lb; ++l) {
     S->cap[l] = level_cap(n, l);
     S->lv.cap[l] = S->cap[l];
@@ -312,9 +365,9 @@ int build_set(fmm_ctx* c, SetArrays* S, int Lb, bool need_occ, bool stall, uint6
   }
   if (err) return err;
   {
-    Launch L(c, "boxes");
-    launch_boxes(kin ? kin : ka, n, Lb, S->lv, bstatus, counters + 15, S->nbox_dev, c->st, wait_ns,
-                 s);
+    Launch L(c, "finish_boxes");
+    launch_finish_boxes(kin ? kin : ka, vin ? vin : va, n, Lb, S->Ls, S->lv, S->perm, bstatus,
+                        counters + 15, S->nbox_dev, c->st, wait_ns, s);
   }
   if (need_occ && Lb >= 1) {
     Launch L(c, "occupancy");
@@ -326,49 +379,17 @@ int build_set(fmm_ctx* c, SetArrays* S, int Lb, bool need_occ, bool stall, uint6
 // Redoes the order of one set with the full 63-bit sort (a box was longer
 // than the finishing sort's window).  Only the permutation changes.
 int full_sort_perm(fmm_ctx* c, SetArrays* S, uint64_t wait_ns) {
-  cudaStream_t s = c->stream;
   int err = FMM_OK;
   const uint32_t n = S->n;
   const SortPlan plan = make_sort_plan(n, kMaxLevel);
-  const uint32_t radix = 1u << plan.bits;
-  const size_t sort_status = (size_t)plan.passes * plan.ntiles * radix;
-  const size_t zero_bytes = align_up(sizeof(uint32_t) * 8 * kRadixMax) +
-                            align_up(sizeof(uint64_t) * std::max<size_t>(sort_status, 1)) +
-                            align_up(sizeof(uint32_t) * 16);
-  char* z = arena_get<char>(c, zero_bytes, &err);
   uint64_t* ka = arena_get<uint64_t>(c, n, &err);
   uint32_t* va = arena_get<uint32_t>(c, n, &err);
   uint64_t* kb = arena_get<uint64_t>(c, n, &err);
   uint32_t* vb = arena_get<uint32_t>(c, n, &err);
   if (err) return err;
-  FMM_CUDA(cudaMemsetAsync(z, 0, zero_bytes, s));
-  uint32_t* hist = reinterpret_cast<uint32_t*>(z);
-  uint64_t* sstatus =
-      reinterpret_cast<uint64_t*>(z + align_up(sizeof(uint32_t) * 8 * kRadixMax));
-  uint32_t* counters = reinterpret_cast<uint32_t*>(
-      z + align_up(sizeof(uint32_t) * 8 * kRadixMax) +
-      align_up(sizeof(uint64_t) * std::max<size_t>(sort_status, 1)));
-  {
-    Launch L(c, "upfront_hist");
-    launch_upfront_hist(S->xyz, n, plan, hist, c->st, s);
-  }
-  {
-    Launch L(c, "digit_scan");
-    launch_digit_scan(plan, hist, s);
-  }
-  uint64_t* kin = nullptr;
-  uint32_t* vin = nullptr;
-  for (int p = 0; p < plan.passes; ++p) {
-    uint64_t* ko = (p & 1) ? kb : ka;
-    uint32_t* vo = (p == plan.passes - 1) ? S->perm : ((p & 1) ? vb : va);
-    Launch L(c, "onesweep");
-    launch_onesweep_pass(p, S->xyz, kin, vin, ko, vo, n, plan, hist + p * kRadixMax,
-                         sstatus + (size_t)p * plan.ntiles * radix, counters + p, c->st, wait_ns,
-                         -1, s);
-    kin = ko;
-    vin = vo;
-  }
-  return FMM_OK;
+  uint64_t* kout;
+  uint32_t* vout;
+  return sort_pairs(c, plan, S->xyz, n, false, wait_ns, ka, va, kb, vb, S->perm, &kout, &vout);
 }
 
 struct SetReadback {
@@ -709,6 +730,18 @@ int fmm_morton_keys(fmm_ctx* c, const float* xyz, uint32_t n, uint64_t* keys, vo
   FMM_CUDA(cudaStreamSynchronize(s));
   if (c->timing) collect_times(c);
   return (int)hb->st.code;
+}
+
+int fmm_set_tuning(fmm_ctx* c, const fmm_tuning* t) {
+  if (!c || !t || t->sort_kind > FMM_SORT_ONESWEEP) return FMM_ERR_ARG;
+  c->tuning = *t;
+  return FMM_OK;
+}
+
+int fmm_get_tuning(fmm_ctx* c, fmm_tuning* t) {
+  if (!c || !t) return FMM_ERR_ARG;
+  *t = c->tuning;
+  return FMM_OK;
 }
 
 int fmm_set_timing(fmm_ctx* c, int enable) {

@@ -1,5 +1,6 @@
 // boxes.cu -- non-empty boxes, bookmarks, parents and children at every
-// level (Alg. 3, Sec. 2.2), from keys sorted by their top 3*Lb bits.
+// level (Alg. 3, Sec. 2.2), from keys sorted by their top 3*Lb bits, fused
+// with the finishing sort of the point order inside each box.
 //
 // Alg. 3 scans a dense histogram of all 8^lmax boxes.  Here nothing dense is
 // built: sorted point i opens a box at level l exactly when its level-l key
@@ -19,19 +20,23 @@ uint32_t boxes_tiles(uint32_t n) {
   return t == 0 ? 1u : (uint32_t)t;
 }
 
-__global__ void __launch_bounds__(kBoxThreads) boxes_kernel(const uint64_t* __restrict__ keys,
-                                                            uint32_t n, int Lb, LevelArrays lv,
-                                                            uint64_t* status, uint32_t* counter,
-                                                            uint32_t* nbox, DevStatus* st,
-                                                            uint64_t wait_ns, uint32_t ntiles) {
-  constexpr int W = kBoxThreads / 32;
-  __shared__ uint32_t s_tile;
-  __shared__ uint64_t s_key[kBoxTile + 1];
-  __shared__ uint32_t s_wtot[W][kLevels];
-  __shared__ uint32_t s_texcl[kLevels];  // starts in all tiles before this one
-  __shared__ uint32_t s_ttot[kLevels];   // starts in this tile
+constexpr int kWin = kBoxTile + kBoxHalo;  // points held per tile
+constexpr size_t kBoxSmem = sizeof(uint64_t) * (kWin + 1) + sizeof(uint32_t) * kWin;
 
-  __shared__ uint32_t s_abort;
+// kLv: level slots held in registers (8 when Lb <= 7, else 22).
+template <int kLv>
+__global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
+    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint32_t n, int Lb,
+    int Ls, LevelArrays lv, uint32_t* __restrict__ perm, uint64_t* status, uint32_t* counter,
+    uint32_t* nbox, DevStatus* st, uint64_t wait_ns, uint32_t ntiles) {
+  constexpr int W = kBoxThreads / 32;
+  __shared__ uint32_t s_tile, s_abort;
+  __shared__ uint32_t s_wtot[W][kLevels];
+  __shared__ uint32_t s_texcl[kLevels];  // box starts in all tiles before this one
+  __shared__ uint32_t s_ttot[kLevels];   // box starts in this tile
+  extern __shared__ __align__(16) uint64_t s_key[];  // s_key[j + 1] = key of point t0 + j
+  uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kWin + 1);
+
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     s_tile = atomicAdd(counter, 1u);
@@ -40,22 +45,29 @@ __global__ void __launch_bounds__(kBoxThreads) boxes_kernel(const uint64_t* __re
   __syncthreads();
   if (s_abort) return;  // an earlier kernel failed: leave the outputs alone
   const uint32_t tile = s_tile;
-  const int64_t base = (int64_t)tile * kBoxTile;
-  for (int j = threadIdx.x; j < kBoxTile + 1; j += kBoxThreads) {
-    const int64_t i = base - 1 + j;
-    s_key[j] = (i >= 0 && i < (int64_t)n) ? keys[i] : 0ull;
+  const int64_t t0 = (int64_t)tile * kBoxTile;
+  const int64_t nn = n;
+  for (int j = threadIdx.x; j < kWin + 1; j += kBoxThreads) {
+    const int64_t i = t0 - 1 + j;
+    s_key[j] = (i >= 0 && i < nn) ? keys[i] : 0ull;
+  }
+  for (int j = threadIdx.x; j < kWin; j += kBoxThreads) {
+    const int64_t i = t0 + j;
+    s_val[j] = i < nn ? vals[i] : 0u;
   }
   __syncthreads();
 
-  // d[k]: coarsest level at which item k opens a box (0xff: none <= Lb).
+  // Box starts of levels 0..Lb.  d[k]: coarsest level at which item k
+  // opens a box (0xff: none).  Items are blocked: thread t holds kBoxItems
+  // consecutive points.
   const int hshift = 63 - 3 * Lb;
   uint32_t d[kBoxItems];
 #pragma unroll
   for (int k = 0; k < kBoxItems; ++k) {
     const int j = threadIdx.x * kBoxItems + k;
-    const int64_t i = base + j;
+    const int64_t i = t0 + j;
     uint32_t v = 0xffu;
-    if (i < (int64_t)n) {
+    if (i < nn) {
       if (i == 0) {
         v = 0;
       } else {
@@ -68,11 +80,9 @@ __global__ void __launch_bounds__(kBoxThreads) boxes_kernel(const uint64_t* __re
     }
     d[k] = v;
   }
-
-  // Per level: lane counts, warp-inclusive scan, warp totals.
-  uint32_t lex[kLevels];  // lane-exclusive prefix within the warp, per level
+  uint32_t lex[kLv];  // lane-exclusive prefix within the warp, per level
 #pragma unroll
-  for (int l = 0; l < kLevels; ++l) {
+  for (int l = 0; l < kLv; ++l) {
     lex[l] = 0;
     if (l <= Lb) {
       uint32_t c = 0;
@@ -90,29 +100,64 @@ __global__ void __launch_bounds__(kBoxThreads) boxes_kernel(const uint64_t* __re
   }
   __syncthreads();
 
-  // Thread l of warp 0 handles level l: warp prefixes, tile total, look-back.
-  if (threadIdx.x <= (unsigned)Lb) {
-    const int l = threadIdx.x;
-    uint32_t run = 0;
-    for (int w = 0; w < W; ++w) {
-      const uint32_t c = s_wtot[w][l];
-      s_wtot[w][l] = run;
-      run += c;
+  // Warp w handles levels w, w + 8, ...: warp prefixes and the tile total,
+  // published at once as this tile's aggregate.
+  for (int l = warp; l <= Lb; l += W) {
+    if (lane == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < W; ++w) {
+        const uint32_t c = s_wtot[w][l];
+        s_wtot[w][l] = run;
+        run += c;
+      }
+      s_ttot[l] = run;
+      st_relaxed(status + (uint64_t)tile * kLevels + l, (tile == 0 ? kFlagIncl : kFlagAgg) | run);
     }
-    s_ttot[l] = run;
-    uint64_t* sw = status + (uint64_t)tile * kLevels + l;
+  }
+
+  // Finishing sort inside the level-Ls boxes that START in this tile,
+  // including their points in the halo past the tile's end; a box begun in an
+  // earlier tile is finished by that tile.  In a box the points stand in index
+  // order already.  It runs between publishing this tile's aggregate and
+  // reading the earlier tiles', which gives them time to publish.
+  {
+    const int loS = 63 - 3 * Ls;
+    const int jend = (int)((nn - t0) < kWin ? (nn - t0) : kWin);  // valid window points
+    bool long_box = false;
+    for (int j = threadIdx.x; j < jend; j += kBoxThreads) {
+      const uint64_t k = s_key[j + 1];
+      const uint64_t top = k >> loS;
+      int a = j;
+      while (a > 0 && (s_key[a] >> loS) == top) --a;  // s_key[a] is point a - 1
+      if (a >= kBoxTile) continue;                                 // the next tile's box
+      if (a == 0 && t0 > 0 && (s_key[0] >> loS) == top) continue;  // an earlier tile's box
+      int b = j + 1;
+      while (b < jend && (s_key[b + 1] >> loS) == top) ++b;
+      if (b == jend && t0 + jend < nn) {
+        long_box = true;  // runs past the window: the host redoes the order
+        continue;
+      }
+      uint32_t r = 0;
+      for (int q = a; q < b; ++q) {
+        const uint64_t kq = s_key[q + 1];
+        r += (kq < k) || (kq == k && q < j);
+      }
+      perm[t0 + a + r] = s_val[j];
+    }
+    if (long_box) atomicExch(&st->seg_long, 1u);
+  }
+
+  // Windowed look-back over the earlier tiles, one warp per level.
+  for (int l = warp; l <= Lb; l += W) {
     uint64_t prev = 0;
-    if (tile == 0) {
-      st_relaxed(sw, kFlagIncl | run);
-    } else {
-      st_relaxed(sw, kFlagAgg | run);
-      prev = lookback(status + l, tile, kLevels, st, wait_ns);
-      st_relaxed(sw, kFlagIncl | (prev + run));
+    if (tile > 0) {
+      prev = lookback_warp(status + l, tile, kLevels, st, wait_ns);
+      if (lane == 0) st_relaxed(status + (uint64_t)tile * kLevels + l, kFlagIncl | (prev + s_ttot[l]));
     }
-    s_texcl[l] = (uint32_t)prev;
+    if (lane == 0) s_texcl[l] = (uint32_t)prev;
   }
   __syncthreads();
-  if (threadIdx.x <= (unsigned)Lb && tile > 0 && ld_relaxed_u32(&st->abort)) s_abort = 1;
+  if (threadIdx.x == 0 && tile > 0 && ld_relaxed_u32(&st->abort)) s_abort = 1;
   __syncthreads();
   if (s_abort) return;  // a wait gave up: ranks may be wrong, write nothing
   if (tile == ntiles - 1 && threadIdx.x == 0) {
@@ -125,21 +170,18 @@ __global__ void __launch_bounds__(kBoxThreads) boxes_kernel(const uint64_t* __re
     }
   }
 
-  // Running rank per level: starts before this thread's first item.
-  uint32_t run[kLevels];
+  uint32_t run[kLv];  // running rank per level: starts before the current item
 #pragma unroll
-  for (int l = 0; l < kLevels; ++l)
-    run[l] = (l <= Lb) ? s_texcl[l] + s_wtot[warp][l] + lex[l] : 0u;
-
+  for (int l = 0; l < kLv; ++l) run[l] = (l <= Lb) ? s_texcl[l] + s_wtot[warp][l] + lex[l] : 0u;
 #pragma unroll
   for (int k = 0; k < kBoxItems; ++k) {
     const uint32_t dk = d[k];
     if (dk <= (uint32_t)Lb) {
       const int j = threadIdx.x * kBoxItems + k;
-      const uint32_t i = (uint32_t)(base + j);
+      const uint32_t i = (uint32_t)(t0 + j);
       const uint64_t key = s_key[j + 1];
 #pragma unroll
-      for (int l = 0; l < kLevels; ++l) {
+      for (int l = 0; l < kLv; ++l) {
         if (l <= Lb && (uint32_t)l >= dk && run[l] < lv.cap[l]) {
           const uint32_t rank = run[l];
           lv.key[l][rank] = l == 0 ? 0ull : key >> (63 - 3 * l);
@@ -152,17 +194,30 @@ __global__ void __launch_bounds__(kBoxThreads) boxes_kernel(const uint64_t* __re
         }
       }
 #pragma unroll
-      for (int l = 0; l < kLevels; ++l)
+      for (int l = 0; l < kLv; ++l)
         if (l <= Lb && (uint32_t)l >= dk) ++run[l];
     }
   }
 }
 
-void launch_boxes(const uint64_t* keys, uint32_t n, int Lb, LevelArrays lv, uint64_t* status,
-                  uint32_t* counter, uint32_t* nbox, DevStatus* st, uint64_t wait_ns,
-                  cudaStream_t s) {
+void launch_finish_boxes(const uint64_t* keys, const uint32_t* vals, uint32_t n, int Lb, int Ls,
+                         LevelArrays lv, uint32_t* perm, uint64_t* status, uint32_t* counter,
+                         uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(finish_boxes_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kBoxSmem);
+    cudaFuncSetAttribute(finish_boxes_kernel<kLevels>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
+    attr = true;
+  }
   const uint32_t t = boxes_tiles(n);
-  boxes_kernel<<<t, kBoxThreads, 0, s>>>(keys, n, Lb, lv, status, counter, nbox, st, wait_ns, t);
+  if (Lb < 8)
+    finish_boxes_kernel<8><<<t, kBoxThreads, kBoxSmem, s>>>(keys, vals, n, Lb, Ls, lv, perm,
+                                                             status, counter, nbox, st, wait_ns, t);
+  else
+    finish_boxes_kernel<kLevels><<<t, kBoxThreads, kBoxSmem, s>>>(
+        keys, vals, n, Lb, Ls, lv, perm, status, counter, nbox, st, wait_ns, t);
 }
 
 // ---------------------------------------------------------------------------

@@ -98,43 +98,90 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
   return v;
 }
 
-// Exclusive prefix of tile `tile` for one counter, looking back over the
-// words status[j * stride] of the tiles j < tile.  Every wait is bounded:
-// after `wait_ns` (or once another thread has given up) it records
-// FMM_ERR_TIMEOUT and returns what it has.
-__device__ __forceinline__ uint64_t lookback(const uint64_t* status, uint32_t tile, uint32_t stride,
-                                             DevStatus* st, uint64_t wait_ns) {
-  uint64_t excl = 0;
-  int64_t j = (int64_t)tile - 1;
+// Bounded wait step shared by the look-back loops: returns true when the
+// caller must give up (time limit reached, or another thread gave up first).
+struct WaitClock {
   uint64_t t0 = 0;
   uint32_t spins = 0;
-  while (j >= 0) {
-    uint64_t w = ld_relaxed(status + (uint64_t)j * stride);
-    uint64_t f = w & ~kValMask;
-    if (f == kFlagIncl) {
-      excl += w & kValMask;
-      break;
-    }
-    if (f == kFlagAgg) {
-      excl += w & kValMask;
-      --j;
-      spins = 0;
-      continue;
-    }
-    // not yet published
+  __device__ __forceinline__ bool expired(DevStatus* st, uint64_t wait_ns) {
     ++spins;
-    if (spins > 64) {
-      if (t0 == 0) t0 = global_timer_ns();
-      __nanosleep(spins > 1024 ? 1000 : 64);
-      if ((spins & 63) == 0) {
-        if (ld_relaxed_u32(&st->abort) != 0) break;
-        if (global_timer_ns() - t0 > wait_ns) {
-          set_error(st, FMM_ERR_TIMEOUT);
-          atomicExch(&st->abort, 1u);
-          break;
-        }
+    if (spins <= 32) return false;
+    if (t0 == 0) t0 = global_timer_ns();
+    __nanosleep(spins > 1024 ? 1000 : 64);
+    if ((spins & 31) != 0) return false;
+    if (ld_relaxed_u32(&st->abort) != 0) return true;
+    if (global_timer_ns() - t0 > wait_ns) {
+      set_error(st, FMM_ERR_TIMEOUT);
+      atomicExch(&st->abort, 1u);
+      return true;
+    }
+    return false;
+  }
+};
+
+// Exclusive prefix of tile `tile` for one counter, one thread: the words
+// status[j * stride] of the tiles j < tile are read kWin at a time (independent
+// loads), aggregates are summed back to the first inclusive prefix.
+template <int kWin>
+__device__ __forceinline__ uint64_t lookback_thread(const uint64_t* status, uint32_t tile,
+                                                    uint32_t stride, DevStatus* st,
+                                                    uint64_t wait_ns) {
+  uint64_t excl = 0;
+  int64_t j = (int64_t)tile - 1;
+  WaitClock clk;
+  while (j >= 0) {
+    uint64_t w[kWin];
+#pragma unroll
+    for (int i = 0; i < kWin; ++i)
+      w[i] = (j - i >= 0) ? ld_relaxed(status + (uint64_t)(j - i) * stride) : kFlagIncl;
+    int used = 0;
+    bool done = false, stall = false;
+#pragma unroll
+    for (int i = 0; i < kWin; ++i) {
+      if (done || stall) continue;
+      const uint64_t f = w[i] & ~kValMask;
+      if (f == 0) {
+        stall = true;
+      } else {
+        excl += (j - i >= 0) ? (w[i] & kValMask) : 0;
+        ++used;
+        if (f == kFlagIncl) done = true;
       }
     }
+    if (done) break;
+    j -= used;
+    if (stall && clk.expired(st, wait_ns)) break;
+  }
+  return excl;
+}
+
+// The same for one counter with a whole warp: lane i reads tile j - i, so 32
+// predecessors are examined per round trip.  All lanes return the result.
+__device__ __forceinline__ uint64_t lookback_warp(const uint64_t* status, uint32_t tile,
+                                                  uint32_t stride, DevStatus* st,
+                                                  uint64_t wait_ns) {
+  const int lane = threadIdx.x & 31;
+  uint64_t excl = 0;
+  int64_t j = (int64_t)tile - 1;
+  WaitClock clk;
+  while (j >= 0) {
+    const int64_t t = j - lane;
+    const uint64_t w = t >= 0 ? ld_relaxed(status + (uint64_t)t * stride) : kFlagIncl;
+    const uint64_t f = w & ~kValMask;
+    const uint32_t not_ready = __ballot_sync(0xffffffffu, f == 0);
+    const uint32_t incl = __ballot_sync(0xffffffffu, f == kFlagIncl);
+    // lanes below the first blocking word (not ready, or inclusive) are usable
+    const uint32_t stop = not_ready | incl;
+    const int first = stop ? __ffs(stop) - 1 : 32;
+    const bool take_incl = first < 32 && ((incl >> first) & 1u);  // stop word is inclusive
+    const int upto = take_incl ? first + 1 : first;
+    uint64_t v = (lane < upto && t >= 0) ? (w & kValMask) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (take_incl) break;
+    j -= upto;
+    if (upto == 0 && clk.expired(st, wait_ns)) break;
   }
   return excl;
 }
@@ -148,17 +195,14 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // ---------------------------------------------------------------------------
 // Tunables of the kernels.
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
+constexpr int kSortItems = 12;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 3072
 constexpr int kRadixMax = 256;
 
-constexpr int kSegThreads = 256;
-constexpr int kSegTile = 2048;
-constexpr int kSegHalo = 1024;  // longest box the finishing sort handles
-
 constexpr int kBoxThreads = 256;
-constexpr int kBoxItems = 8;
-constexpr int kBoxTile = kBoxThreads * kBoxItems;  // 2048
+constexpr int kBoxItems = 16;
+constexpr int kBoxTile = kBoxThreads * kBoxItems;  // 4096
+constexpr int kBoxHalo = 512;  // a box the finishing sort handles ends within it
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
@@ -193,6 +237,15 @@ SortPlan make_sort_plan(uint32_t n, int Ls);
 void launch_upfront_hist(const float* xyz, uint32_t n, const SortPlan& p, uint32_t* hist,
                          DevStatus* st, cudaStream_t s);
 void launch_digit_scan(const SortPlan& p, uint32_t* hist, cudaStream_t s);
+// Reduce-then-scan pass: per-tile digit histograms, digit-major
+// ([digit][tile]), so that one exclusive scan of the flattened array gives
+// every (digit, tile) its first output position; then the scatter.
+void launch_tile_hist(int pass, const float* xyz, const uint64_t* keys, uint32_t n,
+                      const SortPlan& p, uint32_t* hist, DevStatus* st, cudaStream_t s);
+void launch_rts_scatter(int pass, const float* xyz, const uint64_t* keys_in,
+                        const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                        uint32_t n, const SortPlan& p, const uint32_t* offsets, DevStatus* st,
+                        cudaStream_t s);
 // One onesweep pass.  pass 0 reads xyz (values = point index), later passes
 // read keys_in/vals_in.  status: [ntiles][256] zeroed; counter: zeroed.
 void launch_onesweep_pass(int pass, const float* xyz, const uint64_t* keys_in,
@@ -200,15 +253,13 @@ void launch_onesweep_pass(int pass, const float* xyz, const uint64_t* keys_in,
                           uint32_t n, const SortPlan& p, const uint32_t* digit_base,
                           uint64_t* status, uint32_t* counter, DevStatus* st, uint64_t wait_ns,
                           int stall_tile, cudaStream_t s);
-// Finishing sort inside each level-Ls box by (full key, index) -> perm.
-void launch_segment_finish(const uint64_t* keys, const uint32_t* vals, uint32_t n, int Ls,
-                           uint32_t* perm, DevStatus* st, cudaStream_t s);
-
-// Boxes of levels 0..Lb from keys sorted by their top 3*Lb bits.
-// status: [ntiles][kLevels] zeroed; counter zeroed; nbox: [kLevels].
-void launch_boxes(const uint64_t* keys, uint32_t n, int Lb, LevelArrays lv, uint64_t* status,
-                  uint32_t* counter, uint32_t* nbox, DevStatus* st, uint64_t wait_ns,
-                  cudaStream_t s);
+// From (key, index) pairs sorted by the top 3*Ls key bits: the finishing
+// sort inside each level-Ls box by (full key, index) -> perm, and the boxes of
+// levels 0..Lb (Lb <= Ls).  status: [ntiles][kLevels] zeroed; counter
+// zeroed; nbox: [kLevels].
+void launch_finish_boxes(const uint64_t* keys, const uint32_t* vals, uint32_t n, int Lb, int Ls,
+                         LevelArrays lv, uint32_t* perm, uint64_t* status, uint32_t* counter,
+                         uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s);
 uint32_t boxes_tiles(uint32_t n);
 // Child-occupancy masks of the boxes of levels 0..Lb-1.
 void launch_occupancy(int Lb, LevelArrays lv, const uint32_t* nbox, uint32_t n,
@@ -218,9 +269,10 @@ void launch_max_occupancy(int Lb, LevelArrays lv, const uint32_t* nbox, uint32_t
                           uint32_t* maxocc, const DevStatus* st, cudaStream_t s);
 
 // Exclusive scan of u32 counts in place (count entries at data[0..count)),
-// writes data[count] = total (low 32 bits) and total64; flags
+// writes data[count] = total (low 32 bits) and total64 (if not null); flags
 // FMM_ERR_CAPACITY if the total needs more than 32 bits.  `count` is read
-// from device memory (*count_dev) and bounded by cap.
+// from device memory (*count_dev) and bounded by cap; count_dev == null
+// means count = cap.
 void launch_scan_u32(uint32_t* data, const uint32_t* count_dev, uint32_t cap, uint64_t* status,
                      uint32_t* counter, uint64_t* total64, DevStatus* st, uint64_t wait_ns,
                      cudaStream_t s);

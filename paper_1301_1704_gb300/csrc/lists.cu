@@ -103,33 +103,75 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(ListArgs a) {
   }
 }
 
+// Per-warp staging of one parent's output: all E4 lists of its receiver
+// children (at most 8 x 189 entries) and all E2 lists (8 x 27), each placed
+// at the alignment (mod 4 words) of its global destination so that the copy
+// out can use 16-byte stores.
+constexpr int kStageE4 = 8 * 189 + 4;
+constexpr int kStageE2 = 8 * 27 + 4;
+constexpr int kStageWords = kStageE4 + kStageE2;  // 1736 words, a multiple of 4
+constexpr int kListWarps = kListThreads / 32;
+constexpr size_t kListSmem = sizeof(uint32_t) * kStageWords * kListWarps;
+
+// Coalesced copy of the run sbuf[s0 .. s0+T) to g[0 .. T), g = s0 (mod 4).
+__device__ __forceinline__ void warp_copy_out(const uint32_t* sbuf, uint32_t s0, uint32_t* g,
+                                              uint32_t T, int lane) {
+  uint32_t head = (4u - s0) & 3u;
+  if (head > T) head = T;
+  if ((uint32_t)lane < head) g[lane] = sbuf[s0 + lane];
+  const uint32_t body = T - head;
+  const uint32_t nv = body >> 2;
+  const uint4* sv = reinterpret_cast<const uint4*>(sbuf + s0 + head);
+  uint4* gv = reinterpret_cast<uint4*>(g + head);
+  for (uint32_t v = lane; v < nv; v += 32) __stcs(gv + v, sv[v]);
+  const uint32_t rem = body & 3u;
+  if ((uint32_t)lane < rem) {
+    const uint32_t i = head + (nv << 2) + lane;
+    g[i] = sbuf[s0 + i];
+  }
+}
+
 __global__ void __launch_bounds__(kListThreads) list_fill_kernel(ListArgs a, DevStatus* st) {
+  extern __shared__ __align__(16) uint32_t s_stage[];
+  if (failed(st)) return;  // set before this launch: the same for every thread
   if ((a.nnz[0] >> 32) != 0 || (a.nnz[1] >> 32) != 0) return;  // capacity error already set
   const int lane = threadIdx.x & 31;
+  uint32_t* buf4 = s_stage + (threadIdx.x >> 5) * kStageWords;
+  uint32_t* buf2 = buf4 + kStageE4;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const uint32_t np = a.nbox_recv[a.l - 1];
   for (uint32_t p = gw; p < np; p += nw) {
     const Neighbour q = load_neighbour(a, p, lane);
-    const uint32_t c1 = a.rchild_up[p + 1];
-    for (uint32_t r = a.rchild_up[p]; r < c1; ++r) {
+    const uint32_t c0 = a.rchild_up[p], c1 = a.rchild_up[p + 1];
+    const uint32_t g2 = a.e2_off[c0], g4 = a.e4_off[c0];
+    const uint32_t s2 = g2 & 3u, s4 = g4 & 3u;
+    const uint32_t T2 = a.e2_off[c1] - g2, T4 = a.e4_off[c1] - g4;
+    if (c1 - c0 > 8 || T2 + s2 > (uint32_t)kStageE2 || T4 + s4 > (uint32_t)kStageE4) {
+      set_error(st, FMM_ERR_CAPACITY);  // impossible for consistent offsets
+      continue;
+    }
+    for (uint32_t r = c0; r < c1; ++r) {
       const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
       const uint32_t m2 = q.occ & e2_child_mask(q.dx, q.dy, q.dz, rho);
-      const uint32_t m4 = q.occ & ~m2;
-      uint32_t o2 = a.e2_off[r] + warp_excl(__popc(m2), lane);
-      uint32_t o4 = a.e4_off[r] + warp_excl(__popc(m4), lane);
+      uint32_t o2 = a.e2_off[r] - g2 + s2 + warp_excl(__popc(m2), lane);
+      uint32_t o4 = a.e4_off[r] - g4 + s4 + warp_excl(__popc(q.occ & ~m2), lane);
       uint32_t bits = q.occ;
       uint32_t rank = q.child;
       while (bits) {
         const uint32_t o = __ffs(bits) - 1;
         bits &= bits - 1;
         if ((m2 >> o) & 1u)
-          a.e2_idx[o2++] = rank;
+          buf2[o2++] = rank;
         else
-          a.e4_idx[o4++] = rank;
+          buf4[o4++] = rank;
         ++rank;
       }
     }
+    __syncwarp();
+    warp_copy_out(buf4, s4, a.e4_idx + g4, T4, lane);
+    warp_copy_out(buf2, s2, a.e2_idx + g2, T2, lane);
+    __syncwarp();
   }
 }
 
@@ -141,10 +183,16 @@ void launch_list_count(const ListArgs& a, uint32_t nparents_cap, cudaStream_t s)
 }
 
 void launch_list_fill(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(list_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kListSmem);
+    attr = true;
+  }
   uint32_t blocks = (uint32_t)(((uint64_t)nparents_cap * 32 + kListThreads - 1) / kListThreads);
-  if (blocks > 152u * 8u) blocks = 152u * 8u;
+  if (blocks > 152u * 4u) blocks = 152u * 4u;
   if (blocks == 0) blocks = 1;
-  list_fill_kernel<<<blocks, kListThreads, 0, s>>>(a, st);
+  list_fill_kernel<<<blocks, kListThreads, kListSmem, s>>>(a, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -166,7 +214,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(uint32_t* data,
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wsum[W];
   __shared__ uint64_t s_prev;
-  const uint32_t count = *count_dev < cap ? *count_dev : cap;
+  const uint32_t count = (count_dev && *count_dev < cap) ? *count_dev : cap;
   const uint32_t need = scan_tiles_of(count);
   if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
   __syncthreads();
@@ -189,27 +237,32 @@ __global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(uint32_t* data,
   }
   if (lane == 31) s_wsum[warp] = x;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
     uint32_t run = 0;
-    for (int w = 0; w < W; ++w) {
-      const uint32_t c = s_wsum[w];
-      s_wsum[w] = run;
-      run += c;
+    if (lane == 0) {
+      for (int w = 0; w < W; ++w) {
+        const uint32_t c = s_wsum[w];
+        s_wsum[w] = run;
+        run += c;
+      }
     }
+    run = __shfl_sync(0xffffffffu, run, 0);
     uint64_t prev = 0;
     if (tile == 0) {
-      st_relaxed(status, kFlagIncl | run);
+      if (lane == 0) st_relaxed(status, kFlagIncl | run);
     } else {
-      st_relaxed(status + tile, kFlagAgg | run);
-      prev = lookback(status, tile, 1, st, wait_ns);
-      st_relaxed(status + tile, kFlagIncl | (prev + run));
+      if (lane == 0) st_relaxed(status + tile, kFlagAgg | run);
+      prev = lookback_warp(status, tile, 1, st, wait_ns);
+      if (lane == 0) st_relaxed(status + tile, kFlagIncl | (prev + run));
     }
-    s_prev = prev;
-    if (tile == need - 1) {
-      const uint64_t total = prev + run;
-      *total64 = total;
-      data[count] = (uint32_t)total;
-      if (total >> 32) set_error(st, FMM_ERR_CAPACITY);
+    if (lane == 0) {
+      s_prev = prev;
+      if (tile == need - 1) {
+        const uint64_t total = prev + run;
+        if (total64) *total64 = total;
+        data[count] = (uint32_t)total;
+        if (total >> 32) set_error(st, FMM_ERR_CAPACITY);
+      }
     }
   }
   __syncthreads();

@@ -12,11 +12,8 @@
 //      the stores of one digit are contiguous.  The first pass reads the
 //      coordinates and forms the keys on the fly; the digit histograms of all
 //      passes come from one upfront read of the coordinates.
-//   2. a finishing sort inside each level-Ls box by the full key: boxes are
-//      short (about 8 points at the benchmark sizes), so each point counts
-//      the points of its box that precede it.  A box longer than the halo of
-//      a tile is reported (seg_long) and the host redoes the set with the full
-//      63-bit sort.
+//   2. a finishing sort inside each level-Ls box by the full key, fused with
+//      the box construction (boxes.cu).
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -54,34 +51,45 @@ void launch_keys(const float* xyz, uint32_t n, uint64_t* keys, DevStatus* st, cu
 
 // ---------------------------------------------------------------------------
 // Upfront histograms: one read of the coordinates gives the digit counts of
-// every pass.  Warp-aggregated shared-memory atomics (match_any) keep hot
-// digits of clustered inputs from serialising.
+// every pass.  Four points per thread and step come in as three float4 loads
+// (the coordinates must then be 16-byte aligned); block-private histograms
+// in shared memory take plain atomics.
+__device__ __forceinline__ void hist_point(float x, float y, float z, int passes, int bits,
+                                           int lo, uint32_t mask, uint32_t* sh, bool* bad) {
+  bool ok;
+  const uint64_t key = morton_key(x, y, z, &ok);
+  *bad |= !ok;
+  for (int p = 0; p < passes; ++p)
+    atomicAdd(&sh[p * kRadixMax + ((uint32_t)(key >> (lo + p * bits)) & mask)], 1u);
+}
+
 __global__ void __launch_bounds__(256) upfront_hist_kernel(const float* __restrict__ xyz,
                                                            uint32_t n, int passes, int bits,
-                                                           int lo, uint32_t* __restrict__ hist,
+                                                           int lo, bool vec,
+                                                           uint32_t* __restrict__ hist,
                                                            DevStatus* st) {
   __shared__ uint32_t sh[8 * kRadixMax];
   for (int i = threadIdx.x; i < 8 * kRadixMax; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const uint32_t mask = (1u << bits) - 1u;
-  const uint32_t lt = lanemask_lt();
   bool bad = false;
-  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
-       i0 += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t i = i0 + threadIdx.x;
-    const bool valid = i < n;
-    uint64_t key = 0;
-    if (valid) {
-      bool ok;
-      key = morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok);
-      bad |= !ok;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t done = 0;
+  if (vec) {
+    const float4* v = reinterpret_cast<const float4*>(xyz);
+    const uint64_t groups = n / 4;
+    for (uint64_t g = tid; g < groups; g += stride) {
+      const float4 a = __ldcs(v + 3 * g), b = __ldcs(v + 3 * g + 1), c = __ldcs(v + 3 * g + 2);
+      hist_point(a.x, a.y, a.z, passes, bits, lo, mask, sh, &bad);
+      hist_point(a.w, b.x, b.y, passes, bits, lo, mask, sh, &bad);
+      hist_point(b.z, b.w, c.x, passes, bits, lo, mask, sh, &bad);
+      hist_point(c.y, c.z, c.w, passes, bits, lo, mask, sh, &bad);
     }
-    for (int p = 0; p < passes; ++p) {
-      const uint32_t d = valid ? (uint32_t)(key >> (lo + p * bits)) & mask : 0xffffffffu;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (valid && (peers & lt) == 0) atomicAdd(&sh[p * kRadixMax + d], (uint32_t)__popc(peers));
-    }
+    done = groups * 4;
   }
+  for (uint64_t i = done + tid; i < n; i += stride)
+    hist_point(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], passes, bits, lo, mask, sh, &bad);
   __syncthreads();
   const int radix = 1 << bits;
   for (int i = threadIdx.x; i < passes * kRadixMax; i += blockDim.x) {
@@ -94,9 +102,11 @@ __global__ void __launch_bounds__(256) upfront_hist_kernel(const float* __restri
 void launch_upfront_hist(const float* xyz, uint32_t n, const SortPlan& p, uint32_t* hist,
                          DevStatus* st, cudaStream_t s) {
   if (n == 0 || p.passes == 0) return;
-  uint32_t blocks = (uint32_t)(((uint64_t)n + 255) / 256);
+  const bool vec = ((uintptr_t)xyz & 15u) == 0;
+  uint32_t blocks = (uint32_t)(((uint64_t)n / 4 + 255) / 256);
   if (blocks > 152u * 8u) blocks = 152u * 8u;
-  upfront_hist_kernel<<<blocks, 256, 0, s>>>(xyz, n, p.passes, p.bits, p.lo, hist, st);
+  if (blocks == 0) blocks = 1;
+  upfront_hist_kernel<<<blocks, 256, 0, s>>>(xyz, n, p.passes, p.bits, p.lo, vec, hist, st);
 }
 
 // Exclusive scan of each pass's digit counts (one block, one warp per pass).
@@ -124,25 +134,28 @@ void launch_digit_scan(const SortPlan& p, uint32_t* hist, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// One onesweep pass.
+// One onesweep pass.  Shared memory: per-warp digit counters, then the tile
+// reordered by digit as (key, index) so that each digit's run leaves as one
+// contiguous store sequence.
+constexpr size_t kSortSmem = sizeof(uint64_t) * kSortTile + sizeof(uint32_t) * kSortTile;
+
 template <bool kFromXyz>
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
+__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     const float* __restrict__ xyz, const uint64_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint32_t n, int shift, int bits,
     const uint32_t* __restrict__ digit_base, uint64_t* status, uint32_t* counter,
     DevStatus* st, uint64_t wait_ns, int stall_tile) {
   constexpr int W = kSortThreads / 32;
-  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_tile, s_abort;
   __shared__ uint32_t s_wcnt[W][kRadixMax];  // per-warp digit counts, then prefixes
-  __shared__ uint32_t s_doff[kRadixMax];     // block-exclusive digit offsets
   __shared__ uint32_t s_gbase[kRadixMax];    // global position of block slot 0, per digit
   __shared__ uint32_t s_wsum[W];
-  __shared__ __align__(16) uint64_t s_buf[kSortTile];
+  extern __shared__ __align__(16) uint64_t s_keys[];
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kSortTile);
 
   const uint32_t radix = 1u << bits, mask = radix - 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ uint32_t s_abort;
   for (int i = threadIdx.x; i < W * kRadixMax; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
   if (threadIdx.x == 0) {
     s_tile = atomicAdd(counter, 1u);
@@ -156,25 +169,25 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
 
   // Warp-striped load: item k of lane j is element wbase + 32k + j, so the
   // (k, lane) order below is the input order and ranking stays stable.
+  // Values are fetched only when the tile is reordered (shorter live range);
+  // in the first pass the value is the point index itself.
   uint64_t key[kSortItems];
-  uint32_t val[kSortItems];
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const uint64_t i = wbase + k * 32 + lane;
     key[k] = 0;
-    val[k] = 0;
     if (i < n) {
       if (kFromXyz) {
         bool ok;
         key[k] = morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok);
-        val[k] = (uint32_t)i;
       } else {
         key[k] = keys_in[i];
-        val[k] = vals_in[i];
       }
     }
   }
 
+  // Stable rank within the warp: peers with the same digit by match_any,
+  // running per-warp digit counters in shared memory.
   const uint32_t lt = lanemask_lt();
   uint32_t pos[kSortItems];
 #pragma unroll
@@ -190,7 +203,8 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
   }
   __syncthreads();
 
-  // Digit totals of the tile; s_wcnt becomes the per-warp exclusive prefix.
+  // Digit totals of the tile (published at once as an aggregate); s_wcnt
+  // becomes the per-warp exclusive prefix.
   uint32_t tot = 0;
   if (threadIdx.x < radix) {
 #pragma unroll
@@ -199,9 +213,8 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
       s_wcnt[w][threadIdx.x] = tot;
       tot += c;
     }
-    const bool stalled = (int)tile == stall_tile;
-    if (!stalled)
-      st_relaxed(status + base / kSortTile * radix + threadIdx.x,
+    if ((int)tile != stall_tile)
+      st_relaxed(status + (uint64_t)tile * radix + threadIdx.x,
                  (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
   }
   // Block-exclusive scan of the digit totals.
@@ -213,21 +226,42 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
   }
   if (lane == 31) s_wsum[warp] = x;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int w = 0; w < W; ++w) {
-      const uint32_t c = s_wsum[w];
-      s_wsum[w] = run;
-      run += c;
+  if (threadIdx.x < 32) {
+    const uint32_t v = lane < W ? s_wsum[lane] : 0u;
+    uint32_t y = v;
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+      const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
     }
+    if (lane < W) s_wsum[lane] = y - v;
   }
   __syncthreads();
   const uint32_t excl_blk = x - tot + s_wsum[warp];
   if (threadIdx.x < radix) {
-    s_doff[threadIdx.x] = excl_blk;
+    // s_wcnt[w][d] + excl_blk: block slot of warp w's first item of digit d
+#pragma unroll
+    for (int w = 0; w < W; ++w) s_wcnt[w][threadIdx.x] += excl_blk;
+  }
+  __syncthreads();
+
+  // Reorder the tile by digit in shared memory (values are fetched here).
+  // This work sits between publishing the aggregate and reading the earlier
+  // tiles' words, which gives them time to publish.
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const uint64_t i = wbase + k * 32 + lane;
+    if (i < n) {
+      const uint32_t d = (uint32_t)(key[k] >> shift) & mask;
+      const uint32_t p = pos[k] + s_wcnt[warp][d];
+      s_keys[p] = key[k];
+      s_vals[p] = kFromXyz ? (uint32_t)i : vals_in[i];
+    }
+  }
+  if (threadIdx.x < radix) {
     uint64_t prev = 0;
     if (tile > 0) {
-      prev = lookback(status + threadIdx.x, tile, radix, st, wait_ns);
+      prev = lookback_thread<16>(status + threadIdx.x, tile, radix, st, wait_ns);
       if ((int)tile != stall_tile)
         st_relaxed(status + (uint64_t)tile * radix + threadIdx.x, kFlagIncl | (prev + tot));
     }
@@ -238,39 +272,18 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
   __syncthreads();
   if (s_abort) return;  // a wait gave up: offsets may be wrong, write nothing
 
-  // Scatter through shared memory: keys first, then values.
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    if (wbase + k * 32 + lane < n) {
-      const uint32_t d = (uint32_t)(key[k] >> shift) & mask;
-      pos[k] += s_doff[d] + s_wcnt[warp][d];
-      s_buf[pos[k]] = key[k];
-    }
-  }
-  __syncthreads();
   const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
-  uint32_t gdst[kSortItems];
-#pragma unroll
+#pragma unroll 4
   for (int j = 0; j < kSortItems; ++j) {
     const uint32_t p = threadIdx.x + j * kSortThreads;
-    gdst[j] = 0;
     if (p < cnt) {
-      const uint64_t kk = s_buf[p];
-      const uint32_t d = (uint32_t)(kk >> shift) & mask;
-      gdst[j] = s_gbase[d] + p;
-      if (gdst[j] < n) keys_out[gdst[j]] = kk;
+      const uint64_t kk = s_keys[p];
+      const uint32_t g = s_gbase[(uint32_t)(kk >> shift) & mask] + p;
+      if (g < n) {
+        keys_out[g] = kk;
+        vals_out[g] = s_vals[p];
+      }
     }
-  }
-  __syncthreads();
-  uint32_t* s_vbuf = reinterpret_cast<uint32_t*>(s_buf);
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k)
-    if (wbase + k * 32 + lane < n) s_vbuf[pos[k]] = val[k];
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    const uint32_t p = threadIdx.x + j * kSortThreads;
-    if (p < cnt && gdst[j] < n) vals_out[gdst[j]] = s_vbuf[p];
   }
 }
 
@@ -280,70 +293,232 @@ void launch_onesweep_pass(int pass, const float* xyz, const uint64_t* keys_in,
                           uint64_t* status, uint32_t* counter, DevStatus* st, uint64_t wait_ns,
                           int stall_tile, cudaStream_t s) {
   if (n == 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSortSmem);
+    cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSortSmem);
+    attr = true;
+  }
   const int shift = p.lo + pass * p.bits;
   if (pass == 0)
-    onesweep_kernel<true><<<p.ntiles, kSortThreads, 0, s>>>(
+    onesweep_kernel<true><<<p.ntiles, kSortThreads, kSortSmem, s>>>(
         xyz, nullptr, nullptr, keys_out, vals_out, n, shift, p.bits, digit_base, status, counter,
         st, wait_ns, stall_tile);
   else
-    onesweep_kernel<false><<<p.ntiles, kSortThreads, 0, s>>>(
+    onesweep_kernel<false><<<p.ntiles, kSortThreads, kSortSmem, s>>>(
         nullptr, keys_in, vals_in, keys_out, vals_out, n, shift, p.bits, digit_base, status,
         counter, st, wait_ns, -1);
 }
 
 // ---------------------------------------------------------------------------
-// Finishing sort inside level-Ls boxes.  A block owns kSegTile points and
-// loads kSegHalo more on each side, so every box of at most kSegHalo points
-// that touches the tile is entirely in shared memory.  Each point finds its
-// box by walking to equal top bits on both sides, counts the points of the box
-// that precede it in (full key, index) order -- inside a box the points
-// already stand in index order -- and writes its index there.
-__global__ void __launch_bounds__(kSegThreads) segment_finish_kernel(
-    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint32_t n, int lo,
-    uint32_t* __restrict__ perm, DevStatus* st) {
-  constexpr int W = kSegTile + 2 * kSegHalo;
-  __shared__ uint64_t s_key[W];
-  __shared__ uint32_t s_val[W];
-  if (__syncthreads_or(threadIdx.x == 0 && failed(st))) return;  // uniform
-  const int64_t w0 = (int64_t)blockIdx.x * kSegTile - kSegHalo;
-  for (int j = threadIdx.x; j < W; j += kSegThreads) {
-    const int64_t i = w0 + j;
-    if (i >= 0 && i < (int64_t)n) {
-      s_key[j] = keys[i];
-      s_val[j] = vals[i];
+// Reduce-then-scan passes.  No tile waits for another: each tile's digit
+// counts come from a separate read (of the coordinates for the first pass, of
+// the keys for the later ones), one prefix sum over the digit-major counts
+// gives every (digit, tile) its output start, and the scatter kernel streams.
+
+__device__ __forceinline__ void count_digit(uint64_t key, int shift, uint32_t mask, uint32_t* sh) {
+  atomicAdd(&sh[(uint32_t)(key >> shift) & mask], 1u);
+}
+
+template <bool kFromXyz>
+__global__ void __launch_bounds__(256) tile_hist_kernel(const float* __restrict__ xyz,
+                                                        const uint64_t* __restrict__ keys,
+                                                        uint32_t n, int shift, int bits,
+                                                        uint32_t ntiles, bool vec,
+                                                        uint32_t* __restrict__ hist,
+                                                        DevStatus* st) {
+  __shared__ uint32_t sh[kRadixMax];
+  const uint32_t radix = 1u << bits, mask = radix - 1u;
+  for (int i = threadIdx.x; i < kRadixMax; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const uint32_t tile = blockIdx.x;
+  const uint64_t base = (uint64_t)tile * kSortTile;
+  const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
+  bool bad = false;
+  uint32_t done = 0;
+  if (kFromXyz) {
+    if (vec) {  // 4 points = 3 float4; tiles start at multiples of 4 points
+      const float4* v = reinterpret_cast<const float4*>(xyz + 3 * base);
+      for (uint32_t g = threadIdx.x; g < cnt / 4; g += blockDim.x) {
+        const float4 a = __ldcs(v + 3 * g), b = __ldcs(v + 3 * g + 1), c = __ldcs(v + 3 * g + 2);
+        bool ok0, ok1, ok2, ok3;
+        count_digit(morton_key(a.x, a.y, a.z, &ok0), shift, mask, sh);
+        count_digit(morton_key(a.w, b.x, b.y, &ok1), shift, mask, sh);
+        count_digit(morton_key(b.z, b.w, c.x, &ok2), shift, mask, sh);
+        count_digit(morton_key(c.y, c.z, c.w, &ok3), shift, mask, sh);
+        bad |= !(ok0 && ok1 && ok2 && ok3);
+      }
+      done = cnt & ~3u;
+    }
+    for (uint32_t j = done + threadIdx.x; j < cnt; j += blockDim.x) {
+      const uint64_t i = base + j;
+      bool ok;
+      count_digit(morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok), shift, mask, sh);
+      bad |= !ok;
+    }
+  } else {
+    const ulonglong2* v = reinterpret_cast<const ulonglong2*>(keys + base);
+    for (uint32_t g = threadIdx.x; g < cnt / 2; g += blockDim.x) {
+      const ulonglong2 k = __ldcs(v + g);
+      count_digit(k.x, shift, mask, sh);
+      count_digit(k.y, shift, mask, sh);
+    }
+    if ((cnt & 1u) && threadIdx.x == 0) count_digit(keys[base + cnt - 1], shift, mask, sh);
+  }
+  __syncthreads();
+  for (uint32_t d = threadIdx.x; d < radix; d += blockDim.x) hist[(uint64_t)d * ntiles + tile] = sh[d];
+  if (bad) set_error(st, FMM_ERR_DOMAIN);
+}
+
+void launch_tile_hist(int pass, const float* xyz, const uint64_t* keys, uint32_t n,
+                      const SortPlan& p, uint32_t* hist, DevStatus* st, cudaStream_t s) {
+  if (n == 0) return;
+  const int shift = p.lo + pass * p.bits;
+  if (pass == 0) {
+    const bool vec = ((uintptr_t)xyz & 15u) == 0;
+    tile_hist_kernel<true><<<p.ntiles, 256, 0, s>>>(xyz, nullptr, n, shift, p.bits, p.ntiles, vec,
+                                                     hist, st);
+  } else {
+    tile_hist_kernel<false><<<p.ntiles, 256, 0, s>>>(nullptr, keys, n, shift, p.bits, p.ntiles,
+                                                      false, hist, st);
+  }
+}
+
+template <bool kFromXyz>
+__global__ void __launch_bounds__(kSortThreads, 3) rts_scatter_kernel(
+    const float* __restrict__ xyz, const uint64_t* __restrict__ keys_in,
+    const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, uint32_t n, int shift, int bits, uint32_t ntiles,
+    const uint32_t* __restrict__ offsets, DevStatus* st) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ uint32_t s_fail;
+  __shared__ uint32_t s_wcnt[W][kRadixMax];  // per-warp digit counts, then block slots
+  __shared__ uint32_t s_gbase[kRadixMax];    // global position of block slot 0, per digit
+  __shared__ uint32_t s_wsum[W];
+  extern __shared__ __align__(16) uint64_t s_keys[];
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kSortTile);
+
+  const uint32_t radix = 1u << bits, mask = radix - 1u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < W * kRadixMax; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+  if (threadIdx.x == 0) s_fail = failed(st) ? 1u : 0u;
+  __syncthreads();
+  if (s_fail) return;  // an earlier kernel failed (domain error): leave the outputs alone
+  const uint32_t tile = blockIdx.x;
+  const uint64_t base = (uint64_t)tile * kSortTile;
+  const uint64_t wbase = base + (uint64_t)warp * (kSortItems * 32);
+
+  uint64_t key[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const uint64_t i = wbase + k * 32 + lane;
+    key[k] = 0;
+    if (i < n) {
+      if (kFromXyz) {
+        bool ok;
+        key[k] = morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok);
+      } else {
+        key[k] = keys_in[i];
+      }
+    }
+  }
+  const uint32_t lt = lanemask_lt();
+  uint32_t pos[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const bool valid = wbase + k * 32 + lane < n;
+    const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & mask : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = valid ? s_wcnt[warp][d] : 0u;
+    __syncwarp();
+    if (valid && (peers & lt) == 0) s_wcnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+    pos[k] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  uint32_t tot = 0;
+  if (threadIdx.x < radix) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const uint32_t c = s_wcnt[w][threadIdx.x];
+      s_wcnt[w][threadIdx.x] = tot;
+      tot += c;
+    }
+  }
+  uint32_t x = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wsum[warp] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const uint32_t v = lane < W ? s_wsum[lane] : 0u;
+    uint32_t y = v;
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+      const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    if (lane < W) s_wsum[lane] = y - v;
+  }
+  __syncthreads();
+  if (threadIdx.x < radix) {
+    const uint32_t excl_blk = x - tot + s_wsum[warp];
+#pragma unroll
+    for (int w = 0; w < W; ++w) s_wcnt[w][threadIdx.x] += excl_blk;
+    s_gbase[threadIdx.x] = offsets[(uint64_t)threadIdx.x * ntiles + tile] - excl_blk;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const uint64_t i = wbase + k * 32 + lane;
+    if (i < n) {
+      const uint32_t d = (uint32_t)(key[k] >> shift) & mask;
+      const uint32_t p = pos[k] + s_wcnt[warp][d];
+      s_keys[p] = key[k];
+      s_vals[p] = kFromXyz ? (uint32_t)i : vals_in[i];
     }
   }
   __syncthreads();
-  const int jlo = (int)((w0 < 0 ? 0 : w0) - w0);                              // first valid slot
-  const int jhi = (int)(((w0 + W) > (int64_t)n ? (int64_t)n : (w0 + W)) - w0);  // one past last
-  bool long_box = false;
-  for (int j = kSegHalo + threadIdx.x; j < kSegHalo + kSegTile; j += kSegThreads) {
-    if (j >= jhi) break;
-    const uint64_t k = s_key[j];
-    const uint64_t top = k >> lo;
-    int a = j;
-    while (a > jlo && (s_key[a - 1] >> lo) == top) --a;
-    int b = j + 1;
-    while (b < jhi && (s_key[b] >> lo) == top) ++b;
-    if ((a == jlo && w0 + a > 0) || (b == jhi && w0 + b < (int64_t)n)) {
-      long_box = true;  // the box runs past the loaded window
-      continue;
+  const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
+#pragma unroll 4
+  for (int j = 0; j < kSortItems; ++j) {
+    const uint32_t p = threadIdx.x + j * kSortThreads;
+    if (p < cnt) {
+      const uint64_t kk = s_keys[p];
+      const uint32_t g = s_gbase[(uint32_t)(kk >> shift) & mask] + p;
+      if (g < n) {
+        keys_out[g] = kk;
+        vals_out[g] = s_vals[p];
+      }
     }
-    uint32_t r = 0;
-    for (int q = a; q < b; ++q) {
-      const uint64_t kq = s_key[q];
-      r += (kq < k) || (kq == k && q < j);
-    }
-    perm[w0 + a + r] = s_val[j];
   }
-  if (long_box) atomicExch(&st->seg_long, 1u);
 }
 
-void launch_segment_finish(const uint64_t* keys, const uint32_t* vals, uint32_t n, int Ls,
-                           uint32_t* perm, DevStatus* st, cudaStream_t s) {
+void launch_rts_scatter(int pass, const float* xyz, const uint64_t* keys_in,
+                        const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                        uint32_t n, const SortPlan& p, const uint32_t* offsets, DevStatus* st,
+                        cudaStream_t s) {
   if (n == 0) return;
-  const uint32_t blocks = (uint32_t)(((uint64_t)n + kSegTile - 1) / kSegTile);
-  segment_finish_kernel<<<blocks, kSegThreads, 0, s>>>(keys, vals, n, 63 - 3 * Ls, perm, st);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(rts_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSortSmem);
+    cudaFuncSetAttribute(rts_scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSortSmem);
+    attr = true;
+  }
+  const int shift = p.lo + pass * p.bits;
+  if (pass == 0)
+    rts_scatter_kernel<true><<<p.ntiles, kSortThreads, kSortSmem, s>>>(
+        xyz, nullptr, nullptr, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st);
+  else
+    rts_scatter_kernel<false><<<p.ntiles, kSortThreads, kSortSmem, s>>>(
+        nullptr, keys_in, vals_in, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st);
 }
 
 }  // namespace fmm

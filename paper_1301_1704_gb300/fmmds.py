@@ -59,9 +59,16 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 # Every function declared in include/fmmds.h.
 EXPORTS = (
     "fmm_create", "fmm_destroy", "fmm_build", "fmm_morton_keys", "fmm_query_workspace",
-    "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing", "fmm_last_launch_count",
-    "fmm_status_string",
+    "fmm_set_tuning", "fmm_get_tuning", "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing",
+    "fmm_last_launch_count", "fmm_status_string",
 )
+
+FMM_SORT_RTS = 0
+FMM_SORT_ONESWEEP = 1
+
+
+class Tuning(C.Structure):
+    _fields_ = [("sort_kind", C.c_uint32)]
 
 _lib = None
 
@@ -92,6 +99,10 @@ def _load():
     lib.fmm_morton_keys.restype = C.c_int
     lib.fmm_query_workspace.argtypes = [C.c_uint32, C.c_uint32, Params, _u64p]
     lib.fmm_query_workspace.restype = C.c_int
+    lib.fmm_set_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
+    lib.fmm_set_tuning.restype = C.c_int
+    lib.fmm_get_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
+    lib.fmm_get_tuning.restype = C.c_int
     lib.fmm_set_timing.argtypes = [C.c_void_p, C.c_int]
     lib.fmm_set_timing.restype = C.c_int
     lib.fmm_reset_timing.argtypes = [C.c_void_p]
@@ -276,6 +287,17 @@ class Context:
         if st != FMM_OK:
             raise FmmError(st, "fmm_morton_keys")
         return out
+
+    def set_tuning(self, sort_kind: int):
+        t = Tuning(sort_kind)
+        st = _load().fmm_set_tuning(self._h, C.byref(t))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_set_tuning")
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _load().fmm_get_tuning(self._h, C.byref(t))
+        return {"sort_kind": int(t.sort_kind)}
 
     def set_timing(self, on: bool):
         _load().fmm_set_timing(self._h, 1 if on else 0)

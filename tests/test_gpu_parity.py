@@ -63,6 +63,22 @@ def test_morton_keys_match_oracle(ctx, orc):
         assert np.array_equal(got, orc.keys(p))
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_sort_kinds_agree(ctx, orc, kind):
+    from paper_1301_1704_gb300 import fmmds
+    src = workloads.clumps(150000, 30, nclumps=10, sigma=0.03)
+    recv = workloads.uniform(90001, 31)
+    ctx.set_tuning(kind)
+    try:
+        got, want = run_both(ctx, orc, src, recv, 6)
+        compare_full(got, want, 6)
+        p = workloads.clumps(40000, 32, nclumps=3, sigma=0.01)  # long boxes: full 63-bit sort
+        got, want = run_both(ctx, orc, p, p[:5000].copy(), 2)
+        compare_full(got, want, 2)
+    finally:
+        ctx.set_tuning(fmmds.FMM_SORT_RTS)
+
+
 def test_config1_full_tree_brute(ctx, orc):
     src, recv, L = workloads.config_inputs(1)
     got, want = run_both(ctx, orc, src, recv, L, mode=orc.MODE_BRUTE)
