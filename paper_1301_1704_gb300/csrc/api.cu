@@ -76,6 +76,9 @@ struct fmm_ctx {
 namespace {
 
 constexpr size_t kHostBuf = 1 << 16;
+// Largest list capacity (bytes) reserved from the box-count bounds alone;
+// above it the box counts are read back first.
+constexpr uint64_t kAsyncListBytes = 16ull << 30;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
@@ -464,15 +467,29 @@ int do_build(fmm_ctx* c, const float* src, uint32_t N, const float* recv, uint32
     }
   }
 
-  // Read back box counts, occupancy and status.
+  // With a fixed level and list capacities bounded by the box capacities
+  // (27 and 189 per receiver box), everything is launched without waiting
+  // for the box counts; otherwise read them back first.
   Readback* hb = static_cast<Readback*>(c->host_buf);
-  FMM_CUDA(cudaMemcpyAsync(&hb->st, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-  for (int k = 0; k < 2; ++k)
-    FMM_CUDA(cudaMemcpyAsync(&hb->set[k], S[k].nbox_dev, sizeof(SetReadback),
-                             cudaMemcpyDeviceToHost, s));
-  FMM_CUDA(cudaStreamSynchronize(s));
-  if (hb->st.code) return (int)hb->st.code;
-  Readback rb1 = *hb;
+  Readback rb1{};
+  uint64_t list_bound = 0;
+  if (!smode)
+    for (int l = 2; l <= prm.L; ++l) list_bound += 4ull * (2 + 27 + 189) * level_cap(M, l);
+  const bool async_lists = !smode && list_bound <= kAsyncListBytes;
+  if (!async_lists) {
+    FMM_CUDA(cudaMemcpyAsync(&hb->st, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    for (int k = 0; k < 2; ++k)
+      FMM_CUDA(cudaMemcpyAsync(&hb->set[k], S[k].nbox_dev, sizeof(SetReadback),
+                               cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
+    if (hb->st.code) return (int)hb->st.code;
+    rb1 = *hb;
+  } else {
+    for (int l = 0; l <= prm.L; ++l) {
+      rb1.set[0].nbox[l] = level_cap(N, l);
+      rb1.set[1].nbox[l] = level_cap(M, l);
+    }
+  }
 
   int L = prm.L;
   uint32_t s_unmet = 0;
@@ -523,7 +540,7 @@ int do_build(fmm_ctx* c, const float* src, uint32_t N, const float* recv, uint32
       }
     }
   }
-  if (rb1.st.seg_long) {
+  if (!async_lists && rb1.st.seg_long) {
     // A box outran the finishing sort: redo the order(s) with all 63 bits.
     for (int k = 0; k < (aliased ? 1 : 2); ++k) FMM_TRY(full_sort_perm(c, &S[k], wait_ns));
     if (aliased) S[1].perm = S[0].perm;
@@ -570,7 +587,7 @@ int do_build(fmm_ctx* c, const float* src, uint32_t N, const float* recv, uint32
     const uint32_t np = rb1.set[1].nbox[l - 1];
     {
       Launch Lk(c, "list_count");
-      launch_list_count(a, np, s);
+      launch_list_count(a, np, c->st, s);
     }
     {
       Launch Lk(c, "scan");
@@ -591,8 +608,23 @@ int do_build(fmm_ctx* c, const float* src, uint32_t N, const float* recv, uint32
   FMM_CUDA(cudaMemcpyAsync(&hb->st, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   FMM_CUDA(cudaMemcpyAsync(hb->nnz, nnz_dev, sizeof(uint64_t) * kLevels * 2,
                            cudaMemcpyDeviceToHost, s));
+  if (async_lists)
+    for (int k = 0; k < 2; ++k)
+      FMM_CUDA(cudaMemcpyAsync(&hb->set[k], S[k].nbox_dev, sizeof(SetReadback),
+                               cudaMemcpyDeviceToHost, s));
   FMM_CUDA(cudaStreamSynchronize(s));
   if (hb->st.code) return (int)hb->st.code;
+  if (async_lists) {
+    for (int k = 0; k < 2; ++k) rb1.set[k] = hb->set[k];
+    if (hb->st.seg_long) {
+      // A box outran the finishing sort: redo the order(s) with all 63 bits.
+      for (int k = 0; k < (aliased ? 1 : 2); ++k) FMM_TRY(full_sort_perm(c, &S[k], wait_ns));
+      if (aliased) S[1].perm = S[0].perm;
+      FMM_CUDA(cudaMemcpyAsync(&hb->st, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+      FMM_CUDA(cudaStreamSynchronize(s));
+      if (hb->st.code) return (int)hb->st.code;
+    }
+  }
 
   std::memset(out, 0, sizeof(*out));
   out->L = L;

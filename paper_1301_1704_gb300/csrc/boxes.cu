@@ -21,10 +21,21 @@ uint32_t boxes_tiles(uint32_t n) {
 }
 
 constexpr int kWin = kBoxTile + kBoxHalo;  // points held per tile
-constexpr size_t kBoxSmem = sizeof(uint64_t) * (kWin + 1) + sizeof(uint32_t) * kWin;
+// Shared memory: keys [kWin + 1] (u64), then the per-point first differing
+// levels [kWin] (u8, 16-byte aligned for vector reads), then the indices
+// [kWin] (u32).
+constexpr size_t kBoxDdOff = (sizeof(uint64_t) * (kWin + 1) + 15) & ~(size_t)15;
+constexpr size_t kBoxValOff = kBoxDdOff + kWin;
+constexpr size_t kBoxSmem = kBoxValOff + sizeof(uint32_t) * kWin;
+static_assert(kWin % 16 == 0 && kBoxValOff % 16 == 0, "shared layout alignment");
 
-// kLv: level slots held in registers (8 when Lb <= 7, else 22).
-template <int kLv>
+// First level at which a key differs from the key before it (22: equal keys;
+// the keys use bits 0..62, level l owns bits 63-3l .. 65-3l).
+__device__ __forceinline__ uint32_t first_diff_level(uint64_t a, uint64_t b) {
+  const uint64_t x = a ^ b;
+  return x == 0 ? 22u : (uint32_t)((2 + __clzll((long long)x)) / 3);
+}
+
 __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint32_t n, int Lb,
     int Ls, LevelArrays lv, uint32_t* __restrict__ perm, uint64_t* status, uint32_t* counter,
@@ -35,7 +46,8 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
   __shared__ uint32_t s_texcl[kLevels];  // box starts in all tiles before this one
   __shared__ uint32_t s_ttot[kLevels];   // box starts in this tile
   extern __shared__ __align__(16) uint64_t s_key[];  // s_key[j + 1] = key of point t0 + j
-  uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kWin + 1);
+  uint8_t* s_dd = reinterpret_cast<uint8_t*>(s_key) + kBoxDdOff;  // first differing level
+  uint32_t* s_val = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(s_key) + kBoxValOff);
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
@@ -47,63 +59,49 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
   const uint32_t tile = s_tile;
   const int64_t t0 = (int64_t)tile * kBoxTile;
   const int64_t nn = n;
+  const int jend = (int)((nn - t0) < kWin ? (nn - t0) : kWin);  // valid window points
   for (int j = threadIdx.x; j < kWin + 1; j += kBoxThreads) {
     const int64_t i = t0 - 1 + j;
-    s_key[j] = (i >= 0 && i < nn) ? keys[i] : 0ull;
+    s_key[j] = (i >= 0 && i < nn) ? __ldcs(keys + i) : 0ull;
   }
   for (int j = threadIdx.x; j < kWin; j += kBoxThreads) {
     const int64_t i = t0 + j;
-    s_val[j] = i < nn ? vals[i] : 0u;
+    s_val[j] = i < nn ? __ldcs(vals + i) : 0u;
   }
   __syncthreads();
+  // dd[j]: the point opens a box at every level >= dd[j].  Past the end of
+  // the data every slot reads 0, which ends every box walk there.
+  for (int j = threadIdx.x; j < kWin; j += kBoxThreads)
+    s_dd[j] = (j >= jend || t0 + j == 0) ? 0u : (uint8_t)first_diff_level(s_key[j + 1], s_key[j]);
+  __syncthreads();
 
-  // Box starts of levels 0..Lb.  d[k]: coarsest level at which item k
-  // opens a box (0xff: none).  Items are blocked: thread t holds kBoxItems
-  // consecutive points.
-  const int hshift = 63 - 3 * Lb;
-  uint32_t d[kBoxItems];
+  // Per-level counts of box starts: thread t owns points 16t .. 16t+15.
+  uint32_t dd[kBoxItems];
+  {
+    static_assert(kBoxItems == 8, "one 8-byte read of the level bytes per thread");
+    const uint2 w = *reinterpret_cast<const uint2*>(s_dd + threadIdx.x * kBoxItems);
+    const uint32_t wv[2] = {w.x, w.y};
 #pragma unroll
-  for (int k = 0; k < kBoxItems; ++k) {
-    const int j = threadIdx.x * kBoxItems + k;
-    const int64_t i = t0 + j;
-    uint32_t v = 0xffu;
-    if (i < nn) {
-      if (i == 0) {
-        v = 0;
-      } else {
-        const uint64_t x = (s_key[j + 1] ^ s_key[j]) >> hshift;
-        if (x != 0) {
-          const int h = 63 - __clzll((long long)x) + hshift;  // highest differing bit
-          v = (uint32_t)((65 - h) / 3);
-        }
-      }
-    }
-    d[k] = v;
+    for (int k = 0; k < kBoxItems; ++k)
+      dd[k] = threadIdx.x * kBoxItems + k < jend ? (wv[k >> 2] >> (8 * (k & 3))) & 0xffu : 0xffu;
   }
-  uint32_t lex[kLv];  // lane-exclusive prefix within the warp, per level
+  for (int l = 0; l <= Lb; ++l) {
+    uint32_t c = 0;
 #pragma unroll
-  for (int l = 0; l < kLv; ++l) {
-    lex[l] = 0;
-    if (l <= Lb) {
-      uint32_t c = 0;
+    for (int k = 0; k < kBoxItems; ++k) c += (dd[k] <= (uint32_t)l);
 #pragma unroll
-      for (int k = 0; k < kBoxItems; ++k) c += (d[k] <= (uint32_t)l);
-      uint32_t x = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      lex[l] = x - c;
-      if (lane == 31) s_wtot[warp][l] = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
+      if (lane >= o) c += y;
     }
+    if (lane == 31) s_wtot[warp][l] = c;
   }
   __syncthreads();
 
   // Warp w handles levels w, w + 8, ...: warp prefixes and the tile total,
   // published at once as this tile's aggregate.
-  for (int l = warp; l <= Lb; l += W) {
-    if (lane == 0) {
+  if (lane == 0) {
+    for (int l = warp; l <= Lb; l += W) {
       uint32_t run = 0;
       for (int w = 0; w < W; ++w) {
         const uint32_t c = s_wtot[w][l];
@@ -116,31 +114,57 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
   }
 
   // Finishing sort inside the level-Ls boxes that START in this tile,
-  // including their points in the halo past the tile's end; a box begun in an
-  // earlier tile is finished by that tile.  In a box the points stand in index
-  // order already.  It runs between publishing this tile's aggregate and
-  // reading the earlier tiles', which gives them time to publish.
+  // including their points in the halo past the tile's end (a box begun in
+  // an earlier tile is that tile's).  Inside a box the points stand in index
+  // order, so a point's rank counts the box's points with a smaller key, and
+  // the earlier points with an equal key.  Each warp takes 32 consecutive
+  // points; box bounds inside the warp come from one ballot of box starts.
+  // This runs between publishing the aggregate and reading the earlier
+  // tiles' words, which gives them time to publish.
   {
-    const int loS = 63 - 3 * Ls;
-    const int jend = (int)((nn - t0) < kWin ? (nn - t0) : kWin);  // valid window points
+    const uint32_t lt = lanemask_lt();
     bool long_box = false;
-    for (int j = threadIdx.x; j < jend; j += kBoxThreads) {
-      const uint64_t k = s_key[j + 1];
-      const uint64_t top = k >> loS;
-      int a = j;
-      while (a > 0 && (s_key[a] >> loS) == top) --a;  // s_key[a] is point a - 1
-      if (a >= kBoxTile) continue;                                 // the next tile's box
-      if (a == 0 && t0 > 0 && (s_key[0] >> loS) == top) continue;  // an earlier tile's box
-      int b = j + 1;
-      while (b < jend && (s_key[b + 1] >> loS) == top) ++b;
+    const int lowbits = 63 - 3 * Ls;
+    const uint64_t lowmask = lowbits >= 64 ? ~0ull : ((1ull << lowbits) - 1ull);
+    for (int c0 = warp * 32; c0 < jend; c0 += W * 32) {
+      const int j = c0 + lane;
+      const bool in = j < jend;
+      const bool start = in && s_dd[j] <= (uint32_t)Ls;
+      const uint32_t f = __ballot_sync(0xffffffffu, start);
+      // box start: last start at or before this lane, else walk back
+      int a;
+      const uint32_t le = f & (lt | (1u << lane));
+      if (le) {
+        a = c0 + 31 - __clz(le);
+      } else {
+        a = c0;
+        while (a > 0 && s_dd[a] > (uint32_t)Ls) --a;
+      }
+      // box end: next start after this lane, else walk on
+      int b;
+      const uint32_t gt = f & ~(lt | (1u << lane));
+      if (gt) {
+        b = c0 + __ffs(gt) - 1;
+      } else {
+        b = c0 + 32;
+        while (b < jend && s_dd[b] > (uint32_t)Ls) ++b;
+        if (b > jend) b = jend;
+      }
+      if (!in) continue;
+      if (a >= kBoxTile) continue;                                    // the next tile's box
+      if (a == 0 && t0 > 0 && s_dd[0] > (uint32_t)Ls) continue;      // an earlier tile's box
       if (b == jend && t0 + jend < nn) {
         long_box = true;  // runs past the window: the host redoes the order
         continue;
       }
       uint32_t r = 0;
-      for (int q = a; q < b; ++q) {
-        const uint64_t kq = s_key[q + 1];
-        r += (kq < k) || (kq == k && q < j);
+      if (b - a > 1) {
+        // within a box the top bits agree: order by (low key bits, slot)
+        const uint64_t mine = s_key[j + 1] & lowmask;
+        for (int q = a; q < b; ++q) {
+          const uint64_t kq = s_key[q + 1] & lowmask;
+          r += (kq < mine) || (kq == mine && q < j);
+        }
       }
       perm[t0 + a + r] = s_val[j];
     }
@@ -170,33 +194,50 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
     }
   }
 
-  uint32_t run[kLv];  // running rank per level: starts before the current item
+  // Outputs, level by level.  For point k of this thread starting a level-l
+  // box: rank = base_l + (starts of this thread before k); its parent is the
+  // level-(l-1) box holding it and, if it also starts a level-(l-1) box, it is
+  // that box's first child.
+  uint32_t prev_mask = 0, prev_base = 0;
+  for (int l = 0; l <= Lb; ++l) {
+    uint32_t mask = 0;
 #pragma unroll
-  for (int l = 0; l < kLv; ++l) run[l] = (l <= Lb) ? s_texcl[l] + s_wtot[warp][l] + lex[l] : 0u;
+    for (int k = 0; k < kBoxItems; ++k) mask |= (dd[k] <= (uint32_t)l ? 1u : 0u) << k;
+    const uint32_t c = __popc(mask);
+    uint32_t x = c;
 #pragma unroll
-  for (int k = 0; k < kBoxItems; ++k) {
-    const uint32_t dk = d[k];
-    if (dk <= (uint32_t)Lb) {
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const uint32_t base = s_texcl[l] + s_wtot[warp][l] + (x - c);
+    uint64_t* okey = lv.key[l];
+    uint32_t* ooff = lv.off[l];
+    uint32_t* opar = lv.parent[l];
+    uint32_t* ochild = l >= 1 ? lv.child[l - 1] : nullptr;
+    const uint32_t cap = lv.cap[l], capup = l >= 1 ? lv.cap[l - 1] : 0u;
+    const int shift = 63 - 3 * l;
+    uint32_t m = mask, rank = base;
+    while (m) {
+      const int k = __ffs(m) - 1;
+      m &= m - 1;
       const int j = threadIdx.x * kBoxItems + k;
-      const uint32_t i = (uint32_t)(t0 + j);
-      const uint64_t key = s_key[j + 1];
-#pragma unroll
-      for (int l = 0; l < kLv; ++l) {
-        if (l <= Lb && (uint32_t)l >= dk && run[l] < lv.cap[l]) {
-          const uint32_t rank = run[l];
-          lv.key[l][rank] = l == 0 ? 0ull : key >> (63 - 3 * l);
-          lv.off[l][rank] = i;
-          if (l >= 1) {
-            const bool up_starts = dk <= (uint32_t)(l - 1);
-            lv.parent[l][rank] = up_starts ? run[l - 1] : run[l - 1] - 1u;
-            if (up_starts && run[l - 1] < lv.cap[l - 1]) lv.child[l - 1][run[l - 1]] = rank;
+      if (rank < cap) {
+        okey[rank] = l == 0 ? 0ull : s_key[j + 1] >> shift;
+        ooff[rank] = (uint32_t)(t0 + j);
+        if (l >= 1) {
+          const uint32_t below = __popc(prev_mask & ((2u << k) - 1u));  // level l-1 starts <= k
+          opar[rank] = prev_base + below - 1u;
+          if ((prev_mask >> k) & 1u) {
+            const uint32_t up = prev_base + below - 1u;
+            if (up < capup) ochild[up] = rank;
           }
         }
       }
-#pragma unroll
-      for (int l = 0; l < kLv; ++l)
-        if (l <= Lb && (uint32_t)l >= dk) ++run[l];
+      ++rank;
     }
+    prev_mask = mask;
+    prev_base = base;
   }
 }
 
@@ -205,19 +246,13 @@ void launch_finish_boxes(const uint64_t* keys, const uint32_t* vals, uint32_t n,
                          uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(finish_boxes_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(finish_boxes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBoxSmem);
-    cudaFuncSetAttribute(finish_boxes_kernel<kLevels>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
     attr = true;
   }
   const uint32_t t = boxes_tiles(n);
-  if (Lb < 8)
-    finish_boxes_kernel<8><<<t, kBoxThreads, kBoxSmem, s>>>(keys, vals, n, Lb, Ls, lv, perm,
-                                                             status, counter, nbox, st, wait_ns, t);
-  else
-    finish_boxes_kernel<kLevels><<<t, kBoxThreads, kBoxSmem, s>>>(
-        keys, vals, n, Lb, Ls, lv, perm, status, counter, nbox, st, wait_ns, t);
+  finish_boxes_kernel<<<t, kBoxThreads, kBoxSmem, s>>>(keys, vals, n, Lb, Ls, lv, perm, status,
+                                                        counter, nbox, st, wait_ns, t);
 }
 
 // ---------------------------------------------------------------------------

@@ -194,13 +194,13 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 // ---------------------------------------------------------------------------
 // Tunables of the kernels.
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 12;
+constexpr int kSortThreads = 512;
+constexpr int kSortItems = 6;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 3072
 constexpr int kRadixMax = 256;
 
-constexpr int kBoxThreads = 256;
-constexpr int kBoxItems = 16;
+constexpr int kBoxThreads = 512;
+constexpr int kBoxItems = 8;
 constexpr int kBoxTile = kBoxThreads * kBoxItems;  // 4096
 constexpr int kBoxHalo = 512;  // a box the finishing sort handles ends within it
 
@@ -300,7 +300,7 @@ struct ListArgs {
   uint32_t* e4_idx;
   const uint64_t* nnz;  // device [2]: E2, E4 totals of this level (fill)
 };
-void launch_list_count(const ListArgs& a, uint32_t nparents_cap, cudaStream_t s);
+void launch_list_count(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s);
 void launch_list_fill(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s);
 
 // Morton keys of n points (public fmm_morton_keys).

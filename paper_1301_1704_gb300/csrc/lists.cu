@@ -83,116 +83,110 @@ __device__ __forceinline__ Neighbour load_neighbour(const ListArgs& a, uint32_t 
   return q;
 }
 
-__global__ void __launch_bounds__(kListThreads) list_count_kernel(ListArgs a) {
+// Counts: per receiver child r of parent p, |E2(r)| = sum over the parent's
+// neighbours Q of popc(occ(Q) & mask(delta_Q, rho_r)), and |E2| + |E4| = the
+// number of non-empty children of all Q.  The eight possible sibling octants
+// are counted at once: byte rho of a packed pair of words.
+__global__ void __launch_bounds__(kListThreads) list_count_kernel(ListArgs a, DevStatus* st) {
+  if (failed(st)) return;  // set before this launch: the same for every thread
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const uint32_t np = a.nbox_recv[a.l - 1];
   for (uint32_t p = gw; p < np; p += nw) {
     const Neighbour q = load_neighbour(a, p, lane);
+    uint32_t lo = 0, hi = 0;  // byte rho: popc(occ & mask(delta, rho))
+#pragma unroll
+    for (uint32_t rho = 0; rho < 4; ++rho)
+      lo |= (uint32_t)__popc(q.occ & e2_child_mask(q.dx, q.dy, q.dz, rho)) << (8 * rho);
+#pragma unroll
+    for (uint32_t rho = 4; rho < 8; ++rho)
+      hi |= (uint32_t)__popc(q.occ & e2_child_mask(q.dx, q.dy, q.dz, rho)) << (8 * (rho - 4));
     const uint32_t tot = warp_sum(__popc(q.occ));
+    lo = warp_sum(lo);
+    hi = warp_sum(hi);
+    const uint32_t c0 = a.rchild_up[p], c1 = a.rchild_up[p + 1];
+    const uint32_t r = c0 + lane;
+    if (r < c1) {
+      const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
+      const uint32_t n2 = ((rho < 4 ? lo : hi) >> (8 * (rho & 3))) & 0xffu;
+      a.e2_off[r] = n2;
+      a.e4_off[r] = tot - n2;
+    }
+  }
+}
+
+// Fill: per parent p, the candidate list C -- the non-empty children of p's
+// neighbours in ascending rank -- is built once in shared memory with, per
+// candidate, the byte of sibling octants rho whose E2 it belongs to.  Because
+// the E2 condition |2 delta + o - rho| <= 1 is symmetric under
+// (delta, o, rho) -> (-delta, rho, o), that byte is e2_child_mask(-delta, o).
+// Every receiver child then splits C by one ballot per 32 candidates: its E2
+// and E4 lists come out in ascending order as contiguous, coalesced stores.
+constexpr int kCand = 27 * 8;  // at most 27 neighbours x 8 children
+constexpr int kListWarps = kListThreads / 32;
+
+__global__ void __launch_bounds__(kListThreads) list_fill_kernel(ListArgs a, DevStatus* st) {
+  __shared__ uint32_t s_rank[kListWarps][kCand];
+  __shared__ uint8_t s_sib[kListWarps][kCand];
+  if (failed(st)) return;  // set before this launch: the same for every thread
+  if ((a.nnz[0] >> 32) != 0 || (a.nnz[1] >> 32) != 0) return;  // capacity error already set
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = lanemask_lt();
+  uint32_t* crank = s_rank[warp];
+  uint8_t* csib = s_sib[warp];
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t np = a.nbox_recv[a.l - 1];
+  for (uint32_t p = gw; p < np; p += nw) {
+    const Neighbour q = load_neighbour(a, p, lane);
+    const uint32_t nc = __popc(q.occ);
+    uint32_t e = warp_excl(nc, lane);
+    const uint32_t total = __shfl_sync(0xffffffffu, e + nc, 31);
+    uint32_t bits = q.occ, rank = q.child;
+    while (bits) {
+      const uint32_t o = __ffs(bits) - 1;
+      bits &= bits - 1;
+      crank[e] = rank++;
+      csib[e] = (uint8_t)e2_child_mask(-q.dx, -q.dy, -q.dz, o);
+      ++e;
+    }
+    __syncwarp();
     const uint32_t c1 = a.rchild_up[p + 1];
     for (uint32_t r = a.rchild_up[p]; r < c1; ++r) {
       const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
-      const uint32_t n2 = warp_sum(__popc(q.occ & e2_child_mask(q.dx, q.dy, q.dz, rho)));
-      if (lane == 0) {
-        a.e2_off[r] = n2;
-        a.e4_off[r] = tot - n2;
-      }
-    }
-  }
-}
-
-// Per-warp staging of one parent's output: all E4 lists of its receiver
-// children (at most 8 x 189 entries) and all E2 lists (8 x 27), each placed
-// at the alignment (mod 4 words) of its global destination so that the copy
-// out can use 16-byte stores.
-constexpr int kStageE4 = 8 * 189 + 4;
-constexpr int kStageE2 = 8 * 27 + 4;
-constexpr int kStageWords = kStageE4 + kStageE2;  // 1736 words, a multiple of 4
-constexpr int kListWarps = kListThreads / 32;
-constexpr size_t kListSmem = sizeof(uint32_t) * kStageWords * kListWarps;
-
-// Coalesced copy of the run sbuf[s0 .. s0+T) to g[0 .. T), g = s0 (mod 4).
-__device__ __forceinline__ void warp_copy_out(const uint32_t* sbuf, uint32_t s0, uint32_t* g,
-                                              uint32_t T, int lane) {
-  uint32_t head = (4u - s0) & 3u;
-  if (head > T) head = T;
-  if ((uint32_t)lane < head) g[lane] = sbuf[s0 + lane];
-  const uint32_t body = T - head;
-  const uint32_t nv = body >> 2;
-  const uint4* sv = reinterpret_cast<const uint4*>(sbuf + s0 + head);
-  uint4* gv = reinterpret_cast<uint4*>(g + head);
-  for (uint32_t v = lane; v < nv; v += 32) __stcs(gv + v, sv[v]);
-  const uint32_t rem = body & 3u;
-  if ((uint32_t)lane < rem) {
-    const uint32_t i = head + (nv << 2) + lane;
-    g[i] = sbuf[s0 + i];
-  }
-}
-
-__global__ void __launch_bounds__(kListThreads) list_fill_kernel(ListArgs a, DevStatus* st) {
-  extern __shared__ __align__(16) uint32_t s_stage[];
-  if (failed(st)) return;  // set before this launch: the same for every thread
-  if ((a.nnz[0] >> 32) != 0 || (a.nnz[1] >> 32) != 0) return;  // capacity error already set
-  const int lane = threadIdx.x & 31;
-  uint32_t* buf4 = s_stage + (threadIdx.x >> 5) * kStageWords;
-  uint32_t* buf2 = buf4 + kStageE4;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t np = a.nbox_recv[a.l - 1];
-  for (uint32_t p = gw; p < np; p += nw) {
-    const Neighbour q = load_neighbour(a, p, lane);
-    const uint32_t c0 = a.rchild_up[p], c1 = a.rchild_up[p + 1];
-    const uint32_t g2 = a.e2_off[c0], g4 = a.e4_off[c0];
-    const uint32_t s2 = g2 & 3u, s4 = g4 & 3u;
-    const uint32_t T2 = a.e2_off[c1] - g2, T4 = a.e4_off[c1] - g4;
-    if (c1 - c0 > 8 || T2 + s2 > (uint32_t)kStageE2 || T4 + s4 > (uint32_t)kStageE4) {
-      set_error(st, FMM_ERR_CAPACITY);  // impossible for consistent offsets
-      continue;
-    }
-    for (uint32_t r = c0; r < c1; ++r) {
-      const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
-      const uint32_t m2 = q.occ & e2_child_mask(q.dx, q.dy, q.dz, rho);
-      uint32_t o2 = a.e2_off[r] - g2 + s2 + warp_excl(__popc(m2), lane);
-      uint32_t o4 = a.e4_off[r] - g4 + s4 + warp_excl(__popc(q.occ & ~m2), lane);
-      uint32_t bits = q.occ;
-      uint32_t rank = q.child;
-      while (bits) {
-        const uint32_t o = __ffs(bits) - 1;
-        bits &= bits - 1;
-        if ((m2 >> o) & 1u)
-          buf2[o2++] = rank;
-        else
-          buf4[o4++] = rank;
-        ++rank;
+      uint32_t* o2 = a.e2_idx + a.e2_off[r];
+      uint32_t* o4 = a.e4_idx + a.e4_off[r];
+      for (uint32_t c = 0; c < total; c += 32) {
+        const uint32_t i = c + lane;
+        const bool valid = i < total;
+        const uint32_t v = valid ? crank[i] : 0u;
+        const bool in2 = valid && ((csib[i] >> rho) & 1u);
+        const bool in4 = valid && !in2;
+        const uint32_t b2 = __ballot_sync(0xffffffffu, in2);
+        const uint32_t b4 = __ballot_sync(0xffffffffu, in4);
+        if (in2) __stcs(o2 + __popc(b2 & lt), v);
+        if (in4) __stcs(o4 + __popc(b4 & lt), v);
+        o2 += __popc(b2);
+        o4 += __popc(b4);
       }
     }
     __syncwarp();
-    warp_copy_out(buf4, s4, a.e4_idx + g4, T4, lane);
-    warp_copy_out(buf2, s2, a.e2_idx + g2, T2, lane);
-    __syncwarp();
   }
 }
 
-void launch_list_count(const ListArgs& a, uint32_t nparents_cap, cudaStream_t s) {
+void launch_list_count(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s) {
   uint32_t blocks = (uint32_t)(((uint64_t)nparents_cap * 32 + kListThreads - 1) / kListThreads);
   if (blocks > 152u * 8u) blocks = 152u * 8u;
   if (blocks == 0) blocks = 1;
-  list_count_kernel<<<blocks, kListThreads, 0, s>>>(a);
+  list_count_kernel<<<blocks, kListThreads, 0, s>>>(a, st);
 }
 
 void launch_list_fill(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(list_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kListSmem);
-    attr = true;
-  }
   uint32_t blocks = (uint32_t)(((uint64_t)nparents_cap * 32 + kListThreads - 1) / kListThreads);
-  if (blocks > 152u * 4u) blocks = 152u * 4u;
+  if (blocks > 152u * 8u) blocks = 152u * 8u;
   if (blocks == 0) blocks = 1;
-  list_fill_kernel<<<blocks, kListThreads, kListSmem, s>>>(a, st);
+  list_fill_kernel<<<blocks, kListThreads, 0, s>>>(a, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -140,7 +140,7 @@ void launch_digit_scan(const SortPlan& p, uint32_t* hist, cudaStream_t s) {
 constexpr size_t kSortSmem = sizeof(uint64_t) * kSortTile + sizeof(uint32_t) * kSortTile;
 
 template <bool kFromXyz>
-__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
+__global__ void __launch_bounds__(kSortThreads, 2) onesweep_kernel(
     const float* __restrict__ xyz, const uint64_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint32_t n, int shift, int bits,
@@ -387,7 +387,7 @@ void launch_tile_hist(int pass, const float* xyz, const uint64_t* keys, uint32_t
 }
 
 template <bool kFromXyz>
-__global__ void __launch_bounds__(kSortThreads, 3) rts_scatter_kernel(
+__global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     const float* __restrict__ xyz, const uint64_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint32_t n, int shift, int bits, uint32_t ntiles,
