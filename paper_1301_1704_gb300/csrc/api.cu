@@ -226,11 +226,15 @@ uint32_t level_cap(uint32_t n, int l) {
 }
 
 // Sort depth: at least the tree depth, and deep enough that a box averages
-// about 8 points, which keeps the finishing sort short.
+// about 8 points, which keeps the finishing sort short; then as deep as the
+// radix passes it needs allow at 8 bits per pass (3 passes sort 24 bits:
+// level 8 costs no more than level 7).
 int sort_level(uint32_t n, int L) {
   int lvl = 1;
   while (lvl < kMaxLevel && ((uint64_t)n >> (3 * lvl)) > 8) ++lvl;
-  return std::max(std::max(lvl, L), 1);
+  lvl = std::max(std::max(lvl, L), 1);
+  const int passes = (3 * lvl + 7) / 8;
+  return std::min(kMaxLevel, std::max(lvl, 8 * passes / 3));
 }
 
 uint64_t wait_ns_of(const fmm_params& p) {
@@ -331,14 +335,18 @@ int build_set(fmm_ctx* c, SetArrays* S, int Lb, bool need_occ, bool stall, uint6
   // Zero-initialised scratch of the box pass: look-back words, tile counter,
   // box counts.
   const uint32_t btiles = boxes_tiles(n);
-  const size_t zero_bytes = align_up(sizeof(uint64_t) * (size_t)btiles * kLevels) +
+  const uint32_t ctiles = coarse_tiles(level_cap(n, Lb));
+  const size_t zero_bytes = align_up(sizeof(uint64_t) * (size_t)btiles) +
+                            align_up(sizeof(uint64_t) * (size_t)ctiles * kLevels) +
                             align_up(sizeof(uint32_t) * 16) +
                             align_up(sizeof(uint32_t) * kLevels * 2);
   char* z = arena_get<char>(c, zero_bytes, &err);
   if (!z) return err;
   FMM_CUDA(cudaMemsetAsync(z, 0, zero_bytes, s));
   uint64_t* bstatus = reinterpret_cast<uint64_t*>(z);
-  z += align_up(sizeof(uint64_t) * (size_t)btiles * kLevels);
+  z += align_up(sizeof(uint64_t) * (size_t)btiles);
+  uint64_t* cstatus = reinterpret_cast<uint64_t*>(z);
+  z += align_up(sizeof(uint64_t) * (size_t)ctiles * kLevels);
   uint32_t* counters = reinterpret_cast<uint32_t*>(z);
   z += align_up(sizeof(uint32_t) * 16);
   S->nbox_dev = reinterpret_cast<uint32_t*>(z);
@@ -371,6 +379,10 @@ int build_set(fmm_ctx* c, SetArrays* S, int Lb, bool need_occ, bool stall, uint6
     Launch L(c, "finish_boxes");
     launch_finish_boxes(kin ? kin : ka, vin ? vin : va, n, Lb, S->Ls, S->lv, S->perm, bstatus,
                         counters + 15, S->nbox_dev, c->st, wait_ns, s);
+  }
+  if (Lb >= 1) {
+    Launch L(c, "coarse_boxes");
+    launch_coarse_boxes(Lb, S->lv, n, cstatus, counters + 14, S->nbox_dev, c->st, wait_ns, s);
   }
   if (need_occ && Lb >= 1) {
     Launch L(c, "occupancy");

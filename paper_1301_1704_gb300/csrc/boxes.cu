@@ -41,10 +41,8 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
     int Ls, LevelArrays lv, uint32_t* __restrict__ perm, uint64_t* status, uint32_t* counter,
     uint32_t* nbox, DevStatus* st, uint64_t wait_ns, uint32_t ntiles) {
   constexpr int W = kBoxThreads / 32;
-  __shared__ uint32_t s_tile, s_abort;
-  __shared__ uint32_t s_wtot[W][kLevels];
-  __shared__ uint32_t s_texcl[kLevels];  // box starts in all tiles before this one
-  __shared__ uint32_t s_ttot[kLevels];   // box starts in this tile
+  __shared__ uint32_t s_tile, s_abort, s_ttot, s_texcl;
+  __shared__ uint32_t s_wtot[W];
   extern __shared__ __align__(16) uint64_t s_key[];  // s_key[j + 1] = key of point t0 + j
   uint8_t* s_dd = reinterpret_cast<uint8_t*>(s_key) + kBoxDdOff;  // first differing level
   uint32_t* s_val = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(s_key) + kBoxValOff);
@@ -75,42 +73,36 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
     s_dd[j] = (j >= jend || t0 + j == 0) ? 0u : (uint8_t)first_diff_level(s_key[j + 1], s_key[j]);
   __syncthreads();
 
-  // Per-level counts of box starts: thread t owns points 16t .. 16t+15.
-  uint32_t dd[kBoxItems];
+  // Level-Lb box starts among this thread's points 8t .. 8t+7.
+  uint32_t mask = 0;
   {
     static_assert(kBoxItems == 8, "one 8-byte read of the level bytes per thread");
     const uint2 w = *reinterpret_cast<const uint2*>(s_dd + threadIdx.x * kBoxItems);
-    const uint32_t wv[2] = {w.x, w.y};
+    const uint64_t w64 = ((uint64_t)w.y << 32) | w.x;
 #pragma unroll
-    for (int k = 0; k < kBoxItems; ++k)
-      dd[k] = threadIdx.x * kBoxItems + k < jend ? (wv[k >> 2] >> (8 * (k & 3))) & 0xffu : 0xffu;
-  }
-  for (int l = 0; l <= Lb; ++l) {
-    uint32_t c = 0;
-#pragma unroll
-    for (int k = 0; k < kBoxItems; ++k) c += (dd[k] <= (uint32_t)l);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
-      if (lane >= o) c += y;
+    for (int k = 0; k < kBoxItems; ++k) {
+      const uint32_t d = (uint32_t)(w64 >> (8 * k)) & 0xffu;
+      if (threadIdx.x * kBoxItems + k < jend && d <= (uint32_t)Lb) mask |= 1u << k;
     }
-    if (lane == 31) s_wtot[warp][l] = c;
   }
+  const uint32_t c = __popc(mask);
+  uint32_t x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wtot[warp] = x;
   __syncthreads();
-
-  // Warp w handles levels w, w + 8, ...: warp prefixes and the tile total,
-  // published at once as this tile's aggregate.
-  if (lane == 0) {
-    for (int l = warp; l <= Lb; l += W) {
-      uint32_t run = 0;
-      for (int w = 0; w < W; ++w) {
-        const uint32_t c = s_wtot[w][l];
-        s_wtot[w][l] = run;
-        run += c;
-      }
-      s_ttot[l] = run;
-      st_relaxed(status + (uint64_t)tile * kLevels + l, (tile == 0 ? kFlagIncl : kFlagAgg) | run);
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < W; ++w) {
+      const uint32_t v = s_wtot[w];
+      s_wtot[w] = run;
+      run += v;
     }
+    s_ttot = run;
+    st_relaxed(status + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | run);
   }
 
   // Finishing sort inside the level-Ls boxes that START in this tile,
@@ -131,8 +123,7 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
       const bool in = j < jend;
       const bool start = in && s_dd[j] <= (uint32_t)Ls;
       const uint32_t f = __ballot_sync(0xffffffffu, start);
-      // box start: last start at or before this lane, else walk back
-      int a;
+      int a;  // box start: last start at or before this lane, else walk back
       const uint32_t le = f & (lt | (1u << lane));
       if (le) {
         a = c0 + 31 - __clz(le);
@@ -140,8 +131,7 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
         a = c0;
         while (a > 0 && s_dd[a] > (uint32_t)Ls) --a;
       }
-      // box end: next start after this lane, else walk on
-      int b;
+      int b;  // box end: next start after this lane, else walk on
       const uint32_t gt = f & ~(lt | (1u << lane));
       if (gt) {
         b = c0 + __ffs(gt) - 1;
@@ -151,8 +141,8 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
         if (b > jend) b = jend;
       }
       if (!in) continue;
-      if (a >= kBoxTile) continue;                                    // the next tile's box
-      if (a == 0 && t0 > 0 && s_dd[0] > (uint32_t)Ls) continue;      // an earlier tile's box
+      if (a >= kBoxTile) continue;                                // the next tile's box
+      if (a == 0 && t0 > 0 && s_dd[0] > (uint32_t)Ls) continue;  // an earlier tile's box
       if (b == jend && t0 + jend < nn) {
         long_box = true;  // runs past the window: the host redoes the order
         continue;
@@ -171,12 +161,114 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
     if (long_box) atomicExch(&st->seg_long, 1u);
   }
 
-  // Windowed look-back over the earlier tiles, one warp per level.
-  for (int l = warp; l <= Lb; l += W) {
+  // Windowed look-back over the earlier tiles.
+  if (warp == 0) {
+    uint64_t prev = 0;
+    if (tile > 0) {
+      prev = lookback_warp(status, tile, 1, st, wait_ns);
+      if (lane == 0) st_relaxed(status + tile, kFlagIncl | (prev + s_ttot));
+    }
+    if (lane == 0) s_texcl = (uint32_t)prev;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && tile > 0 && ld_relaxed_u32(&st->abort)) s_abort = 1;
+  __syncthreads();
+  if (s_abort) return;  // a wait gave up: ranks may be wrong, write nothing
+  if (tile == ntiles - 1 && threadIdx.x == 0) {
+    const uint32_t nb = s_texcl + s_ttot;
+    nbox[Lb] = nb;
+    if (nb <= lv.cap[Lb]) lv.off[Lb][nb] = n;
+  }
+  // Level-Lb keys and bookmarks.
+  const int shift = 63 - 3 * Lb;
+  uint32_t rank = s_texcl + s_wtot[warp] + (x - c);
+  const uint32_t cap = lv.cap[Lb];
+  while (mask) {
+    const int k = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const int j = threadIdx.x * kBoxItems + k;
+    if (rank < cap) {
+      lv.key[Lb][rank] = Lb == 0 ? 0ull : s_key[j + 1] >> shift;
+      lv.off[Lb][rank] = (uint32_t)(t0 + j);
+    }
+    ++rank;
+  }
+}
+
+// Levels 0..Lb-1 (and the parents of the level-Lb boxes) from the level-Lb
+// boxes: box b opens a level-l box exactly when its key differs from box
+// b-1's in the level-l prefix.  A multi-level prefix sum over the boxes (one
+// decoupled look-back chain per level) gives each start its rank.
+__global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(
+    int Lb, LevelArrays lv, uint32_t n, uint64_t* status, uint32_t* counter, uint32_t* nbox,
+    DevStatus* st, uint64_t wait_ns) {
+  constexpr int W = kBoxThreads / 32;
+  __shared__ uint32_t s_tile, s_abort;
+  __shared__ uint32_t s_wtot[W][kLevels];
+  __shared__ uint32_t s_texcl[kLevels];
+  __shared__ uint32_t s_ttot[kLevels];
+  __shared__ uint64_t s_key[kBoxTile + 1];  // s_key[j + 1] = level-Lb key of box t0 + j
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    s_tile = atomicAdd(counter, 1u);
+    s_abort = failed(st) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_abort) return;
+  const uint32_t nb = nbox[Lb] < lv.cap[Lb] ? nbox[Lb] : lv.cap[Lb];
+  const uint32_t ntiles = nb == 0 ? 1u : (nb + kBoxTile - 1) / kBoxTile;
+  const uint32_t tile = s_tile;
+  if (tile >= ntiles) return;  // the grid is sized for the capacity
+  const int64_t t0 = (int64_t)tile * kBoxTile;
+  const uint64_t* kLb = lv.key[Lb];
+  const int up = 63 - 3 * Lb;  // level-Lb key -> full-key position
+  for (int j = threadIdx.x; j < kBoxTile + 1; j += kBoxThreads) {
+    const int64_t b = t0 - 1 + j;
+    s_key[j] = (b >= 0 && b < (int64_t)nb) ? kLb[b] << up : 0ull;
+  }
+  __syncthreads();
+  uint32_t dd[kBoxItems];
+#pragma unroll
+  for (int k = 0; k < kBoxItems; ++k) {
+    const int j = threadIdx.x * kBoxItems + k;
+    const int64_t b = t0 + j;
+    dd[k] = b >= (int64_t)nb ? 0xffu : (b == 0 ? 0u : first_diff_level(s_key[j + 1], s_key[j]));
+  }
+  uint32_t lex[kLevels];
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    lex[l] = 0;
+    if (l < Lb) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int k = 0; k < kBoxItems; ++k) c += (dd[k] <= (uint32_t)l);
+      uint32_t x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      lex[l] = x - c;
+      if (lane == 31) s_wtot[warp][l] = x;
+    }
+  }
+  __syncthreads();
+  for (int l = warp; l < Lb; l += W) {
+    if (lane == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < W; ++w) {
+        const uint32_t c = s_wtot[w][l];
+        s_wtot[w][l] = run;
+        run += c;
+      }
+      s_ttot[l] = run;
+      st_relaxed(status + (uint64_t)tile * kLevels + l, (tile == 0 ? kFlagIncl : kFlagAgg) | run);
+    }
     uint64_t prev = 0;
     if (tile > 0) {
       prev = lookback_warp(status + l, tile, kLevels, st, wait_ns);
-      if (lane == 0) st_relaxed(status + (uint64_t)tile * kLevels + l, kFlagIncl | (prev + s_ttot[l]));
+      if (lane == 0)
+        st_relaxed(status + (uint64_t)tile * kLevels + l, kFlagIncl | (prev + s_ttot[l]));
     }
     if (lane == 0) s_texcl[l] = (uint32_t)prev;
   }
@@ -185,60 +277,57 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
   __syncthreads();
   if (s_abort) return;  // a wait gave up: ranks may be wrong, write nothing
   if (tile == ntiles - 1 && threadIdx.x == 0) {
-    for (int l = 0; l <= Lb; ++l) {
-      const uint32_t nb = s_texcl[l] + s_ttot[l];
-      nbox[l] = nb;
-      if (nb <= lv.cap[l]) lv.off[l][nb] = n;
-      if (l >= 1 && s_texcl[l - 1] + s_ttot[l - 1] <= lv.cap[l - 1])
-        lv.child[l - 1][s_texcl[l - 1] + s_ttot[l - 1]] = nb;
+    for (int l = 0; l < Lb; ++l) {
+      const uint32_t c = s_texcl[l] + s_ttot[l];
+      nbox[l] = c;
+      if (c <= lv.cap[l]) lv.off[l][c] = n;
+      if (c <= lv.cap[l]) lv.child[l][c] = l + 1 < Lb ? s_texcl[l + 1] + s_ttot[l + 1] : nb;
     }
   }
-
-  // Outputs, level by level.  For point k of this thread starting a level-l
-  // box: rank = base_l + (starts of this thread before k); its parent is the
-  // level-(l-1) box holding it and, if it also starts a level-(l-1) box, it is
-  // that box's first child.
-  uint32_t prev_mask = 0, prev_base = 0;
-  for (int l = 0; l <= Lb; ++l) {
-    uint32_t mask = 0;
+  uint32_t run[kLevels];
 #pragma unroll
-    for (int k = 0; k < kBoxItems; ++k) mask |= (dd[k] <= (uint32_t)l ? 1u : 0u) << k;
-    const uint32_t c = __popc(mask);
-    uint32_t x = c;
+  for (int l = 0; l < kLevels; ++l) run[l] = (l < Lb) ? s_texcl[l] + s_wtot[warp][l] + lex[l] : 0u;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+  for (int k = 0; k < kBoxItems; ++k) {
+    const int j = threadIdx.x * kBoxItems + k;
+    const int64_t b = t0 + j;
+    if (b >= (int64_t)nb) continue;
+    const uint32_t dk = dd[k];
+    const uint64_t key = s_key[j + 1];
+    // parent of the level-Lb box: the level-(Lb-1) box holding it
+    if (Lb >= 1) {
+      uint32_t pr = 0;
+#pragma unroll
+      for (int l = 0; l < kLevels; ++l)
+        if (l == Lb - 1) pr = dk <= (uint32_t)l ? run[l] : run[l] - 1u;
+      lv.parent[Lb][b] = pr;
+      if (dk <= (uint32_t)(Lb - 1) && pr < lv.cap[Lb - 1]) lv.child[Lb - 1][pr] = (uint32_t)b;
     }
-    const uint32_t base = s_texcl[l] + s_wtot[warp][l] + (x - c);
-    uint64_t* okey = lv.key[l];
-    uint32_t* ooff = lv.off[l];
-    uint32_t* opar = lv.parent[l];
-    uint32_t* ochild = l >= 1 ? lv.child[l - 1] : nullptr;
-    const uint32_t cap = lv.cap[l], capup = l >= 1 ? lv.cap[l - 1] : 0u;
-    const int shift = 63 - 3 * l;
-    uint32_t m = mask, rank = base;
-    while (m) {
-      const int k = __ffs(m) - 1;
-      m &= m - 1;
-      const int j = threadIdx.x * kBoxItems + k;
-      if (rank < cap) {
-        okey[rank] = l == 0 ? 0ull : s_key[j + 1] >> shift;
-        ooff[rank] = (uint32_t)(t0 + j);
-        if (l >= 1) {
-          const uint32_t below = __popc(prev_mask & ((2u << k) - 1u));  // level l-1 starts <= k
-          opar[rank] = prev_base + below - 1u;
-          if ((prev_mask >> k) & 1u) {
-            const uint32_t up = prev_base + below - 1u;
-            if (up < capup) ochild[up] = rank;
+    if (dk < (uint32_t)Lb) {
+      const uint32_t off = lv.off[Lb][b];
+#pragma unroll
+      for (int l = 0; l < kLevels; ++l) {
+        if (l < Lb && (uint32_t)l >= dk && run[l] < lv.cap[l]) {
+          const uint32_t rk = run[l];
+          lv.key[l][rk] = l == 0 ? 0ull : key >> (63 - 3 * l);
+          lv.off[l][rk] = off;
+          if (l >= 1) {
+            const bool up_starts = dk <= (uint32_t)(l - 1);
+            lv.parent[l][rk] = up_starts ? run[l - 1] : run[l - 1] - 1u;
+            if (up_starts && run[l - 1] < lv.cap[l - 1]) lv.child[l - 1][run[l - 1]] = rk;
           }
         }
       }
-      ++rank;
     }
-    prev_mask = mask;
-    prev_base = base;
+#pragma unroll
+    for (int l = 0; l < kLevels; ++l)
+      if (l < Lb && (uint32_t)l >= dk) ++run[l];
   }
+}
+
+uint32_t coarse_tiles(uint32_t cap) {
+  const uint64_t t = ((uint64_t)cap + kBoxTile - 1) / kBoxTile;
+  return t == 0 ? 1u : (uint32_t)t;
 }
 
 void launch_finish_boxes(const uint64_t* keys, const uint32_t* vals, uint32_t n, int Lb, int Ls,
@@ -253,6 +342,13 @@ void launch_finish_boxes(const uint64_t* keys, const uint32_t* vals, uint32_t n,
   const uint32_t t = boxes_tiles(n);
   finish_boxes_kernel<<<t, kBoxThreads, kBoxSmem, s>>>(keys, vals, n, Lb, Ls, lv, perm, status,
                                                         counter, nbox, st, wait_ns, t);
+}
+
+void launch_coarse_boxes(int Lb, LevelArrays lv, uint32_t n, uint64_t* status, uint32_t* counter,
+                         uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+  if (Lb < 1) return;
+  coarse_boxes_kernel<<<coarse_tiles(lv.cap[Lb]), kBoxThreads, 0, s>>>(Lb, lv, n, status, counter,
+                                                                       nbox, st, wait_ns);
 }
 
 // ---------------------------------------------------------------------------

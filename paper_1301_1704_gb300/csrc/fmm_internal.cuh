@@ -186,6 +186,15 @@ __device__ __forceinline__ uint64_t lookback_warp(const uint64_t* status, uint32
   return excl;
 }
 
+// Store with a per-lane predicate as one predicated instruction (streaming
+// cache hint): no branch around it.
+__device__ __forceinline__ void st_cs_if(uint32_t* p, uint32_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.cs.u32 [%0], %1;\n\t}"
+      ::"l"(p), "r"(v), "r"((uint32_t)pred)
+      : "memory");
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -254,13 +263,18 @@ void launch_onesweep_pass(int pass, const float* xyz, const uint64_t* keys_in,
                           uint64_t* status, uint32_t* counter, DevStatus* st, uint64_t wait_ns,
                           int stall_tile, cudaStream_t s);
 // From (key, index) pairs sorted by the top 3*Ls key bits: the finishing
-// sort inside each level-Ls box by (full key, index) -> perm, and the boxes of
-// levels 0..Lb (Lb <= Ls).  status: [ntiles][kLevels] zeroed; counter
-// zeroed; nbox: [kLevels].
+// sort inside each level-Ls box by (full key, index) -> perm, and the boxes
+// of level Lb (Lb <= Ls): keys and bookmarks.  status: [ntiles] zeroed;
+// counter zeroed; writes nbox[Lb].
 void launch_finish_boxes(const uint64_t* keys, const uint32_t* vals, uint32_t n, int Lb, int Ls,
                          LevelArrays lv, uint32_t* perm, uint64_t* status, uint32_t* counter,
                          uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s);
 uint32_t boxes_tiles(uint32_t n);
+// Levels 0..Lb-1, parents of level Lb and children of level Lb-1, from the
+// level-Lb boxes.  status: [coarse_tiles(cap[Lb])][kLevels] zeroed.
+void launch_coarse_boxes(int Lb, LevelArrays lv, uint32_t n, uint64_t* status, uint32_t* counter,
+                         uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s);
+uint32_t coarse_tiles(uint32_t cap);
 // Child-occupancy masks of the boxes of levels 0..Lb-1.
 void launch_occupancy(int Lb, LevelArrays lv, const uint32_t* nbox, uint32_t n,
                       const DevStatus* st, cudaStream_t s);

@@ -124,51 +124,99 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(ListArgs a, De
 // Every receiver child then splits C by one ballot per 32 candidates: its E2
 // and E4 lists come out in ascending order as contiguous, coalesced stores.
 constexpr int kCand = 27 * 8;  // at most 27 neighbours x 8 children
+constexpr int kNear = 64;      // candidates in some sibling's E2: the 4x4x4 block
 constexpr int kListWarps = kListThreads / 32;
 
 __global__ void __launch_bounds__(kListThreads) list_fill_kernel(ListArgs a, DevStatus* st) {
   __shared__ uint32_t s_rank[kListWarps][kCand];
   __shared__ uint8_t s_sib[kListWarps][kCand];
+  __shared__ uint32_t s_nrank[kListWarps][kNear];
+  __shared__ uint8_t s_nsib[kListWarps][kNear];
   if (failed(st)) return;  // set before this launch: the same for every thread
   if ((a.nnz[0] >> 32) != 0 || (a.nnz[1] >> 32) != 0) return;  // capacity error already set
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   uint32_t* crank = s_rank[warp];
   uint8_t* csib = s_sib[warp];
+  uint32_t* nrank = s_nrank[warp];
+  uint8_t* nsibm = s_nsib[warp];
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const uint32_t np = a.nbox_recv[a.l - 1];
   for (uint32_t p = gw; p < np; p += nw) {
+    // The receiver children of p (at most 8): lane j fetches child j's octant
+    // and list starts up front, so their loads overlap the neighbour loads.
+    const uint32_t c0 = a.rchild_up[p], c1 = a.rchild_up[p + 1];
+    uint32_t my_rho = 0, my_o2 = 0, my_o4 = 0;
+    if (c0 + lane < c1) {
+      my_rho = (uint32_t)(a.rkey[c0 + lane] & 7u);
+      my_o2 = a.e2_off[c0 + lane];
+      my_o4 = a.e4_off[c0 + lane];
+    }
     const Neighbour q = load_neighbour(a, p, lane);
+    const uint32_t nsib = c1 - c0;
+
+    // Candidates C (children of p's neighbours, ascending rank) and the near
+    // candidates (those in some sibling's E2), each with its sibling byte.
     const uint32_t nc = __popc(q.occ);
     uint32_t e = warp_excl(nc, lane);
     const uint32_t total = __shfl_sync(0xffffffffu, e + nc, 31);
-    uint32_t bits = q.occ, rank = q.child;
-    while (bits) {
-      const uint32_t o = __ffs(bits) - 1;
-      bits &= bits - 1;
-      crank[e] = rank++;
-      csib[e] = (uint8_t)e2_child_mask(-q.dx, -q.dy, -q.dz, o);
-      ++e;
+    {
+      uint32_t bits = q.occ, rank = q.child;
+      while (bits) {
+        const uint32_t o = __ffs(bits) - 1;
+        bits &= bits - 1;
+        crank[e] = rank++;
+        csib[e] = (uint8_t)e2_child_mask(-q.dx, -q.dy, -q.dz, o);
+        ++e;
+      }
     }
     __syncwarp();
-    const uint32_t c1 = a.rchild_up[p + 1];
-    for (uint32_t r = a.rchild_up[p]; r < c1; ++r) {
-      const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
-      uint32_t* o2 = a.e2_idx + a.e2_off[r];
-      uint32_t* o4 = a.e4_idx + a.e4_off[r];
-      for (uint32_t c = 0; c < total; c += 32) {
-        const uint32_t i = c + lane;
-        const bool valid = i < total;
-        const uint32_t v = valid ? crank[i] : 0u;
-        const bool in2 = valid && ((csib[i] >> rho) & 1u);
-        const bool in4 = valid && !in2;
+    uint32_t nnear = 0;
+    for (uint32_t c = 0; c < total; c += 32) {
+      const uint32_t i = c + lane;
+      const uint32_t sb = i < total ? csib[i] : 0u;
+      const uint32_t bn = __ballot_sync(0xffffffffu, sb != 0u);
+      if (sb) {
+        const uint32_t k = nnear + __popc(bn & lt);
+        nrank[k] = crank[i];
+        nsibm[k] = (uint8_t)sb;
+      }
+      nnear += __popc(bn);
+    }
+    __syncwarp();
+
+    uint32_t sbit[8], w2[8], w4[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      sbit[j] = (uint32_t)j < nsib ? 1u << __shfl_sync(0xffffffffu, my_rho, j) : 0u;
+      w2[j] = __shfl_sync(0xffffffffu, my_o2, j);
+      w4[j] = __shfl_sync(0xffffffffu, my_o4, j);
+    }
+    // E2 of sibling j: the near candidates whose byte has bit rho_j.
+    for (uint32_t c = 0; c < nnear; c += 32) {
+      const uint32_t i = c + lane;
+      const uint32_t v = i < nnear ? nrank[i] : 0u;
+      const uint32_t sb = i < nnear ? nsibm[i] : 0u;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {  // absent siblings have sbit 0: nothing stored
+        const bool in2 = (sb & sbit[j]) != 0u;
         const uint32_t b2 = __ballot_sync(0xffffffffu, in2);
+        st_cs_if(a.e2_idx + w2[j] + __popc(b2 & lt), v, in2);
+        w2[j] += __popc(b2);
+      }
+    }
+    // E4 of sibling j: the candidates without bit rho_j.
+    for (uint32_t c = 0; c < total; c += 32) {
+      const uint32_t i = c + lane;
+      const uint32_t v = i < total ? crank[i] : 0u;
+      const uint32_t sb = i < total ? csib[i] : 0xffu;  // past the end: never stored
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {  // absent siblings: in4 is false everywhere
+        const bool in4 = (sb & sbit[j]) == 0u && (uint32_t)j < nsib;
         const uint32_t b4 = __ballot_sync(0xffffffffu, in4);
-        if (in2) __stcs(o2 + __popc(b2 & lt), v);
-        if (in4) __stcs(o4 + __popc(b4 & lt), v);
-        o2 += __popc(b2);
-        o4 += __popc(b4);
+        st_cs_if(a.e4_idx + w4[j] + __popc(b4 & lt), v, in4);
+        w4[j] += __popc(b4);
       }
     }
     __syncwarp();

@@ -410,17 +410,24 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
   const uint64_t base = (uint64_t)tile * kSortTile;
   const uint64_t wbase = base + (uint64_t)warp * (kSortItems * 32);
 
+  // Every global read of the tile is issued up front: keys, values and this
+  // tile's output starts.
+  const uint32_t my_off =
+      threadIdx.x < radix ? __ldg(offsets + (uint64_t)threadIdx.x * ntiles + tile) : 0u;
   uint64_t key[kSortItems];
+  uint32_t val[kSortItems];
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const uint64_t i = wbase + k * 32 + lane;
     key[k] = 0;
+    val[k] = (uint32_t)i;
     if (i < n) {
       if (kFromXyz) {
         bool ok;
         key[k] = morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok);
       } else {
-        key[k] = keys_in[i];
+        key[k] = __ldcs(keys_in + i);
+        val[k] = __ldcs(vals_in + i);
       }
     }
   }
@@ -470,7 +477,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     const uint32_t excl_blk = x - tot + s_wsum[warp];
 #pragma unroll
     for (int w = 0; w < W; ++w) s_wcnt[w][threadIdx.x] += excl_blk;
-    s_gbase[threadIdx.x] = offsets[(uint64_t)threadIdx.x * ntiles + tile] - excl_blk;
+    s_gbase[threadIdx.x] = my_off - excl_blk;
   }
   __syncthreads();
 #pragma unroll
@@ -480,7 +487,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
       const uint32_t d = (uint32_t)(key[k] >> shift) & mask;
       const uint32_t p = pos[k] + s_wcnt[warp][d];
       s_keys[p] = key[k];
-      s_vals[p] = kFromXyz ? (uint32_t)i : vals_in[i];
+      s_vals[p] = val[k];
     }
   }
   __syncthreads();
