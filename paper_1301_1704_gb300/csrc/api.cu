@@ -313,7 +313,10 @@ int sort_pairs(fmm_ctx* c, const SortPlan& plan, const float* xyz, uint32_t n, b
                         counters + p, nullptr, c->st, wait_ns, s);
       }
       Launch L(c, "rts_scatter");
-      launch_rts_scatter(p, xyz, kin, vin, ko, vo, n, plan, h, c->st, s);
+      // The first pass may leave equal digits in any order when a finishing
+      // sort follows; the full-key fallback writes the order directly.
+      launch_rts_scatter(p, xyz, kin, vin, ko, vo, n, plan, h, vals_last != nullptr || p > 0,
+                         c->st, wait_ns, s);
     }
     kin = ko;
     vin = vo;

@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
 
   // Finishing sort inside the level-Ls boxes that START in this tile,
   // including their points in the halo past the tile's end (a box begun in
-  // an earlier tile is that tile's).  Inside a box the points stand in index
-  // order, so a point's rank counts the box's points with a smaller key, and
-  // the earlier points with an equal key.  Each warp takes 32 consecutive
+  // an earlier tile is that tile's).  A point's rank counts the points of its
+  // box that come before it in (full key, original index) order; the order
+  // the radix passes left inside a box does not matter.  Each warp takes 32 consecutive
   // points; box bounds inside the warp come from one ballot of box starts.
   // This runs between publishing the aggregate and reading the earlier
   // tiles' words, which gives them time to publish.
@@ -149,11 +149,12 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
       }
       uint32_t r = 0;
       if (b - a > 1) {
-        // within a box the top bits agree: order by (low key bits, slot)
+        // within a box the top bits agree: order by (low key bits, index)
         const uint64_t mine = s_key[j + 1] & lowmask;
+        const uint32_t vj = s_val[j];
         for (int q = a; q < b; ++q) {
           const uint64_t kq = s_key[q + 1] & lowmask;
-          r += (kq < mine) || (kq == mine && q < j);
+          r += (kq < mine) || (kq == mine && s_val[q] < vj);
         }
       }
       perm[t0 + a + r] = s_val[j];

@@ -195,6 +195,59 @@ __device__ __forceinline__ void st_cs_if(uint32_t* p, uint32_t v, bool pred) {
       : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, untiled) into shared memory, completed on an
+// mbarrier.  Addresses and sizes must be multiples of 16 bytes.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's earlier shared-memory accesses before later bulk
+// copies into the same memory.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+          smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 "
+      "%0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of an mbarrier; false after wait_ns (or
+// once another thread gave up), with FMM_ERR_TIMEOUT recorded.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st,
+                                          uint64_t wait_ns) {
+  WaitClock clk;
+  while (!mbar_try_wait(bar, parity))
+    if (clk.expired(st, wait_ns)) return false;
+  return true;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -253,8 +306,8 @@ void launch_tile_hist(int pass, const float* xyz, const uint64_t* keys, uint32_t
                       const SortPlan& p, uint32_t* hist, DevStatus* st, cudaStream_t s);
 void launch_rts_scatter(int pass, const float* xyz, const uint64_t* keys_in,
                         const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                        uint32_t n, const SortPlan& p, const uint32_t* offsets, DevStatus* st,
-                        cudaStream_t s);
+                        uint32_t n, const SortPlan& p, const uint32_t* offsets, bool stable,
+                        DevStatus* st, uint64_t wait_ns, cudaStream_t s);
 // One onesweep pass.  pass 0 reads xyz (values = point index), later passes
 // read keys_in/vals_in.  status: [ntiles][256] zeroed; counter: zeroed.
 void launch_onesweep_pass(int pass, const float* xyz, const uint64_t* keys_in,

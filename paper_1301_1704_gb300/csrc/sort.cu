@@ -386,146 +386,245 @@ void launch_tile_hist(int pass, const float* xyz, const uint64_t* keys, uint32_t
   }
 }
 
-template <bool kFromXyz>
+// Scatter of one reduce-then-scan pass, persistent: each block walks the
+// tiles t = blockIdx.x, + gridDim.x, ... and, while it ranks and scatters one
+// tile, a bulk copy (TMA) brings the next tile's input -- the coordinates in
+// the first pass, the (key, index) pairs in later ones -- into the other
+// half of a double buffer.  A partial last tile is read with plain loads.
+constexpr uint32_t kInBytes = kSortTile * 12;  // xyz of a tile, or its keys + indices
+constexpr size_t kScatterSmem = 2 * (size_t)kInBytes;
+
+// kStable: keep the input order inside a digit (every pass but an unstable
+// first one).
+template <bool kFromXyz, bool kStable>
 __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     const float* __restrict__ xyz, const uint64_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint32_t n, int shift, int bits, uint32_t ntiles,
-    const uint32_t* __restrict__ offsets, DevStatus* st) {
+    const uint32_t* __restrict__ offsets, DevStatus* st, uint64_t wait_ns, bool use_bulk) {
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t s_fail;
+  __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_wcnt[W][kRadixMax];  // per-warp digit counts, then block slots
   __shared__ uint32_t s_gbase[kRadixMax];    // global position of block slot 0, per digit
   __shared__ uint32_t s_wsum[W];
-  extern __shared__ __align__(16) uint64_t s_keys[];
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kSortTile);
+  extern __shared__ __align__(128) unsigned char s_in[];  // two input buffers
 
   const uint32_t radix = 1u << bits, mask = radix - 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < W * kRadixMax; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
-  if (threadIdx.x == 0) s_fail = failed(st) ? 1u : 0u;
+  const uint32_t lt = lanemask_lt();
+  if (threadIdx.x == 0) {
+    s_fail = failed(st) ? 1u : 0u;
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_mbar_init();
+  }
   __syncthreads();
   if (s_fail) return;  // an earlier kernel failed (domain error): leave the outputs alone
-  const uint32_t tile = blockIdx.x;
-  const uint64_t base = (uint64_t)tile * kSortTile;
-  const uint64_t wbase = base + (uint64_t)warp * (kSortItems * 32);
 
-  // Every global read of the tile is issued up front: keys, values and this
-  // tile's output starts.
-  const uint32_t my_off =
-      threadIdx.x < radix ? __ldg(offsets + (uint64_t)threadIdx.x * ntiles + tile) : 0u;
-  uint64_t key[kSortItems];
-  uint32_t val[kSortItems];
+  // tiles read by bulk copy (all full tiles, when the sources are 16-byte aligned)
+  const uint32_t full_tiles = use_bulk ? (uint32_t)(n / kSortTile) : 0u;
+  auto issue = [&](uint32_t t, int b) {  // thread 0 only, full tiles only
+    unsigned char* dst = s_in + b * kInBytes;
+    const uint64_t base = (uint64_t)t * kSortTile;
+    mbar_expect_tx(&s_bar[b], kInBytes);
+    if (kFromXyz) {
+      bulk_load(dst, xyz + 3 * base, kInBytes, &s_bar[b]);
+    } else {
+      bulk_load(dst, keys_in + base, kSortTile * 8, &s_bar[b]);
+      bulk_load(dst + kSortTile * 8, vals_in + base, kSortTile * 4, &s_bar[b]);
+    }
+  };
+  uint32_t phase[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  uint32_t t = blockIdx.x;
+  if (t < full_tiles) {
+    if (threadIdx.x == 0) issue(t, 0);
+    pending[0] = true;
+  }
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int b = it & 1;
+    unsigned char* buf = s_in + b * kInBytes;
+    const uint64_t base = (uint64_t)t * kSortTile;
+    const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
+    const bool full = t < full_tiles;
+    const uint32_t tn = t + gridDim.x;
+    if (tn < full_tiles) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        issue(tn, b ^ 1);
+      }
+      pending[b ^ 1] = true;
+    }
+    const uint32_t my_off =
+        threadIdx.x < radix ? __ldg(offsets + (uint64_t)threadIdx.x * ntiles + t) : 0u;
+    for (int i = threadIdx.x; i < W * kRadixMax; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+    bool ok = true;
+    if (full) {
+      ok = mbar_wait(&s_bar[b], phase[b], st, wait_ns);
+      phase[b] ^= 1u;
+      pending[b] = false;
+    }
+    if (__syncthreads_or(!ok)) {
+      // a copy never completed: let any other copy land, then leave
+      for (int k = 0; k < 2; ++k)
+        if (pending[k]) mbar_wait(&s_bar[k], phase[k], st, wait_ns);
+      return;
+    }
+
+    // Items, warp-striped: item k of lane j is tile slot 32 * (kSortItems *
+    // warp + k) + j, so (k, lane) order is the input order.
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems];
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const uint64_t i = wbase + k * 32 + lane;
-    key[k] = 0;
-    val[k] = (uint32_t)i;
-    if (i < n) {
-      if (kFromXyz) {
-        bool ok;
-        key[k] = morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok);
-      } else {
-        key[k] = __ldcs(keys_in + i);
-        val[k] = __ldcs(vals_in + i);
+    for (int k = 0; k < kSortItems; ++k) {
+      const uint32_t j = (uint32_t)warp * (kSortItems * 32) + k * 32 + lane;
+      key[k] = 0;
+      val[k] = (uint32_t)(base + j);
+      if (j < cnt) {
+        if (kFromXyz) {
+          const float* f = full ? reinterpret_cast<const float*>(buf) + 3 * j : xyz + 3 * (base + j);
+          bool okk;
+          key[k] = morton_key(f[0], f[1], f[2], &okk);
+        } else if (full) {
+          key[k] = reinterpret_cast<const uint64_t*>(buf)[j];
+          val[k] = reinterpret_cast<const uint32_t*>(buf + kSortTile * 8)[j];
+        } else {
+          key[k] = keys_in[base + j];
+          val[k] = vals_in[base + j];
+        }
       }
     }
-  }
-  const uint32_t lt = lanemask_lt();
-  uint32_t pos[kSortItems];
+    uint32_t pos[kSortItems];
+    if (!kStable) {
+      // First pass: there is no earlier order to keep, so the rank inside a
+      // digit needs no stability -- one shared-memory atomic per item (the
+      // paper's Alg. 1 takes box ranks the same way).  Counts go to warp 0's
+      // row; the finishing sort orders points inside a box by (key, index).
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const bool valid = wbase + k * 32 + lane < n;
-    const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & mask : 0xffffffffu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t before = valid ? s_wcnt[warp][d] : 0u;
-    __syncwarp();
-    if (valid && (peers & lt) == 0) s_wcnt[warp][d] = before + __popc(peers);
-    __syncwarp();
-    pos[k] = before + __popc(peers & lt);
-  }
-  __syncthreads();
-  uint32_t tot = 0;
-  if (threadIdx.x < radix) {
+      for (int k = 0; k < kSortItems; ++k) {
+        const bool valid = (uint32_t)warp * (kSortItems * 32) + k * 32 + lane < cnt;
+        pos[k] = valid ? atomicAdd(&s_wcnt[0][(uint32_t)(key[k] >> shift) & mask], 1u) : 0u;
+      }
+    } else {
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      const uint32_t c = s_wcnt[w][threadIdx.x];
-      s_wcnt[w][threadIdx.x] = tot;
-      tot += c;
-    }
-  }
-  uint32_t x = tot;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_wsum[warp] = x;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const uint32_t v = lane < W ? s_wsum[lane] : 0u;
-    uint32_t y = v;
-#pragma unroll
-    for (int o = 1; o < W; o <<= 1) {
-      const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
-      if (lane >= o) y += z;
-    }
-    if (lane < W) s_wsum[lane] = y - v;
-  }
-  __syncthreads();
-  if (threadIdx.x < radix) {
-    const uint32_t excl_blk = x - tot + s_wsum[warp];
-#pragma unroll
-    for (int w = 0; w < W; ++w) s_wcnt[w][threadIdx.x] += excl_blk;
-    s_gbase[threadIdx.x] = my_off - excl_blk;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const uint64_t i = wbase + k * 32 + lane;
-    if (i < n) {
-      const uint32_t d = (uint32_t)(key[k] >> shift) & mask;
-      const uint32_t p = pos[k] + s_wcnt[warp][d];
-      s_keys[p] = key[k];
-      s_vals[p] = val[k];
-    }
-  }
-  __syncthreads();
-  const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
-#pragma unroll 4
-  for (int j = 0; j < kSortItems; ++j) {
-    const uint32_t p = threadIdx.x + j * kSortThreads;
-    if (p < cnt) {
-      const uint64_t kk = s_keys[p];
-      const uint32_t g = s_gbase[(uint32_t)(kk >> shift) & mask] + p;
-      if (g < n) {
-        keys_out[g] = kk;
-        vals_out[g] = s_vals[p];
+      for (int k = 0; k < kSortItems; ++k) {
+        const bool valid = (uint32_t)warp * (kSortItems * 32) + k * 32 + lane < cnt;
+        const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & mask : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? s_wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) s_wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        pos[k] = before + __popc(peers & lt);
       }
     }
+    __syncthreads();
+    uint32_t tot = 0;
+    if (threadIdx.x < radix) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const uint32_t c = s_wcnt[w][threadIdx.x];
+        s_wcnt[w][threadIdx.x] = tot;
+        tot += c;
+      }
+    }
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const uint32_t v = lane < W ? s_wsum[lane] : 0u;
+      uint32_t y = v;
+#pragma unroll
+      for (int o = 1; o < W; o <<= 1) {
+        const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += z;
+      }
+      if (lane < W) s_wsum[lane] = y - v;
+    }
+    __syncthreads();
+    if (threadIdx.x < radix) {
+      const uint32_t excl_blk = x - tot + s_wsum[warp];
+#pragma unroll
+      for (int w = 0; w < W; ++w) s_wcnt[w][threadIdx.x] += excl_blk;
+      s_gbase[threadIdx.x] = my_off - excl_blk;
+    }
+    __syncthreads();
+    // Reorder the tile by digit into the (now consumed) input buffer.
+    uint64_t* r_keys = reinterpret_cast<uint64_t*>(buf);
+    uint32_t* r_vals = reinterpret_cast<uint32_t*>(buf + kSortTile * 8);
+    const int row = kStable ? warp : 0;
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      if ((uint32_t)warp * (kSortItems * 32) + k * 32 + lane < cnt) {
+        const uint32_t p = pos[k] + s_wcnt[row][(uint32_t)(key[k] >> shift) & mask];
+        r_keys[p] = key[k];
+        r_vals[p] = val[k];
+      }
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int j = 0; j < kSortItems; ++j) {
+      const uint32_t p = threadIdx.x + j * kSortThreads;
+      if (p < cnt) {
+        const uint64_t kk = r_keys[p];
+        const uint32_t g = s_gbase[(uint32_t)(kk >> shift) & mask] + p;
+        if (g < n) {
+          keys_out[g] = kk;
+          vals_out[g] = r_vals[p];
+        }
+      }
+    }
+    __syncthreads();  // the buffer is free for the copy issued next iteration
   }
 }
 
 void launch_rts_scatter(int pass, const float* xyz, const uint64_t* keys_in,
                         const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                        uint32_t n, const SortPlan& p, const uint32_t* offsets, DevStatus* st,
-                        cudaStream_t s) {
+                        uint32_t n, const SortPlan& p, const uint32_t* offsets, bool stable,
+                        DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
   if (n == 0) return;
   static bool attr = false;
+  static int sms = 0;
   if (!attr) {
-    cudaFuncSetAttribute(rts_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kSortSmem);
-    cudaFuncSetAttribute(rts_scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kSortSmem);
+    cudaFuncSetAttribute(rts_scatter_kernel<true, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    cudaFuncSetAttribute(rts_scatter_kernel<true, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    cudaFuncSetAttribute(rts_scatter_kernel<false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
     attr = true;
   }
   const int shift = p.lo + pass * p.bits;
-  if (pass == 0)
-    rts_scatter_kernel<true><<<p.ntiles, kSortThreads, kSortSmem, s>>>(
-        xyz, nullptr, nullptr, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st);
-  else
-    rts_scatter_kernel<false><<<p.ntiles, kSortThreads, kSortSmem, s>>>(
-        nullptr, keys_in, vals_in, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st);
+  uint32_t grid = (uint32_t)sms * 2u;
+  if (grid > p.ntiles) grid = p.ntiles;
+  // The bulk copies need 16-byte aligned sources; otherwise every tile takes
+  // the plain-load path.
+  if (pass == 0) {
+    const bool aligned = ((uintptr_t)xyz & 15u) == 0;
+    if (stable)
+      rts_scatter_kernel<true, true><<<grid, kSortThreads, kScatterSmem, s>>>(
+          xyz, nullptr, nullptr, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st,
+          wait_ns, aligned);
+    else
+      rts_scatter_kernel<true, false><<<grid, kSortThreads, kScatterSmem, s>>>(
+          xyz, nullptr, nullptr, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st,
+          wait_ns, aligned);
+  } else {
+    const bool aligned = (((uintptr_t)keys_in | (uintptr_t)vals_in) & 15u) == 0;
+    rts_scatter_kernel<false, true><<<grid, kSortThreads, kScatterSmem, s>>>(
+        nullptr, keys_in, vals_in, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st,
+        wait_ns, aligned);
+  }
 }
 
 }  // namespace fmm

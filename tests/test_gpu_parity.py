@@ -136,6 +136,18 @@ def test_faces_and_corners(ctx, orc):
     compare_full(got, want, 6)
 
 
+def test_unaligned_coordinates(ctx, orc):
+    """Coordinates starting 4 bytes past a 16-byte boundary take the plain-load path."""
+    src = workloads.uniform(50001, 40)
+    recv = workloads.clumps(30000, 41, nclumps=4, sigma=0.03)
+    buf = torch.zeros(3 * 50001 + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(src.ravel()).cuda()
+    s_dev = buf[1:].view(50001, 3)
+    assert s_dev.data_ptr() % 16 == 4
+    got = ctx.build(s_dev, _dev(recv), L=6).numpy()
+    compare_full(got, orc.build_tree(src, recv, L=6), 6)
+
+
 def test_aliased_sets(ctx, orc):
     p = workloads.clumps(30000, 14, nclumps=6, sigma=0.03)
     got, want = run_both(ctx, orc, p, p, 6, aliased=True)
