@@ -185,6 +185,33 @@ int fmm_reset_timing(fmm_ctx* ctx);
 /* Number of kernels launched by the last fmm_build on this context. */
 int fmm_last_launch_count(fmm_ctx* ctx, uint64_t* launches);
 
+/* Exclusive prefix sum of n uint32 counts that allocates nothing.  The paper
+ * has no counterpart: this serves callers that must not allocate device
+ * memory while they run -- for example a time-stepping loop that reserved
+ * all device memory up front, or code running where the CUDA allocator may
+ * not be called -- and that want the CSR row starts of their own per-box list
+ * counts (the role of NeighborBookmark).
+ *
+ *   counts  [n] device, read-only; offsets [n + 1] device: offsets[i] = sum
+ *   of counts[0..i), offsets[n] = the total (low 32 bits); total: optional
+ *   device uint64 receiving the full total (all ones if a bounded device-side
+ *   wait gave up).  Both buffers are the caller's.
+ *
+ * n must not exceed FMM_NOALLOC_SCAN_MAX (FMM_ERR_ARG otherwise).  The only
+ * scratch is a fixed static device array (about 128 KiB) that every GPU
+ * loading this library keeps until the process exits; the call allocates
+ * nothing (no cudaMalloc, no allocator callback) and clears the part of the
+ * scratch it uses on `stream` before its kernel runs.  The first call on a
+ * device looks up that array's device address (once per device, with the
+ * device current): make that first call before any stream capture.  All calls
+ * share the one array, which keeps the last call's contents, so calls that
+ * overlap on the GPU (on different streams, or from several threads) race
+ * and give wrong results: order them.  Asynchronous on `stream`; returns
+ * after launching.  Runs on the current device. */
+#define FMM_NOALLOC_SCAN_MAX (1u << 26)
+int fmm_exclusive_scan_noalloc(const uint32_t* counts, uint32_t n, uint32_t* offsets,
+                               uint64_t* total, void* stream);
+
 /* Static description of a status code. */
 const char* fmm_status_string(int status);
 

@@ -60,8 +60,9 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 EXPORTS = (
     "fmm_create", "fmm_destroy", "fmm_build", "fmm_morton_keys", "fmm_query_workspace",
     "fmm_set_tuning", "fmm_get_tuning", "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing",
-    "fmm_last_launch_count", "fmm_status_string",
+    "fmm_last_launch_count", "fmm_status_string", "fmm_exclusive_scan_noalloc",
 )
+FMM_NOALLOC_SCAN_MAX = 1 << 26
 
 FMM_SORT_RTS = 0
 FMM_SORT_ONESWEEP = 1
@@ -111,6 +112,9 @@ def _load():
     lib.fmm_get_timing.restype = C.c_int
     lib.fmm_last_launch_count.argtypes = [C.c_void_p, _u64p]
     lib.fmm_last_launch_count.restype = C.c_int
+    lib.fmm_exclusive_scan_noalloc.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
+                                               C.c_void_p]
+    lib.fmm_exclusive_scan_noalloc.restype = C.c_int
     lib.fmm_status_string.argtypes = [C.c_int]
     lib.fmm_status_string.restype = C.c_char_p
     _lib = lib
@@ -317,6 +321,20 @@ class Context:
         v = C.c_uint64()
         _load().fmm_last_launch_count(self._h, C.byref(v))
         return int(v.value)
+
+
+def exclusive_scan_noalloc(counts, offsets, total=None, stream=None) -> None:
+    """fmm_exclusive_scan_noalloc: offsets[0..n] from counts[0..n) (CUDA
+    tensors of 4-byte integers, offsets one longer); allocates nothing."""
+    n = counts.numel()
+    if offsets.numel() != n + 1:
+        raise ValueError("offsets needs n + 1 entries")
+    st = _load().fmm_exclusive_scan_noalloc(
+        C.c_void_p(counts.data_ptr() if n else 0), n, C.c_void_p(offsets.data_ptr()),
+        C.c_void_p(total.data_ptr() if total is not None else 0),
+        C.c_void_p(Context._stream(stream)))
+    if st != FMM_OK:
+        raise FmmError(st, "fmm_exclusive_scan_noalloc")
 
 
 def query_workspace(N: int, M: int, L: int | None = None, s: int | None = None, flags: int = 0) -> int:
