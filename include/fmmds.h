@@ -144,6 +144,26 @@ int fmm_destroy(fmm_ctx* ctx);
 int fmm_build(fmm_ctx* ctx, const float* src_xyz, uint32_t N, const float* recv_xyz,
               uint32_t M, fmm_params params, fmm_tree* out, void* stream);
 
+/* One (Src, Recv) pair of a batched build. */
+typedef struct fmm_set {
+  const float* src;
+  uint32_t N;
+  const float* recv;
+  uint32_t M;
+} fmm_set;
+
+/* Alg. 5 for nsets independent pairs at once: every stage (radix passes,
+ * boxes, lists) covers all sets in one kernel launch, so many small builds
+ * cost about as many launches as one.  Same conventions as fmm_build per
+ * set; params apply to every set (in cluster-size mode each set gets its own
+ * L).  outs[k] receives set k's tree, with values local to the set (point
+ * indices, box ranks and list entries as if the set were built alone); all
+ * arrays live in the context's arena until its next build.  Inputs must not
+ * overlap partially: a set's src and recv may be the same array (N == M).
+ * FMM_FLAG_TEST_STALL is not accepted here. */
+int fmm_build_batched(fmm_ctx* ctx, const fmm_set* sets, uint32_t nsets, fmm_params params,
+                      fmm_tree* outs, void* stream);
+
 /* Sec. 2 "BoxIndex" + Sec. 1.4 interleave: the 63-bit Morton keys of n
  * points in input order.  xyz [n][3] and keys [n] are device pointers owned
  * by the caller.  Asynchronous on `stream`; returns FMM_ERR_DOMAIN (after a

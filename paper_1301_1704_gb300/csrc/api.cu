@@ -1,14 +1,15 @@
 // api.cu -- the C ABI (include/fmmds.h): context, arena, and the build
-// pipeline of Alg. 5 on one stream.
+// pipeline of Alg. 5 on one stream, for one (Src, Recv) pair or a batch.
 //
-// Per set (sources, then receivers; once if both are the same array):
-//   upfront digit histograms -> digit offsets -> onesweep passes (the first
-//   one forms the Morton keys from the coordinates) -> finishing sort inside
-//   boxes (permutation) fused with the boxes of all levels -> child
-//   occupancy.
-// Then, after one read-back of the box counts (for list capacities and the
-// cluster-size level), for l = 2..L: list counts -> two prefix sums -> fill.
-// A final read-back returns sizes and the device status word.
+// A build is a list of point sets (sources and receivers; a set given as both
+// is built once) and a list of jobs (source set, receiver set) whose lists
+// are wanted.  Every stage covers all sets in one launch:
+//   radix passes (per-tile digit histograms -> one prefix sum -> scatter; the
+//   first pass forms the Morton keys from the coordinates) -> finishing sort
+//   inside boxes + finest boxes -> coarser boxes -> child occupancy;
+// then for l = 2..L: job prefix -> list counts -> two prefix sums -> fill.
+// The host synchronises once at the end (and once after the boxes in
+// cluster-size mode, or when the list capacity bound is too large).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -37,20 +38,6 @@ struct TimeAcc {
   double ms;
 };
 
-// Arrays of one point set.
-struct SetArrays {
-  uint32_t n = 0;
-  const float* xyz = nullptr;
-  uint32_t* perm = nullptr;
-  LevelArrays lv{};
-  uint32_t* nbox_dev = nullptr;    // [kLevels]
-  uint32_t* maxocc_dev = nullptr;  // [kLevels]
-  uint32_t cap[kLevels] = {};
-  uint64_t* skeys = nullptr;  // keys sorted by the top 3*Ls bits
-  uint32_t* svals = nullptr;
-  int Ls = 0;
-};
-
 }  // namespace
 
 struct fmm_ctx {
@@ -61,9 +48,12 @@ struct fmm_ctx {
   std::vector<Chunk> chunks;
   size_t cur = 0, off = 0;
   size_t peak_request = 0;
-  DevStatus* st = nullptr;          // persistent device status word
-  void* host_buf = nullptr;         // pinned read-back buffer
-  cudaStream_t stream = nullptr;    // stream of the call in progress
+  DevStatus* st = nullptr;        // persistent device status word
+  void* up_buf = nullptr;         // pinned staging of descriptor uploads
+  size_t up_bytes = 0, up_cursor = 0;
+  void* rb_buf = nullptr;         // pinned read-back buffer
+  size_t rb_bytes = 0;
+  cudaStream_t stream = nullptr;  // stream of the call in progress
   bool timing = false;
   std::vector<PendingTime> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -75,11 +65,10 @@ struct fmm_ctx {
 
 namespace {
 
-constexpr size_t kHostBuf = 1 << 16;
+constexpr size_t kAlign = 256;
 // Largest list capacity (bytes) reserved from the box-count bounds alone;
 // above it the box counts are read back first.
 constexpr uint64_t kAsyncListBytes = 16ull << 30;
-constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -150,6 +139,22 @@ T* arena_get(fmm_ctx* c, size_t count, int* err) {
   c->cur = c->chunks.size() - 1;
   c->off = bytes;
   return reinterpret_cast<T*>(p);
+}
+
+// Pinned host buffers (grown on demand; the caller has synchronised the
+// stream when a buffer in use could be replaced).
+int pinned_reserve(void** buf, size_t* have, size_t bytes) {
+  if (bytes <= *have) return FMM_OK;
+  if (*buf) cudaFreeHost(*buf);
+  *buf = nullptr;
+  *have = 0;
+  const size_t want = std::max<size_t>(bytes, 1 << 20);
+  if (cudaMallocHost(buf, want) != cudaSuccess) {
+    cudaGetLastError();
+    return FMM_ERR_OOM;
+  }
+  *have = want;
+  return FMM_OK;
 }
 
 cudaEvent_t get_event(fmm_ctx* c) {
@@ -233,7 +238,7 @@ int sort_level(uint32_t n, int L) {
   int lvl = 1;
   while (lvl < kMaxLevel && ((uint64_t)n >> (3 * lvl)) > 8) ++lvl;
   lvl = std::max(std::max(lvl, L), 1);
-  const int passes = (3 * lvl + 7) / 8;
+  const int passes = passes_for(lvl);
   return std::min(kMaxLevel, std::max(lvl, 8 * passes / 3));
 }
 
@@ -241,426 +246,771 @@ uint64_t wait_ns_of(const fmm_params& p) {
   return (uint64_t)(p.wait_ms ? p.wait_ms : 2000u) * 1000000ull;
 }
 
-// Radix passes over the (key, index) pairs of one set: the first pass forms
-// the keys from the coordinates.  Output in (*kout, *vout); with
-// vals_last != null the last pass writes its values there instead.
-int sort_pairs(fmm_ctx* c, const SortPlan& plan, const float* xyz, uint32_t n, bool stall,
-               uint64_t wait_ns, uint64_t* ka, uint32_t* va, uint64_t* kb, uint32_t* vb,
-               uint32_t* vals_last, uint64_t** kout, uint32_t** vout) {
-  cudaStream_t s = c->stream;
-  int err = FMM_OK;
-  *kout = nullptr;
-  *vout = nullptr;
-  if (n == 0 || plan.passes == 0) return FMM_OK;
-  const uint32_t radix = 1u << plan.bits;
-  // The bounded-wait test needs a look-back pass: it always takes onesweep.
-  const bool onesweep = stall || c->tuning.sort_kind == FMM_SORT_ONESWEEP;
-  uint32_t* hist = nullptr;
-  uint64_t* sstatus = nullptr;
-  uint32_t* counters = nullptr;
-  size_t per_pass = 0;
-  if (onesweep) {
-    per_pass = (size_t)plan.ntiles * radix;
-    const size_t zb = align_up(sizeof(uint32_t) * 8 * kRadixMax) +
-                      align_up(sizeof(uint64_t) * per_pass * plan.passes) +
-                      align_up(sizeof(uint32_t) * 16);
-    char* z = arena_get<char>(c, zb, &err);
-    if (err) return err;
-    FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
-    hist = reinterpret_cast<uint32_t*>(z);
-    sstatus = reinterpret_cast<uint64_t*>(z + align_up(sizeof(uint32_t) * 8 * kRadixMax));
-    counters = reinterpret_cast<uint32_t*>(z + align_up(sizeof(uint32_t) * 8 * kRadixMax) +
-                                           align_up(sizeof(uint64_t) * per_pass * plan.passes));
-    {
-      Launch L(c, "upfront_hist");
-      launch_upfront_hist(xyz, n, plan, hist, c->st, s);
-    }
-    Launch L(c, "digit_scan");
-    launch_digit_scan(plan, hist, s);
-  } else {
-    per_pass = (size_t)radix * plan.ntiles;  // digit-major tile histogram
-    const uint32_t stiles = scan_tiles((uint32_t)per_pass);
-    const size_t zb = align_up(sizeof(uint64_t) * stiles) * plan.passes +
-                      align_up(sizeof(uint32_t) * 16);
-    char* z = arena_get<char>(c, zb, &err);
-    hist = arena_get<uint32_t>(c, (per_pass + 1) * plan.passes, &err);
-    if (err) return err;
-    FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
-    sstatus = reinterpret_cast<uint64_t*>(z);
-    counters = reinterpret_cast<uint32_t*>(z + align_up(sizeof(uint64_t) * stiles) * plan.passes);
-  }
-  uint64_t* kin = nullptr;
-  uint32_t* vin = nullptr;
-  for (int p = 0; p < plan.passes; ++p) {
-    uint64_t* ko = (p & 1) ? kb : ka;
-    uint32_t* vo = (p & 1) ? vb : va;
-    if (vals_last && p == plan.passes - 1) vo = vals_last;
-    if (onesweep) {
-      Launch L(c, "onesweep");
-      launch_onesweep_pass(p, xyz, kin, vin, ko, vo, n, plan, hist + p * kRadixMax,
-                           sstatus + (size_t)p * per_pass, counters + p, c->st, wait_ns,
-                           (stall && p == 0 && plan.ntiles > 2) ? 1 : -1, s);
-    } else {
-      uint32_t* h = hist + (per_pass + 1) * p;
-      const uint32_t stiles = scan_tiles((uint32_t)per_pass);
-      {
-        Launch L(c, "tile_hist");
-        launch_tile_hist(p, xyz, kin, n, plan, h, c->st, s);
-      }
-      {
-        Launch L(c, "scan");
-        launch_scan_u32(h, nullptr, (uint32_t)per_pass, sstatus + (size_t)stiles * p,
-                        counters + p, nullptr, c->st, wait_ns, s);
-      }
-      Launch L(c, "rts_scatter");
-      // The first pass may leave equal digits in any order when a finishing
-      // sort follows; the full-key fallback writes the order directly.
-      launch_rts_scatter(p, xyz, kin, vin, ko, vo, n, plan, h, vals_last != nullptr || p > 0,
-                         c->st, wait_ns, s);
-    }
-    kin = ko;
-    vin = vo;
-  }
-  *kout = kin;
-  *vout = vin;
-  return FMM_OK;
-}
+// ---------------------------------------------------------------------------
+// Host bookkeeping of a build.
 
-// Keys, order, boxes of levels 0..Lb and (sources) occupancy for one set.
-int build_set(fmm_ctx* c, SetArrays* S, int Lb, bool need_occ, bool stall, uint64_t wait_ns,
-              bool full_sort) {
-  cudaStream_t s = c->stream;
-  int err = FMM_OK;
-  const uint32_t n = S->n;
-  S->Ls = full_sort ? kMaxLevel : std::max(sort_level(n, Lb), Lb);
-  const SortPlan plan = make_sort_plan(n, S->Ls);
-
-  // Zero-initialised scratch of the box pass: look-back words, tile counter,
-  // box counts.
-  const uint32_t btiles = boxes_tiles(n);
-  const uint32_t ctiles = coarse_tiles(level_cap(n, Lb));
-  const size_t zero_bytes = align_up(sizeof(uint64_t) * (size_t)btiles) +
-                            align_up(sizeof(uint64_t) * (size_t)ctiles * kLevels) +
-                            align_up(sizeof(uint32_t) * 16) +
-                            align_up(sizeof(uint32_t) * kLevels * 2);
-  char* z = arena_get<char>(c, zero_bytes, &err);
-  if (!z) return err;
-  FMM_CUDA(cudaMemsetAsync(z, 0, zero_bytes, s));
-  uint64_t* bstatus = reinterpret_cast<uint64_t*>(z);
-  z += align_up(sizeof(uint64_t) * (size_t)btiles);
-  uint64_t* cstatus = reinterpret_cast<uint64_t*>(z);
-  z += align_up(sizeof(uint64_t) * (size_t)ctiles * kLevels);
-  uint32_t* counters = reinterpret_cast<uint32_t*>(z);
-  z += align_up(sizeof(uint32_t) * 16);
-  S->nbox_dev = reinterpret_cast<uint32_t*>(z);
-  S->maxocc_dev = S->nbox_dev + kLevels;
-
-  uint64_t* ka = arena_get<uint64_t>(c, n, &err);
-  uint32_t* va = arena_get<uint32_t>(c, n, &err);
-  uint64_t* kb = arena_get<uint64_t>(c, n, &err);
-  uint32_t* vb = arena_get<uint32_t>(c, n, &err);
-  if (!S->perm) S->perm = arena_get<uint32_t>(c, n, &err);
-  if (err) return err;
-  uint64_t* kin = nullptr;
-  uint32_t* vin = nullptr;
-  FMM_TRY(sort_pairs(c, plan, S->xyz, n, stall, wait_ns, ka, va, kb, vb, nullptr, &kin, &vin));
-  S->skeys = kin;
-  S->svals = vin;
-
-  // Boxes of levels 0..Lb, fused with the finishing sort (permutation).
-  for (int l = 0; l <= Lb; ++l) {
-    S->cap[l] = level_cap(n, l);
-    S->lv.cap[l] = S->cap[l];
-    S->lv.key[l] = arena_get<uint64_t>(c, S->cap[l], &err);
-    S->lv.off[l] = arena_get<uint32_t>(c, (size_t)S->cap[l] + 1, &err);
-    S->lv.parent[l] = arena_get<uint32_t>(c, S->cap[l], &err);
-    if (l < Lb) S->lv.child[l] = arena_get<uint32_t>(c, (size_t)S->cap[l] + 1, &err);
-    if (l < Lb && need_occ) S->lv.occ[l] = arena_get<uint8_t>(c, S->cap[l], &err);
-  }
-  if (err) return err;
-  {
-    Launch L(c, "finish_boxes");
-    launch_finish_boxes(kin ? kin : ka, vin ? vin : va, n, Lb, S->Ls, S->lv, S->perm, bstatus,
-                        counters + 15, S->nbox_dev, c->st, wait_ns, s);
-  }
-  if (Lb >= 1) {
-    Launch L(c, "coarse_boxes");
-    launch_coarse_boxes(Lb, S->lv, n, cstatus, counters + 14, S->nbox_dev, c->st, wait_ns, s);
-  }
-  if (need_occ && Lb >= 1) {
-    Launch L(c, "occupancy");
-    launch_occupancy(Lb, S->lv, S->nbox_dev, n, c->st, s);
-  }
-  return FMM_OK;
-}
-
-// Redoes the order of one set with the full 63-bit sort (a box was longer
-// than the finishing sort's window).  Only the permutation changes.
-int full_sort_perm(fmm_ctx* c, SetArrays* S, uint64_t wait_ns) {
-  int err = FMM_OK;
-  const uint32_t n = S->n;
-  const SortPlan plan = make_sort_plan(n, kMaxLevel);
-  uint64_t* ka = arena_get<uint64_t>(c, n, &err);
-  uint32_t* va = arena_get<uint32_t>(c, n, &err);
-  uint64_t* kb = arena_get<uint64_t>(c, n, &err);
-  uint32_t* vb = arena_get<uint32_t>(c, n, &err);
-  if (err) return err;
-  uint64_t* kout;
-  uint32_t* vout;
-  return sort_pairs(c, plan, S->xyz, n, false, wait_ns, ka, va, kb, vb, S->perm, &kout, &vout);
-}
-
-struct SetReadback {
-  uint32_t nbox[kLevels];
-  uint32_t maxocc[kLevels];
+struct SetPlan {
+  const float* xyz = nullptr;
+  uint32_t n = 0;
+  int Lb = 0, Ls = 0;
+  bool full = false;      // sort all 63 bits (the order needs no finishing window)
+  bool need_occ = false;  // used as a source
+  Seg dev{};              // the device descriptor
+  uint32_t cap[kLevels] = {};
 };
 
+struct JobPlan {
+  uint32_t src = 0, recv = 0;
+  int L = 0;
+  uint32_t s_unmet = 0;
+  Job dev{};
+  uint32_t cap[kLevels] = {};  // receiver capacity per list level
+};
+
+// Sizes read back at the end of a build.
 struct Readback {
-  DevStatus st;
-  SetReadback set[2];
-  uint64_t nnz[kLevels][2];
+  DevStatus st{};
+  std::vector<uint32_t> nbox;      // [nsets][2 * kLevels]: counts, largest occupancy
+  std::vector<uint32_t> seg_long;  // [nsets]
+  std::vector<uint64_t> list;      // [kLevels][njobs][4]: base E2, base E4, nnz E2, nnz E4
+  std::vector<uint32_t*> idx;      // [kLevels][2]: the level's E2 / E4 entry arrays
 };
 
-void fill_side(const SetArrays& S, int L, const uint32_t* nbox, uint32_t* out_nbox,
-               const uint64_t** key, const uint32_t** off, const uint32_t** parent,
-               const uint32_t** child, const uint32_t** perm) {
-  *perm = S.perm;
-  for (int l = 0; l < kLevels; ++l) {
-    const bool in = l <= L;
-    out_nbox[l] = in ? nbox[l] : 0;
-    key[l] = in ? S.lv.key[l] : nullptr;
-    off[l] = in ? S.lv.off[l] : nullptr;
-    parent[l] = (in && l >= 1) ? S.lv.parent[l] : nullptr;
-    child[l] = (l < L) ? S.lv.child[l] : nullptr;
+// Device pointers of the tables of one build.
+struct BuildMem {
+  Seg* segs = nullptr;
+  Job* jobs = nullptr;
+  ListLevel* lvls = nullptr;
+  uint8_t* which = nullptr;
+  Slot* pass_slots[8] = {};
+  uint32_t pass_nslots[8] = {}, pass_tiles[8] = {};
+  uint32_t* pass_hist[8] = {};
+  size_t pass_hist_len[8] = {};
+  uint64_t* pass_scan[8] = {};
+  uint32_t* pass_cnt = nullptr;  // scan tickets, one per pass
+  Slot* fin_slots = nullptr;
+  Slot* crs_slots = nullptr;
+  uint32_t fin_units = 0, crs_units = 0;
+  uint64_t* ka = nullptr;
+  uint32_t* va = nullptr;
+  uint64_t* kb = nullptr;
+  uint32_t* vb = nullptr;
+  int max_passes = 0;
+  int max_lb = 0;
+  uint32_t max_n = 0;
+};
+
+// Host image of one upload: descriptors and slot tables, 256-byte aligned.
+struct Upload {
+  std::vector<unsigned char> bytes;
+  template <class T>
+  size_t add(const T* p, size_t count) {
+    const size_t at = (bytes.size() + 255) & ~(size_t)255;
+    bytes.resize(at + sizeof(T) * count);
+    if (count) std::memcpy(bytes.data() + at, p, sizeof(T) * count);
+    return at;
   }
+};
+
+// Copies `up` to fresh device memory on the build's stream; returns the
+// device address of its first byte.
+char* upload(fmm_ctx* c, const Upload& up, int* err) {
+  const size_t need = up.bytes.size();
+  char* dev = arena_get<char>(c, need + 256, err);
+  if (*err) return nullptr;
+  if (c->up_cursor + need > c->up_bytes) {
+    // every earlier copy from the staging buffer must have landed
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      *err = FMM_ERR_CUDA;
+      return nullptr;
+    }
+    c->up_cursor = 0;
+    if (need > c->up_bytes) {
+      *err = pinned_reserve(&c->up_buf, &c->up_bytes, 2 * need);
+      if (*err) return nullptr;
+    }
+  }
+  char* h = static_cast<char*>(c->up_buf) + c->up_cursor;
+  std::memcpy(h, up.bytes.data(), need);
+  if (cudaMemcpyAsync(dev, h, need, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    *err = FMM_ERR_CUDA;
+    return nullptr;
+  }
+  c->up_cursor += (need + 255) & ~(size_t)255;
+  return dev;
 }
 
-int do_build(fmm_ctx* c, const float* src, uint32_t N, const float* recv, uint32_t M,
-             const fmm_params& prm, fmm_tree* out) {
+struct SortTables {
+  std::vector<Slot> slots[8];
+  uint32_t tiles[8] = {};
+  size_t hist_len[8] = {};
+};
+
+// Radix pass p covers the sets with more than p passes.  Per participating
+// set: its first tile, its first histogram entry and the correction from
+// scanned positions (which count only participating points) to its slots.
+SortTables plan_sort(const std::vector<SetPlan>& sets) {
+  SortTables t;
+  for (int p = 0; p < 8; ++p) {
+    uint32_t tiles = 0, compact = 0;
+    size_t hist = 0;
+    for (uint32_t id = 0; id < sets.size(); ++id) {
+      const SetPlan& s = sets[id];
+      if (s.n == 0 || s.dev.passes <= p) continue;
+      Slot sl;
+      sl.seg = id;
+      sl.unit0 = tiles;
+      sl.aux0 = (uint32_t)hist;
+      sl.aux1 = s.dev.base - compact;
+      t.slots[p].push_back(sl);
+      tiles += s.dev.ntiles;
+      hist += (size_t)kRadixMax * s.dev.ntiles;
+      compact += s.n;
+    }
+    t.tiles[p] = tiles;
+    t.hist_len[p] = hist;
+  }
+  return t;
+}
+
+// Radix passes of every set.  Pass p reads buffer (p-1)&1 (the coordinates
+// for p = 0) and writes buffer p&1; a set's result stays in buffer
+// (passes-1)&1 at its base.
+int run_sort(fmm_ctx* c, std::vector<SetPlan>& sets, BuildMem& m, bool stall, uint64_t wait_ns) {
+  cudaStream_t s = c->stream;
+  int err = FMM_OK;
+  bool any_full = false;  // a set sorted in full keeps every pass stable
+  for (auto& sp : sets) any_full |= sp.full;
+  const bool onesweep = stall || c->tuning.sort_kind == FMM_SORT_ONESWEEP;
+  if (onesweep) {
+    // One set at a time, one kernel per pass (decoupled look-back).
+    for (auto& sp : sets) {
+      if (sp.n == 0) continue;
+      const SortPlan plan = make_sort_plan(sp.n, sp.Ls);
+      const uint32_t radix = 1u << plan.bits;
+      const size_t per_pass = (size_t)plan.ntiles * radix;
+      const size_t zb = align_up(sizeof(uint32_t) * 8 * kRadixMax) +
+                        align_up(sizeof(uint64_t) * per_pass * plan.passes) +
+                        align_up(sizeof(uint32_t) * 16);
+      char* z = arena_get<char>(c, zb, &err);
+      if (err) return err;
+      FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
+      uint32_t* hist = reinterpret_cast<uint32_t*>(z);
+      uint64_t* sstatus =
+          reinterpret_cast<uint64_t*>(z + align_up(sizeof(uint32_t) * 8 * kRadixMax));
+      uint32_t* counters = reinterpret_cast<uint32_t*>(
+          z + align_up(sizeof(uint32_t) * 8 * kRadixMax) +
+          align_up(sizeof(uint64_t) * per_pass * plan.passes));
+      {
+        Launch L(c, "upfront_hist");
+        launch_upfront_hist(sp.xyz, sp.n, plan, hist, c->st, s);
+      }
+      {
+        Launch L(c, "digit_scan");
+        launch_digit_scan(plan, hist, s);
+      }
+      const uint32_t b0 = sp.dev.base;
+      for (int p = 0; p < plan.passes; ++p) {
+        uint64_t* ko = ((p & 1) ? m.kb : m.ka) + b0;
+        uint32_t* vo = ((p & 1) ? m.vb : m.va) + b0;
+        const uint64_t* ki = ((p & 1) ? m.ka : m.kb) + b0;
+        const uint32_t* vi = ((p & 1) ? m.va : m.vb) + b0;
+        Launch L(c, "onesweep");
+        launch_onesweep_pass(p, sp.xyz, ki, vi, ko, vo, sp.n, plan, hist + p * kRadixMax,
+                             sstatus + (size_t)p * per_pass, counters + p, c->st, wait_ns,
+                             (stall && p == 0 && plan.ntiles > 2) ? 1 : -1, s);
+      }
+    }
+    return FMM_OK;
+  }
+  for (int p = 0; p < m.max_passes; ++p) {
+    if (m.pass_tiles[p] == 0) continue;
+    const uint64_t* kin = (p & 1) ? m.ka : m.kb;
+    const uint32_t* vin = (p & 1) ? m.va : m.vb;
+    uint64_t* kout = (p & 1) ? m.kb : m.ka;
+    uint32_t* vout = (p & 1) ? m.vb : m.va;
+    {
+      Launch L(c, "tile_hist");
+      launch_tile_hist(p, m.segs, m.pass_slots[p], m.pass_nslots[p], m.pass_tiles[p],
+                       m.pass_hist[p], kin, c->st, s);
+    }
+    {
+      Launch L(c, "scan");
+      launch_scan_u32(m.pass_hist[p], nullptr, (uint32_t)m.pass_hist_len[p], m.pass_scan[p],
+                      m.pass_cnt + p, nullptr, c->st, wait_ns, s);
+    }
+    // The first pass may leave equal digits in any order when a finishing
+    // sort follows; sets sorted in full keep every pass stable.
+    Launch L(c, "rts_scatter");
+    launch_rts_scatter(p, m.segs, m.pass_slots[p], m.pass_nslots[p], m.pass_tiles[p], kin, vin,
+                       kout, vout, m.pass_hist[p], any_full || p > 0, true, c->st, wait_ns, s);
+  }
+  return FMM_OK;
+}
+
+// One build over `sets` and `jobs` (jobs[].L: the tree depth, or for
+// cluster-size mode chosen here).  deepest: the sets' boxes reach level 21,
+// so an unmet cluster size ends at 21 with s_unmet instead of L = -1.
+int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs,
+              const fmm_params& prm, bool smode, bool deepest, bool stall, Readback* rb) {
   cudaStream_t s = c->stream;
   int err = FMM_OK;
   const uint64_t wait_ns = wait_ns_of(prm);
-  const bool stall = (prm.flags & FMM_FLAG_TEST_STALL) != 0;
-  const bool aliased = (src == recv) && (N == M);
-  const bool smode = prm.L < 0;
+  const uint32_t nsets = (uint32_t)sets.size(), njobs = (uint32_t)jobs.size();
+  BuildMem m;
 
-  uint64_t expect = 0;
-  fmm_query_workspace(N, M, prm, &expect);
-  FMM_TRY(arena_reset(c, c->peak_request > expect ? c->peak_request : expect));
-  FMM_CUDA(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
+  // ---- sets: depths, tiles, slots in the concatenated sort arrays.
+  uint64_t slots_total = 0;
+  for (auto& sp : sets) {
+    sp.Ls = sp.full ? kMaxLevel : std::max(sort_level(sp.n, sp.Lb), sp.Lb);
+    Seg& d = sp.dev;
+    std::memset(&d, 0, sizeof(d));
+    d.xyz = sp.xyz;
+    d.n = sp.n;
+    d.base = (uint32_t)slots_total;
+    d.Ls = sp.Ls;
+    d.Lb = sp.Lb;
+    d.passes = sp.n ? passes_for(sp.Ls) : 0;
+    d.lo = 63 - 3 * sp.Ls;
+    d.ntiles = (uint32_t)(((uint64_t)sp.n + kSortTile - 1) / kSortTile);
+    d.btiles = std::max<uint32_t>(1, (uint32_t)(((uint64_t)sp.n + kBoxTile - 1) / kBoxTile));
+    slots_total += ((uint64_t)sp.n + 3) & ~3ull;  // set bases stay 16-byte aligned
+    m.max_passes = std::max(m.max_passes, d.passes);
+    m.max_lb = std::max(m.max_lb, sp.Lb);
+    m.max_n = std::max(m.max_n, sp.n);
+    for (int l = 0; l <= sp.Lb; ++l) sp.cap[l] = level_cap(sp.n, l);
+  }
+  if (slots_total >= (1ull << 32)) return FMM_ERR_ARG;
+  const size_t nslot = (size_t)slots_total + 4;
+  m.ka = arena_get<uint64_t>(c, nslot, &err);
+  m.va = arena_get<uint32_t>(c, nslot, &err);
+  m.kb = arena_get<uint64_t>(c, nslot, &err);
+  m.vb = arena_get<uint32_t>(c, nslot, &err);
+  if (err) return err;
+  SortTables tab = plan_sort(sets);
 
-  SetArrays S[2];
-  S[0].n = N;
-  S[1].n = M;
-  S[0].xyz = src;
-  S[1].xyz = recv;
-  if (prm.flags & FMM_FLAG_HOST_INPUT) {
-    for (int k = 0; k < (aliased ? 1 : 2); ++k) {
-      float* d = arena_get<float>(c, (size_t)S[k].n * 3, &err);
-      if (err) return err;
-      if (S[k].n)
-        FMM_CUDA(cudaMemcpyAsync(d, S[k].xyz, sizeof(float) * 3 * S[k].n,
-                                 cudaMemcpyHostToDevice, s));
-      S[k].xyz = d;
+  // Zero-initialised words: per set look-back words, tickets, counts and
+  // flags; per pass scan words; scan tickets.
+  size_t zero_bytes = 0;
+  std::vector<size_t> zoff(nsets);
+  for (uint32_t i = 0; i < nsets; ++i) {
+    zoff[i] = zero_bytes;
+    zero_bytes += align_up(sizeof(uint64_t) * sets[i].dev.btiles) +
+                  align_up(sizeof(uint64_t) * coarse_tiles(sets[i].cap[sets[i].Lb]) * kLevels) +
+                  align_up(sizeof(uint32_t) * (2 + 2 * kLevels + 1));
+  }
+  size_t scan_off[8] = {};
+  for (int p = 0; p < m.max_passes; ++p) {
+    scan_off[p] = zero_bytes;
+    zero_bytes += align_up(sizeof(uint64_t) * scan_tiles((uint32_t)tab.hist_len[p]));
+  }
+  const size_t cnt_off = zero_bytes;
+  zero_bytes += align_up(sizeof(uint32_t) * 16);
+  char* zero = arena_get<char>(c, zero_bytes, &err);
+  if (err) return err;
+  m.pass_cnt = reinterpret_cast<uint32_t*>(zero + cnt_off);
+  for (int p = 0; p < m.max_passes; ++p) {
+    m.pass_scan[p] = reinterpret_cast<uint64_t*>(zero + scan_off[p]);
+    m.pass_hist[p] = arena_get<uint32_t>(c, tab.hist_len[p] + 1, &err);
+    m.pass_hist_len[p] = tab.hist_len[p];
+    m.pass_tiles[p] = tab.tiles[p];
+    m.pass_nslots[p] = (uint32_t)tab.slots[p].size();
+  }
+  if (err) return err;
+
+  // Per-set outputs.
+  for (uint32_t i = 0; i < nsets; ++i) {
+    SetPlan& sp = sets[i];
+    Seg& d = sp.dev;
+    char* z = zero + zoff[i];
+    d.bstatus = reinterpret_cast<uint64_t*>(z);
+    z += align_up(sizeof(uint64_t) * d.btiles);
+    d.cstatus = reinterpret_cast<uint64_t*>(z);
+    z += align_up(sizeof(uint64_t) * coarse_tiles(sp.cap[sp.Lb]) * kLevels);
+    d.tickets = reinterpret_cast<uint32_t*>(z);
+    d.nbox = d.tickets + 2;
+    d.seg_long = d.nbox + 2 * kLevels;
+    d.perm = arena_get<uint32_t>(c, sp.n, &err);
+    const int last = d.passes > 0 ? (d.passes - 1) & 1 : 0;
+    d.skeys = (last ? m.kb : m.ka) + d.base;
+    d.svals = (last ? m.vb : m.va) + d.base;
+    for (int l = 0; l <= sp.Lb; ++l) {
+      d.lv.cap[l] = sp.cap[l];
+      d.lv.key[l] = arena_get<uint64_t>(c, sp.cap[l], &err);
+      d.lv.off[l] = arena_get<uint32_t>(c, (size_t)sp.cap[l] + 1, &err);
+      d.lv.parent[l] = arena_get<uint32_t>(c, sp.cap[l], &err);
+      if (l < sp.Lb) d.lv.child[l] = arena_get<uint32_t>(c, (size_t)sp.cap[l] + 1, &err);
+      if (l < sp.Lb && sp.need_occ) d.lv.occ[l] = arena_get<uint8_t>(c, sp.cap[l], &err);
     }
-    if (aliased) S[1].xyz = S[0].xyz;
+    if (err) return err;
   }
 
-  // In cluster-size mode the boxes are built down to the sort depth of the
-  // larger set; the level is picked from their occupancy.
-  const int Lb = smode ? std::max(sort_level(std::max(N, M), 2), 2) : prm.L;
-  FMM_TRY(build_set(c, &S[0], Lb, true, stall, wait_ns, false));
-  if (aliased) {
-    S[1] = S[0];
-  } else {
-    FMM_TRY(build_set(c, &S[1], Lb, false, false, wait_ns, false));
-  }
-  if (smode) {
-    for (int k = 0; k < (aliased ? 1 : 2); ++k) {
-      Launch Lq(c, "max_occupancy");
-      launch_max_occupancy(Lb, S[k].lv, S[k].nbox_dev, S[k].n, S[k].maxocc_dev, c->st, s);
+  // Box-stage slots.
+  std::vector<Slot> fin, crs;
+  for (uint32_t i = 0; i < nsets; ++i) {
+    fin.push_back(Slot{i, m.fin_units, 0, 0});
+    m.fin_units += sets[i].dev.btiles;
+    if (sets[i].Lb >= 1) {
+      crs.push_back(Slot{i, m.crs_units, 0, 0});
+      m.crs_units += coarse_tiles(sets[i].cap[sets[i].Lb]);
     }
   }
 
-  // With a fixed level and list capacities bounded by the box capacities
-  // (27 and 189 per receiver box), everything is launched without waiting
-  // for the box counts; otherwise read them back first.
-  Readback* hb = static_cast<Readback*>(c->host_buf);
-  Readback rb1{};
+  // ---- lists: capacities from the box-count bounds when they fit.
+  int Lmax = 0;
+  for (auto& jp : jobs) Lmax = std::max(Lmax, jp.L);
   uint64_t list_bound = 0;
-  if (!smode)
-    for (int l = 2; l <= prm.L; ++l) list_bound += 4ull * (2 + 27 + 189) * level_cap(M, l);
+  for (auto& jp : jobs)
+    for (int l = 2; l <= jp.L; ++l) list_bound += 4ull * (2 + 27 + 189) * sets[jp.recv].cap[l];
   const bool async_lists = !smode && list_bound <= kAsyncListBytes;
-  if (!async_lists) {
-    FMM_CUDA(cudaMemcpyAsync(&hb->st, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-    for (int k = 0; k < 2; ++k)
-      FMM_CUDA(cudaMemcpyAsync(&hb->set[k], S[k].nbox_dev, sizeof(SetReadback),
-                               cudaMemcpyDeviceToHost, s));
-    FMM_CUDA(cudaStreamSynchronize(s));
-    if (hb->st.code) return (int)hb->st.code;
-    rb1 = *hb;
-  } else {
-    for (int l = 0; l <= prm.L; ++l) {
-      rb1.set[0].nbox[l] = level_cap(N, l);
-      rb1.set[1].nbox[l] = level_cap(M, l);
+
+  std::vector<uint8_t> which(nsets);
+  for (uint32_t i = 0; i < nsets; ++i) which[i] = sets[i].need_occ ? 1 : 0;
+  std::vector<ListLevel> lvls(kLevels);
+  std::memset(lvls.data(), 0, sizeof(ListLevel) * kLevels);
+  auto upload_all = [&](bool with_lists) -> int {
+    Upload up;
+    std::vector<Seg> segs_host(nsets);
+    for (uint32_t i = 0; i < nsets; ++i) segs_host[i] = sets[i].dev;
+    const size_t o_segs = up.add(segs_host.data(), nsets);
+    const size_t o_which = up.add(which.data(), nsets);
+    size_t o_pass[8] = {};
+    for (int p = 0; p < m.max_passes; ++p)
+      o_pass[p] = up.add(tab.slots[p].data(), tab.slots[p].size());
+    const size_t o_fin = up.add(fin.data(), fin.size());
+    const size_t o_crs = up.add(crs.data(), crs.size());
+    size_t o_jobs = 0, o_lvls = 0;
+    std::vector<Job> jobs_host(njobs);
+    if (with_lists) {
+      for (uint32_t j = 0; j < njobs; ++j) jobs_host[j] = jobs[j].dev;
+      o_jobs = up.add(jobs_host.data(), njobs);
+      o_lvls = up.add(lvls.data(), kLevels);
     }
+    char* dev = upload(c, up, &err);
+    if (err) return err;
+    m.segs = reinterpret_cast<Seg*>(dev + o_segs);
+    m.which = reinterpret_cast<uint8_t*>(dev + o_which);
+    for (int p = 0; p < m.max_passes; ++p)
+      m.pass_slots[p] = reinterpret_cast<Slot*>(dev + o_pass[p]);
+    m.fin_slots = reinterpret_cast<Slot*>(dev + o_fin);
+    m.crs_slots = reinterpret_cast<Slot*>(dev + o_crs);
+    if (with_lists) {
+      m.jobs = reinterpret_cast<Job*>(dev + o_jobs);
+      m.lvls = reinterpret_cast<ListLevel*>(dev + o_lvls);
+    }
+    return FMM_OK;
+  };
+
+  // List arrays (per level, shared by the jobs) and per-job row starts.
+  std::vector<size_t> work_len(kLevels, 0), zo_scan(kLevels, 0);
+  char* list_zero = nullptr;
+  size_t list_zero_bytes = 0;
+  auto plan_lists = [&]() -> int {
+    for (auto& jp : jobs) {
+      std::memset(&jp.dev, 0, sizeof(jp.dev));
+      jp.dev.src = jp.src;
+      jp.dev.recv = jp.recv;
+      jp.dev.L = jp.L;
+    }
+    std::vector<size_t> zo(kLevels, 0), i2(kLevels, 0), i4(kLevels, 0);
+    for (int l = 2; l <= Lmax; ++l) {
+      size_t run = 0;
+      for (auto& jp : jobs) {
+        if (jp.L < l) continue;
+        jp.dev.region[l] = (uint32_t)run;
+        run += (size_t)jp.cap[l] + 1;
+        i2[l] += 27ull * jp.cap[l];
+        i4[l] += 189ull * jp.cap[l];
+      }
+      if (run >= (1ull << 32)) return FMM_ERR_CAPACITY;
+      work_len[l] = run;
+      zo[l] = list_zero_bytes;
+      // work arrays hold run + 1 entries: the scan writes its total at [run]
+      list_zero_bytes += 2 * align_up(sizeof(uint32_t) * (run + 1)) +
+                         2 * align_up(sizeof(uint64_t) * scan_tiles((uint32_t)run)) +
+                         align_up(sizeof(uint32_t) * 2) +
+                         2 * align_up(sizeof(uint64_t) * 2 * njobs) + align_up(sizeof(uint64_t) * 2);
+    }
+    list_zero = arena_get<char>(c, std::max<size_t>(list_zero_bytes, 1), &err);
+    if (err) return err;
+    for (int l = 2; l <= Lmax; ++l) {
+      char* z = list_zero + zo[l];
+      const size_t run = work_len[l];
+      ListLevel& LV = lvls[l];
+      LV.work2 = reinterpret_cast<uint32_t*>(z);
+      z += align_up(sizeof(uint32_t) * (run + 1));
+      LV.work4 = reinterpret_cast<uint32_t*>(z);
+      z += align_up(sizeof(uint32_t) * (run + 1));
+      zo_scan[l] = (size_t)(z - list_zero);
+      z += 2 * align_up(sizeof(uint64_t) * scan_tiles((uint32_t)run)) + align_up(sizeof(uint32_t) * 2);
+      LV.base = reinterpret_cast<uint64_t*>(z);
+      z += align_up(sizeof(uint64_t) * 2 * njobs);
+      LV.nnz = reinterpret_cast<uint64_t*>(z);
+      z += align_up(sizeof(uint64_t) * 2 * njobs);
+      LV.total = reinterpret_cast<uint64_t*>(z);
+      LV.idx2 = arena_get<uint32_t>(c, i2[l], &err);
+      LV.idx4 = arena_get<uint32_t>(c, i4[l], &err);
+      LV.jprefix = arena_get<uint32_t>(c, (size_t)njobs + 1, &err);
+      for (auto& jp : jobs) {
+        if (jp.L < l) continue;
+        jp.dev.out2[l] = arena_get<uint32_t>(c, (size_t)jp.cap[l] + 1, &err);
+        jp.dev.out4[l] = arena_get<uint32_t>(c, (size_t)jp.cap[l] + 1, &err);
+      }
+      if (err) return err;
+    }
+    return FMM_OK;
+  };
+
+  if (async_lists) {
+    for (auto& jp : jobs)
+      for (int l = 2; l <= jp.L; ++l) jp.cap[l] = sets[jp.recv].cap[l];
+    FMM_TRY(plan_lists());
+  }
+  FMM_TRY(upload_all(async_lists));
+  FMM_CUDA(cudaMemsetAsync(zero, 0, zero_bytes, s));
+  if (async_lists && list_zero_bytes) FMM_CUDA(cudaMemsetAsync(list_zero, 0, list_zero_bytes, s));
+
+  // ---- sort, boxes, occupancy.
+  FMM_TRY(run_sort(c, sets, m, stall, wait_ns));
+  {
+    Launch L(c, "finish_boxes");
+    launch_finish_boxes(m.segs, m.fin_slots, (uint32_t)fin.size(), m.fin_units, c->st, wait_ns, s);
+  }
+  if (m.crs_units) {
+    Launch L(c, "coarse_boxes");
+    launch_coarse_boxes(m.segs, m.crs_slots, (uint32_t)crs.size(), m.crs_units, c->st, wait_ns,
+                        s);
+  }
+  {
+    Launch L(c, "occupancy");
+    launch_occupancy(m.segs, nsets, m.which, m.max_n, m.max_lb, c->st, s);
   }
 
-  int L = prm.L;
-  uint32_t s_unmet = 0;
-  if (smode) {
-    L = -1;
-    for (int l = 2; l <= Lb; ++l) {
-      if (rb1.set[0].maxocc[l] <= prm.s && rb1.set[1].maxocc[l] <= prm.s) {
-        L = l;
-        break;
+  const size_t per_set = 2 * kLevels + 1;
+  auto read_sets = [&](bool lists) -> int {
+    const size_t list_words = lists ? 4 * (size_t)njobs * kLevels : 0;
+    const size_t need = 64 + sizeof(uint32_t) * nsets * per_set + 16 + sizeof(uint64_t) * list_words;
+    FMM_CUDA(cudaStreamSynchronize(s));  // the read-back buffer may be replaced
+    FMM_TRY(pinned_reserve(&c->rb_buf, &c->rb_bytes, need));
+    char* h = static_cast<char*>(c->rb_buf);
+    FMM_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    uint32_t* hn = reinterpret_cast<uint32_t*>(h + 64);
+    for (uint32_t i = 0; i < nsets; ++i)
+      FMM_CUDA(cudaMemcpyAsync(hn + (size_t)i * per_set, sets[i].dev.nbox,
+                               sizeof(uint32_t) * per_set, cudaMemcpyDeviceToHost, s));
+    uint64_t* hl = reinterpret_cast<uint64_t*>(
+        (reinterpret_cast<uintptr_t>(hn + (size_t)nsets * per_set) + 15) & ~(uintptr_t)15);
+    if (lists)
+      for (int l = 2; l <= Lmax; ++l) {
+        FMM_CUDA(cudaMemcpyAsync(hl + (size_t)l * njobs * 4, lvls[l].base,
+                                 sizeof(uint64_t) * 2 * njobs, cudaMemcpyDeviceToHost, s));
+        FMM_CUDA(cudaMemcpyAsync(hl + (size_t)l * njobs * 4 + 2 * njobs, lvls[l].nnz,
+                                 sizeof(uint64_t) * 2 * njobs, cudaMemcpyDeviceToHost, s));
       }
+    FMM_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(&rb->st, h, sizeof(DevStatus));
+    rb->nbox.assign((size_t)nsets * 2 * kLevels, 0);
+    rb->seg_long.assign(nsets, 0);
+    for (uint32_t i = 0; i < nsets; ++i) {
+      std::memcpy(&rb->nbox[(size_t)i * 2 * kLevels], hn + (size_t)i * per_set,
+                  sizeof(uint32_t) * 2 * kLevels);
+      rb->seg_long[i] = hn[(size_t)i * per_set + 2 * kLevels];
     }
-    if (L < 0) {
-      // Not met down to the sort depth: rebuild with the full 63-bit order
-      // and every level.
-      FMM_CUDA(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
-      SetArrays T[2];
-      T[0].n = N;
-      T[1].n = M;
-      T[0].xyz = S[0].xyz;
-      T[1].xyz = S[1].xyz;
-      FMM_TRY(build_set(c, &T[0], kMaxLevel, true, false, wait_ns, true));
-      if (aliased)
-        T[1] = T[0];
-      else
-        FMM_TRY(build_set(c, &T[1], kMaxLevel, false, false, wait_ns, true));
-      for (int k = 0; k < (aliased ? 1 : 2); ++k) {
-        Launch Lq(c, "max_occupancy");
-        launch_max_occupancy(kMaxLevel, T[k].lv, T[k].nbox_dev, T[k].n, T[k].maxocc_dev, c->st,
-                             s);
-      }
-      FMM_CUDA(cudaMemcpyAsync(&hb->st, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-      for (int k = 0; k < 2; ++k)
-        FMM_CUDA(cudaMemcpyAsync(&hb->set[k], T[k].nbox_dev, sizeof(SetReadback),
-                                 cudaMemcpyDeviceToHost, s));
-      FMM_CUDA(cudaStreamSynchronize(s));
-      if (hb->st.code) return (int)hb->st.code;
-      rb1 = *hb;
-      S[0] = T[0];
-      S[1] = T[1];
-      L = kMaxLevel;
-      s_unmet = 1;
-      for (int l = 2; l <= kMaxLevel; ++l) {
-        if (rb1.set[0].maxocc[l] <= prm.s && rb1.set[1].maxocc[l] <= prm.s) {
-          L = l;
-          s_unmet = 0;
-          break;
+    if (lists) {
+      rb->list.assign((size_t)kLevels * njobs * 4, 0);
+      for (int l = 2; l <= Lmax; ++l)
+        for (uint32_t j = 0; j < njobs; ++j) {
+          if (jobs[j].L < l) continue;
+          const uint64_t* b = hl + (size_t)l * njobs * 4;
+          uint64_t* o = &rb->list[((size_t)l * njobs + j) * 4];
+          o[0] = b[2 * j];
+          o[1] = b[2 * j + 1];
+          o[2] = b[2 * njobs + 2 * j];
+          o[3] = b[2 * njobs + 2 * j + 1];
+        }
+    }
+    return FMM_OK;
+  };
+
+  if (!async_lists) {
+    if (smode) {
+      Launch L(c, "max_occupancy");
+      launch_max_occupancy(m.segs, nsets, m.max_n, m.max_lb, c->st, s);
+    }
+    FMM_TRY(read_sets(false));
+    if (rb->st.code) return (int)rb->st.code;
+    if (smode) {
+      // Sec. 2.1: the smallest L >= 2 at which no box of either set holds
+      // more than s points.
+      for (auto& jp : jobs) {
+        const uint32_t* a = &rb->nbox[(size_t)jp.src * 2 * kLevels + kLevels];
+        const uint32_t* b = &rb->nbox[(size_t)jp.recv * 2 * kLevels + kLevels];
+        const int lb = std::min(sets[jp.src].Lb, sets[jp.recv].Lb);
+        jp.L = -1;
+        for (int l = 2; l <= lb; ++l)
+          if (a[l] <= prm.s && b[l] <= prm.s) {
+            jp.L = l;
+            break;
+          }
+        if (jp.L < 0 && deepest) {
+          jp.L = kMaxLevel;
+          jp.s_unmet = 1;
         }
       }
+      Lmax = 0;
+      for (auto& jp : jobs) Lmax = std::max(Lmax, jp.L);
     }
-  }
-  if (!async_lists && rb1.st.seg_long) {
-    // A box outran the finishing sort: redo the order(s) with all 63 bits.
-    for (int k = 0; k < (aliased ? 1 : 2); ++k) FMM_TRY(full_sort_perm(c, &S[k], wait_ns));
-    if (aliased) S[1].perm = S[0].perm;
+    for (auto& jp : jobs)
+      for (int l = 2; l <= jp.L; ++l) jp.cap[l] = rb->nbox[(size_t)jp.recv * 2 * kLevels + l];
+    FMM_TRY(plan_lists());
+    FMM_TRY(upload_all(true));
+    if (list_zero_bytes) FMM_CUDA(cudaMemsetAsync(list_zero, 0, list_zero_bytes, s));
   }
 
-  // Lists, levels 2..L.
-  uint32_t* lst_off[2][kLevels] = {};
-  uint32_t* lst_idx[2][kLevels] = {};
-  uint64_t* nnz_dev = arena_get<uint64_t>(c, (size_t)kLevels * 2, &err);
-  if (err) return err;
-  FMM_CUDA(cudaMemsetAsync(nnz_dev, 0, sizeof(uint64_t) * kLevels * 2, s));
-  for (int l = 2; l <= L; ++l) {
-    const uint32_t nr = rb1.set[1].nbox[l];
-    lst_off[0][l] = arena_get<uint32_t>(c, (size_t)nr + 1, &err);
-    lst_off[1][l] = arena_get<uint32_t>(c, (size_t)nr + 1, &err);
-    lst_idx[0][l] = arena_get<uint32_t>(c, (size_t)nr * 27, &err);
-    lst_idx[1][l] = arena_get<uint32_t>(c, (size_t)nr * 189, &err);
-    const uint32_t tiles = scan_tiles(nr);
-    const size_t zb = align_up(sizeof(uint64_t) * tiles) * 2 + align_up(sizeof(uint32_t) * 2);
-    char* z = arena_get<char>(c, zb, &err);
-    if (err) return err;
-    FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
-    uint64_t* st2 = reinterpret_cast<uint64_t*>(z);
-    uint64_t* st4 = reinterpret_cast<uint64_t*>(z + align_up(sizeof(uint64_t) * tiles));
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(z + 2 * align_up(sizeof(uint64_t) * tiles));
-
-    ListArgs a{};
-    a.l = l;
-    a.nbox_recv = S[1].nbox_dev;
-    a.nbox_src = S[0].nbox_dev;
-    a.rkey_up = S[1].lv.key[l - 1];
-    a.rchild_up = S[1].lv.child[l - 1];
-    a.rkey = S[1].lv.key[l];
-    a.e2_off_up = l >= 3 ? lst_off[0][l - 1] : nullptr;
-    a.e2_idx_up = l >= 3 ? lst_idx[0][l - 1] : nullptr;
-    a.skey_up = S[0].lv.key[l - 1];
-    a.schild_up = S[0].lv.child[l - 1];
-    a.socc_up = S[0].lv.occ[l - 1];
-    a.e2_off = lst_off[0][l];
-    a.e4_off = lst_off[1][l];
-    a.e2_idx = lst_idx[0][l];
-    a.e4_idx = lst_idx[1][l];
-    a.nnz = nnz_dev + 2 * l;
-    const uint32_t np = rb1.set[1].nbox[l - 1];
+  // ---- lists, levels 2..Lmax.
+  for (int l = 2; l <= Lmax; ++l) {
+    char* zs = list_zero + zo_scan[l];
+    const size_t sw = align_up(sizeof(uint64_t) * scan_tiles((uint32_t)work_len[l]));
+    uint64_t* st2 = reinterpret_cast<uint64_t*>(zs);
+    uint64_t* st4 = reinterpret_cast<uint64_t*>(zs + sw);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(zs + 2 * sw);
+    {
+      Launch Lk(c, "job_prefix");
+      launch_job_prefix(m.segs, m.jobs, njobs, l, m.lvls, c->st, s);
+    }
     {
       Launch Lk(c, "list_count");
-      launch_list_count(a, np, c->st, s);
+      launch_list_count(m.segs, m.jobs, njobs, l, m.lvls, c->st, s);
     }
     {
       Launch Lk(c, "scan");
-      launch_scan_u32(a.e2_off, S[1].nbox_dev + l, nr, st2, cnt, nnz_dev + 2 * l, c->st, wait_ns,
-                      s);
+      launch_scan_u32(lvls[l].work2, nullptr, (uint32_t)work_len[l], st2, cnt, lvls[l].total,
+                      c->st, wait_ns, s);
     }
     {
       Launch Lk(c, "scan");
-      launch_scan_u32(a.e4_off, S[1].nbox_dev + l, nr, st4, cnt + 1, nnz_dev + 2 * l + 1, c->st,
-                      wait_ns, s);
+      launch_scan_u32(lvls[l].work4, nullptr, (uint32_t)work_len[l], st4, cnt + 1,
+                      lvls[l].total + 1, c->st, wait_ns, s);
     }
     {
       Launch Lk(c, "list_fill");
-      launch_list_fill(a, np, c->st, s);
+      launch_list_fill(m.segs, m.jobs, njobs, l, m.lvls, c->st, s);
     }
   }
   FMM_CUDA(cudaGetLastError());
-  FMM_CUDA(cudaMemcpyAsync(&hb->st, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-  FMM_CUDA(cudaMemcpyAsync(hb->nnz, nnz_dev, sizeof(uint64_t) * kLevels * 2,
-                           cudaMemcpyDeviceToHost, s));
-  if (async_lists)
-    for (int k = 0; k < 2; ++k)
-      FMM_CUDA(cudaMemcpyAsync(&hb->set[k], S[k].nbox_dev, sizeof(SetReadback),
-                               cudaMemcpyDeviceToHost, s));
+
+  // ---- sizes and status.
+  FMM_TRY(read_sets(true));
+  if (rb->st.code) return (int)rb->st.code;
+  rb->idx.assign((size_t)kLevels * 2, nullptr);
+  for (int l = 2; l <= Lmax; ++l) {
+    rb->idx[2 * l] = lvls[l].idx2;
+    rb->idx[2 * l + 1] = lvls[l].idx4;
+  }
+  return FMM_OK;
+}
+
+// Redoes the order of the flagged sets with the full 63-bit sort (a box was
+// longer than the finishing window).  Only their permutations change.
+int full_sort_perms(fmm_ctx* c, std::vector<SetPlan>& sets, const std::vector<uint32_t>& ids,
+                    const fmm_params& prm) {
+  if (ids.empty()) return FMM_OK;
+  std::vector<SetPlan> sub;
+  for (uint32_t id : ids) {
+    SetPlan sp;
+    sp.xyz = sets[id].xyz;
+    sp.n = sets[id].n;
+    sp.Lb = 0;
+    sp.full = true;
+    sub.push_back(sp);
+  }
+  std::vector<JobPlan> nojobs;
+  Readback rb;
+  FMM_TRY(run_build(c, sub, nojobs, prm, false, false, false, &rb));
+  // Every pass of a full sort is stable: the values of the last pass are the
+  // order by (key, index).
+  cudaStream_t s = c->stream;
+  for (size_t k = 0; k < ids.size(); ++k)
+    FMM_CUDA(cudaMemcpyAsync(sets[ids[k]].dev.perm, sub[k].dev.svals,
+                             sizeof(uint32_t) * sub[k].n, cudaMemcpyDeviceToDevice, s));
   FMM_CUDA(cudaStreamSynchronize(s));
-  if (hb->st.code) return (int)hb->st.code;
-  if (async_lists) {
-    for (int k = 0; k < 2; ++k) rb1.set[k] = hb->set[k];
-    if (hb->st.seg_long) {
-      // A box outran the finishing sort: redo the order(s) with all 63 bits.
-      for (int k = 0; k < (aliased ? 1 : 2); ++k) FMM_TRY(full_sort_perm(c, &S[k], wait_ns));
-      if (aliased) S[1].perm = S[0].perm;
-      FMM_CUDA(cudaMemcpyAsync(&hb->st, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-      FMM_CUDA(cudaStreamSynchronize(s));
-      if (hb->st.code) return (int)hb->st.code;
+  return FMM_OK;
+}
+
+void fill_tree(const std::vector<SetPlan>& sets, const JobPlan& J, const Readback& rb,
+               uint32_t ji, uint32_t njobs, fmm_tree* out) {
+  std::memset(out, 0, sizeof(*out));
+  const int L = J.L;
+  const SetPlan& S = sets[J.src];
+  const SetPlan& R = sets[J.recv];
+  out->L = L;
+  out->s_unmet = J.s_unmet;
+  out->n_src = S.n;
+  out->n_recv = R.n;
+  const SetPlan* side[2] = {&S, &R};
+  const uint32_t idx[2] = {J.src, J.recv};
+  for (int k = 0; k < 2; ++k) {
+    const Seg& d = side[k]->dev;
+    const uint32_t* nb = &rb.nbox[(size_t)idx[k] * 2 * kLevels];
+    uint32_t* onb = k ? out->nbox_recv : out->nbox_src;
+    const uint64_t** okey = k ? out->key_recv : out->key_src;
+    const uint32_t** ooff = k ? out->off_recv : out->off_src;
+    const uint32_t** opar = k ? out->parent_recv : out->parent_src;
+    const uint32_t** ochi = k ? out->child_recv : out->child_src;
+    (k ? out->perm_recv : out->perm_src) = d.perm;
+    for (int l = 0; l <= L; ++l) {
+      onb[l] = nb[l];
+      okey[l] = d.lv.key[l];
+      ooff[l] = d.lv.off[l];
+      opar[l] = l >= 1 ? d.lv.parent[l] : nullptr;
+      ochi[l] = l < L ? d.lv.child[l] : nullptr;
     }
   }
-
-  std::memset(out, 0, sizeof(*out));
-  out->L = L;
-  out->s_unmet = s_unmet;
-  out->n_src = N;
-  out->n_recv = M;
-  fill_side(S[0], L, rb1.set[0].nbox, out->nbox_src, out->key_src, out->off_src, out->parent_src,
-            out->child_src, &out->perm_src);
-  fill_side(S[1], L, rb1.set[1].nbox, out->nbox_recv, out->key_recv, out->off_recv, out->parent_recv,
-            out->child_recv, &out->perm_recv);
   for (int l = 2; l <= L; ++l) {
-    out->nnz_e2[l] = hb->nnz[l][0];
-    out->nnz_e4[l] = hb->nnz[l][1];
-    out->e2_off[l] = lst_off[0][l];
-    out->e4_off[l] = lst_off[1][l];
-    out->e2_idx[l] = lst_idx[0][l];
-    out->e4_idx[l] = lst_idx[1][l];
+    const uint64_t* o = &rb.list[((size_t)l * njobs + ji) * 4];
+    out->nnz_e2[l] = o[2];
+    out->nnz_e4[l] = o[3];
+    out->e2_off[l] = J.dev.out2[l];
+    out->e4_off[l] = J.dev.out4[l];
+    out->e2_idx[l] = rb.idx[2 * l] + o[0];
+    out->e4_idx[l] = rb.idx[2 * l + 1] + o[1];
+  }
+}
+
+struct PairIn {
+  const float* src;
+  uint32_t N;
+  const float* recv;
+  uint32_t M;
+};
+
+int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes);
+
+// The build of one or many (Src, Recv) pairs, outputs in outs[].
+int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params& prm,
+              fmm_tree* outs) {
+  cudaStream_t s = c->stream;
+  int err = FMM_OK;
+  const bool smode = prm.L < 0;
+  const bool stall = (prm.flags & FMM_FLAG_TEST_STALL) != 0;
+  const bool host_in = (prm.flags & FMM_FLAG_HOST_INPUT) != 0;
+
+  uint64_t expect = 0;
+  for (uint32_t k = 0; k < npairs; ++k) {
+    uint64_t b = 0;
+    query_workspace(pairs[k].N, pairs[k].M, prm, &b);
+    expect += b;
+  }
+  FMM_TRY(arena_reset(c, c->peak_request > expect ? c->peak_request : expect));
+  c->up_cursor = 0;
+  FMM_CUDA(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
+
+  // Sets (the same array given as a pair's sources and receivers is one set)
+  // and jobs.
+  std::vector<SetPlan> sets;
+  std::vector<JobPlan> jobs(npairs);
+  auto add_set = [&](const float* p, uint32_t n) {
+    SetPlan sp;
+    sp.xyz = p;
+    sp.n = n;
+    sets.push_back(sp);
+    return (uint32_t)sets.size() - 1;
+  };
+  for (uint32_t k = 0; k < npairs; ++k) {
+    const bool aliased = pairs[k].src == pairs[k].recv && pairs[k].N == pairs[k].M;
+    jobs[k].src = add_set(pairs[k].src, pairs[k].N);
+    jobs[k].recv = aliased ? jobs[k].src : add_set(pairs[k].recv, pairs[k].M);
+  }
+  if (host_in) {
+    for (auto& sp : sets) {
+      float* d = arena_get<float>(c, (size_t)sp.n * 3, &err);
+      if (err) return err;
+      if (sp.n)
+        FMM_CUDA(cudaMemcpyAsync(d, sp.xyz, sizeof(float) * 3 * sp.n, cudaMemcpyHostToDevice, s));
+      sp.xyz = d;
+    }
+  }
+  // Box depth: the tree depth, or (cluster-size mode) the sort depth of the
+  // larger set of the job; both sets of a job share it.
+  for (auto& jp : jobs) {
+    const int want = smode ? std::max(std::max(sort_level(sets[jp.src].n, 2),
+                                               sort_level(sets[jp.recv].n, 2)), 2)
+                           : prm.L;
+    jp.L = want;
+    sets[jp.src].Lb = std::max(sets[jp.src].Lb, want);
+    sets[jp.recv].Lb = std::max(sets[jp.recv].Lb, want);
+    sets[jp.src].need_occ = true;
+  }
+  Readback rb;
+  FMM_TRY(run_build(c, sets, jobs, prm, smode, false, stall, &rb));
+
+  // Cluster-size jobs not met at that depth: rebuild with full keys and
+  // boxes down to level 21.
+  std::vector<int> deep_of(npairs, -1);
+  std::vector<SetPlan> dsets;
+  std::vector<JobPlan> djobs;
+  Readback drb;
+  {
+    std::vector<int> map(sets.size(), -1);
+    for (uint32_t j = 0; j < npairs; ++j) {
+      if (jobs[j].L >= 0) continue;
+      JobPlan jp;
+      for (int k = 0; k < 2; ++k) {
+        const uint32_t id = k ? jobs[j].recv : jobs[j].src;
+        if (map[id] < 0) {
+          SetPlan sp;
+          sp.xyz = sets[id].xyz;
+          sp.n = sets[id].n;
+          sp.Lb = kMaxLevel;
+          sp.full = true;
+          map[id] = (int)dsets.size();
+          dsets.push_back(sp);
+        }
+        (k ? jp.recv : jp.src) = (uint32_t)map[id];
+      }
+      dsets[jp.src].need_occ = true;
+      jp.L = kMaxLevel;
+      deep_of[j] = (int)djobs.size();
+      djobs.push_back(jp);
+    }
+    if (!djobs.empty()) FMM_TRY(run_build(c, dsets, djobs, prm, true, true, false, &drb));
+  }
+
+  // Boxes that outran the finishing window: redo those orders in full.
+  std::vector<uint32_t> longs;
+  for (uint32_t i = 0; i < sets.size(); ++i)
+    if (rb.seg_long[i]) longs.push_back(i);
+  FMM_TRY(full_sort_perms(c, sets, longs, prm));
+
+  for (uint32_t j = 0; j < npairs; ++j) {
+    if (deep_of[j] >= 0)
+      fill_tree(dsets, djobs[deep_of[j]], drb, (uint32_t)deep_of[j], (uint32_t)djobs.size(),
+                &outs[j]);
+    else
+      fill_tree(sets, jobs[j], rb, j, npairs, &outs[j]);
   }
   size_t used = 0;
   for (size_t i = 0; i < c->chunks.size(); ++i) used += c->chunks[i].bytes;
   c->peak_request = std::max(c->peak_request, used);
+  return FMM_OK;
+}
+
+int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes) {
+  const int L = p.L >= 0 ? p.L : std::max(sort_level(std::max(N, M), 2), 2);
+  uint64_t total = 64 << 10;
+  const uint32_t ns[2] = {N, M};
+  for (int k = 0; k < 2; ++k) {
+    const uint64_t n = ns[k];
+    if (p.flags & FMM_FLAG_HOST_INPUT) total += align_up(12 * n);
+    total += 2 * align_up(12 * n + 48) + align_up(4 * n) + (16 << 10);
+    total += (n / kSortTile + 1) * kRadixMax * 4 * 3 + (n / kBoxTile + 1) * 8 * (1 + kLevels);
+    for (int l = 0; l <= L; ++l) total += align_up(21ull * level_cap(ns[k], l) + 8) + 1024;
+  }
+  for (int l = 2; l <= L; ++l)
+    total += align_up(4ull * (4 + 27 + 189) * level_cap(M, l) + 64) + 4096;
+  *bytes = total;
   return FMM_OK;
 }
 
@@ -676,6 +1026,22 @@ struct DeviceGuard {
     if (prev >= 0 && cur != prev) cudaSetDevice(prev);
   }
 };
+
+int check_params(const fmm_params& p) {
+  if (p.flags & ~(FMM_FLAG_HOST_INPUT | FMM_FLAG_TEST_STALL)) return FMM_ERR_ARG;
+  if (p.L > kMaxLevel || p.L < -1 || (p.L == -1 && p.s == 0)) return FMM_ERR_LEVEL;
+  return FMM_OK;
+}
+
+int finish_call(fmm_ctx* c, int st, uint64_t l0) {
+  if (st != FMM_OK) {
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+  }
+  if (c->timing) collect_times(c);
+  c->last_launches = c->launches - l0;
+  return st;
+}
 
 }  // namespace
 
@@ -697,13 +1063,14 @@ int fmm_create(fmm_ctx** ctx, int device, fmm_alloc_fn alloc, fmm_free_fn free_f
   c->free_fn = free_fn;
   c->user = user;
   if (cudaMalloc(&c->st, sizeof(DevStatus)) != cudaSuccess ||
-      cudaMallocHost(&c->host_buf, kHostBuf) != cudaSuccess) {
+      pinned_reserve(&c->up_buf, &c->up_bytes, 1 << 20) != FMM_OK ||
+      pinned_reserve(&c->rb_buf, &c->rb_bytes, 1 << 16) != FMM_OK) {
     cudaGetLastError();
     if (c->st) cudaFree(c->st);
+    if (c->up_buf) cudaFreeHost(c->up_buf);
     delete c;
     return FMM_ERR_CUDA;
   }
-  static_assert(sizeof(Readback) <= kHostBuf, "read-back buffer");
   *ctx = c;
   return FMM_OK;
 }
@@ -719,7 +1086,8 @@ int fmm_destroy(fmm_ctx* c) {
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
   cudaFree(c->st);
-  cudaFreeHost(c->host_buf);
+  if (c->up_buf) cudaFreeHost(c->up_buf);
+  if (c->rb_buf) cudaFreeHost(c->rb_buf);
   delete c;
   return FMM_OK;
 }
@@ -727,39 +1095,35 @@ int fmm_destroy(fmm_ctx* c) {
 int fmm_query_workspace(uint32_t N, uint32_t M, fmm_params p, uint64_t* bytes) {
   if (!bytes) return FMM_ERR_ARG;
   if (p.L > kMaxLevel || p.L < -1 || (p.L == -1 && p.s == 0)) return FMM_ERR_LEVEL;
-  const int L = p.L >= 0 ? p.L : std::max(sort_level(std::max(N, M), 2), 2);
-  uint64_t total = 1 << 20;
-  const uint32_t ns[2] = {N, M};
-  for (int k = 0; k < 2; ++k) {
-    const uint64_t n = ns[k];
-    if (p.flags & FMM_FLAG_HOST_INPUT) total += align_up(12 * n);
-    total += 4 * align_up(12 * n + 8) / 2 + align_up(4 * n) + (8u << 20);
-    total += (n / kSortTile + 1) * 256 * 8 * 8;
-    for (int l = 0; l <= L; ++l) total += 4 * align_up(8ull * level_cap(ns[k], l) + 8);
-  }
-  for (int l = 2; l <= L; ++l) total += align_up(4ull * (2 + 27 + 189) * level_cap(M, l) + 64) + 4096;
-  *bytes = total;
-  return FMM_OK;
+  return query_workspace(N, M, p, bytes);
 }
 
 int fmm_build(fmm_ctx* c, const float* src_xyz, uint32_t N, const float* recv_xyz, uint32_t M,
               fmm_params params, fmm_tree* out, void* stream) {
   if (!c || !out) return FMM_ERR_ARG;
   if ((N > 0 && !src_xyz) || (M > 0 && !recv_xyz)) return FMM_ERR_ARG;
-  if (params.flags & ~(FMM_FLAG_HOST_INPUT | FMM_FLAG_TEST_STALL)) return FMM_ERR_ARG;
-  if (params.L > kMaxLevel || params.L < -1 || (params.L == -1 && params.s == 0))
-    return FMM_ERR_LEVEL;
+  FMM_TRY(check_params(params));
   DeviceGuard g(c->device);
   c->stream = static_cast<cudaStream_t>(stream);
   const uint64_t l0 = c->launches;
-  int st = do_build(c, src_xyz, N, recv_xyz, M, params, out);
-  if (st != FMM_OK) {
-    cudaStreamSynchronize(c->stream);
-    cudaGetLastError();
-  }
-  if (c->timing) collect_times(c);
-  c->last_launches = c->launches - l0;
-  return st;
+  const PairIn pin{src_xyz, N, recv_xyz, M};
+  return finish_call(c, do_builds(c, &pin, 1, params, out), l0);
+}
+
+int fmm_build_batched(fmm_ctx* c, const fmm_set* sets, uint32_t nsets, fmm_params params,
+                      fmm_tree* outs, void* stream) {
+  if (!c || (nsets > 0 && (!sets || !outs))) return FMM_ERR_ARG;
+  FMM_TRY(check_params(params));
+  if (params.flags & FMM_FLAG_TEST_STALL) return FMM_ERR_ARG;
+  for (uint32_t k = 0; k < nsets; ++k)
+    if ((sets[k].N > 0 && !sets[k].src) || (sets[k].M > 0 && !sets[k].recv)) return FMM_ERR_ARG;
+  if (nsets == 0) return FMM_OK;
+  DeviceGuard g(c->device);
+  c->stream = static_cast<cudaStream_t>(stream);
+  const uint64_t l0 = c->launches;
+  std::vector<PairIn> pins(nsets);
+  for (uint32_t k = 0; k < nsets; ++k) pins[k] = {sets[k].src, sets[k].N, sets[k].recv, sets[k].M};
+  return finish_call(c, do_builds(c, pins.data(), nsets, params, outs), l0);
 }
 
 int fmm_morton_keys(fmm_ctx* c, const float* xyz, uint32_t n, uint64_t* keys, void* stream) {
@@ -772,11 +1136,11 @@ int fmm_morton_keys(fmm_ctx* c, const float* xyz, uint32_t n, uint64_t* keys, vo
     Launch L(c, "keys");
     launch_keys(xyz, n, keys, c->st, s);
   }
-  Readback* hb = static_cast<Readback*>(c->host_buf);
-  FMM_CUDA(cudaMemcpyAsync(&hb->st, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  DevStatus* h = static_cast<DevStatus*>(c->rb_buf);
+  FMM_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   FMM_CUDA(cudaStreamSynchronize(s));
   if (c->timing) collect_times(c);
-  return (int)hb->st.code;
+  return (int)h->code;
 }
 
 int fmm_set_tuning(fmm_ctx* c, const fmm_tuning* t) {

@@ -36,10 +36,10 @@ __device__ __forceinline__ uint32_t first_diff_level(uint64_t a, uint64_t b) {
   return x == 0 ? 22u : (uint32_t)((2 + __clzll((long long)x)) / 3);
 }
 
-__global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
-    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint32_t n, int Lb,
-    int Ls, LevelArrays lv, uint32_t* __restrict__ perm, uint64_t* status, uint32_t* counter,
-    uint32_t* nbox, DevStatus* st, uint64_t wait_ns, uint32_t ntiles) {
+__global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __restrict__ segs,
+                                                                   const Slot* __restrict__ slots,
+                                                                   uint32_t nslots, DevStatus* st,
+                                                                   uint64_t wait_ns) {
   constexpr int W = kBoxThreads / 32;
   __shared__ uint32_t s_tile, s_abort, s_ttot, s_texcl;
   __shared__ uint32_t s_wtot[W];
@@ -47,9 +47,18 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
   uint8_t* s_dd = reinterpret_cast<uint8_t*>(s_key) + kBoxDdOff;  // first differing level
   uint32_t* s_val = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(s_key) + kBoxValOff);
 
+  const Seg& sg = segs[slots[find_slot(slots, nslots, blockIdx.x)].seg];
+  const uint64_t* __restrict__ keys = sg.skeys;
+  const uint32_t* __restrict__ vals = sg.svals;
+  const uint32_t n = sg.n;
+  const int Lb = sg.Lb, Ls = sg.Ls;
+  const LevelArrays& lv = sg.lv;
+  uint32_t* __restrict__ perm = sg.perm;
+  uint64_t* status = sg.bstatus;
+  const uint32_t ntiles = sg.btiles;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    s_tile = atomicAdd(counter, 1u);
+    s_tile = atomicAdd(&sg.tickets[0], 1u);
     s_abort = failed(st) ? 1u : 0u;
   }
   __syncthreads();
@@ -159,7 +168,10 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
       }
       perm[t0 + a + r] = s_val[j];
     }
-    if (long_box) atomicExch(&st->seg_long, 1u);
+    if (long_box) {
+      atomicExch(&st->seg_long, 1u);
+      atomicExch(sg.seg_long, 1u);
+    }
   }
 
   // Windowed look-back over the earlier tiles.
@@ -177,7 +189,7 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
   if (s_abort) return;  // a wait gave up: ranks may be wrong, write nothing
   if (tile == ntiles - 1 && threadIdx.x == 0) {
     const uint32_t nb = s_texcl + s_ttot;
-    nbox[Lb] = nb;
+    sg.nbox[Lb] = nb;
     if (nb <= lv.cap[Lb]) lv.off[Lb][nb] = n;
   }
   // Level-Lb keys and bookmarks.
@@ -200,22 +212,29 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(
 // boxes: box b opens a level-l box exactly when its key differs from box
 // b-1's in the level-l prefix.  A multi-level prefix sum over the boxes (one
 // decoupled look-back chain per level) gives each start its rank.
-__global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(
-    int Lb, LevelArrays lv, uint32_t n, uint64_t* status, uint32_t* counter, uint32_t* nbox,
-    DevStatus* st, uint64_t wait_ns) {
+__global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(const Seg* __restrict__ segs,
+                                                                   const Slot* __restrict__ slots,
+                                                                   uint32_t nslots, DevStatus* st,
+                                                                   uint64_t wait_ns) {
   constexpr int W = kBoxThreads / 32;
   __shared__ uint32_t s_tile, s_abort;
   __shared__ uint32_t s_wtot[W][kLevels];
   __shared__ uint32_t s_texcl[kLevels];
   __shared__ uint32_t s_ttot[kLevels];
   __shared__ uint64_t s_key[kBoxTile + 1];  // s_key[j + 1] = level-Lb key of box t0 + j
+  const Seg& sg = segs[slots[find_slot(slots, nslots, blockIdx.x)].seg];
+  const int Lb = sg.Lb;
+  const LevelArrays& lv = sg.lv;
+  const uint32_t n = sg.n;
+  uint64_t* status = sg.cstatus;
+  uint32_t* nbox = sg.nbox;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    s_tile = atomicAdd(counter, 1u);
+    s_tile = atomicAdd(&sg.tickets[1], 1u);
     s_abort = failed(st) ? 1u : 0u;
   }
   __syncthreads();
-  if (s_abort) return;
+  if (s_abort || Lb < 1) return;
   const uint32_t nb = nbox[Lb] < lv.cap[Lb] ? nbox[Lb] : lv.cap[Lb];
   const uint32_t ntiles = nb == 0 ? 1u : (nb + kBoxTile - 1) / kBoxTile;
   const uint32_t tile = s_tile;
@@ -331,82 +350,86 @@ uint32_t coarse_tiles(uint32_t cap) {
   return t == 0 ? 1u : (uint32_t)t;
 }
 
-void launch_finish_boxes(const uint64_t* keys, const uint32_t* vals, uint32_t n, int Lb, int Ls,
-                         LevelArrays lv, uint32_t* perm, uint64_t* status, uint32_t* counter,
-                         uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+void launch_finish_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
+                         DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+  if (units == 0) return;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(finish_boxes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBoxSmem);
     attr = true;
   }
-  const uint32_t t = boxes_tiles(n);
-  finish_boxes_kernel<<<t, kBoxThreads, kBoxSmem, s>>>(keys, vals, n, Lb, Ls, lv, perm, status,
-                                                        counter, nbox, st, wait_ns, t);
+  finish_boxes_kernel<<<units, kBoxThreads, kBoxSmem, s>>>(segs, slots, nslots, st, wait_ns);
 }
 
-void launch_coarse_boxes(int Lb, LevelArrays lv, uint32_t n, uint64_t* status, uint32_t* counter,
-                         uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
-  if (Lb < 1) return;
-  coarse_boxes_kernel<<<coarse_tiles(lv.cap[Lb]), kBoxThreads, 0, s>>>(Lb, lv, n, status, counter,
-                                                                       nbox, st, wait_ns);
+void launch_coarse_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
+                         DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+  if (units == 0) return;
+  coarse_boxes_kernel<<<units, kBoxThreads, 0, s>>>(segs, slots, nslots, st, wait_ns);
 }
 
 // ---------------------------------------------------------------------------
-// Child-occupancy mask of every box of levels 0..Lb-1: bit o is set when the
-// child in octant o (x + 2y + 4z) is non-empty.  Lists use it to enumerate the
-// children of a parent-level neighbour without reading their keys.
-__global__ void occupancy_kernel(int Lb, LevelArrays lv, const uint32_t* __restrict__ nbox,
+// Child-occupancy byte of every box of levels 0..Lb-1 of the sets flagged in
+// `which` (grid y = set): bit o is set when the child in octant o
+// (x + 2y + 4z) is non-empty.  Lists use it to enumerate the children of a
+// parent-level neighbour without reading their keys.
+__global__ void occupancy_kernel(const Seg* __restrict__ segs, const uint8_t* which,
                                  const DevStatus* st) {
-  const int l = blockIdx.y;
-  if (l >= Lb || failed(st)) return;
-  const uint32_t nb = nbox[l] < lv.cap[l] ? nbox[l] : lv.cap[l];
-  const uint32_t* ch = lv.child[l];
-  const uint64_t* ck = lv.key[l + 1];
-  uint8_t* occ = lv.occ[l];
-  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+  const Seg& sg = segs[blockIdx.y];
+  if (!which[blockIdx.y] || failed(st)) return;
+  for (int l = 0; l < sg.Lb; ++l) {
+    const uint32_t nb = sg.nbox[l] < sg.lv.cap[l] ? sg.nbox[l] : sg.lv.cap[l];
+    const uint32_t* ch = sg.lv.child[l];
+    const uint64_t* ck = sg.lv.key[l + 1];
+    uint8_t* occ = sg.lv.occ[l];
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+      uint32_t m = 0;
+      const uint32_t c1 = ch[b + 1];
+      for (uint32_t c = ch[b]; c < c1; ++c) m |= 1u << (uint32_t)(ck[c] & 7u);
+      occ[b] = (uint8_t)m;
+    }
+  }
+}
+
+void launch_occupancy(const Seg* segs, uint32_t nsegs, const uint8_t* which, uint32_t max_n,
+                      int max_lb, DevStatus* st, cudaStream_t s) {
+  if (nsegs == 0 || max_lb < 1) return;
+  uint32_t bx = (uint32_t)(((uint64_t)max_n / 4 + 255) / 256);
+  if (bx > 152u * 4u) bx = 152u * 4u;
+  if (bx == 0) bx = 1;
+  occupancy_kernel<<<dim3(bx, nsegs), 256, 0, s>>>(segs, which, st);
+}
+
+// Largest box occupancy of each level 0..Lb (cluster-size mode, Sec. 2.1),
+// into nbox[kLevels + l] (zeroed).
+__global__ void max_occupancy_kernel(const Seg* __restrict__ segs, const DevStatus* st) {
+  const Seg& sg = segs[blockIdx.y];
+  if (failed(st)) return;
+  for (int l = 0; l <= sg.Lb; ++l) {
+    const uint32_t nb = sg.nbox[l] < sg.lv.cap[l] ? sg.nbox[l] : sg.lv.cap[l];
+    const uint32_t* off = sg.lv.off[l];
     uint32_t m = 0;
-    const uint32_t c1 = ch[b + 1];
-    for (uint32_t c = ch[b]; c < c1; ++c) m |= 1u << (uint32_t)(ck[c] & 7u);
-    occ[b] = (uint8_t)m;
-  }
-}
-
-void launch_occupancy(int Lb, LevelArrays lv, const uint32_t* nbox, uint32_t n,
-                      const DevStatus* st, cudaStream_t s) {
-  if (Lb < 1) return;
-  uint32_t bx = (uint32_t)(((uint64_t)n + 255) / 256);
-  if (bx > 152u * 4u) bx = 152u * 4u;
-  if (bx == 0) bx = 1;
-  occupancy_kernel<<<dim3(bx, Lb), 256, 0, s>>>(Lb, lv, nbox, st);
-}
-
-// Largest box occupancy of each level 0..Lb (cluster-size mode, Sec. 2.1).
-__global__ void max_occupancy_kernel(int Lb, LevelArrays lv, const uint32_t* __restrict__ nbox,
-                                     uint32_t* maxocc, const DevStatus* st) {
-  const int l = blockIdx.y;
-  if (l > Lb || failed(st)) return;
-  const uint32_t nb = nbox[l] < lv.cap[l] ? nbox[l] : lv.cap[l];
-  const uint32_t* off = lv.off[l];
-  uint32_t m = 0;
-  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-    const uint32_t c = off[b + 1] - off[b];
-    m = c > m ? c : m;
-  }
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+      const uint32_t c = off[b + 1] - off[b];
+      m = c > m ? c : m;
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint32_t y = __shfl_xor_sync(0xffffffffu, m, o);
-    m = y > m ? y : m;
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t y = __shfl_xor_sync(0xffffffffu, m, o);
+      m = y > m ? y : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&sg.nbox[kLevels + l], m);
   }
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(&maxocc[l], m);
 }
 
-void launch_max_occupancy(int Lb, LevelArrays lv, const uint32_t* nbox, uint32_t n,
-                          uint32_t* maxocc, const DevStatus* st, cudaStream_t s) {
-  uint32_t bx = (uint32_t)(((uint64_t)n + 255) / 256);
+void launch_max_occupancy(const Seg* segs, uint32_t nsegs, uint32_t max_n, int max_lb,
+                          DevStatus* st, cudaStream_t s) {
+  if (nsegs == 0) return;
+  uint32_t bx = (uint32_t)(((uint64_t)max_n / 4 + 255) / 256);
   if (bx > 152u * 4u) bx = 152u * 4u;
   if (bx == 0) bx = 1;
-  max_occupancy_kernel<<<dim3(bx, Lb + 1), 256, 0, s>>>(Lb, lv, nbox, maxocc, st);
+  (void)max_lb;
+  max_occupancy_kernel<<<dim3(bx, nsegs), 256, 0, s>>>(segs, st);
 }
 
 }  // namespace fmm

@@ -255,11 +255,92 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // ---------------------------------------------------------------------------
+// Per-level device views of one point set.
+struct LevelArrays {
+  uint32_t cap[kLevels];  // allocated boxes per level (writes are bounded by it)
+  uint64_t* key[kLevels];
+  uint32_t* off[kLevels];
+  uint32_t* parent[kLevels];
+  uint32_t* child[kLevels];
+  uint8_t* occ[kLevels];
+};
+
+// One point set of a build ("segment").  A build holds one or two (sources,
+// receivers) or, batched, many; their points are concatenated in the sort
+// arrays, everything else is per set.  Device-resident; built on the host.
+struct Seg {
+  const float* xyz;  // [n][3]
+  uint32_t n;
+  uint32_t base;      // first slot of this set in the concatenated sort arrays
+  int Ls, Lb;         // sort depth (top 3*Ls key bits), box depth
+  int passes, lo;     // radix passes of 8 bits, lowest sorted key bit
+  uint32_t ntiles;    // sort tiles
+  uint32_t btiles;    // finishing / finest-box tiles
+  uint32_t* perm;
+  const uint64_t* skeys;  // this set's keys after the last pass (concatenated array + base)
+  const uint32_t* svals;  // ... and point indices (local to the set)
+  LevelArrays lv;
+  uint64_t* bstatus;  // [btiles] look-back words of the finest level
+  uint64_t* cstatus;  // [coarse tiles][kLevels]
+  uint32_t* tickets;  // [2]: finishing tiles, coarse tiles
+  uint32_t* nbox;     // [kLevels] box counts, then [kLevels] largest occupancy
+  uint32_t* seg_long; // set when a box outruns the finishing window
+};
+
+// A range of work units of one launch that belongs to one set.
+struct Slot {
+  uint32_t seg;    // set index
+  uint32_t unit0;  // first work unit (tile, or level-major unit) of the range
+  uint32_t aux0;   // per-kernel: first histogram entry, ...
+  uint32_t aux1;   // per-kernel: position correction, ...
+};
+
+// Slot holding work unit u: slots[k].unit0 <= u < slots[k+1].unit0.
+__device__ __forceinline__ uint32_t find_slot(const Slot* slots, uint32_t nslots, uint32_t u) {
+  uint32_t lo = 0, hi = nslots;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (slots[mid].unit0 <= u)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// One (sources, receivers) pair whose E2 / E4 lists are built.  The list
+// arrays of a level are shared by all jobs of a build: counts go to the
+// job's region of the level's work array (scanned once for all jobs), list
+// entries to one array in job order; each job's row starts come out rebased
+// to its own lists.
+struct Job {
+  uint32_t src, recv;  // set indices
+  int L;               // lists at levels 2..L
+  uint32_t pad;
+  uint32_t region[kLevels];     // first entry of the job in the level's work array
+  uint32_t* out2[kLevels];      // rebased E2 row starts [nbox_recv + 1]
+  uint32_t* out4[kLevels];      // rebased E4 row starts
+};
+
+// Per-level arrays shared by the jobs of a build.
+struct ListLevel {
+  uint32_t* work2;   // counts, then global row starts (all jobs)
+  uint32_t* work4;
+  uint32_t* idx2;    // list entries (all jobs)
+  uint32_t* idx4;
+  uint32_t* jprefix; // [njobs + 1] parents (receiver boxes at l-1) before each job
+  uint64_t* base;    // [njobs][2] first E2 / E4 entry of each job
+  uint64_t* nnz;     // [njobs][2] E2 / E4 entries of each job
+  uint64_t* total;   // [2] scanned totals of the level (capacity check)
+};
+
+// ---------------------------------------------------------------------------
 // Tunables of the kernels.
 constexpr int kSortThreads = 512;
 constexpr int kSortItems = 6;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 3072
-constexpr int kRadixMax = 256;
+constexpr int kRadixBits = 8;
+constexpr int kRadixMax = 1 << kRadixBits;
 
 constexpr int kBoxThreads = 512;
 constexpr int kBoxItems = 8;
@@ -272,68 +353,56 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 constexpr int kListThreads = 256;
 
-// ---------------------------------------------------------------------------
-// Per-level device views handed to the kernels.
-struct LevelArrays {
-  uint32_t cap[kLevels];  // allocated boxes per level (writes are bounded by it)
-  uint64_t* key[kLevels];
-  uint32_t* off[kLevels];
-  uint32_t* parent[kLevels];
-  uint32_t* child[kLevels];
-  uint8_t* occ[kLevels];
-};
+// Radix passes (8-bit digits) that sort the top 3*Ls key bits.
+__host__ __device__ inline int passes_for(int Ls) { return (3 * Ls + kRadixBits - 1) / kRadixBits; }
 
 // ---------------------------------------------------------------------------
-// Launchers (host side).  All asynchronous on `s`.
+// Launchers (host side).  All asynchronous on `s`.  `segs` / `jobs` and the
+// slot tables are device pointers.
+
+// Reduce-then-scan radix pass p over the sets of `slots` (units = sort tiles;
+// aux0 = first histogram entry of the set, aux1 = scan-to-slot correction):
+// per-tile digit histograms, digit-major per set, set after set.
+void launch_tile_hist(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
+                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, DevStatus* st,
+                      cudaStream_t s);
+// Scatter of pass p from `in` (or the coordinates) to `out` (concatenated
+// arrays).  stable = false only for a first pass that a finishing sort follows.
+void launch_rts_scatter(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
+                        uint32_t ntiles, const uint64_t* keys_in, const uint32_t* vals_in,
+                        uint64_t* keys_out, uint32_t* vals_out, const uint32_t* offsets,
+                        bool stable, bool bulk, DevStatus* st, uint64_t wait_ns, cudaStream_t s);
+
+// Onesweep pass over one set (keys_in / keys_out point at the set's slots).
 struct SortPlan {
-  int Ls;        // sort by the level-Ls key (top 3*Ls bits)
-  int passes;    // onesweep passes
-  int bits;      // digit width
-  int lo;        // lowest sorted bit
+  int Ls, passes, bits, lo;
   uint32_t ntiles;
 };
 SortPlan make_sort_plan(uint32_t n, int Ls);
-
-// Upfront digit histograms of every pass (keys computed from xyz), domain
-// check, then the exclusive digit offsets.  hist: [passes][256] zeroed.
 void launch_upfront_hist(const float* xyz, uint32_t n, const SortPlan& p, uint32_t* hist,
                          DevStatus* st, cudaStream_t s);
 void launch_digit_scan(const SortPlan& p, uint32_t* hist, cudaStream_t s);
-// Reduce-then-scan pass: per-tile digit histograms, digit-major
-// ([digit][tile]), so that one exclusive scan of the flattened array gives
-// every (digit, tile) its first output position; then the scatter.
-void launch_tile_hist(int pass, const float* xyz, const uint64_t* keys, uint32_t n,
-                      const SortPlan& p, uint32_t* hist, DevStatus* st, cudaStream_t s);
-void launch_rts_scatter(int pass, const float* xyz, const uint64_t* keys_in,
-                        const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                        uint32_t n, const SortPlan& p, const uint32_t* offsets, bool stable,
-                        DevStatus* st, uint64_t wait_ns, cudaStream_t s);
-// One onesweep pass.  pass 0 reads xyz (values = point index), later passes
-// read keys_in/vals_in.  status: [ntiles][256] zeroed; counter: zeroed.
 void launch_onesweep_pass(int pass, const float* xyz, const uint64_t* keys_in,
                           const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
                           uint32_t n, const SortPlan& p, const uint32_t* digit_base,
                           uint64_t* status, uint32_t* counter, DevStatus* st, uint64_t wait_ns,
                           int stall_tile, cudaStream_t s);
-// From (key, index) pairs sorted by the top 3*Ls key bits: the finishing
-// sort inside each level-Ls box by (full key, index) -> perm, and the boxes
-// of level Lb (Lb <= Ls): keys and bookmarks.  status: [ntiles] zeroed;
-// counter zeroed; writes nbox[Lb].
-void launch_finish_boxes(const uint64_t* keys, const uint32_t* vals, uint32_t n, int Lb, int Ls,
-                         LevelArrays lv, uint32_t* perm, uint64_t* status, uint32_t* counter,
-                         uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s);
-uint32_t boxes_tiles(uint32_t n);
-// Levels 0..Lb-1, parents of level Lb and children of level Lb-1, from the
-// level-Lb boxes.  status: [coarse_tiles(cap[Lb])][kLevels] zeroed.
-void launch_coarse_boxes(int Lb, LevelArrays lv, uint32_t n, uint64_t* status, uint32_t* counter,
-                         uint32_t* nbox, DevStatus* st, uint64_t wait_ns, cudaStream_t s);
+
+// Finishing sort inside level-Ls boxes (-> perm) and the finest level Lb of
+// every set of `slots` (units = box tiles).
+void launch_finish_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
+                         DevStatus* st, uint64_t wait_ns, cudaStream_t s);
+// Levels 0..Lb-1, parents of level Lb, children of level Lb-1 (units =
+// coarse tiles by capacity).
+void launch_coarse_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
+                         DevStatus* st, uint64_t wait_ns, cudaStream_t s);
+// Child-occupancy bytes (sets flagged in `which`, grid y = set) and largest
+// occupancy per level.
+void launch_occupancy(const Seg* segs, uint32_t nsegs, const uint8_t* which, uint32_t max_n,
+                      int max_lb, DevStatus* st, cudaStream_t s);
+void launch_max_occupancy(const Seg* segs, uint32_t nsegs, uint32_t max_n, int max_lb,
+                          DevStatus* st, cudaStream_t s);
 uint32_t coarse_tiles(uint32_t cap);
-// Child-occupancy masks of the boxes of levels 0..Lb-1.
-void launch_occupancy(int Lb, LevelArrays lv, const uint32_t* nbox, uint32_t n,
-                      const DevStatus* st, cudaStream_t s);
-// Largest box occupancy per level -> maxocc[kLevels] (zeroed).
-void launch_max_occupancy(int Lb, LevelArrays lv, const uint32_t* nbox, uint32_t n,
-                          uint32_t* maxocc, const DevStatus* st, cudaStream_t s);
 
 // Exclusive scan of u32 counts in place (count entries at data[0..count)),
 // writes data[count] = total (low 32 bits) and total64 (if not null); flags
@@ -345,30 +414,16 @@ void launch_scan_u32(uint32_t* data, const uint32_t* count_dev, uint32_t cap, ui
                      cudaStream_t s);
 uint32_t scan_tiles(uint32_t cap);
 
-struct ListArgs {
-  int l;
-  // receivers: parents at level l-1, boxes at level l
-  const uint32_t* nbox_recv;  // device [kLevels]
-  const uint32_t* nbox_src;
-  const uint64_t* rkey_up;    // key_recv[l-1]
-  const uint32_t* rchild_up;  // child_recv[l-1]
-  const uint64_t* rkey;       // key_recv[l]
-  // parent's E2 list at l-1 (l >= 3)
-  const uint32_t* e2_off_up;
-  const uint32_t* e2_idx_up;
-  // sources at level l-1
-  const uint64_t* skey_up;
-  const uint32_t* schild_up;
-  const uint8_t* socc_up;
-  // outputs
-  uint32_t* e2_off;
-  uint32_t* e4_off;
-  uint32_t* e2_idx;
-  uint32_t* e4_idx;
-  const uint64_t* nnz;  // device [2]: E2, E4 totals of this level (fill)
-};
-void launch_list_count(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s);
-void launch_list_fill(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s);
+// Lists of level l for every job.  jprefix of the level is computed first
+// (parents before each job; 0 for jobs whose L < l).
+// lvls: device array of kLevels ListLevel (level l and its parent level l-1
+// are read).
+void launch_job_prefix(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
+                       const ListLevel* lvls, DevStatus* st, cudaStream_t s);
+void launch_list_count(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
+                       const ListLevel* lvls, DevStatus* st, cudaStream_t s);
+void launch_list_fill(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
+                      const ListLevel* lvls, DevStatus* st, cudaStream_t s);
 
 // Morton keys of n points (public fmm_morton_keys).
 void launch_keys(const float* xyz, uint32_t n, uint64_t* keys, DevStatus* st, cudaStream_t s);

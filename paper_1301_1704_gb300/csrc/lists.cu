@@ -53,6 +53,42 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t v, int lane) {
   return x - v;
 }
 
+// Everything one warp needs to serve the parents of one job at level l.
+struct ListCtx {
+  uint32_t nsrc1;              // non-empty source boxes at level 1 (level 2 only)
+  const uint64_t* rkey_up;     // receiver keys, level l-1
+  const uint32_t* rchild_up;   // receiver children, level l-1
+  const uint64_t* rkey;        // receiver keys, level l
+  const uint32_t* e2_off_up;   // the job's E2 row starts, level l-1 (rebased)
+  const uint32_t* e2_idx_up;   // the job's E2 entries, level l-1
+  const uint64_t* skey_up;     // source keys, level l-1
+  const uint32_t* schild_up;   // source children, level l-1
+  const uint8_t* socc_up;      // source child occupancy, level l-1
+  uint32_t region;             // the job's first entry in the level's work arrays
+  uint32_t nrecv;              // receiver boxes of the job at level l
+  uint32_t np;                 // parents (receiver boxes at l-1) of the job
+};
+
+__device__ __forceinline__ ListCtx make_ctx(const Seg* segs, const Job& J, int l,
+                                            const ListLevel* lvls, uint32_t jidx) {
+  const Seg& S = segs[J.src];
+  const Seg& R = segs[J.recv];
+  ListCtx c;
+  c.nsrc1 = S.nbox[1];
+  c.rkey_up = R.lv.key[l - 1];
+  c.rchild_up = R.lv.child[l - 1];
+  c.rkey = R.lv.key[l];
+  c.e2_off_up = l >= 3 ? J.out2[l - 1] : nullptr;
+  c.e2_idx_up = l >= 3 ? lvls[l - 1].idx2 + lvls[l - 1].base[2 * jidx] : nullptr;
+  c.skey_up = S.lv.key[l - 1];
+  c.schild_up = S.lv.child[l - 1];
+  c.socc_up = S.lv.occ[l - 1];
+  c.region = J.region[l];
+  c.nrecv = R.nbox[l];
+  c.np = 0;
+  return c;
+}
+
 // Per-lane view of one parent-level neighbour.
 struct Neighbour {
   int dx, dy, dz;
@@ -60,18 +96,18 @@ struct Neighbour {
   uint32_t child;
 };
 
-__device__ __forceinline__ Neighbour load_neighbour(const ListArgs& a, uint32_t p, int lane) {
+__device__ __forceinline__ Neighbour load_neighbour(const ListCtx& a, int l, uint32_t p, int lane) {
   Neighbour q{0, 0, 0, 0u, 0u};
   uint32_t m, first;
-  if (a.l == 2) {
+  if (l == 2) {
     first = 0;
-    m = a.nbox_src[1];
+    m = a.nsrc1;
   } else {
     first = a.e2_off_up[p];
     m = a.e2_off_up[p + 1] - first;
   }
   if ((uint32_t)lane < m) {
-    const uint32_t Q = (a.l == 2) ? (uint32_t)lane : a.e2_idx_up[first + lane];
+    const uint32_t Q = (l == 2) ? (uint32_t)lane : a.e2_idx_up[first + lane];
     const uint64_t pk = a.rkey_up[p];
     const uint64_t qk = a.skey_up[Q];
     q.dx = (int)compact3(qk) - (int)compact3(pk);
@@ -83,18 +119,109 @@ __device__ __forceinline__ Neighbour load_neighbour(const ListArgs& a, uint32_t 
   return q;
 }
 
+// Job holding global parent g: jp[j] <= g < jp[j + 1].
+__device__ __forceinline__ uint32_t find_job(const uint32_t* jp, uint32_t njobs, uint32_t g) {
+  uint32_t lo = 0, hi = njobs;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (jp[mid] <= g)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Parents before each job at level l (0 for jobs whose lists stop below l).
+__global__ void job_prefix_kernel(const Seg* __restrict__ segs, const Job* __restrict__ jobs,
+                                  uint32_t njobs, int l, const ListLevel* lvls, DevStatus* st) {
+  __shared__ uint32_t s_carry, s_wsum[32];
+  if (failed(st)) return;
+  const ListLevel& LV = lvls[l];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t c = 0; c < njobs; c += blockDim.x) {
+    const uint32_t j = c + threadIdx.x;
+    uint32_t np = 0;
+    if (j < njobs && jobs[j].L >= l) {
+      const Seg& R = segs[jobs[j].recv];
+      np = R.nbox[l - 1];
+      if (R.nbox[l] == 0) {
+        jobs[j].out2[l][0] = 0;
+        jobs[j].out4[l][0] = 0;
+      }
+    }
+    uint32_t x = np;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = s_carry;
+      for (int w = 0; w < nw; ++w) {
+        const uint32_t v = s_wsum[w];
+        s_wsum[w] = run;
+        run += v;
+      }
+      s_carry = run;
+    }
+    __syncthreads();
+    if (j < njobs) LV.jprefix[j] = s_wsum[warp] + x - np;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) LV.jprefix[njobs] = s_carry;
+}
+
+void launch_job_prefix(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
+                       const ListLevel* lvls, DevStatus* st, cudaStream_t s) {
+  job_prefix_kernel<<<1, 1024, 0, s>>>(segs, jobs, njobs, l, lvls, st);
+}
+
+// Each warp takes a contiguous run of the level's parents (over all jobs) and
+// walks it, switching job descriptors as it crosses job boundaries.
+struct WarpRange {
+  uint32_t g0, g1;
+};
+
+__device__ __forceinline__ WarpRange warp_range(uint32_t total) {
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t per = (total + nw - 1) / nw;
+  const uint64_t a = (uint64_t)gw * per, b = a + per;
+  return WarpRange{(uint32_t)(a < total ? a : total), (uint32_t)(b < total ? b : total)};
+}
+
 // Counts: per receiver child r of parent p, |E2(r)| = sum over the parent's
 // neighbours Q of popc(occ(Q) & mask(delta_Q, rho_r)), and |E2| + |E4| = the
 // number of non-empty children of all Q.  The eight possible sibling octants
 // are counted at once: byte rho of a packed pair of words.
-__global__ void __launch_bounds__(kListThreads) list_count_kernel(ListArgs a, DevStatus* st) {
+__global__ void __launch_bounds__(kListThreads) list_count_kernel(const Seg* __restrict__ segs,
+                                                                 const Job* __restrict__ jobs,
+                                                                 uint32_t njobs, int l,
+                                                                 const ListLevel* lvls,
+                                                                 DevStatus* st) {
   if (failed(st)) return;  // set before this launch: the same for every thread
   const int lane = threadIdx.x & 31;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t np = a.nbox_recv[a.l - 1];
-  for (uint32_t p = gw; p < np; p += nw) {
-    const Neighbour q = load_neighbour(a, p, lane);
+  const ListLevel& LV = lvls[l];
+  const WarpRange wr = warp_range(LV.jprefix[njobs]);
+  if (wr.g0 >= wr.g1) return;
+  uint32_t j = find_job(LV.jprefix, njobs, wr.g0);
+  ListCtx a = make_ctx(segs, jobs[j], l, lvls, j);
+  uint32_t jstart = LV.jprefix[j], jend = LV.jprefix[j + 1];
+  for (uint32_t g = wr.g0; g < wr.g1; ++g) {
+    while (g >= jend) {
+      ++j;
+      a = make_ctx(segs, jobs[j], l, lvls, j);
+      jstart = jend;
+      jend = LV.jprefix[j + 1];
+    }
+    const uint32_t p = g - jstart;
+    const Neighbour q = load_neighbour(a, l, p, lane);
     uint32_t lo = 0, hi = 0;  // byte rho: popc(occ & mask(delta, rho))
 #pragma unroll
     for (uint32_t rho = 0; rho < 4; ++rho)
@@ -110,8 +237,8 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(ListArgs a, De
     if (r < c1) {
       const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
       const uint32_t n2 = ((rho < 4 ? lo : hi) >> (8 * (rho & 3))) & 0xffu;
-      a.e2_off[r] = n2;
-      a.e4_off[r] = tot - n2;
+      LV.work2[a.region + r] = n2;
+      LV.work4[a.region + r] = tot - n2;
     }
   }
 }
@@ -123,37 +250,72 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(ListArgs a, De
 // (delta, o, rho) -> (-delta, rho, o), that byte is e2_child_mask(-delta, o).
 // Every receiver child then splits C by one ballot per 32 candidates: its E2
 // and E4 lists come out in ascending order as contiguous, coalesced stores.
+// Row starts are written rebased to the job's own lists.
 constexpr int kCand = 27 * 8;  // at most 27 neighbours x 8 children
 constexpr int kNear = 64;      // candidates in some sibling's E2: the 4x4x4 block
 constexpr int kListWarps = kListThreads / 32;
 
-__global__ void __launch_bounds__(kListThreads) list_fill_kernel(ListArgs a, DevStatus* st) {
+__global__ void __launch_bounds__(kListThreads) list_fill_kernel(const Seg* __restrict__ segs,
+                                                                const Job* __restrict__ jobs,
+                                                                uint32_t njobs, int l,
+                                                                const ListLevel* lvls,
+                                                                DevStatus* st) {
   __shared__ uint32_t s_rank[kListWarps][kCand];
   __shared__ uint8_t s_sib[kListWarps][kCand];
   __shared__ uint32_t s_nrank[kListWarps][kNear];
   __shared__ uint8_t s_nsib[kListWarps][kNear];
   if (failed(st)) return;  // set before this launch: the same for every thread
-  if ((a.nnz[0] >> 32) != 0 || (a.nnz[1] >> 32) != 0) return;  // capacity error already set
+  const ListLevel& LV = lvls[l];
+  if ((LV.total[0] >> 32) != 0 || (LV.total[1] >> 32) != 0) return;  // capacity error set
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   uint32_t* crank = s_rank[warp];
   uint8_t* csib = s_sib[warp];
   uint32_t* nrank = s_nrank[warp];
   uint8_t* nsibm = s_nsib[warp];
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t np = a.nbox_recv[a.l - 1];
-  for (uint32_t p = gw; p < np; p += nw) {
+  const WarpRange wr = warp_range(LV.jprefix[njobs]);
+  if (wr.g0 >= wr.g1) return;
+  uint32_t j = find_job(LV.jprefix, njobs, wr.g0);
+  ListCtx a = make_ctx(segs, jobs[j], l, lvls, j);
+  uint32_t jstart = LV.jprefix[j], jend = LV.jprefix[j + 1];
+  uint32_t* out2 = jobs[j].out2[l];
+  uint32_t* out4 = jobs[j].out4[l];
+  uint32_t G2 = LV.work2[a.region], G4 = LV.work4[a.region];
+  for (uint32_t g = wr.g0; g < wr.g1; ++g) {
+    while (g >= jend) {
+      ++j;
+      a = make_ctx(segs, jobs[j], l, lvls, j);
+      jstart = jend;
+      jend = LV.jprefix[j + 1];
+      out2 = jobs[j].out2[l];
+      out4 = jobs[j].out4[l];
+      G2 = LV.work2[a.region];
+      G4 = LV.work4[a.region];
+    }
+    const uint32_t p = g - jstart;
     // The receiver children of p (at most 8): lane j fetches child j's octant
     // and list starts up front, so their loads overlap the neighbour loads.
     const uint32_t c0 = a.rchild_up[p], c1 = a.rchild_up[p + 1];
     uint32_t my_rho = 0, my_o2 = 0, my_o4 = 0;
     if (c0 + lane < c1) {
       my_rho = (uint32_t)(a.rkey[c0 + lane] & 7u);
-      my_o2 = a.e2_off[c0 + lane];
-      my_o4 = a.e4_off[c0 + lane];
+      my_o2 = LV.work2[a.region + c0 + lane];
+      my_o4 = LV.work4[a.region + c0 + lane];
+      out2[c0 + lane] = my_o2 - G2;
+      out4[c0 + lane] = my_o4 - G4;
     }
-    const Neighbour q = load_neighbour(a, p, lane);
+    if (g + 1 == jend) {  // the job's last parent closes its rows
+      const uint32_t e2 = LV.work2[a.region + a.nrecv], e4 = LV.work4[a.region + a.nrecv];
+      if (lane == 0) {
+        out2[a.nrecv] = e2 - G2;
+        out4[a.nrecv] = e4 - G4;
+        LV.base[2 * j] = G2;
+        LV.base[2 * j + 1] = G4;
+        LV.nnz[2 * j] = e2 - G2;
+        LV.nnz[2 * j + 1] = e4 - G4;
+      }
+    }
+    const Neighbour q = load_neighbour(a, l, p, lane);
     const uint32_t nsib = c1 - c0;
 
     // Candidates C (children of p's neighbours, ascending rank) and the near
@@ -188,53 +350,49 @@ __global__ void __launch_bounds__(kListThreads) list_fill_kernel(ListArgs a, Dev
 
     uint32_t sbit[8], w2[8], w4[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      sbit[j] = (uint32_t)j < nsib ? 1u << __shfl_sync(0xffffffffu, my_rho, j) : 0u;
-      w2[j] = __shfl_sync(0xffffffffu, my_o2, j);
-      w4[j] = __shfl_sync(0xffffffffu, my_o4, j);
+    for (int jj = 0; jj < 8; ++jj) {
+      sbit[jj] = (uint32_t)jj < nsib ? 1u << __shfl_sync(0xffffffffu, my_rho, jj) : 0u;
+      w2[jj] = __shfl_sync(0xffffffffu, my_o2, jj);
+      w4[jj] = __shfl_sync(0xffffffffu, my_o4, jj);
     }
-    // E2 of sibling j: the near candidates whose byte has bit rho_j.
+    // E2 of sibling jj: the near candidates whose byte has bit rho_jj.
     for (uint32_t c = 0; c < nnear; c += 32) {
       const uint32_t i = c + lane;
       const uint32_t v = i < nnear ? nrank[i] : 0u;
       const uint32_t sb = i < nnear ? nsibm[i] : 0u;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {  // absent siblings have sbit 0: nothing stored
-        const bool in2 = (sb & sbit[j]) != 0u;
+      for (int jj = 0; jj < 8; ++jj) {  // absent siblings have sbit 0: nothing stored
+        const bool in2 = (sb & sbit[jj]) != 0u;
         const uint32_t b2 = __ballot_sync(0xffffffffu, in2);
-        st_cs_if(a.e2_idx + w2[j] + __popc(b2 & lt), v, in2);
-        w2[j] += __popc(b2);
+        st_cs_if(LV.idx2 + w2[jj] + __popc(b2 & lt), v, in2);
+        w2[jj] += __popc(b2);
       }
     }
-    // E4 of sibling j: the candidates without bit rho_j.
+    // E4 of sibling jj: the candidates without bit rho_jj.
     for (uint32_t c = 0; c < total; c += 32) {
       const uint32_t i = c + lane;
       const uint32_t v = i < total ? crank[i] : 0u;
       const uint32_t sb = i < total ? csib[i] : 0xffu;  // past the end: never stored
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {  // absent siblings: in4 is false everywhere
-        const bool in4 = (sb & sbit[j]) == 0u && (uint32_t)j < nsib;
+      for (int jj = 0; jj < 8; ++jj) {  // absent siblings: in4 is false everywhere
+        const bool in4 = (sb & sbit[jj]) == 0u && (uint32_t)jj < nsib;
         const uint32_t b4 = __ballot_sync(0xffffffffu, in4);
-        st_cs_if(a.e4_idx + w4[j] + __popc(b4 & lt), v, in4);
-        w4[j] += __popc(b4);
+        st_cs_if(LV.idx4 + w4[jj] + __popc(b4 & lt), v, in4);
+        w4[jj] += __popc(b4);
       }
     }
     __syncwarp();
   }
 }
 
-void launch_list_count(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s) {
-  uint32_t blocks = (uint32_t)(((uint64_t)nparents_cap * 32 + kListThreads - 1) / kListThreads);
-  if (blocks > 152u * 8u) blocks = 152u * 8u;
-  if (blocks == 0) blocks = 1;
-  list_count_kernel<<<blocks, kListThreads, 0, s>>>(a, st);
+void launch_list_count(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
+                       const ListLevel* lvls, DevStatus* st, cudaStream_t s) {
+  list_count_kernel<<<152u * 8u, kListThreads, 0, s>>>(segs, jobs, njobs, l, lvls, st);
 }
 
-void launch_list_fill(const ListArgs& a, uint32_t nparents_cap, DevStatus* st, cudaStream_t s) {
-  uint32_t blocks = (uint32_t)(((uint64_t)nparents_cap * 32 + kListThreads - 1) / kListThreads);
-  if (blocks > 152u * 8u) blocks = 152u * 8u;
-  if (blocks == 0) blocks = 1;
-  list_fill_kernel<<<blocks, kListThreads, 0, s>>>(a, st);
+void launch_list_fill(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
+                      const ListLevel* lvls, DevStatus* st, cudaStream_t s) {
+  list_fill_kernel<<<152u * 8u, kListThreads, 0, s>>>(segs, jobs, njobs, l, lvls, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -313,41 +313,47 @@ void launch_onesweep_pass(int pass, const float* xyz, const uint64_t* keys_in,
 }
 
 // ---------------------------------------------------------------------------
-// Reduce-then-scan passes.  No tile waits for another: each tile's digit
-// counts come from a separate read (of the coordinates for the first pass, of
-// the keys for the later ones), one prefix sum over the digit-major counts
-// gives every (digit, tile) its output start, and the scatter kernel streams.
+// Reduce-then-scan passes over one or many point sets.  No tile waits for
+// another: each tile's digit counts come from a separate read (of the
+// coordinates for the first pass, of the keys for the later ones), one prefix
+// sum over the counts -- laid out set after set, digit-major inside a set --
+// gives every (set, digit, tile) its output start in the concatenated
+// arrays, and the scatter kernel streams.
 
-__device__ __forceinline__ void count_digit(uint64_t key, int shift, uint32_t mask, uint32_t* sh) {
-  atomicAdd(&sh[(uint32_t)(key >> shift) & mask], 1u);
+__device__ __forceinline__ void count_digit(uint64_t key, int shift, uint32_t* sh) {
+  atomicAdd(&sh[(uint32_t)(key >> shift) & (kRadixMax - 1u)], 1u);
 }
 
 template <bool kFromXyz>
-__global__ void __launch_bounds__(256) tile_hist_kernel(const float* __restrict__ xyz,
+__global__ void __launch_bounds__(256) tile_hist_kernel(const Seg* __restrict__ segs,
+                                                        const Slot* __restrict__ slots,
+                                                        uint32_t nslots, int pass,
                                                         const uint64_t* __restrict__ keys,
-                                                        uint32_t n, int shift, int bits,
-                                                        uint32_t ntiles, bool vec,
                                                         uint32_t* __restrict__ hist,
                                                         DevStatus* st) {
   __shared__ uint32_t sh[kRadixMax];
-  const uint32_t radix = 1u << bits, mask = radix - 1u;
   for (int i = threadIdx.x; i < kRadixMax; i += blockDim.x) sh[i] = 0;
+  const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
+  const Seg& sg = segs[sl.seg];
+  const uint32_t t = blockIdx.x - sl.unit0;  // tile of the set
+  const uint32_t n = sg.n;
+  const int shift = sg.lo + kRadixBits * pass;
   __syncthreads();
-  const uint32_t tile = blockIdx.x;
-  const uint64_t base = (uint64_t)tile * kSortTile;
+  const uint64_t base = (uint64_t)t * kSortTile;
   const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
   bool bad = false;
-  uint32_t done = 0;
   if (kFromXyz) {
-    if (vec) {  // 4 points = 3 float4; tiles start at multiples of 4 points
+    const float* xyz = sg.xyz;
+    uint32_t done = 0;
+    if (((uintptr_t)xyz & 15u) == 0) {  // 4 points = 3 float4; tiles start at multiples of 4
       const float4* v = reinterpret_cast<const float4*>(xyz + 3 * base);
       for (uint32_t g = threadIdx.x; g < cnt / 4; g += blockDim.x) {
         const float4 a = __ldcs(v + 3 * g), b = __ldcs(v + 3 * g + 1), c = __ldcs(v + 3 * g + 2);
         bool ok0, ok1, ok2, ok3;
-        count_digit(morton_key(a.x, a.y, a.z, &ok0), shift, mask, sh);
-        count_digit(morton_key(a.w, b.x, b.y, &ok1), shift, mask, sh);
-        count_digit(morton_key(b.z, b.w, c.x, &ok2), shift, mask, sh);
-        count_digit(morton_key(c.y, c.z, c.w, &ok3), shift, mask, sh);
+        count_digit(morton_key(a.x, a.y, a.z, &ok0), shift, sh);
+        count_digit(morton_key(a.w, b.x, b.y, &ok1), shift, sh);
+        count_digit(morton_key(b.z, b.w, c.x, &ok2), shift, sh);
+        count_digit(morton_key(c.y, c.z, c.w, &ok3), shift, sh);
         bad |= !(ok0 && ok1 && ok2 && ok3);
       }
       done = cnt & ~3u;
@@ -355,42 +361,43 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(const float* __restrict_
     for (uint32_t j = done + threadIdx.x; j < cnt; j += blockDim.x) {
       const uint64_t i = base + j;
       bool ok;
-      count_digit(morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok), shift, mask, sh);
+      count_digit(morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok), shift, sh);
       bad |= !ok;
     }
   } else {
-    const ulonglong2* v = reinterpret_cast<const ulonglong2*>(keys + base);
+    const uint64_t* k0 = keys + sg.base + base;  // set bases are multiples of 4 slots
+    const ulonglong2* v = reinterpret_cast<const ulonglong2*>(k0);
     for (uint32_t g = threadIdx.x; g < cnt / 2; g += blockDim.x) {
       const ulonglong2 k = __ldcs(v + g);
-      count_digit(k.x, shift, mask, sh);
-      count_digit(k.y, shift, mask, sh);
+      count_digit(k.x, shift, sh);
+      count_digit(k.y, shift, sh);
     }
-    if ((cnt & 1u) && threadIdx.x == 0) count_digit(keys[base + cnt - 1], shift, mask, sh);
+    if ((cnt & 1u) && threadIdx.x == 0) count_digit(k0[cnt - 1], shift, sh);
   }
   __syncthreads();
-  for (uint32_t d = threadIdx.x; d < radix; d += blockDim.x) hist[(uint64_t)d * ntiles + tile] = sh[d];
+  for (uint32_t d = threadIdx.x; d < kRadixMax; d += blockDim.x)
+    hist[sl.aux0 + (uint64_t)d * sg.ntiles + t] = sh[d];
   if (bad) set_error(st, FMM_ERR_DOMAIN);
 }
 
-void launch_tile_hist(int pass, const float* xyz, const uint64_t* keys, uint32_t n,
-                      const SortPlan& p, uint32_t* hist, DevStatus* st, cudaStream_t s) {
-  if (n == 0) return;
-  const int shift = p.lo + pass * p.bits;
-  if (pass == 0) {
-    const bool vec = ((uintptr_t)xyz & 15u) == 0;
-    tile_hist_kernel<true><<<p.ntiles, 256, 0, s>>>(xyz, nullptr, n, shift, p.bits, p.ntiles, vec,
-                                                     hist, st);
-  } else {
-    tile_hist_kernel<false><<<p.ntiles, 256, 0, s>>>(nullptr, keys, n, shift, p.bits, p.ntiles,
-                                                      false, hist, st);
-  }
+void launch_tile_hist(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
+                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, DevStatus* st,
+                      cudaStream_t s) {
+  if (ntiles == 0) return;
+  if (pass == 0)
+    tile_hist_kernel<true><<<ntiles, 256, 0, s>>>(segs, slots, nslots, 0, nullptr, hist, st);
+  else
+    tile_hist_kernel<false><<<ntiles, 256, 0, s>>>(segs, slots, nslots, pass, keys, hist, st);
 }
 
-// Scatter of one reduce-then-scan pass, persistent: each block walks the
-// tiles t = blockIdx.x, + gridDim.x, ... and, while it ranks and scatters one
-// tile, a bulk copy (TMA) brings the next tile's input -- the coordinates in
-// the first pass, the (key, index) pairs in later ones -- into the other
-// half of a double buffer.  A partial last tile is read with plain loads.
+// Scatter of one pass, persistent: each block walks the tiles u = blockIdx.x,
+// + gridDim.x, ... of all sets and, while it ranks and scatters one tile, a
+// bulk copy (TMA) brings the next tile's input -- the coordinates in the
+// first pass, the (key, index) pairs in later ones -- into the other half of
+// a double buffer.  Partial tiles, and inputs that are not 16-byte aligned,
+// are read with plain loads.  Global output position of (set, digit, tile) =
+// scanned offset + the slot's correction (set base minus the points of the
+// sets before it in this pass).
 constexpr uint32_t kInBytes = kSortTile * 12;  // xyz of a tile, or its keys + indices
 constexpr size_t kScatterSmem = 2 * (size_t)kInBytes;
 
@@ -398,11 +405,13 @@ constexpr size_t kScatterSmem = 2 * (size_t)kInBytes;
 // first one).
 template <bool kFromXyz, bool kStable>
 __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
-    const float* __restrict__ xyz, const uint64_t* __restrict__ keys_in,
+    const Seg* __restrict__ segs, const Slot* __restrict__ slots, uint32_t nslots,
+    uint32_t ntiles, int pass, const uint64_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out, uint32_t n, int shift, int bits, uint32_t ntiles,
-    const uint32_t* __restrict__ offsets, DevStatus* st, uint64_t wait_ns, bool use_bulk) {
+    uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ offsets, bool bulk,
+    DevStatus* st, uint64_t wait_ns) {
   constexpr int W = kSortThreads / 32;
+  constexpr uint32_t mask = kRadixMax - 1u;
   __shared__ uint32_t s_fail;
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_wcnt[W][kRadixMax];  // per-warp digit counts, then block slots
@@ -410,7 +419,6 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
   __shared__ uint32_t s_wsum[W];
   extern __shared__ __align__(128) unsigned char s_in[];  // two input buffers
 
-  const uint32_t radix = 1u << bits, mask = radix - 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   if (threadIdx.x == 0) {
@@ -422,42 +430,68 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
   __syncthreads();
   if (s_fail) return;  // an earlier kernel failed (domain error): leave the outputs alone
 
-  // tiles read by bulk copy (all full tiles, when the sources are 16-byte aligned)
-  const uint32_t full_tiles = use_bulk ? (uint32_t)(n / kSortTile) : 0u;
-  auto issue = [&](uint32_t t, int b) {  // thread 0 only, full tiles only
+  // Whether unit u is a full tile read by bulk copy; its source and slot.
+  auto bulk_src = [&](uint32_t u, const unsigned char** src) -> bool {
+    if (!bulk) return false;
+    const Slot sl = slots[find_slot(slots, nslots, u)];
+    const Seg& sg = segs[sl.seg];
+    const uint32_t t = u - sl.unit0;
+    if ((uint64_t)(t + 1) * kSortTile > sg.n) return false;
+    if (kFromXyz) {
+      if (((uintptr_t)sg.xyz & 15u) != 0) return false;
+      *src = reinterpret_cast<const unsigned char*>(sg.xyz + 3ull * t * kSortTile);
+    } else {
+      *src = reinterpret_cast<const unsigned char*>(keys_in + sg.base + (uint64_t)t * kSortTile);
+      src[1] = reinterpret_cast<const unsigned char*>(vals_in + sg.base + (uint64_t)t * kSortTile);
+    }
+    return true;
+  };
+  auto issue = [&](const unsigned char* const* src, int b) {  // thread 0 only
     unsigned char* dst = s_in + b * kInBytes;
-    const uint64_t base = (uint64_t)t * kSortTile;
     mbar_expect_tx(&s_bar[b], kInBytes);
     if (kFromXyz) {
-      bulk_load(dst, xyz + 3 * base, kInBytes, &s_bar[b]);
+      bulk_load(dst, src[0], kInBytes, &s_bar[b]);
     } else {
-      bulk_load(dst, keys_in + base, kSortTile * 8, &s_bar[b]);
-      bulk_load(dst + kSortTile * 8, vals_in + base, kSortTile * 4, &s_bar[b]);
+      bulk_load(dst, src[0], kSortTile * 8, &s_bar[b]);
+      bulk_load(dst + kSortTile * 8, src[1], kSortTile * 4, &s_bar[b]);
     }
   };
   uint32_t phase[2] = {0u, 0u};
   bool pending[2] = {false, false};
-  uint32_t t = blockIdx.x;
-  if (t < full_tiles) {
-    if (threadIdx.x == 0) issue(t, 0);
-    pending[0] = true;
+  uint32_t u = blockIdx.x;
+  {
+    const unsigned char* src[2] = {nullptr, nullptr};
+    if (u < ntiles && bulk_src(u, src)) {
+      if (threadIdx.x == 0) issue(src, 0);
+      pending[0] = true;
+    }
   }
-  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+  for (int it = 0; u < ntiles; u += gridDim.x, ++it) {
     const int b = it & 1;
     unsigned char* buf = s_in + b * kInBytes;
+    const Slot sl = slots[find_slot(slots, nslots, u)];
+    const Seg& sg = segs[sl.seg];
+    const uint32_t t = u - sl.unit0;
+    const uint32_t n = sg.n;
+    const int shift = sg.lo + kRadixBits * pass;
     const uint64_t base = (uint64_t)t * kSortTile;
     const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
-    const bool full = t < full_tiles;
-    const uint32_t tn = t + gridDim.x;
-    if (tn < full_tiles) {
-      if (threadIdx.x == 0) {
-        fence_proxy_async();
-        issue(tn, b ^ 1);
+    const bool full = pending[b];
+    {
+      const uint32_t un = u + gridDim.x;
+      const unsigned char* src[2] = {nullptr, nullptr};
+      if (un < ntiles && bulk_src(un, src)) {
+        if (threadIdx.x == 0) {
+          fence_proxy_async();
+          issue(src, b ^ 1);
+        }
+        pending[b ^ 1] = true;
       }
-      pending[b ^ 1] = true;
     }
     const uint32_t my_off =
-        threadIdx.x < radix ? __ldg(offsets + (uint64_t)threadIdx.x * ntiles + t) : 0u;
+        threadIdx.x < kRadixMax
+            ? __ldg(offsets + sl.aux0 + (uint64_t)threadIdx.x * sg.ntiles + t) + sl.aux1
+            : 0u;
     for (int i = threadIdx.x; i < W * kRadixMax; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
     bool ok = true;
     if (full) {
@@ -473,7 +507,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     }
 
     // Items, warp-striped: item k of lane j is tile slot 32 * (kSortItems *
-    // warp + k) + j, so (k, lane) order is the input order.
+    // warp + k) + j, so (k, lane) order is the input order.  Values are point
+    // indices local to the set.
     uint64_t key[kSortItems];
     uint32_t val[kSortItems];
 #pragma unroll
@@ -483,15 +518,16 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
       val[k] = (uint32_t)(base + j);
       if (j < cnt) {
         if (kFromXyz) {
-          const float* f = full ? reinterpret_cast<const float*>(buf) + 3 * j : xyz + 3 * (base + j);
+          const float* f =
+              full ? reinterpret_cast<const float*>(buf) + 3 * j : sg.xyz + 3 * (base + j);
           bool okk;
           key[k] = morton_key(f[0], f[1], f[2], &okk);
         } else if (full) {
           key[k] = reinterpret_cast<const uint64_t*>(buf)[j];
           val[k] = reinterpret_cast<const uint32_t*>(buf + kSortTile * 8)[j];
         } else {
-          key[k] = keys_in[base + j];
-          val[k] = vals_in[base + j];
+          key[k] = keys_in[sg.base + base + j];
+          val[k] = vals_in[sg.base + base + j];
         }
       }
     }
@@ -521,7 +557,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     }
     __syncthreads();
     uint32_t tot = 0;
-    if (threadIdx.x < radix) {
+    if (threadIdx.x < kRadixMax) {
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         const uint32_t c = s_wcnt[w][threadIdx.x];
@@ -548,7 +584,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
       if (lane < W) s_wsum[lane] = y - v;
     }
     __syncthreads();
-    if (threadIdx.x < radix) {
+    if (threadIdx.x < kRadixMax) {
       const uint32_t excl_blk = x - tot + s_wsum[warp];
 #pragma unroll
       for (int w = 0; w < W; ++w) s_wcnt[w][threadIdx.x] += excl_blk;
@@ -568,13 +604,14 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
       }
     }
     __syncthreads();
+    const uint32_t lim = sg.base + n;  // this set's slots end here
 #pragma unroll 2
     for (int j = 0; j < kSortItems; ++j) {
       const uint32_t p = threadIdx.x + j * kSortThreads;
       if (p < cnt) {
         const uint64_t kk = r_keys[p];
         const uint32_t g = s_gbase[(uint32_t)(kk >> shift) & mask] + p;
-        if (g < n) {
+        if (g >= sg.base && g < lim) {
           keys_out[g] = kk;
           vals_out[g] = r_vals[p];
         }
@@ -584,11 +621,11 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
   }
 }
 
-void launch_rts_scatter(int pass, const float* xyz, const uint64_t* keys_in,
-                        const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                        uint32_t n, const SortPlan& p, const uint32_t* offsets, bool stable,
-                        DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
-  if (n == 0) return;
+void launch_rts_scatter(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
+                        uint32_t ntiles, const uint64_t* keys_in, const uint32_t* vals_in,
+                        uint64_t* keys_out, uint32_t* vals_out, const uint32_t* offsets,
+                        bool stable, bool bulk, DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+  if (ntiles == 0) return;
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
@@ -604,26 +641,21 @@ void launch_rts_scatter(int pass, const float* xyz, const uint64_t* keys_in,
     if (sms <= 0) sms = 152;
     attr = true;
   }
-  const int shift = p.lo + pass * p.bits;
   uint32_t grid = (uint32_t)sms * 2u;
-  if (grid > p.ntiles) grid = p.ntiles;
-  // The bulk copies need 16-byte aligned sources; otherwise every tile takes
-  // the plain-load path.
+  if (grid > ntiles) grid = ntiles;
   if (pass == 0) {
-    const bool aligned = ((uintptr_t)xyz & 15u) == 0;
     if (stable)
       rts_scatter_kernel<true, true><<<grid, kSortThreads, kScatterSmem, s>>>(
-          xyz, nullptr, nullptr, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st,
-          wait_ns, aligned);
+          segs, slots, nslots, ntiles, 0, nullptr, nullptr, keys_out, vals_out, offsets, bulk,
+          st, wait_ns);
     else
       rts_scatter_kernel<true, false><<<grid, kSortThreads, kScatterSmem, s>>>(
-          xyz, nullptr, nullptr, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st,
-          wait_ns, aligned);
+          segs, slots, nslots, ntiles, 0, nullptr, nullptr, keys_out, vals_out, offsets, bulk,
+          st, wait_ns);
   } else {
-    const bool aligned = (((uintptr_t)keys_in | (uintptr_t)vals_in) & 15u) == 0;
     rts_scatter_kernel<false, true><<<grid, kSortThreads, kScatterSmem, s>>>(
-        nullptr, keys_in, vals_in, keys_out, vals_out, n, shift, p.bits, p.ntiles, offsets, st,
-        wait_ns, aligned);
+        segs, slots, nslots, ntiles, pass, keys_in, vals_in, keys_out, vals_out, offsets, bulk,
+        st, wait_ns);
   }
 }
 

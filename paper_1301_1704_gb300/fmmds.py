@@ -49,6 +49,10 @@ class TreeC(C.Structure):
     ]
 
 
+class SetC(C.Structure):
+    _fields_ = [("src", C.c_void_p), ("N", C.c_uint32), ("recv", C.c_void_p), ("M", C.c_uint32)]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
@@ -58,7 +62,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 # Every function declared in include/fmmds.h.
 EXPORTS = (
-    "fmm_create", "fmm_destroy", "fmm_build", "fmm_morton_keys", "fmm_query_workspace",
+    "fmm_create", "fmm_destroy", "fmm_build", "fmm_build_batched", "fmm_morton_keys",
+    "fmm_query_workspace",
     "fmm_set_tuning", "fmm_get_tuning", "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing",
     "fmm_last_launch_count", "fmm_status_string", "fmm_exclusive_scan_noalloc",
 )
@@ -96,6 +101,9 @@ def _load():
     lib.fmm_build.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, Params,
                               C.POINTER(TreeC), C.c_void_p]
     lib.fmm_build.restype = C.c_int
+    lib.fmm_build_batched.argtypes = [C.c_void_p, C.POINTER(SetC), C.c_uint32, Params,
+                                      C.POINTER(TreeC), C.c_void_p]
+    lib.fmm_build_batched.restype = C.c_int
     lib.fmm_morton_keys.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]
     lib.fmm_morton_keys.restype = C.c_int
     lib.fmm_query_workspace.argtypes = [C.c_uint32, C.c_uint32, Params, _u64p]
@@ -200,6 +208,20 @@ def _side(tc: TreeC, which: str, L: int, n: int) -> Side:
     return sd
 
 
+def _tree_from(tc: TreeC, n: int, m: int) -> Tree:
+    Lr = tc.L
+    tree = Tree(L=Lr, s_unmet=tc.s_unmet, src=_side(tc, "src", Lr, n),
+                recv=_side(tc, "recv", Lr, m), nnz_e2=list(tc.nnz_e2), nnz_e4=list(tc.nnz_e4),
+                e2_off={}, e2_idx={}, e4_off={}, e4_idx={})
+    for l in range(2, Lr + 1):
+        nr = tc.nbox_recv[l]
+        tree.e2_off[l] = _view(tc.e2_off[l], nr + 1, "<i4")
+        tree.e4_off[l] = _view(tc.e4_off[l], nr + 1, "<i4")
+        tree.e2_idx[l] = _view(tc.e2_idx[l], tc.nnz_e2[l], "<i4")
+        tree.e4_idx[l] = _view(tc.e4_idx[l], tc.nnz_e4[l], "<i4")
+    return tree
+
+
 class Context:
     """One fmm_ctx on one CUDA device, its arena backed by torch's allocator."""
 
@@ -266,17 +288,32 @@ class Context:
             raise FmmError(st, "fmm_build")
         if raw:
             return tc
-        Lr = tc.L
-        tree = Tree(L=Lr, s_unmet=tc.s_unmet, src=_side(tc, "src", Lr, n),
-                    recv=_side(tc, "recv", Lr, m), nnz_e2=list(tc.nnz_e2), nnz_e4=list(tc.nnz_e4),
-                    e2_off={}, e2_idx={}, e4_off={}, e4_idx={})
-        for l in range(2, Lr + 1):
-            nr = tc.nbox_recv[l]
-            tree.e2_off[l] = _view(tc.e2_off[l], nr + 1, "<i4")
-            tree.e4_off[l] = _view(tc.e4_off[l], nr + 1, "<i4")
-            tree.e2_idx[l] = _view(tc.e2_idx[l], tc.nnz_e2[l], "<i4")
-            tree.e4_idx[l] = _view(tc.e4_idx[l], tc.nnz_e4[l], "<i4")
-        return tree
+        return _tree_from(tc, n, m)
+
+    def build_batched(self, sets, L: int | None = None, s: int | None = None, stream=None,
+                      flags: int = 0, raw: bool = False):
+        """fmm_build_batched.  ``sets``: list of (src, recv) pairs of float32
+        [n, 3] CUDA tensors (the same tensor twice for an aliased set).
+        Returns one :class:`Tree` per set (or the raw ``TreeC`` array)."""
+        lib = _load()
+        if (L is None) == (s is None):
+            raise ValueError("give exactly one of L or s")
+        p = Params(L if L is not None else -1, s if s is not None else 0, flags, 0)
+        k = len(sets)
+        arr = (SetC * max(k, 1))()
+        for i, (a, b) in enumerate(sets):
+            for t in (a, b):
+                if t.dtype.itemsize != 4 or (t.numel() and not t.is_contiguous()):
+                    raise ValueError("points must be contiguous float32 [n, 3]")
+            arr[i] = SetC(a.data_ptr() if a.shape[0] else 0, a.shape[0],
+                          b.data_ptr() if b.shape[0] else 0, b.shape[0])
+        outs = (TreeC * max(k, 1))()
+        st = lib.fmm_build_batched(self._h, arr, k, p, outs, C.c_void_p(self._stream(stream)))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_build_batched")
+        if raw:
+            return outs
+        return [_tree_from(outs[i], sets[i][0].shape[0], sets[i][1].shape[0]) for i in range(k)]
 
     def morton_keys(self, xyz, out=None, stream=None):
         """fmm_morton_keys: int64 CUDA tensor carrying the uint64 keys."""

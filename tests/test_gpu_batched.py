@@ -1,0 +1,85 @@
+"""Batched builds: every set's result must equal the oracle's build of that
+set alone, bit for bit, and equal fmm_build of the set alone ("the same alone
+and in the mix")."""
+import numpy as np
+import pytest
+
+from paper_1301_1704_gb300 import workloads
+from tests.test_gpu_parity import compare_full
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1301_1704_gb300 import build, fmmds
+    build.build()
+    c = fmmds.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _mixed_sets(seed, k, lo=50, hi=40000):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(k):
+        n = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        kind = i % 3
+        gen = (workloads.uniform, workloads.sphere,
+               lambda m, sd: workloads.clumps(m, sd, nclumps=4, sigma=0.02))[kind]
+        out.append(gen(n, seed * 1000 + i))
+    return out
+
+
+def test_batched_aliased_cluster_size(ctx, orc):
+    pts = _mixed_sets(3, 24)
+    devs = [_dev(p) for p in pts]
+    trees = ctx.build_batched([(d, d) for d in devs], s=64)
+    for p, t in zip(pts, trees):
+        want = orc.build_tree(p, p, L=-1, s=64)
+        got = t.numpy()
+        assert (got["L"], got["s_unmet"]) == (want["L"], want["s_unmet"])
+        compare_full(got, want, want["L"])
+
+
+def test_batched_pairs_fixed_level(ctx, orc):
+    srcs = _mixed_sets(5, 9, lo=1, hi=20000)
+    recvs = _mixed_sets(6, 9, lo=1, hi=20000)
+    srcs[2] = np.zeros((0, 3), np.float32)  # an empty source set in the mix
+    pairs = [(_dev(a), _dev(b)) for a, b in zip(srcs, recvs)]
+    trees = ctx.build_batched(pairs, L=5)
+    for a, b, t in zip(srcs, recvs, trees):
+        compare_full(t.numpy(), orc.build_tree(a, b, L=5), 5)
+
+
+def test_batched_equals_alone(ctx):
+    pts = _mixed_sets(9, 6, lo=1000, hi=60000)
+    devs = [_dev(p) for p in pts]
+    mix = [t.numpy() for t in ctx.build_batched([(d, d) for d in devs], s=32)]
+    for d, got in zip(devs, mix):
+        alone = ctx.build(d, d, s=32).numpy()
+        compare_full(got, alone, alone["L"])
+
+
+def test_batched_long_boxes_and_deep_levels(ctx, orc):
+    # a tight clump needs levels past the first sort depth; identical points
+    # never meet s (capped at 21)
+    rng = np.random.default_rng(17)
+    tight = (0.5 + 1e-5 * rng.standard_normal((3000, 3))).astype(np.float32)
+    same = np.repeat(np.array([[0.25, 0.5, 0.75]], np.float32), 100, axis=0)
+    pts = [tight, same, workloads.uniform(5000, 18)]
+    devs = [_dev(p) for p in pts]
+    trees = ctx.build_batched([(d, d) for d in devs], s=8)
+    for p, t in zip(pts, trees):
+        want = orc.build_tree(p, p, L=-1, s=8)
+        got = t.numpy()
+        assert (got["L"], got["s_unmet"]) == (want["L"], want["s_unmet"])
+        compare_full(got, want, want["L"])
