@@ -232,6 +232,74 @@ def reference_arm(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def _pct(ms, q):
+    ms = sorted(ms)
+    return ms[min(len(ms) - 1, max(0, int(np.ceil(q * len(ms))) - 1))]
+
+
+def batched_section(ctx, stream, steps: int, warmup: int, plain_steps: int) -> dict:
+    """Batched workload: 512 aliased sets (sizes log-uniform in [1e3, 1e6],
+    uniform / sphere / clumps), cluster size s = 64, built by one
+    fmm_build_batched call per step, against the same sets built one
+    fmm_build call at a time (per-instance plain launches)."""
+    import torch
+    from paper_1301_1704_gb300 import workloads
+    sets, kinds = workloads.batch_sets(workloads.CONFIG_SEEDS[4])
+    devs = [torch.from_numpy(p).cuda() for p in sets]
+    pairs = [(d, d) for d in devs]
+    npts = int(sum(len(p) for p in sets))  # aliased: each point counted once
+    batch = ctx.batch(pairs)
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        launches = 0
+        torch.cuda.synchronize()
+        for a, b in ev:
+            a.record(stream)
+            launches += fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], launches
+
+    def one_batched():
+        ctx.build_batched(batch, s=64, stream=stream, raw=True)
+        return ctx.last_launch_count()
+
+    def one_plain():
+        n = 0
+        for d in devs:
+            ctx.build(d, d, s=64, stream=stream, raw=True)
+            n += ctx.last_launch_count()
+        return n
+
+    for _ in range(warmup):
+        one_batched()
+    bt, bl = timed(one_batched, steps)
+    for _ in range(min(warmup, 2)):
+        one_plain()
+    pt, pl = timed(one_plain, plain_steps)
+    out = {}
+    for name, t, nl in (("batched", bt, bl), ("plain", pt, pl)):
+        p50 = _pct(t, 0.5)
+        out[name] = {"value": npts / (sum(t) / len(t) / 1e3) / 1e6, "unit": "Mpts/s",
+                     "p50_ms": p50, "p99_ms": _pct(t, 0.99), "steps": len(t),
+                     "gpu_launches_per_step": nl / len(t)}
+    ctx.reset_timing()
+    ctx.set_timing(True)
+    for _ in range(3):
+        one_batched()
+    torch.cuda.synchronize()
+    ctx.set_timing(False)
+    out["batched"]["kernel_ms_per_step"] = {k: v[1] / 3 for k, v in sorted(ctx.timing().items())}
+    out["workload"] = ("512 aliased sets, sizes log-uniform in [1e3, 1e6], uniform / sphere / "
+                       "clumps with p = 1/3, s = 64 (per-set L); batched = one fmm_build_batched "
+                       "call, plain = one fmm_build call per set")
+    out["points"] = npts
+    out["speedup_vs_plain"] = out["batched"]["value"] / out["plain"]["value"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -244,6 +312,9 @@ def main():
                     help="points per set (default 2^24; smaller values only for profiling)")
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--sort-kind", type=int, default=None, help="0 reduce-then-scan, 1 onesweep")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
+    ap.add_argument("--plain-steps", type=int, default=5,
+                    help="steps of the per-instance comparison of the batched workload")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -327,8 +398,16 @@ def main():
     peak, peak_kind = _peaks()
     alg = _algorithmic_bytes(tree)
     def alg_of(name):
-        if name in ("onesweep", "rts_scatter"):
-            return 24 * pts_per_step * (ktimes[name][0] / args.steps) / 2
+        # A radix pass reads and writes 12 bytes per point: the coordinates,
+        # then (u64 key, u32 index).  rts_scatter sorts both sets in one launch
+        # per pass, onesweep one set per launch.
+        per_build = ktimes[name][0] / args.steps
+        if name == "rts_scatter":
+            return 24 * pts_per_step * per_build
+        if name == "onesweep":
+            return 24 * pts_per_step * per_build / 2
+        if name == "tile_hist":  # first pass reads the coordinates, later ones the keys
+            return pts_per_step * (12 + 8 * (per_build - 1))
         return _kernel_alg_bytes(name, tree)
 
     measured = {k: v for k, v in ktimes.items() if alg_of(k) is not None}
@@ -364,6 +443,9 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_val = pts_per_step * args.e2e_steps * ws / (e2e_ms / 1e3) / 1e6 if args.e2e_steps else None
+    batched = None
+    if not args.no_batched:
+        batched = batched_section(ctx, stream, args.steps, args.warmup, args.plain_steps)
 
     if rank == 0:
         line = {
@@ -389,6 +471,8 @@ def main():
         }
         if not args.no_cpu_baseline and ws == 1 and (npts, level) == (N_PTS, LEVEL):
             line["cpu_baseline"] = cpu_baseline()
+        if batched is not None:
+            line["batched"] = batched
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

@@ -285,6 +285,7 @@ struct BuildMem {
   Slot* pass_slots[8] = {};
   uint32_t pass_nslots[8] = {}, pass_tiles[8] = {};
   uint32_t* pass_hist[8] = {};
+  TileRec* pass_recs[8] = {};
   size_t pass_hist_len[8] = {};
   uint64_t* pass_scan[8] = {};
   uint32_t* pass_cnt = nullptr;  // scan tickets, one per pass
@@ -434,7 +435,7 @@ int run_sort(fmm_ctx* c, std::vector<SetPlan>& sets, BuildMem& m, bool stall, ui
     {
       Launch L(c, "tile_hist");
       launch_tile_hist(p, m.segs, m.pass_slots[p], m.pass_nslots[p], m.pass_tiles[p],
-                       m.pass_hist[p], kin, c->st, s);
+                       m.pass_hist[p], kin, m.pass_recs[p], c->st, s);
     }
     {
       Launch L(c, "scan");
@@ -444,8 +445,8 @@ int run_sort(fmm_ctx* c, std::vector<SetPlan>& sets, BuildMem& m, bool stall, ui
     // The first pass may leave equal digits in any order when a finishing
     // sort follows; sets sorted in full keep every pass stable.
     Launch L(c, "rts_scatter");
-    launch_rts_scatter(p, m.segs, m.pass_slots[p], m.pass_nslots[p], m.pass_tiles[p], kin, vin,
-                       kout, vout, m.pass_hist[p], any_full || p > 0, true, c->st, wait_ns, s);
+    launch_rts_scatter(p, m.pass_recs[p], m.pass_tiles[p], kin, vin, kout, vout, m.pass_hist[p],
+                       any_full || p > 0, true, c->st, wait_ns, s);
   }
   return FMM_OK;
 }
@@ -514,6 +515,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   for (int p = 0; p < m.max_passes; ++p) {
     m.pass_scan[p] = reinterpret_cast<uint64_t*>(zero + scan_off[p]);
     m.pass_hist[p] = arena_get<uint32_t>(c, tab.hist_len[p] + 1, &err);
+    m.pass_recs[p] = arena_get<TileRec>(c, tab.tiles[p], &err);
     m.pass_hist_len[p] = tab.hist_len[p];
     m.pass_tiles[p] = tab.tiles[p];
     m.pass_nslots[p] = (uint32_t)tab.slots[p].size();
@@ -1006,6 +1008,7 @@ int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes
     if (p.flags & FMM_FLAG_HOST_INPUT) total += align_up(12 * n);
     total += 2 * align_up(12 * n + 48) + align_up(4 * n) + (16 << 10);
     total += (n / kSortTile + 1) * kRadixMax * 4 * 3 + (n / kBoxTile + 1) * 8 * (1 + kLevels);
+    total += (n / kSortTile + 1) * sizeof(TileRec) * 8 + 8 * 256;  // tile records, 8 passes
     for (int l = 0; l <= L; ++l) total += align_up(21ull * level_cap(ns[k], l) + 8) + 1024;
   }
   for (int l = 2; l <= L; ++l)

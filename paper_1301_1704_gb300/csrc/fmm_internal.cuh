@@ -295,6 +295,23 @@ struct Slot {
   uint32_t aux1;   // per-kernel: position correction, ...
 };
 
+// What the scatter of one radix pass needs about one tile, written by the
+// pass's histogram kernel so that the scatter reads one record per tile
+// instead of searching the slot table and the set descriptor.
+struct alignas(16) TileRec {
+  const float* xyz;  // the tile's first point (first pass)
+  uint32_t first;    // the tile's first slot in the concatenated sort arrays
+  uint32_t local;    // its first point index within the set
+  uint32_t cnt;      // points in the tile
+  uint32_t shift;    // lowest key bit of this pass's digit
+  uint32_t hist;     // scanned offset of (digit 0, tile); digit d at hist + d * hstride
+  uint32_t hstride;
+  uint32_t corr;     // added to scanned offsets: set base minus earlier sets' points
+  uint32_t lo, hi;   // the set's slots [lo, hi)
+  uint32_t pad;
+};
+static_assert(sizeof(TileRec) == 48, "TileRec layout");
+
 // Slot holding work unit u: slots[k].unit0 <= u < slots[k+1].unit0.
 __device__ __forceinline__ uint32_t find_slot(const Slot* slots, uint32_t nslots, uint32_t u) {
   uint32_t lo = 0, hi = nslots;  // answer in [lo, hi)
@@ -363,15 +380,17 @@ __host__ __device__ inline int passes_for(int Ls) { return (3 * Ls + kRadixBits 
 // Reduce-then-scan radix pass p over the sets of `slots` (units = sort tiles;
 // aux0 = first histogram entry of the set, aux1 = scan-to-slot correction):
 // per-tile digit histograms, digit-major per set, set after set.
+// Per-tile digit counts of pass p, and the tiles' records for the scatter.
 void launch_tile_hist(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
-                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, DevStatus* st,
-                      cudaStream_t s);
+                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, TileRec* recs,
+                      DevStatus* st, cudaStream_t s);
 // Scatter of pass p from `in` (or the coordinates) to `out` (concatenated
-// arrays).  stable = false only for a first pass that a finishing sort follows.
-void launch_rts_scatter(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
-                        uint32_t ntiles, const uint64_t* keys_in, const uint32_t* vals_in,
-                        uint64_t* keys_out, uint32_t* vals_out, const uint32_t* offsets,
-                        bool stable, bool bulk, DevStatus* st, uint64_t wait_ns, cudaStream_t s);
+// arrays of `slots_total` entries).  stable = false only for a first pass
+// that a finishing sort follows.
+void launch_rts_scatter(int pass, const TileRec* recs, uint32_t ntiles, const uint64_t* keys_in,
+                        const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                        const uint32_t* offsets, bool stable, bool bulk, DevStatus* st,
+                        uint64_t wait_ns, cudaStream_t s);
 
 // Onesweep pass over one set (keys_in / keys_out point at the set's slots).
 struct SortPlan {

@@ -182,20 +182,6 @@ void launch_job_prefix(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
   job_prefix_kernel<<<1, 1024, 0, s>>>(segs, jobs, njobs, l, lvls, st);
 }
 
-// Each warp takes a contiguous run of the level's parents (over all jobs) and
-// walks it, switching job descriptors as it crosses job boundaries.
-struct WarpRange {
-  uint32_t g0, g1;
-};
-
-__device__ __forceinline__ WarpRange warp_range(uint32_t total) {
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t per = (total + nw - 1) / nw;
-  const uint64_t a = (uint64_t)gw * per, b = a + per;
-  return WarpRange{(uint32_t)(a < total ? a : total), (uint32_t)(b < total ? b : total)};
-}
-
 // Counts: per receiver child r of parent p, |E2(r)| = sum over the parent's
 // neighbours Q of popc(occ(Q) & mask(delta_Q, rho_r)), and |E2| + |E4| = the
 // number of non-empty children of all Q.  The eight possible sibling octants
@@ -207,18 +193,22 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(const Seg* __r
                                                                  DevStatus* st) {
   if (failed(st)) return;  // set before this launch: the same for every thread
   const int lane = threadIdx.x & 31;
-  const ListLevel& LV = lvls[l];
-  const WarpRange wr = warp_range(LV.jprefix[njobs]);
-  if (wr.g0 >= wr.g1) return;
-  uint32_t j = find_job(LV.jprefix, njobs, wr.g0);
-  ListCtx a = make_ctx(segs, jobs[j], l, lvls, j);
-  uint32_t jstart = LV.jprefix[j], jend = LV.jprefix[j + 1];
-  for (uint32_t g = wr.g0; g < wr.g1; ++g) {
-    while (g >= jend) {
-      ++j;
+  // The level's arrays in registers: stores through them must not force
+  // reloads of the descriptor.
+  const uint32_t* const jprefix = lvls[l].jprefix;
+  uint32_t* const work2 = lvls[l].work2;
+  uint32_t* const work4 = lvls[l].work4;
+  const uint32_t total = jprefix[njobs];
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  uint32_t j = 0, jstart = 0, jend = 0;
+  ListCtx a{};
+  for (uint32_t g = gw; g < total; g += nw) {
+    if (g >= jend) {  // g only grows: look its job up when it leaves the current one
+      j = find_job(jprefix, njobs, g);
       a = make_ctx(segs, jobs[j], l, lvls, j);
-      jstart = jend;
-      jend = LV.jprefix[j + 1];
+      jstart = jprefix[j];
+      jend = jprefix[j + 1];
     }
     const uint32_t p = g - jstart;
     const Neighbour q = load_neighbour(a, l, p, lane);
@@ -237,8 +227,8 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(const Seg* __r
     if (r < c1) {
       const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
       const uint32_t n2 = ((rho < 4 ? lo : hi) >> (8 * (rho & 3))) & 0xffu;
-      LV.work2[a.region + r] = n2;
-      LV.work4[a.region + r] = tot - n2;
+      work2[a.region + r] = n2;
+      work4[a.region + r] = tot - n2;
     }
   }
 }
@@ -255,7 +245,16 @@ constexpr int kCand = 27 * 8;  // at most 27 neighbours x 8 children
 constexpr int kNear = 64;      // candidates in some sibling's E2: the 4x4x4 block
 constexpr int kListWarps = kListThreads / 32;
 
-__global__ void __launch_bounds__(kListThreads) list_fill_kernel(const Seg* __restrict__ segs,
+// A warp's current job in the fill kernel.
+struct WarpJob {
+  ListCtx a;
+  uint32_t* out2;  // the job's row starts, level l
+  uint32_t* out4;
+  uint32_t G2, G4;  // the job's first entries in the level's lists
+  uint32_t j, jstart, jend;
+};
+
+__global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* __restrict__ segs,
                                                                 const Job* __restrict__ jobs,
                                                                 uint32_t njobs, int l,
                                                                 const ListLevel* lvls,
@@ -264,58 +263,78 @@ __global__ void __launch_bounds__(kListThreads) list_fill_kernel(const Seg* __re
   __shared__ uint8_t s_sib[kListWarps][kCand];
   __shared__ uint32_t s_nrank[kListWarps][kNear];
   __shared__ uint8_t s_nsib[kListWarps][kNear];
+  __shared__ WarpJob s_job[kListWarps];
   if (failed(st)) return;  // set before this launch: the same for every thread
   const ListLevel& LV = lvls[l];
   if ((LV.total[0] >> 32) != 0 || (LV.total[1] >> 32) != 0) return;  // capacity error set
+  // The level's arrays in registers: the list stores must not force reloads
+  // of the descriptor.
+  const uint32_t* const jprefix = LV.jprefix;
+  const uint32_t* const work2 = LV.work2;
+  const uint32_t* const work4 = LV.work4;
+  uint32_t* const idx2 = LV.idx2;
+  uint32_t* const idx4 = LV.idx4;
+  uint64_t* const lbase = LV.base;
+  uint64_t* const lnnz = LV.nnz;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   uint32_t* crank = s_rank[warp];
   uint8_t* csib = s_sib[warp];
   uint32_t* nrank = s_nrank[warp];
   uint8_t* nsibm = s_nsib[warp];
-  const WarpRange wr = warp_range(LV.jprefix[njobs]);
-  if (wr.g0 >= wr.g1) return;
-  uint32_t j = find_job(LV.jprefix, njobs, wr.g0);
-  ListCtx a = make_ctx(segs, jobs[j], l, lvls, j);
-  uint32_t jstart = LV.jprefix[j], jend = LV.jprefix[j + 1];
-  uint32_t* out2 = jobs[j].out2[l];
-  uint32_t* out4 = jobs[j].out4[l];
-  uint32_t G2 = LV.work2[a.region], G4 = LV.work4[a.region];
-  for (uint32_t g = wr.g0; g < wr.g1; ++g) {
-    while (g >= jend) {
-      ++j;
-      a = make_ctx(segs, jobs[j], l, lvls, j);
-      jstart = jend;
-      jend = LV.jprefix[j + 1];
-      out2 = jobs[j].out2[l];
-      out4 = jobs[j].out4[l];
-      G2 = LV.work2[a.region];
-      G4 = LV.work4[a.region];
+  const uint32_t npar = jprefix[njobs];
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  // The warp's current job lives in shared memory, not in registers: the
+  // list loops below need the registers for the eight siblings' cursors.
+  WarpJob& J = s_job[warp];
+  uint32_t jend = 0;
+  // Parents are dealt round-robin to the warps, so the warps in flight work on
+  // neighbouring parents and their list stores land close together.
+  for (uint32_t g = gw; g < npar; g += nw) {
+    if (g >= jend) {  // g only grows: look its job up when it leaves the current one
+      if (lane == 0) {
+        const uint32_t j = find_job(jprefix, njobs, g);
+        J.a = make_ctx(segs, jobs[j], l, lvls, j);
+        J.j = j;
+        J.jstart = jprefix[j];
+        J.jend = jprefix[j + 1];
+        J.out2 = jobs[j].out2[l];
+        J.out4 = jobs[j].out4[l];
+        J.G2 = work2[J.a.region];
+        J.G4 = work4[J.a.region];
+      }
+      __syncwarp();
+      jend = J.jend;
     }
-    const uint32_t p = g - jstart;
+    const uint32_t p = g - J.jstart;
+    const uint32_t region = J.a.region, G2 = J.G2, G4 = J.G4;
+    uint32_t* const out2 = J.out2;
+    uint32_t* const out4 = J.out4;
     // The receiver children of p (at most 8): lane j fetches child j's octant
     // and list starts up front, so their loads overlap the neighbour loads.
-    const uint32_t c0 = a.rchild_up[p], c1 = a.rchild_up[p + 1];
+    const uint32_t c0 = J.a.rchild_up[p], c1 = J.a.rchild_up[p + 1];
     uint32_t my_rho = 0, my_o2 = 0, my_o4 = 0;
     if (c0 + lane < c1) {
-      my_rho = (uint32_t)(a.rkey[c0 + lane] & 7u);
-      my_o2 = LV.work2[a.region + c0 + lane];
-      my_o4 = LV.work4[a.region + c0 + lane];
+      my_rho = (uint32_t)(J.a.rkey[c0 + lane] & 7u);
+      my_o2 = work2[region + c0 + lane];
+      my_o4 = work4[region + c0 + lane];
       out2[c0 + lane] = my_o2 - G2;
       out4[c0 + lane] = my_o4 - G4;
     }
     if (g + 1 == jend) {  // the job's last parent closes its rows
-      const uint32_t e2 = LV.work2[a.region + a.nrecv], e4 = LV.work4[a.region + a.nrecv];
+      const uint32_t nrecv = J.a.nrecv, j = J.j;
+      const uint32_t e2 = work2[region + nrecv], e4 = work4[region + nrecv];
       if (lane == 0) {
-        out2[a.nrecv] = e2 - G2;
-        out4[a.nrecv] = e4 - G4;
-        LV.base[2 * j] = G2;
-        LV.base[2 * j + 1] = G4;
-        LV.nnz[2 * j] = e2 - G2;
-        LV.nnz[2 * j + 1] = e4 - G4;
+        out2[nrecv] = e2 - G2;
+        out4[nrecv] = e4 - G4;
+        lbase[2 * j] = G2;
+        lbase[2 * j + 1] = G4;
+        lnnz[2 * j] = e2 - G2;
+        lnnz[2 * j + 1] = e4 - G4;
       }
     }
-    const Neighbour q = load_neighbour(a, l, p, lane);
+    const Neighbour q = load_neighbour(J.a, l, p, lane);
     const uint32_t nsib = c1 - c0;
 
     // Candidates C (children of p's neighbours, ascending rank) and the near
@@ -364,7 +383,7 @@ __global__ void __launch_bounds__(kListThreads) list_fill_kernel(const Seg* __re
       for (int jj = 0; jj < 8; ++jj) {  // absent siblings have sbit 0: nothing stored
         const bool in2 = (sb & sbit[jj]) != 0u;
         const uint32_t b2 = __ballot_sync(0xffffffffu, in2);
-        st_cs_if(LV.idx2 + w2[jj] + __popc(b2 & lt), v, in2);
+        st_cs_if(idx2 + w2[jj] + __popc(b2 & lt), v, in2);
         w2[jj] += __popc(b2);
       }
     }
@@ -377,7 +396,7 @@ __global__ void __launch_bounds__(kListThreads) list_fill_kernel(const Seg* __re
       for (int jj = 0; jj < 8; ++jj) {  // absent siblings: in4 is false everywhere
         const bool in4 = (sb & sbit[jj]) == 0u && (uint32_t)jj < nsib;
         const uint32_t b4 = __ballot_sync(0xffffffffu, in4);
-        st_cs_if(LV.idx4 + w4[jj] + __popc(b4 & lt), v, in4);
+        st_cs_if(idx4 + w4[jj] + __popc(b4 & lt), v, in4);
         w4[jj] += __popc(b4);
       }
     }

@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(const Seg* __restrict__ 
                                                         uint32_t nslots, int pass,
                                                         const uint64_t* __restrict__ keys,
                                                         uint32_t* __restrict__ hist,
+                                                        TileRec* __restrict__ recs,
                                                         DevStatus* st) {
   __shared__ uint32_t sh[kRadixMax];
   for (int i = threadIdx.x; i < kRadixMax; i += blockDim.x) sh[i] = 0;
@@ -338,9 +339,24 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(const Seg* __restrict__ 
   const uint32_t t = blockIdx.x - sl.unit0;  // tile of the set
   const uint32_t n = sg.n;
   const int shift = sg.lo + kRadixBits * pass;
-  __syncthreads();
   const uint64_t base = (uint64_t)t * kSortTile;
   const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
+  if (threadIdx.x == 0) {
+    TileRec r;
+    r.xyz = sg.xyz ? sg.xyz + 3 * base : nullptr;
+    r.first = sg.base + (uint32_t)base;
+    r.local = (uint32_t)base;
+    r.cnt = cnt;
+    r.shift = (uint32_t)shift;
+    r.hist = sl.aux0 + t;
+    r.hstride = sg.ntiles;
+    r.corr = sl.aux1;
+    r.lo = sg.base;
+    r.hi = sg.base + n;
+    r.pad = 0;
+    recs[blockIdx.x] = r;
+  }
+  __syncthreads();
   bool bad = false;
   if (kFromXyz) {
     const float* xyz = sg.xyz;
@@ -381,13 +397,15 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(const Seg* __restrict__ 
 }
 
 void launch_tile_hist(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
-                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, DevStatus* st,
-                      cudaStream_t s) {
+                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, TileRec* recs,
+                      DevStatus* st, cudaStream_t s) {
   if (ntiles == 0) return;
   if (pass == 0)
-    tile_hist_kernel<true><<<ntiles, 256, 0, s>>>(segs, slots, nslots, 0, nullptr, hist, st);
+    tile_hist_kernel<true><<<ntiles, 256, 0, s>>>(segs, slots, nslots, 0, nullptr, hist, recs,
+                                                  st);
   else
-    tile_hist_kernel<false><<<ntiles, 256, 0, s>>>(segs, slots, nslots, pass, keys, hist, st);
+    tile_hist_kernel<false><<<ntiles, 256, 0, s>>>(segs, slots, nslots, pass, keys, hist, recs,
+                                                   st);
 }
 
 // Scatter of one pass, persistent: each block walks the tiles u = blockIdx.x,
@@ -405,8 +423,7 @@ constexpr size_t kScatterSmem = 2 * (size_t)kInBytes;
 // first one).
 template <bool kFromXyz, bool kStable>
 __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
-    const Seg* __restrict__ segs, const Slot* __restrict__ slots, uint32_t nslots,
-    uint32_t ntiles, int pass, const uint64_t* __restrict__ keys_in,
+    const TileRec* __restrict__ recs, uint32_t ntiles, const uint64_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ offsets, bool bulk,
     DevStatus* st, uint64_t wait_ns) {
@@ -430,67 +447,55 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
   __syncthreads();
   if (s_fail) return;  // an earlier kernel failed (domain error): leave the outputs alone
 
-  // Whether unit u is a full tile read by bulk copy; its source and slot.
-  auto bulk_src = [&](uint32_t u, const unsigned char** src) -> bool {
-    if (!bulk) return false;
-    const Slot sl = slots[find_slot(slots, nslots, u)];
-    const Seg& sg = segs[sl.seg];
-    const uint32_t t = u - sl.unit0;
-    if ((uint64_t)(t + 1) * kSortTile > sg.n) return false;
-    if (kFromXyz) {
-      if (((uintptr_t)sg.xyz & 15u) != 0) return false;
-      *src = reinterpret_cast<const unsigned char*>(sg.xyz + 3ull * t * kSortTile);
-    } else {
-      *src = reinterpret_cast<const unsigned char*>(keys_in + sg.base + (uint64_t)t * kSortTile);
-      src[1] = reinterpret_cast<const unsigned char*>(vals_in + sg.base + (uint64_t)t * kSortTile);
-    }
-    return true;
+  // Whether a tile is full and read by bulk copy (its source 16-byte aligned).
+  auto is_bulk = [&](const TileRec& r) -> bool {
+    if (!bulk || r.cnt != kSortTile) return false;
+    return kFromXyz ? ((uintptr_t)r.xyz & 15u) == 0 : true;  // set bases: multiples of 4 slots
   };
-  auto issue = [&](const unsigned char* const* src, int b) {  // thread 0 only
+  auto issue = [&](const TileRec& r, int b) {  // thread 0 only
     unsigned char* dst = s_in + b * kInBytes;
     mbar_expect_tx(&s_bar[b], kInBytes);
     if (kFromXyz) {
-      bulk_load(dst, src[0], kInBytes, &s_bar[b]);
+      bulk_load(dst, r.xyz, kInBytes, &s_bar[b]);
     } else {
-      bulk_load(dst, src[0], kSortTile * 8, &s_bar[b]);
-      bulk_load(dst + kSortTile * 8, src[1], kSortTile * 4, &s_bar[b]);
+      bulk_load(dst, keys_in + r.first, kSortTile * 8, &s_bar[b]);
+      bulk_load(dst + kSortTile * 8, vals_in + r.first, kSortTile * 4, &s_bar[b]);
     }
   };
   uint32_t phase[2] = {0u, 0u};
   bool pending[2] = {false, false};
   uint32_t u = blockIdx.x;
-  {
-    const unsigned char* src[2] = {nullptr, nullptr};
-    if (u < ntiles && bulk_src(u, src)) {
-      if (threadIdx.x == 0) issue(src, 0);
+  TileRec rec;
+  if (u < ntiles) {
+    rec = recs[u];
+    if (is_bulk(rec)) {
+      if (threadIdx.x == 0) issue(rec, 0);
       pending[0] = true;
     }
   }
   for (int it = 0; u < ntiles; u += gridDim.x, ++it) {
     const int b = it & 1;
     unsigned char* buf = s_in + b * kInBytes;
-    const Slot sl = slots[find_slot(slots, nslots, u)];
-    const Seg& sg = segs[sl.seg];
-    const uint32_t t = u - sl.unit0;
-    const uint32_t n = sg.n;
-    const int shift = sg.lo + kRadixBits * pass;
-    const uint64_t base = (uint64_t)t * kSortTile;
-    const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
+    const TileRec r = rec;
+    const uint32_t cnt = r.cnt;
+    const int shift = (int)r.shift;
     const bool full = pending[b];
     {
       const uint32_t un = u + gridDim.x;
-      const unsigned char* src[2] = {nullptr, nullptr};
-      if (un < ntiles && bulk_src(un, src)) {
-        if (threadIdx.x == 0) {
-          fence_proxy_async();
-          issue(src, b ^ 1);
+      if (un < ntiles) {
+        rec = recs[un];
+        if (is_bulk(rec)) {
+          if (threadIdx.x == 0) {
+            fence_proxy_async();
+            issue(rec, b ^ 1);
+          }
+          pending[b ^ 1] = true;
         }
-        pending[b ^ 1] = true;
       }
     }
     const uint32_t my_off =
         threadIdx.x < kRadixMax
-            ? __ldg(offsets + sl.aux0 + (uint64_t)threadIdx.x * sg.ntiles + t) + sl.aux1
+            ? __ldg(offsets + r.hist + (uint64_t)threadIdx.x * r.hstride) + r.corr
             : 0u;
     for (int i = threadIdx.x; i < W * kRadixMax; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
     bool ok = true;
@@ -515,19 +520,18 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     for (int k = 0; k < kSortItems; ++k) {
       const uint32_t j = (uint32_t)warp * (kSortItems * 32) + k * 32 + lane;
       key[k] = 0;
-      val[k] = (uint32_t)(base + j);
+      val[k] = r.local + j;
       if (j < cnt) {
         if (kFromXyz) {
-          const float* f =
-              full ? reinterpret_cast<const float*>(buf) + 3 * j : sg.xyz + 3 * (base + j);
+          const float* f = full ? reinterpret_cast<const float*>(buf) + 3 * j : r.xyz + 3 * j;
           bool okk;
           key[k] = morton_key(f[0], f[1], f[2], &okk);
         } else if (full) {
           key[k] = reinterpret_cast<const uint64_t*>(buf)[j];
           val[k] = reinterpret_cast<const uint32_t*>(buf + kSortTile * 8)[j];
         } else {
-          key[k] = keys_in[sg.base + base + j];
-          val[k] = vals_in[sg.base + base + j];
+          key[k] = keys_in[r.first + j];
+          val[k] = vals_in[r.first + j];
         }
       }
     }
@@ -604,14 +608,13 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
       }
     }
     __syncthreads();
-    const uint32_t lim = sg.base + n;  // this set's slots end here
 #pragma unroll 2
     for (int j = 0; j < kSortItems; ++j) {
       const uint32_t p = threadIdx.x + j * kSortThreads;
       if (p < cnt) {
         const uint64_t kk = r_keys[p];
         const uint32_t g = s_gbase[(uint32_t)(kk >> shift) & mask] + p;
-        if (g >= sg.base && g < lim) {
+        if (g >= r.lo && g < r.hi) {  // inside the set's slots
           keys_out[g] = kk;
           vals_out[g] = r_vals[p];
         }
@@ -621,10 +624,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
   }
 }
 
-void launch_rts_scatter(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
-                        uint32_t ntiles, const uint64_t* keys_in, const uint32_t* vals_in,
-                        uint64_t* keys_out, uint32_t* vals_out, const uint32_t* offsets,
-                        bool stable, bool bulk, DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+void launch_rts_scatter(int pass, const TileRec* recs, uint32_t ntiles, const uint64_t* keys_in,
+                        const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                        const uint32_t* offsets, bool stable, bool bulk, DevStatus* st,
+                        uint64_t wait_ns, cudaStream_t s) {
   if (ntiles == 0) return;
   static bool attr = false;
   static int sms = 0;
@@ -646,16 +649,13 @@ void launch_rts_scatter(int pass, const Seg* segs, const Slot* slots, uint32_t n
   if (pass == 0) {
     if (stable)
       rts_scatter_kernel<true, true><<<grid, kSortThreads, kScatterSmem, s>>>(
-          segs, slots, nslots, ntiles, 0, nullptr, nullptr, keys_out, vals_out, offsets, bulk,
-          st, wait_ns);
+          recs, ntiles, nullptr, nullptr, keys_out, vals_out, offsets, bulk, st, wait_ns);
     else
       rts_scatter_kernel<true, false><<<grid, kSortThreads, kScatterSmem, s>>>(
-          segs, slots, nslots, ntiles, 0, nullptr, nullptr, keys_out, vals_out, offsets, bulk,
-          st, wait_ns);
+          recs, ntiles, nullptr, nullptr, keys_out, vals_out, offsets, bulk, st, wait_ns);
   } else {
     rts_scatter_kernel<false, true><<<grid, kSortThreads, kScatterSmem, s>>>(
-        segs, slots, nslots, ntiles, pass, keys_in, vals_in, keys_out, vals_out, offsets, bulk,
-        st, wait_ns);
+        recs, ntiles, keys_in, vals_in, keys_out, vals_out, offsets, bulk, st, wait_ns);
   }
 }
 

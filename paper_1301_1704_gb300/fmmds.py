@@ -53,6 +53,24 @@ class SetC(C.Structure):
     _fields_ = [("src", C.c_void_p), ("N", C.c_uint32), ("recv", C.c_void_p), ("M", C.c_uint32)]
 
 
+class Batch:
+    """fmm_set array (and result array) of a list of (src, recv) tensor pairs."""
+
+    def __init__(self, sets):
+        self.k = len(sets)
+        self.arr = (SetC * max(self.k, 1))()
+        self.outs = (TreeC * max(self.k, 1))()
+        self.sizes = []
+        self._keep = list(sets)
+        for i, (a, b) in enumerate(sets):
+            for t in (a, b):
+                if t.dtype.itemsize != 4 or (t.numel() and not t.is_contiguous()):
+                    raise ValueError("points must be contiguous float32 [n, 3]")
+            self.arr[i] = SetC(a.data_ptr() if a.shape[0] else 0, a.shape[0],
+                               b.data_ptr() if b.shape[0] else 0, b.shape[0])
+            self.sizes.append((a.shape[0], b.shape[0]))
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
@@ -290,30 +308,29 @@ class Context:
             return tc
         return _tree_from(tc, n, m)
 
+    def batch(self, sets) -> "Batch":
+        """The fmm_set array of a list of (src, recv) pairs of float32 [n, 3]
+        CUDA tensors, built once for repeated fmm_build_batched calls on the
+        same tensors (the tensors must stay alive and in place)."""
+        return Batch(sets)
+
     def build_batched(self, sets, L: int | None = None, s: int | None = None, stream=None,
                       flags: int = 0, raw: bool = False):
         """fmm_build_batched.  ``sets``: list of (src, recv) pairs of float32
-        [n, 3] CUDA tensors (the same tensor twice for an aliased set).
-        Returns one :class:`Tree` per set (or the raw ``TreeC`` array)."""
+        [n, 3] CUDA tensors (the same tensor twice for an aliased set), or a
+        :class:`Batch` of them.  Returns one :class:`Tree` per set (or the
+        raw ``TreeC`` array)."""
         lib = _load()
         if (L is None) == (s is None):
             raise ValueError("give exactly one of L or s")
         p = Params(L if L is not None else -1, s if s is not None else 0, flags, 0)
-        k = len(sets)
-        arr = (SetC * max(k, 1))()
-        for i, (a, b) in enumerate(sets):
-            for t in (a, b):
-                if t.dtype.itemsize != 4 or (t.numel() and not t.is_contiguous()):
-                    raise ValueError("points must be contiguous float32 [n, 3]")
-            arr[i] = SetC(a.data_ptr() if a.shape[0] else 0, a.shape[0],
-                          b.data_ptr() if b.shape[0] else 0, b.shape[0])
-        outs = (TreeC * max(k, 1))()
-        st = lib.fmm_build_batched(self._h, arr, k, p, outs, C.c_void_p(self._stream(stream)))
+        b = sets if isinstance(sets, Batch) else Batch(sets)
+        st = lib.fmm_build_batched(self._h, b.arr, b.k, p, b.outs, C.c_void_p(self._stream(stream)))
         if st != FMM_OK:
             raise FmmError(st, "fmm_build_batched")
         if raw:
-            return outs
-        return [_tree_from(outs[i], sets[i][0].shape[0], sets[i][1].shape[0]) for i in range(k)]
+            return b.outs
+        return [_tree_from(b.outs[i], b.sizes[i][0], b.sizes[i][1]) for i in range(b.k)]
 
     def morton_keys(self, xyz, out=None, stream=None):
         """fmm_morton_keys: int64 CUDA tensor carrying the uint64 keys."""
