@@ -285,6 +285,23 @@ def batched_section(ctx, stream, steps: int, warmup: int, plain_steps: int) -> d
         out[name] = {"value": npts / (sum(t) / len(t) / 1e3) / 1e6, "unit": "Mpts/s",
                      "p50_ms": p50, "p99_ms": _pct(t, 0.99), "steps": len(t),
                      "gpu_launches_per_step": nl / len(t)}
+    # Compulsory bytes of one batched build (aliased sets read and written once).
+    outs = ctx.build_batched(batch, s=64, stream=stream, raw=True)
+    torch.cuda.synchronize()
+    alg, nnz2, nnz4, levels = 0, 0, 0, []
+    for i in range(len(sets)):
+        t = outs[i]
+        n = t.n_src
+        alg += 16 * n
+        levels.append(t.L)
+        for l in range(t.L + 1):
+            alg += 16 * t.nbox_src[l] + 4
+        for l in range(2, t.L + 1):
+            nnz2 += t.nnz_e2[l]
+            nnz4 += t.nnz_e4[l]
+            alg += 8 * (t.nbox_recv[l] + 1)
+    alg += 4 * (nnz2 + nnz4)
+    peak, peak_kind = _peaks()
     ctx.reset_timing()
     ctx.set_timing(True)
     for _ in range(3):
@@ -292,6 +309,12 @@ def batched_section(ctx, stream, steps: int, warmup: int, plain_steps: int) -> d
     torch.cuda.synchronize()
     ctx.set_timing(False)
     out["batched"]["kernel_ms_per_step"] = {k: v[1] / 3 for k, v in sorted(ctx.timing().items())}
+    out["batched"]["build_roofline"] = {
+        "alg_bytes": alg, "frac_of_peak": alg / (out["batched"]["p50_ms"] / 1e3) / 1e9 / peak,
+        "peak": peak, "peak_kind": peak_kind, "note": "compulsory bytes / p50 step time"}
+    out["nnz"] = {"e2": int(nnz2), "e4": int(nnz4)}
+    out["levels"] = {"min": int(min(levels)), "max": int(max(levels)),
+                     "mean": float(np.mean(levels))}
     out["workload"] = ("512 aliased sets, sizes log-uniform in [1e3, 1e6], uniform / sphere / "
                        "clumps with p = 1/3, s = 64 (per-set L); batched = one fmm_build_batched "
                        "call, plain = one fmm_build call per set")

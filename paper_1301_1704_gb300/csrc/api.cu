@@ -8,8 +8,9 @@
 //   first pass forms the Morton keys from the coordinates) -> finishing sort
 //   inside boxes + finest boxes -> coarser boxes -> child occupancy;
 // then for l = 2..L: job prefix -> list counts -> two prefix sums -> fill.
-// The host synchronises once at the end (and once after the boxes in
-// cluster-size mode, or when the list capacity bound is too large).
+// The host synchronises once at the end, and also: in cluster-size mode after
+// the sort (to learn each set's depth) and after the full-key sort of the sets
+// that need one; when the list capacity bound is too large, after the boxes.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -255,6 +256,7 @@ struct SetPlan {
   int Lb = 0, Ls = 0;
   bool full = false;      // sort all 63 bits (the order needs no finishing window)
   bool need_occ = false;  // used as a source
+  uint32_t depth = 0;     // cluster-size mode: 1 + deepest level shared by points i, i + s
   Seg dev{};              // the device descriptor
   uint32_t cap[kLevels] = {};
 };
@@ -270,18 +272,15 @@ struct JobPlan {
 // Sizes read back at the end of a build.
 struct Readback {
   DevStatus st{};
-  std::vector<uint32_t> nbox;      // [nsets][2 * kLevels]: counts, largest occupancy
+  std::vector<uint32_t> nbox;      // [nsets][kLevels] box counts
   std::vector<uint32_t> seg_long;  // [nsets]
   std::vector<uint64_t> list;      // [kLevels][njobs][4]: base E2, base E4, nnz E2, nnz E4
   std::vector<uint32_t*> idx;      // [kLevels][2]: the level's E2 / E4 entry arrays
 };
 
-// Device pointers of the tables of one build.
-struct BuildMem {
-  Seg* segs = nullptr;
-  Job* jobs = nullptr;
-  ListLevel* lvls = nullptr;
-  uint8_t* which = nullptr;
+// Device tables of the sort stage.
+struct SortMem {
+  Seg* segs = nullptr;  // descriptors of the sorted sets (sort fields and skeys / svals)
   Slot* pass_slots[8] = {};
   uint32_t pass_nslots[8] = {}, pass_tiles[8] = {};
   uint32_t* pass_hist[8] = {};
@@ -289,16 +288,22 @@ struct BuildMem {
   size_t pass_hist_len[8] = {};
   uint64_t* pass_scan[8] = {};
   uint32_t* pass_cnt = nullptr;  // scan tickets, one per pass
-  Slot* fin_slots = nullptr;
-  Slot* crs_slots = nullptr;
-  uint32_t fin_units = 0, crs_units = 0;
   uint64_t* ka = nullptr;
   uint32_t* va = nullptr;
   uint64_t* kb = nullptr;
   uint32_t* vb = nullptr;
   int max_passes = 0;
-  int max_lb = 0;
-  uint32_t max_n = 0;
+};
+
+// Device tables of the box and list stages.
+struct BuildMem {
+  Seg* segs = nullptr;
+  Job* jobs = nullptr;
+  ListLevel* lvls = nullptr;
+  Slot* fin_slots = nullptr;
+  Slot* crs_slots = nullptr;
+  Slot* occ_slots = nullptr;
+  uint32_t fin_units = 0, crs_units = 0, occ_units = 0;
 };
 
 // Host image of one upload: descriptors and slot tables, 256-byte aligned.
@@ -352,13 +357,13 @@ struct SortTables {
 // Radix pass p covers the sets with more than p passes.  Per participating
 // set: its first tile, its first histogram entry and the correction from
 // scanned positions (which count only participating points) to its slots.
-SortTables plan_sort(const std::vector<SetPlan>& sets) {
+SortTables plan_sort(const std::vector<SetPlan*>& sets) {
   SortTables t;
   for (int p = 0; p < 8; ++p) {
     uint32_t tiles = 0, compact = 0;
     size_t hist = 0;
     for (uint32_t id = 0; id < sets.size(); ++id) {
-      const SetPlan& s = sets[id];
+      const SetPlan& s = *sets[id];
       if (s.n == 0 || s.dev.passes <= p) continue;
       Slot sl;
       sl.seg = id;
@@ -379,17 +384,17 @@ SortTables plan_sort(const std::vector<SetPlan>& sets) {
 // Radix passes of every set.  Pass p reads buffer (p-1)&1 (the coordinates
 // for p = 0) and writes buffer p&1; a set's result stays in buffer
 // (passes-1)&1 at its base.
-int run_sort(fmm_ctx* c, std::vector<SetPlan>& sets, BuildMem& m, bool stall, uint64_t wait_ns) {
+int run_sort(fmm_ctx* c, std::vector<SetPlan*>& sets, SortMem& m, bool stall, uint64_t wait_ns) {
   cudaStream_t s = c->stream;
   int err = FMM_OK;
   bool any_full = false;  // a set sorted in full keeps every pass stable
-  for (auto& sp : sets) any_full |= sp.full;
+  for (auto* sp : sets) any_full |= sp->full;
   const bool onesweep = stall || c->tuning.sort_kind == FMM_SORT_ONESWEEP;
   if (onesweep) {
     // One set at a time, one kernel per pass (decoupled look-back).
-    for (auto& sp : sets) {
-      if (sp.n == 0) continue;
-      const SortPlan plan = make_sort_plan(sp.n, sp.Ls);
+    for (auto* sp : sets) {
+      if (sp->n == 0) continue;
+      const SortPlan plan = make_sort_plan(sp->n, sp->Ls);
       const uint32_t radix = 1u << plan.bits;
       const size_t per_pass = (size_t)plan.ntiles * radix;
       const size_t zb = align_up(sizeof(uint32_t) * 8 * kRadixMax) +
@@ -406,20 +411,20 @@ int run_sort(fmm_ctx* c, std::vector<SetPlan>& sets, BuildMem& m, bool stall, ui
           align_up(sizeof(uint64_t) * per_pass * plan.passes));
       {
         Launch L(c, "upfront_hist");
-        launch_upfront_hist(sp.xyz, sp.n, plan, hist, c->st, s);
+        launch_upfront_hist(sp->xyz, sp->n, plan, hist, c->st, s);
       }
       {
         Launch L(c, "digit_scan");
         launch_digit_scan(plan, hist, s);
       }
-      const uint32_t b0 = sp.dev.base;
+      const uint32_t b0 = sp->dev.base;
       for (int p = 0; p < plan.passes; ++p) {
         uint64_t* ko = ((p & 1) ? m.kb : m.ka) + b0;
         uint32_t* vo = ((p & 1) ? m.vb : m.va) + b0;
         const uint64_t* ki = ((p & 1) ? m.ka : m.kb) + b0;
         const uint32_t* vi = ((p & 1) ? m.va : m.vb) + b0;
         Launch L(c, "onesweep");
-        launch_onesweep_pass(p, sp.xyz, ki, vi, ko, vo, sp.n, plan, hist + p * kRadixMax,
+        launch_onesweep_pass(p, sp->xyz, ki, vi, ko, vo, sp->n, plan, hist + p * kRadixMax,
                              sstatus + (size_t)p * per_pass, counters + p, c->st, wait_ns,
                              (stall && p == 0 && plan.ntiles > 2) ? 1 : -1, s);
       }
@@ -451,57 +456,45 @@ int run_sort(fmm_ctx* c, std::vector<SetPlan>& sets, BuildMem& m, bool stall, ui
   return FMM_OK;
 }
 
-// One build over `sets` and `jobs` (jobs[].L: the tree depth, or for
-// cluster-size mode chosen here).  deepest: the sets' boxes reach level 21,
-// so an unmet cluster size ends at 21 with s_unmet instead of L = -1.
-int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs,
-              const fmm_params& prm, bool smode, bool deepest, bool stall, Readback* rb) {
+// Sort stage: orders the points of `sets` by the top 3 * Ls bits of their
+// keys (all 63 for full sets) into fresh concatenated arrays and points each
+// set's skeys / svals there.  Only the sort fields of the descriptors change.
+int sort_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, bool stall, uint64_t wait_ns, SortMem* out) {
   cudaStream_t s = c->stream;
   int err = FMM_OK;
-  const uint64_t wait_ns = wait_ns_of(prm);
-  const uint32_t nsets = (uint32_t)sets.size(), njobs = (uint32_t)jobs.size();
-  BuildMem m;
-
-  // ---- sets: depths, tiles, slots in the concatenated sort arrays.
+  SortMem& m = *out;
+  m = SortMem{};
   uint64_t slots_total = 0;
-  for (auto& sp : sets) {
-    sp.Ls = sp.full ? kMaxLevel : std::max(sort_level(sp.n, sp.Lb), sp.Lb);
-    Seg& d = sp.dev;
-    std::memset(&d, 0, sizeof(d));
-    d.xyz = sp.xyz;
-    d.n = sp.n;
+  for (auto* sp : sets) {
+    if (sp->full) sp->Ls = kMaxLevel;
+    Seg& d = sp->dev;
+    d.xyz = sp->xyz;
+    d.n = sp->n;
     d.base = (uint32_t)slots_total;
-    d.Ls = sp.Ls;
-    d.Lb = sp.Lb;
-    d.passes = sp.n ? passes_for(sp.Ls) : 0;
-    d.lo = 63 - 3 * sp.Ls;
-    d.ntiles = (uint32_t)(((uint64_t)sp.n + kSortTile - 1) / kSortTile);
-    d.btiles = std::max<uint32_t>(1, (uint32_t)(((uint64_t)sp.n + kBoxTile - 1) / kBoxTile));
-    slots_total += ((uint64_t)sp.n + 3) & ~3ull;  // set bases stay 16-byte aligned
+    d.Ls = sp->Ls;
+    d.passes = sp->n ? passes_for(sp->Ls) : 0;
+    d.lo = 63 - 3 * sp->Ls;
+    d.ntiles = (uint32_t)(((uint64_t)sp->n + kSortTile - 1) / kSortTile);
+    slots_total += ((uint64_t)sp->n + 3) & ~3ull;  // set bases stay 16-byte aligned
+    if (slots_total >= (1ull << 32)) return FMM_ERR_ARG;
     m.max_passes = std::max(m.max_passes, d.passes);
-    m.max_lb = std::max(m.max_lb, sp.Lb);
-    m.max_n = std::max(m.max_n, sp.n);
-    for (int l = 0; l <= sp.Lb; ++l) sp.cap[l] = level_cap(sp.n, l);
   }
-  if (slots_total >= (1ull << 32)) return FMM_ERR_ARG;
   const size_t nslot = (size_t)slots_total + 4;
   m.ka = arena_get<uint64_t>(c, nslot, &err);
   m.va = arena_get<uint32_t>(c, nslot, &err);
   m.kb = arena_get<uint64_t>(c, nslot, &err);
   m.vb = arena_get<uint32_t>(c, nslot, &err);
   if (err) return err;
+  for (auto* sp : sets) {
+    Seg& d = sp->dev;
+    const int last = d.passes > 0 ? (d.passes - 1) & 1 : 0;
+    d.skeys = (last ? m.kb : m.ka) + d.base;
+    d.svals = (last ? m.vb : m.va) + d.base;
+  }
   SortTables tab = plan_sort(sets);
 
-  // Zero-initialised words: per set look-back words, tickets, counts and
-  // flags; per pass scan words; scan tickets.
+  // Zero-initialised words: per pass scan words and scan tickets.
   size_t zero_bytes = 0;
-  std::vector<size_t> zoff(nsets);
-  for (uint32_t i = 0; i < nsets; ++i) {
-    zoff[i] = zero_bytes;
-    zero_bytes += align_up(sizeof(uint64_t) * sets[i].dev.btiles) +
-                  align_up(sizeof(uint64_t) * coarse_tiles(sets[i].cap[sets[i].Lb]) * kLevels) +
-                  align_up(sizeof(uint32_t) * (2 + 2 * kLevels + 1));
-  }
   size_t scan_off[8] = {};
   for (int p = 0; p < m.max_passes; ++p) {
     scan_off[p] = zero_bytes;
@@ -522,6 +515,80 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   }
   if (err) return err;
 
+  Upload up;
+  std::vector<Seg> segs_host(sets.size());
+  for (size_t i = 0; i < sets.size(); ++i) segs_host[i] = sets[i]->dev;
+  const size_t o_segs = up.add(segs_host.data(), segs_host.size());
+  size_t o_pass[8] = {};
+  for (int p = 0; p < m.max_passes; ++p)
+    o_pass[p] = up.add(tab.slots[p].data(), tab.slots[p].size());
+  char* dev = upload(c, up, &err);
+  if (err) return err;
+  m.segs = reinterpret_cast<Seg*>(dev + o_segs);
+  for (int p = 0; p < m.max_passes; ++p)
+    m.pass_slots[p] = reinterpret_cast<Slot*>(dev + o_pass[p]);
+  FMM_CUDA(cudaMemsetAsync(zero, 0, zero_bytes, s));
+  return run_sort(c, sets, m, stall, wait_ns);
+}
+
+// Cluster-size depth of each sorted set (see depth_kernel), read back into
+// SetPlan::depth; also returns the build's status word.
+int depth_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, const SortMem& m, uint32_t s_cluster,
+               DevStatus* st_out) {
+  cudaStream_t s = c->stream;
+  int err = FMM_OK;
+  const size_t nsets = sets.size();
+  uint32_t* dout = arena_get<uint32_t>(c, nsets, &err);
+  if (err) return err;
+  FMM_CUDA(cudaMemsetAsync(dout, 0, sizeof(uint32_t) * nsets, s));
+  {
+    Launch L(c, "depth");
+    launch_depth(m.segs, m.pass_slots[0], m.pass_nslots[0], m.pass_tiles[0], s_cluster, dout,
+                 c->st, s);
+  }
+  const size_t need = 64 + sizeof(uint32_t) * nsets;
+  FMM_CUDA(cudaStreamSynchronize(s));  // the read-back buffer may be replaced
+  FMM_TRY(pinned_reserve(&c->rb_buf, &c->rb_bytes, need));
+  char* h = static_cast<char*>(c->rb_buf);
+  FMM_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(cudaMemcpyAsync(h + 64, dout, sizeof(uint32_t) * nsets, cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(st_out, h, sizeof(DevStatus));
+  const uint32_t* hd = reinterpret_cast<const uint32_t*>(h + 64);
+  for (size_t i = 0; i < nsets; ++i) sets[i]->depth = hd[i];
+  return FMM_OK;
+}
+
+// Box and list stages of a build over sorted `sets` (SetPlan::Lb and
+// JobPlan::L fixed).
+int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs,
+              const fmm_params& prm, Readback* rb) {
+  cudaStream_t s = c->stream;
+  int err = FMM_OK;
+  const uint64_t wait_ns = wait_ns_of(prm);
+  const uint32_t nsets = (uint32_t)sets.size(), njobs = (uint32_t)jobs.size();
+  BuildMem m;
+
+  for (auto& sp : sets) {
+    sp.dev.Lb = sp.Lb;
+    sp.dev.btiles =
+        std::max<uint32_t>(1, (uint32_t)(((uint64_t)sp.n + kBoxTile - 1) / kBoxTile));
+    for (int l = 0; l <= sp.Lb; ++l) sp.cap[l] = level_cap(sp.n, l);
+  }
+
+  // Zero-initialised words per set: look-back words, tickets, box counts and
+  // the long-box flag.
+  size_t zero_bytes = 0;
+  std::vector<size_t> zoff(nsets);
+  for (uint32_t i = 0; i < nsets; ++i) {
+    zoff[i] = zero_bytes;
+    zero_bytes += align_up(sizeof(uint64_t) * sets[i].dev.btiles) +
+                  align_up(sizeof(uint64_t) * coarse_tiles(sets[i].cap[sets[i].Lb]) * kLevels) +
+                  align_up(sizeof(uint32_t) * (2 + kLevels + 1));
+  }
+  char* zero = arena_get<char>(c, std::max<size_t>(zero_bytes, 1), &err);
+  if (err) return err;
+
   // Per-set outputs.
   for (uint32_t i = 0; i < nsets; ++i) {
     SetPlan& sp = sets[i];
@@ -533,11 +600,9 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     z += align_up(sizeof(uint64_t) * coarse_tiles(sp.cap[sp.Lb]) * kLevels);
     d.tickets = reinterpret_cast<uint32_t*>(z);
     d.nbox = d.tickets + 2;
-    d.seg_long = d.nbox + 2 * kLevels;
+    d.seg_long = d.nbox + kLevels;
     d.perm = arena_get<uint32_t>(c, sp.n, &err);
-    const int last = d.passes > 0 ? (d.passes - 1) & 1 : 0;
-    d.skeys = (last ? m.kb : m.ka) + d.base;
-    d.svals = (last ? m.vb : m.va) + d.base;
+    std::memset(&d.lv, 0, sizeof(d.lv));
     for (int l = 0; l <= sp.Lb; ++l) {
       d.lv.cap[l] = sp.cap[l];
       d.lv.key[l] = arena_get<uint64_t>(c, sp.cap[l], &err);
@@ -550,13 +615,18 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   }
 
   // Box-stage slots.
-  std::vector<Slot> fin, crs;
+  std::vector<Slot> fin, crs, occ;
   for (uint32_t i = 0; i < nsets; ++i) {
     fin.push_back(Slot{i, m.fin_units, 0, 0});
     m.fin_units += sets[i].dev.btiles;
     if (sets[i].Lb >= 1) {
       crs.push_back(Slot{i, m.crs_units, 0, 0});
       m.crs_units += coarse_tiles(sets[i].cap[sets[i].Lb]);
+    }
+    if (sets[i].Lb >= 1 && sets[i].need_occ) {
+      const uint32_t u = occupancy_units(sets[i].n);
+      occ.push_back(Slot{i, m.occ_units, u, 0});
+      m.occ_units += u;
     }
   }
 
@@ -566,10 +636,8 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   uint64_t list_bound = 0;
   for (auto& jp : jobs)
     for (int l = 2; l <= jp.L; ++l) list_bound += 4ull * (2 + 27 + 189) * sets[jp.recv].cap[l];
-  const bool async_lists = !smode && list_bound <= kAsyncListBytes;
+  const bool async_lists = list_bound <= kAsyncListBytes;
 
-  std::vector<uint8_t> which(nsets);
-  for (uint32_t i = 0; i < nsets; ++i) which[i] = sets[i].need_occ ? 1 : 0;
   std::vector<ListLevel> lvls(kLevels);
   std::memset(lvls.data(), 0, sizeof(ListLevel) * kLevels);
   auto upload_all = [&](bool with_lists) -> int {
@@ -577,12 +645,9 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     std::vector<Seg> segs_host(nsets);
     for (uint32_t i = 0; i < nsets; ++i) segs_host[i] = sets[i].dev;
     const size_t o_segs = up.add(segs_host.data(), nsets);
-    const size_t o_which = up.add(which.data(), nsets);
-    size_t o_pass[8] = {};
-    for (int p = 0; p < m.max_passes; ++p)
-      o_pass[p] = up.add(tab.slots[p].data(), tab.slots[p].size());
     const size_t o_fin = up.add(fin.data(), fin.size());
     const size_t o_crs = up.add(crs.data(), crs.size());
+    const size_t o_occ = up.add(occ.data(), occ.size());
     size_t o_jobs = 0, o_lvls = 0;
     std::vector<Job> jobs_host(njobs);
     if (with_lists) {
@@ -593,11 +658,9 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     char* dev = upload(c, up, &err);
     if (err) return err;
     m.segs = reinterpret_cast<Seg*>(dev + o_segs);
-    m.which = reinterpret_cast<uint8_t*>(dev + o_which);
-    for (int p = 0; p < m.max_passes; ++p)
-      m.pass_slots[p] = reinterpret_cast<Slot*>(dev + o_pass[p]);
     m.fin_slots = reinterpret_cast<Slot*>(dev + o_fin);
     m.crs_slots = reinterpret_cast<Slot*>(dev + o_crs);
+    m.occ_slots = reinterpret_cast<Slot*>(dev + o_occ);
     if (with_lists) {
       m.jobs = reinterpret_cast<Job*>(dev + o_jobs);
       m.lvls = reinterpret_cast<ListLevel*>(dev + o_lvls);
@@ -674,8 +737,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   FMM_CUDA(cudaMemsetAsync(zero, 0, zero_bytes, s));
   if (async_lists && list_zero_bytes) FMM_CUDA(cudaMemsetAsync(list_zero, 0, list_zero_bytes, s));
 
-  // ---- sort, boxes, occupancy.
-  FMM_TRY(run_sort(c, sets, m, stall, wait_ns));
+  // ---- boxes, occupancy.
   {
     Launch L(c, "finish_boxes");
     launch_finish_boxes(m.segs, m.fin_slots, (uint32_t)fin.size(), m.fin_units, c->st, wait_ns, s);
@@ -685,12 +747,12 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     launch_coarse_boxes(m.segs, m.crs_slots, (uint32_t)crs.size(), m.crs_units, c->st, wait_ns,
                         s);
   }
-  {
+  if (m.occ_units) {
     Launch L(c, "occupancy");
-    launch_occupancy(m.segs, nsets, m.which, m.max_n, m.max_lb, c->st, s);
+    launch_occupancy(m.segs, m.occ_slots, (uint32_t)occ.size(), m.occ_units, c->st, s);
   }
 
-  const size_t per_set = 2 * kLevels + 1;
+  const size_t per_set = kLevels + 1;
   auto read_sets = [&](bool lists) -> int {
     const size_t list_words = lists ? 4 * (size_t)njobs * kLevels : 0;
     const size_t need = 64 + sizeof(uint32_t) * nsets * per_set + 16 + sizeof(uint64_t) * list_words;
@@ -713,12 +775,12 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
       }
     FMM_CUDA(cudaStreamSynchronize(s));
     std::memcpy(&rb->st, h, sizeof(DevStatus));
-    rb->nbox.assign((size_t)nsets * 2 * kLevels, 0);
+    rb->nbox.assign((size_t)nsets * kLevels, 0);
     rb->seg_long.assign(nsets, 0);
     for (uint32_t i = 0; i < nsets; ++i) {
-      std::memcpy(&rb->nbox[(size_t)i * 2 * kLevels], hn + (size_t)i * per_set,
-                  sizeof(uint32_t) * 2 * kLevels);
-      rb->seg_long[i] = hn[(size_t)i * per_set + 2 * kLevels];
+      std::memcpy(&rb->nbox[(size_t)i * kLevels], hn + (size_t)i * per_set,
+                  sizeof(uint32_t) * kLevels);
+      rb->seg_long[i] = hn[(size_t)i * per_set + kLevels];
     }
     if (lists) {
       rb->list.assign((size_t)kLevels * njobs * 4, 0);
@@ -737,35 +799,10 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   };
 
   if (!async_lists) {
-    if (smode) {
-      Launch L(c, "max_occupancy");
-      launch_max_occupancy(m.segs, nsets, m.max_n, m.max_lb, c->st, s);
-    }
     FMM_TRY(read_sets(false));
     if (rb->st.code) return (int)rb->st.code;
-    if (smode) {
-      // Sec. 2.1: the smallest L >= 2 at which no box of either set holds
-      // more than s points.
-      for (auto& jp : jobs) {
-        const uint32_t* a = &rb->nbox[(size_t)jp.src * 2 * kLevels + kLevels];
-        const uint32_t* b = &rb->nbox[(size_t)jp.recv * 2 * kLevels + kLevels];
-        const int lb = std::min(sets[jp.src].Lb, sets[jp.recv].Lb);
-        jp.L = -1;
-        for (int l = 2; l <= lb; ++l)
-          if (a[l] <= prm.s && b[l] <= prm.s) {
-            jp.L = l;
-            break;
-          }
-        if (jp.L < 0 && deepest) {
-          jp.L = kMaxLevel;
-          jp.s_unmet = 1;
-        }
-      }
-      Lmax = 0;
-      for (auto& jp : jobs) Lmax = std::max(Lmax, jp.L);
-    }
     for (auto& jp : jobs)
-      for (int l = 2; l <= jp.L; ++l) jp.cap[l] = rb->nbox[(size_t)jp.recv * 2 * kLevels + l];
+      for (int l = 2; l <= jp.L; ++l) jp.cap[l] = rb->nbox[(size_t)jp.recv * kLevels + l];
     FMM_TRY(plan_lists());
     FMM_TRY(upload_all(true));
     if (list_zero_bytes) FMM_CUDA(cudaMemsetAsync(list_zero, 0, list_zero_bytes, s));
@@ -819,18 +856,16 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
 int full_sort_perms(fmm_ctx* c, std::vector<SetPlan>& sets, const std::vector<uint32_t>& ids,
                     const fmm_params& prm) {
   if (ids.empty()) return FMM_OK;
-  std::vector<SetPlan> sub;
-  for (uint32_t id : ids) {
-    SetPlan sp;
-    sp.xyz = sets[id].xyz;
-    sp.n = sets[id].n;
-    sp.Lb = 0;
-    sp.full = true;
-    sub.push_back(sp);
+  std::vector<SetPlan> sub(ids.size());
+  std::vector<SetPlan*> ps;
+  for (size_t k = 0; k < ids.size(); ++k) {
+    sub[k].xyz = sets[ids[k]].xyz;
+    sub[k].n = sets[ids[k]].n;
+    sub[k].full = true;
+    ps.push_back(&sub[k]);
   }
-  std::vector<JobPlan> nojobs;
-  Readback rb;
-  FMM_TRY(run_build(c, sub, nojobs, prm, false, false, false, &rb));
+  SortMem sm;
+  FMM_TRY(sort_sets(c, ps, false, wait_ns_of(prm), &sm));
   // Every pass of a full sort is stable: the values of the last pass are the
   // order by (key, index).
   cudaStream_t s = c->stream;
@@ -855,7 +890,7 @@ void fill_tree(const std::vector<SetPlan>& sets, const JobPlan& J, const Readbac
   const uint32_t idx[2] = {J.src, J.recv};
   for (int k = 0; k < 2; ++k) {
     const Seg& d = side[k]->dev;
-    const uint32_t* nb = &rb.nbox[(size_t)idx[k] * 2 * kLevels];
+    const uint32_t* nb = &rb.nbox[(size_t)idx[k] * kLevels];
     uint32_t* onb = k ? out->nbox_recv : out->nbox_src;
     const uint64_t** okey = k ? out->key_recv : out->key_src;
     const uint32_t** ooff = k ? out->off_recv : out->off_src;
@@ -898,6 +933,7 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
   const bool smode = prm.L < 0;
   const bool stall = (prm.flags & FMM_FLAG_TEST_STALL) != 0;
   const bool host_in = (prm.flags & FMM_FLAG_HOST_INPUT) != 0;
+  const uint64_t wait_ns = wait_ns_of(prm);
 
   uint64_t expect = 0;
   for (uint32_t k = 0; k < npairs; ++k) {
@@ -924,6 +960,7 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
     const bool aliased = pairs[k].src == pairs[k].recv && pairs[k].N == pairs[k].M;
     jobs[k].src = add_set(pairs[k].src, pairs[k].N);
     jobs[k].recv = aliased ? jobs[k].src : add_set(pairs[k].recv, pairs[k].M);
+    sets[jobs[k].src].need_occ = true;
   }
   if (host_in) {
     for (auto& sp : sets) {
@@ -934,51 +971,71 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
       sp.xyz = d;
     }
   }
-  // Box depth: the tree depth, or (cluster-size mode) the sort depth of the
-  // larger set of the job; both sets of a job share it.
-  for (auto& jp : jobs) {
-    const int want = smode ? std::max(std::max(sort_level(sets[jp.src].n, 2),
-                                               sort_level(sets[jp.recv].n, 2)), 2)
-                           : prm.L;
-    jp.L = want;
-    sets[jp.src].Lb = std::max(sets[jp.src].Lb, want);
-    sets[jp.recv].Lb = std::max(sets[jp.recv].Lb, want);
-    sets[jp.src].need_occ = true;
-  }
-  Readback rb;
-  FMM_TRY(run_build(c, sets, jobs, prm, smode, false, stall, &rb));
+  std::vector<SetPlan*> all;
+  for (auto& sp : sets) all.push_back(&sp);
 
-  // Cluster-size jobs not met at that depth: rebuild with full keys and
-  // boxes down to level 21.
-  std::vector<int> deep_of(npairs, -1);
-  std::vector<SetPlan> dsets;
-  std::vector<JobPlan> djobs;
-  Readback drb;
-  {
-    std::vector<int> map(sets.size(), -1);
-    for (uint32_t j = 0; j < npairs; ++j) {
-      if (jobs[j].L >= 0) continue;
-      JobPlan jp;
-      for (int k = 0; k < 2; ++k) {
-        const uint32_t id = k ? jobs[j].recv : jobs[j].src;
-        if (map[id] < 0) {
-          SetPlan sp;
-          sp.xyz = sets[id].xyz;
-          sp.n = sets[id].n;
-          sp.Lb = kMaxLevel;
-          sp.full = true;
-          map[id] = (int)dsets.size();
-          dsets.push_back(sp);
-        }
-        (k ? jp.recv : jp.src) = (uint32_t)map[id];
-      }
-      dsets[jp.src].need_occ = true;
-      jp.L = kMaxLevel;
-      deep_of[j] = (int)djobs.size();
-      djobs.push_back(jp);
+  if (!smode) {
+    // Fixed depth: box depth L, sorted deep enough for the finishing sort.
+    for (auto& jp : jobs) jp.L = prm.L;
+    for (auto& sp : sets) {
+      sp.Lb = prm.L;
+      sp.Ls = std::max(sort_level(sp.n, sp.Lb), sp.Lb);
     }
-    if (!djobs.empty()) FMM_TRY(run_build(c, dsets, djobs, prm, true, true, false, &drb));
+    SortMem sm;
+    FMM_TRY(sort_sets(c, all, stall, wait_ns, &sm));
+  } else {
+    // Cluster-size mode (Sec. 2.1): sort to each set's natural depth, find the
+    // deepest level at which s + 1 sorted points still share a box; sets whose
+    // boxes are still too full at the sort depth are sorted on all key bits.
+    for (auto& sp : sets) sp.Ls = sort_level(sp.n, 2);
+    SortMem sm;
+    FMM_TRY(sort_sets(c, all, stall, wait_ns, &sm));
+    DevStatus st{};
+    FMM_TRY(depth_sets(c, all, sm, prm.s, &st));
+    if (st.code) return (int)st.code;
+    std::vector<SetPlan*> deep;
+    for (auto& sp : sets)
+      if (!sp.full && sp.depth > (uint32_t)sp.Ls) {
+        sp.full = true;
+        deep.push_back(&sp);
+      }
+    if (!deep.empty()) {
+      SortMem sd;
+      FMM_TRY(sort_sets(c, deep, false, wait_ns, &sd));
+      FMM_TRY(depth_sets(c, deep, sd, prm.s, &st));
+      if (st.code) return (int)st.code;
+    }
+    // A job's depth: the smallest L >= 2 at which neither set has a box of
+    // more than s points; level 21 with s_unmet when no level has.
+    for (auto& jp : jobs) {
+      const uint32_t d = std::max(sets[jp.src].depth, sets[jp.recv].depth);
+      if (d > (uint32_t)kMaxLevel) {
+        jp.L = kMaxLevel;
+        jp.s_unmet = 1;
+      } else {
+        jp.L = std::max(2, (int)d);
+      }
+    }
+    for (auto& sp : sets) sp.Lb = 0;
+    for (auto& jp : jobs) {
+      sets[jp.src].Lb = std::max(sets[jp.src].Lb, jp.L);
+      sets[jp.recv].Lb = std::max(sets[jp.recv].Lb, jp.L);
+    }
+    // A set paired with a deeper one needs its order to that depth.
+    std::vector<SetPlan*> resort;
+    for (auto& sp : sets)
+      if (sp.Lb > sp.Ls) {
+        sp.Ls = std::max(sort_level(sp.n, sp.Lb), sp.Lb);
+        resort.push_back(&sp);
+      }
+    if (!resort.empty()) {
+      SortMem sr;
+      FMM_TRY(sort_sets(c, resort, false, wait_ns, &sr));
+    }
   }
+
+  Readback rb;
+  FMM_TRY(run_build(c, sets, jobs, prm, &rb));
 
   // Boxes that outran the finishing window: redo those orders in full.
   std::vector<uint32_t> longs;
@@ -986,13 +1043,7 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
     if (rb.seg_long[i]) longs.push_back(i);
   FMM_TRY(full_sort_perms(c, sets, longs, prm));
 
-  for (uint32_t j = 0; j < npairs; ++j) {
-    if (deep_of[j] >= 0)
-      fill_tree(dsets, djobs[deep_of[j]], drb, (uint32_t)deep_of[j], (uint32_t)djobs.size(),
-                &outs[j]);
-    else
-      fill_tree(sets, jobs[j], rb, j, npairs, &outs[j]);
-  }
+  for (uint32_t j = 0; j < npairs; ++j) fill_tree(sets, jobs[j], rb, j, npairs, &outs[j]);
   size_t used = 0;
   for (size_t i = 0; i < c->chunks.size(); ++i) used += c->chunks[i].bytes;
   c->peak_request = std::max(c->peak_request, used);

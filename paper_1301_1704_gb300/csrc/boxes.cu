@@ -122,7 +122,12 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __
   // points; box bounds inside the warp come from one ballot of box starts.
   // This runs between publishing the aggregate and reading the earlier
   // tiles' words, which gives them time to publish.
-  {
+  if (Ls >= kMaxLevel) {
+    // Sorted on all 63 key bits with stable passes: the order is already
+    // (key, index).
+    const int own = jend < kBoxTile ? jend : kBoxTile;
+    for (int j = threadIdx.x; j < own; j += kBoxThreads) perm[t0 + j] = s_val[j];
+  } else {
     const uint32_t lt = lanemask_lt();
     bool long_box = false;
     const int lowbits = 63 - 3 * Ls;
@@ -369,20 +374,24 @@ void launch_coarse_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, ui
 }
 
 // ---------------------------------------------------------------------------
-// Child-occupancy byte of every box of levels 0..Lb-1 of the sets flagged in
-// `which` (grid y = set): bit o is set when the child in octant o
-// (x + 2y + 4z) is non-empty.  Lists use it to enumerate the children of a
-// parent-level neighbour without reading their keys.
-__global__ void occupancy_kernel(const Seg* __restrict__ segs, const uint8_t* which,
-                                 const DevStatus* st) {
-  const Seg& sg = segs[blockIdx.y];
-  if (!which[blockIdx.y] || failed(st)) return;
+// Child-occupancy byte of every box of levels 0..Lb-1 of the sets that serve
+// as sources: bit o is set when the child in octant o (x + 2y + 4z) is
+// non-empty.  Lists use it to enumerate the children of a parent-level
+// neighbour without reading their keys.  A set owns a run of units (blocks)
+// in proportion to its size; each unit takes a strided share of every level.
+__global__ void __launch_bounds__(256) occupancy_kernel(const Seg* __restrict__ segs,
+                                                        const Slot* __restrict__ slots,
+                                                        uint32_t nslots, const DevStatus* st) {
+  if (failed(st)) return;
+  const uint32_t k = find_slot(slots, nslots, blockIdx.x);
+  const Seg& sg = segs[slots[k].seg];
+  const uint32_t u = blockIdx.x - slots[k].unit0, units = slots[k].aux0;
   for (int l = 0; l < sg.Lb; ++l) {
     const uint32_t nb = sg.nbox[l] < sg.lv.cap[l] ? sg.nbox[l] : sg.lv.cap[l];
     const uint32_t* ch = sg.lv.child[l];
     const uint64_t* ck = sg.lv.key[l + 1];
     uint8_t* occ = sg.lv.occ[l];
-    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    for (uint32_t b = u * blockDim.x + threadIdx.x; b < nb; b += units * blockDim.x) {
       uint32_t m = 0;
       const uint32_t c1 = ch[b + 1];
       for (uint32_t c = ch[b]; c < c1; ++c) m |= 1u << (uint32_t)(ck[c] & 7u);
@@ -391,45 +400,54 @@ __global__ void occupancy_kernel(const Seg* __restrict__ segs, const uint8_t* wh
   }
 }
 
-void launch_occupancy(const Seg* segs, uint32_t nsegs, const uint8_t* which, uint32_t max_n,
-                      int max_lb, DevStatus* st, cudaStream_t s) {
-  if (nsegs == 0 || max_lb < 1) return;
-  uint32_t bx = (uint32_t)(((uint64_t)max_n / 4 + 255) / 256);
-  if (bx > 152u * 4u) bx = 152u * 4u;
-  if (bx == 0) bx = 1;
-  occupancy_kernel<<<dim3(bx, nsegs), 256, 0, s>>>(segs, which, st);
+void launch_occupancy(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
+                      DevStatus* st, cudaStream_t s) {
+  if (units == 0) return;
+  occupancy_kernel<<<units, 256, 0, s>>>(segs, slots, nslots, st);
 }
 
-// Largest box occupancy of each level 0..Lb (cluster-size mode, Sec. 2.1),
-// into nbox[kLevels + l] (zeroed).
-__global__ void max_occupancy_kernel(const Seg* __restrict__ segs, const DevStatus* st) {
-  const Seg& sg = segs[blockIdx.y];
+uint32_t occupancy_units(uint32_t n) { return 1u + n / 16384u; }
+
+// ---------------------------------------------------------------------------
+// Cluster-size depth (Sec. 2.1: the smallest level whose boxes hold at most
+// s points).  In an order sorted by the top 3*Ls key bits, a level-l box
+// (l <= Ls) is a contiguous run, so it holds more than s points exactly when
+// some sorted point i and point i + s share it, i.e. when their keys agree on
+// the level-l prefix.  One pass over the pairs (i, i + s) therefore gives,
+// for every set, D = max_i (deepest level shared by points i and i + s),
+// capped at Ls; written as D + 1 by atomicMax into out[set] (zeroed, so 0
+// means "no pair": the set has at most s points).  Units are sort tiles.
+__global__ void __launch_bounds__(256) depth_kernel(const Seg* __restrict__ segs,
+                                                    const Slot* __restrict__ slots,
+                                                    uint32_t nslots, uint32_t s,
+                                                    uint32_t* __restrict__ out,
+                                                    const DevStatus* st) {
   if (failed(st)) return;
-  for (int l = 0; l <= sg.Lb; ++l) {
-    const uint32_t nb = sg.nbox[l] < sg.lv.cap[l] ? sg.nbox[l] : sg.lv.cap[l];
-    const uint32_t* off = sg.lv.off[l];
-    uint32_t m = 0;
-    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-      const uint32_t c = off[b + 1] - off[b];
-      m = c > m ? c : m;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint32_t y = __shfl_xor_sync(0xffffffffu, m, o);
-      m = y > m ? y : m;
-    }
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(&sg.nbox[kLevels + l], m);
+  const uint32_t k = find_slot(slots, nslots, blockIdx.x);
+  const uint32_t set = slots[k].seg;
+  const Seg& sg = segs[set];
+  const uint64_t t0 = (uint64_t)(blockIdx.x - slots[k].unit0) * kSortTile;
+  const uint64_t npairs = sg.n > s ? (uint64_t)sg.n - s : 0;
+  const uint64_t* keys = sg.skeys;
+  const uint32_t cap = (uint32_t)sg.Ls;
+  uint32_t m = 0;
+  for (uint64_t i = t0 + threadIdx.x; i < t0 + kSortTile && i < npairs; i += blockDim.x) {
+    const uint32_t shared = first_diff_level(keys[i], keys[i + s]) - 1u;  // 0..21
+    const uint32_t v = (shared < cap ? shared : cap) + 1u;
+    m = v > m ? v : m;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out + set, m);
 }
 
-void launch_max_occupancy(const Seg* segs, uint32_t nsegs, uint32_t max_n, int max_lb,
-                          DevStatus* st, cudaStream_t s) {
-  if (nsegs == 0) return;
-  uint32_t bx = (uint32_t)(((uint64_t)max_n / 4 + 255) / 256);
-  if (bx > 152u * 4u) bx = 152u * 4u;
-  if (bx == 0) bx = 1;
-  (void)max_lb;
-  max_occupancy_kernel<<<dim3(bx, nsegs), 256, 0, s>>>(segs, st);
+void launch_depth(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units, uint32_t s,
+                  uint32_t* out, DevStatus* st, cudaStream_t stream) {
+  if (units == 0) return;
+  depth_kernel<<<units, 256, 0, stream>>>(segs, slots, nslots, s, out, st);
 }
 
 }  // namespace fmm

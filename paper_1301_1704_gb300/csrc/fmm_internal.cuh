@@ -283,7 +283,7 @@ struct Seg {
   uint64_t* bstatus;  // [btiles] look-back words of the finest level
   uint64_t* cstatus;  // [coarse tiles][kLevels]
   uint32_t* tickets;  // [2]: finishing tiles, coarse tiles
-  uint32_t* nbox;     // [kLevels] box counts, then [kLevels] largest occupancy
+  uint32_t* nbox;     // [kLevels] box counts
   uint32_t* seg_long; // set when a box outruns the finishing window
 };
 
@@ -417,10 +417,14 @@ void launch_coarse_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, ui
                          DevStatus* st, uint64_t wait_ns, cudaStream_t s);
 // Child-occupancy bytes (sets flagged in `which`, grid y = set) and largest
 // occupancy per level.
-void launch_occupancy(const Seg* segs, uint32_t nsegs, const uint8_t* which, uint32_t max_n,
-                      int max_lb, DevStatus* st, cudaStream_t s);
-void launch_max_occupancy(const Seg* segs, uint32_t nsegs, uint32_t max_n, int max_lb,
-                          DevStatus* st, cudaStream_t s);
+// Child-occupancy bytes of the slots' sets (slot aux0 = the set's units).
+void launch_occupancy(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
+                      DevStatus* st, cudaStream_t s);
+uint32_t occupancy_units(uint32_t n);
+// Cluster-size depth per set (units: sort tiles of the slots' sets); out[set]
+// = 1 + deepest level shared by sorted points i and i + s, capped at Ls.
+void launch_depth(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units, uint32_t s,
+                  uint32_t* out, DevStatus* st, cudaStream_t stream);
 uint32_t coarse_tiles(uint32_t cap);
 
 // Exclusive scan of u32 counts in place (count entries at data[0..count)),

@@ -182,6 +182,20 @@ void launch_job_prefix(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
   job_prefix_kernel<<<1, 1024, 0, s>>>(segs, jobs, njobs, l, lvls, st);
 }
 
+// Each block takes a contiguous run of the level's parents (over all jobs),
+// dealt round-robin to its warps: a warp changes jobs only where the run
+// crosses a job boundary, and the warps of a block work on neighbouring
+// parents, whose list stores land close together.
+struct BlockRange {
+  uint32_t g0, g1;
+};
+
+__device__ __forceinline__ BlockRange block_range(uint32_t total) {
+  const uint32_t per = (uint32_t)(((uint64_t)total + gridDim.x - 1) / gridDim.x);
+  const uint64_t a = (uint64_t)blockIdx.x * per, b = a + per;
+  return BlockRange{(uint32_t)(a < total ? a : total), (uint32_t)(b < total ? b : total)};
+}
+
 // Counts: per receiver child r of parent p, |E2(r)| = sum over the parent's
 // neighbours Q of popc(occ(Q) & mask(delta_Q, rho_r)), and |E2| + |E4| = the
 // number of non-empty children of all Q.  The eight possible sibling octants
@@ -199,11 +213,10 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(const Seg* __r
   uint32_t* const work2 = lvls[l].work2;
   uint32_t* const work4 = lvls[l].work4;
   const uint32_t total = jprefix[njobs];
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const BlockRange br = block_range(total);
   uint32_t j = 0, jstart = 0, jend = 0;
   ListCtx a{};
-  for (uint32_t g = gw; g < total; g += nw) {
+  for (uint32_t g = br.g0 + (threadIdx.x >> 5); g < br.g1; g += blockDim.x >> 5) {
     if (g >= jend) {  // g only grows: look its job up when it leaves the current one
       j = find_job(jprefix, njobs, g);
       a = make_ctx(segs, jobs[j], l, lvls, j);
@@ -283,15 +296,12 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
   uint32_t* nrank = s_nrank[warp];
   uint8_t* nsibm = s_nsib[warp];
   const uint32_t npar = jprefix[njobs];
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const BlockRange br = block_range(npar);
   // The warp's current job lives in shared memory, not in registers: the
   // list loops below need the registers for the eight siblings' cursors.
   WarpJob& J = s_job[warp];
   uint32_t jend = 0;
-  // Parents are dealt round-robin to the warps, so the warps in flight work on
-  // neighbouring parents and their list stores land close together.
-  for (uint32_t g = gw; g < npar; g += nw) {
+  for (uint32_t g = br.g0 + warp; g < br.g1; g += kListWarps) {
     if (g >= jend) {  // g only grows: look its job up when it leaves the current one
       if (lane == 0) {
         const uint32_t j = find_job(jprefix, njobs, g);
