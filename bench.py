@@ -323,6 +323,71 @@ def batched_section(ctx, stream, steps: int, warmup: int, plain_steps: int) -> d
     return out
 
 
+SERVE_SIZES = (10_000, 10_000, 100_000, 100_000, 1_000_000, 1_000_000, 10_000_000, 10_000_000)
+SERVE_RATE = 2000.0
+
+
+def serve_trace(nsys: int, steps: int, rate: float, seed: int):
+    """Poisson arrivals at `rate`/s, each for a uniformly chosen system,
+    until every system has `steps` requests."""
+    rng = np.random.default_rng(seed)
+    per = np.zeros(nsys, np.int64)
+    arr, sys_ = [], []
+    t = 0.0
+    while per.min() < steps:
+        t += rng.exponential(1.0 / rate)
+        k = int(rng.integers(0, nsys))
+        arr.append(t)
+        sys_.append(k)
+        per[k] += 1
+    return np.array(arr), np.array(sys_, np.uint32)
+
+
+def served_section(ctx, steps: int) -> dict:
+    """Served dynamic rebuilds: 8 resident clump systems (two each of 1e4,
+    1e5, 1e6, 1e7 points), depth fixed from the initial state at s = 64,
+    Poisson requests at 2000/s, each advancing one random system by one step
+    (Gaussian steps of 0.1 h_L, wall reflection) and rebuilding it.  Served =
+    continuous batching over 2 concurrent workers; plain = one worker, one
+    system per build (per-instance launches)."""
+    import torch
+    from paper_1301_1704_gb300 import fmmds, workloads
+    seed = workloads.CONFIG_SEEDS[5]
+    pts = [workloads.clumps(n, seed * 1000 + k) for k, n in enumerate(SERVE_SIZES)]
+    levels = []
+    for p in pts:
+        d = torch.from_numpy(p).cuda()
+        levels.append(ctx.build(d, d, s=64).L)
+        del d
+    torch.cuda.synchronize()
+    arr, sys_ = serve_trace(len(pts), steps, SERVE_RATE, seed)
+    out = {}
+    for name, workers, batch in (("served", 2, 8), ("plain", 1, 1)):
+        srv = fmmds.Server(0, workers=workers, max_batch=batch)
+        try:
+            for k, (p, L) in enumerate(zip(pts, levels)):
+                srv.add_system(p, L, 0.1, seed=seed * 1000 + k)
+            infos = srv.run_trace(arr, sys_)
+        finally:
+            srv.close()
+        lat = np.array([(i["t_done"] - i["t_arrival"]) * 1e3 for i in infos])
+        span = max(i["t_done"] for i in infos) - min(i["t_arrival"] for i in infos)
+        npts = sum(i["points"] for i in infos)
+        out[name] = {"value": npts / span / 1e6, "unit": "Mpts/s",
+                     "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)),
+                     "requests": len(infos), "span_s": span,
+                     "mean_batch": float(np.mean([i["batch_size"] for i in infos])),
+                     "failed": int(sum(i["status"] != 0 for i in infos))}
+    out["workload"] = ("8 resident clump systems (2 x 1e4, 1e5, 1e6, 1e7 points), L from the "
+                       f"initial state at s = 64 ({levels}), Poisson {SERVE_RATE:.0f}/s requests "
+                       f"until every system has {steps} steps; served = continuous batching "
+                       "(2 workers, up to 8 systems per batched build), plain = 1 worker, "
+                       "1 system per build")
+    out["speedup_vs_plain"] = out["served"]["value"] / out["plain"]["value"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,6 +403,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="steps of the per-instance comparison of the batched workload")
+    ap.add_argument("--serve-steps", type=int, default=1000,
+                    help="time steps per system of the served workload (0: skip it)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -469,6 +536,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = batched_section(ctx, stream, args.steps, args.warmup, args.plain_steps)
+    served = None
+    if args.serve_steps > 0 and rank == 0:
+        served = served_section(ctx, args.serve_steps)
 
     if rank == 0:
         line = {
@@ -496,6 +566,8 @@ def main():
             line["cpu_baseline"] = cpu_baseline()
         if batched is not None:
             line["batched"] = batched
+        if served is not None:
+            line["served"] = served
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

@@ -144,19 +144,25 @@ int fmm_destroy(fmm_ctx* ctx);
 int fmm_build(fmm_ctx* ctx, const float* src_xyz, uint32_t N, const float* recv_xyz,
               uint32_t M, fmm_params params, fmm_tree* out, void* stream);
 
-/* One (Src, Recv) pair of a batched build. */
+/* One (Src, Recv) pair of a batched build.  L: the pair's own tree depth
+ * (0..21), or FMM_SET_PARAMS_L (-1) to take it from the call's params (fixed
+ * L, or cluster-size mode). */
+#define FMM_SET_PARAMS_L (-1)
 typedef struct fmm_set {
   const float* src;
   uint32_t N;
   const float* recv;
   uint32_t M;
+  int32_t L;
 } fmm_set;
 
 /* Alg. 5 for nsets independent pairs at once: every stage (radix passes,
  * boxes, lists) covers all sets in one kernel launch, so many small builds
  * cost about as many launches as one.  Same conventions as fmm_build per
- * set; params apply to every set (in cluster-size mode each set gets its own
- * L).  outs[k] receives set k's tree, with values local to the set (point
+ * set; params apply to every set whose L is FMM_SET_PARAMS_L (in cluster-size
+ * mode each such set gets its own L); a set's own L (0..21) overrides them,
+ * and FMM_ERR_LEVEL is returned for an L above 21 or below -1.
+ * outs[k] receives set k's tree, with values local to the set (point
  * indices, box ranks and list entries as if the set were built alone); all
  * arrays live in the context's arena until its next build.  Inputs must not
  * overlap partially: a set's src and recv may be the same array (N == M).
@@ -231,6 +237,88 @@ int fmm_last_launch_count(fmm_ctx* ctx, uint64_t* launches);
 #define FMM_NOALLOC_SCAN_MAX (1u << 26)
 int fmm_exclusive_scan_noalloc(const uint32_t* counts, uint32_t n, uint32_t* offsets,
                                uint64_t* total, void* stream);
+
+/* ---- Served dynamic rebuilds ---------------------------------------------
+ *
+ * Dynamic problems rebuild the structure every time step (Sec. 1).  The
+ * server keeps time-stepped point systems resident on the device.  A request
+ * advances one system by one step: every point moves by an independent
+ * N(0, sigma^2) step per axis, sigma = sigma_scale * 2^-L, reflecting at the
+ * cube walls (fmm_displace), and the system's structure is rebuilt at its
+ * fixed depth L (aliased sources = receivers).  Requests to one system run in
+ * arrival order, one at a time.  Workers (each with its own context and
+ * stream, so their builds overlap on the device) take, whenever they free
+ * up, every waiting system they can -- oldest request first, at most
+ * max_batch, while the systems' workspace estimates fit the worker's share
+ * of the memory budget (always at least one) -- and build them in one
+ * batched build (continuous batching).  A step's result depends only on the
+ * system's state and step number, never on its batch. */
+
+/* One time step of n points in place (xyz [n][3], device): point i, axis
+ * x / y / z, moves by sigma * z_i with standard normal draws from
+ * Philox4x32-10 (Salmon et al., SC'11) at counter (i, step low, step high, 0)
+ * and key (seed low, seed high): output words r0..r3 give uniforms
+ * u_k = (floor(r_k / 2^9) + 1/2) * 2^-23 and Box-Muller normals
+ * z_x = sqrt(-2 ln u0) cos(2 pi u1), z_y = sqrt(-2 ln u0) sin(2 pi u1),
+ * z_z = sqrt(-2 ln u2) cos(2 pi u3); then x < 0 -> -x, x > 1 -> 2 - x.
+ * float32 arithmetic.  Asynchronous on `stream`; runs on the current device. */
+int fmm_displace(float* xyz, uint32_t n, uint64_t seed, uint64_t step, float sigma, void* stream);
+
+typedef struct fmm_server fmm_server;
+
+#define FMM_SERVER_DIGEST 0x1u /* hash every result (for equivalence tests) */
+
+typedef struct fmm_server_params {
+  uint32_t workers;    /* concurrent batched builds, >= 1 */
+  uint32_t max_batch;  /* systems per batched build, >= 1 (1: one build per request) */
+  uint64_t mem_budget; /* workspace bytes shared by the workers; 0: 80% of the
+                          device memory free at creation */
+  uint32_t flags;      /* FMM_SERVER_DIGEST */
+} fmm_server_params;
+
+/* Outcome of one request.  Times in seconds on the server's clock (steady,
+ * zero at creation): arrival (for a trace: the scheduled arrival), start of
+ * its batch, completion (the batch's results read back). */
+typedef struct fmm_request_info {
+  uint64_t id;
+  uint32_t system;
+  uint32_t status;     /* fmm_status of the step */
+  uint64_t step;       /* the system's step count after this request */
+  double t_arrival, t_start, t_done;
+  uint32_t batch_size; /* systems built in the same batched build */
+  uint32_t worker;
+  uint64_t points;     /* points of the system */
+  uint64_t nnz_e2, nnz_e4; /* list entries over all levels */
+  uint64_t digest;     /* FMM_SERVER_DIGEST: hash of every output array, else 0 */
+} fmm_request_info;
+
+/* Creates a server on `device` and starts its worker threads. */
+int fmm_server_create(fmm_server** srv, int device, const fmm_server_params* params);
+/* Finishes every queued request, stops the workers, frees everything. */
+int fmm_server_destroy(fmm_server* srv);
+/* Adds a system of n points (xyz [n][3] float32: host memory if `host`,
+ * else device), copied into the server; depth L (0..21) and step size
+ * sigma_scale * 2^-L are fixed for its life; seed keys its random steps.
+ * The system starts at step 0.  FMM_ERR_DOMAIN for a coordinate outside
+ * [0, 1]. */
+int fmm_server_add_system(fmm_server* srv, const float* xyz, uint32_t n, int host, int L,
+                          float sigma_scale, uint64_t seed, uint32_t* system);
+/* Queues one step of `system` (arrival: now). */
+int fmm_server_submit(fmm_server* srv, uint32_t system, uint64_t* request_id);
+/* Blocks until the request is done. */
+int fmm_server_wait(fmm_server* srv, uint64_t request_id, fmm_request_info* info);
+/* Open-loop replay: request k arrives at (call time + arrival_s[k]) for
+ * system[k] (arrival_s ascending); blocks until every request is done and
+ * fills info[k]. */
+int fmm_server_run_trace(fmm_server* srv, const double* arrival_s, const uint32_t* system,
+                         uint32_t count, fmm_request_info* info);
+/* Copies a system's current points to host memory (xyz [n][3]); the system
+ * must have no request queued or running (FMM_ERR_ARG otherwise). */
+int fmm_server_points(fmm_server* srv, uint32_t system, float* host_xyz);
+/* The system's latest tree (device arrays in a worker's arena): valid while
+ * no request runs, until that worker's next build.  FMM_ERR_ARG if the system
+ * has no result yet or has a request queued or running. */
+int fmm_server_tree(fmm_server* srv, uint32_t system, fmm_tree* out);
 
 /* Static description of a status code. */
 const char* fmm_status_string(int status);

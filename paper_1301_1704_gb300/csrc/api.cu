@@ -921,6 +921,7 @@ struct PairIn {
   uint32_t N;
   const float* recv;
   uint32_t M;
+  int L;  // own depth, or -1: the call's params
 };
 
 int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes);
@@ -930,7 +931,6 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
               fmm_tree* outs) {
   cudaStream_t s = c->stream;
   int err = FMM_OK;
-  const bool smode = prm.L < 0;
   const bool stall = (prm.flags & FMM_FLAG_TEST_STALL) != 0;
   const bool host_in = (prm.flags & FMM_FLAG_HOST_INPUT) != 0;
   const uint64_t wait_ns = wait_ns_of(prm);
@@ -938,7 +938,9 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
   uint64_t expect = 0;
   for (uint32_t k = 0; k < npairs; ++k) {
     uint64_t b = 0;
-    query_workspace(pairs[k].N, pairs[k].M, prm, &b);
+    fmm_params pk = prm;
+    if (pairs[k].L >= 0) pk.L = pairs[k].L;
+    query_workspace(pairs[k].N, pairs[k].M, pk, &b);
     expect += b;
   }
   FMM_TRY(arena_reset(c, c->peak_request > expect ? c->peak_request : expect));
@@ -974,64 +976,84 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
   std::vector<SetPlan*> all;
   for (auto& sp : sets) all.push_back(&sp);
 
-  if (!smode) {
-    // Fixed depth: box depth L, sorted deep enough for the finishing sort.
-    for (auto& jp : jobs) jp.L = prm.L;
-    for (auto& sp : sets) {
-      sp.Lb = prm.L;
-      sp.Ls = std::max(sort_level(sp.n, sp.Lb), sp.Lb);
+  // Jobs of fixed depth (their own, or the call's L) and cluster-size jobs
+  // (L = -1).  Sort depth: at least every fixed depth the set serves, and deep
+  // enough that a box averages a few points, which keeps the finishing sort
+  // short.
+  std::vector<int> fixed_lb(sets.size(), -1);
+  std::vector<uint8_t> in_smode(sets.size(), 0);
+  bool any_smode = false;
+  for (uint32_t k = 0; k < npairs; ++k) {
+    JobPlan& jp = jobs[k];
+    jp.L = pairs[k].L >= 0 ? pairs[k].L : prm.L;
+    if (jp.L >= 0) {
+      fixed_lb[jp.src] = std::max(fixed_lb[jp.src], jp.L);
+      fixed_lb[jp.recv] = std::max(fixed_lb[jp.recv], jp.L);
+    } else {
+      in_smode[jp.src] = in_smode[jp.recv] = 1;
+      any_smode = true;
     }
+  }
+  for (uint32_t i = 0; i < sets.size(); ++i) {
+    SetPlan& sp = sets[i];
+    const int lb = std::max(fixed_lb[i], in_smode[i] ? 2 : 0);
+    sp.Ls = std::max(sort_level(sp.n, lb), lb);
+  }
+  {
     SortMem sm;
     FMM_TRY(sort_sets(c, all, stall, wait_ns, &sm));
-  } else {
-    // Cluster-size mode (Sec. 2.1): sort to each set's natural depth, find the
-    // deepest level at which s + 1 sorted points still share a box; sets whose
-    // boxes are still too full at the sort depth are sorted on all key bits.
-    for (auto& sp : sets) sp.Ls = sort_level(sp.n, 2);
-    SortMem sm;
-    FMM_TRY(sort_sets(c, all, stall, wait_ns, &sm));
-    DevStatus st{};
-    FMM_TRY(depth_sets(c, all, sm, prm.s, &st));
-    if (st.code) return (int)st.code;
-    std::vector<SetPlan*> deep;
-    for (auto& sp : sets)
-      if (!sp.full && sp.depth > (uint32_t)sp.Ls) {
-        sp.full = true;
-        deep.push_back(&sp);
-      }
-    if (!deep.empty()) {
-      SortMem sd;
-      FMM_TRY(sort_sets(c, deep, false, wait_ns, &sd));
-      FMM_TRY(depth_sets(c, deep, sd, prm.s, &st));
+    if (any_smode) {
+      // Cluster-size mode (Sec. 2.1): the deepest level at which s + 1 sorted
+      // points still share a box, per set; sets whose boxes are still too
+      // full at the sort depth are sorted on all key bits and measured again.
+      std::vector<SetPlan*> ss;
+      for (uint32_t i = 0; i < sets.size(); ++i)
+        if (in_smode[i]) ss.push_back(&sets[i]);
+      // (measured over all sorted sets: the sort's descriptors are in that order)
+      DevStatus st{};
+      FMM_TRY(depth_sets(c, all, sm, prm.s, &st));
       if (st.code) return (int)st.code;
-    }
-    // A job's depth: the smallest L >= 2 at which neither set has a box of
-    // more than s points; level 21 with s_unmet when no level has.
-    for (auto& jp : jobs) {
-      const uint32_t d = std::max(sets[jp.src].depth, sets[jp.recv].depth);
-      if (d > (uint32_t)kMaxLevel) {
-        jp.L = kMaxLevel;
-        jp.s_unmet = 1;
-      } else {
-        jp.L = std::max(2, (int)d);
+      std::vector<SetPlan*> deep;
+      for (auto* sp : ss)
+        if (!sp->full && sp->depth > (uint32_t)sp->Ls) {
+          sp->full = true;
+          deep.push_back(sp);
+        }
+      if (!deep.empty()) {
+        SortMem sd;
+        FMM_TRY(sort_sets(c, deep, false, wait_ns, &sd));
+        FMM_TRY(depth_sets(c, deep, sd, prm.s, &st));
+        if (st.code) return (int)st.code;
+      }
+      // A job's depth: the smallest L >= 2 at which neither set has a box of
+      // more than s points; level 21 with s_unmet when no level has.
+      for (auto& jp : jobs) {
+        if (jp.L >= 0) continue;
+        const uint32_t d = std::max(sets[jp.src].depth, sets[jp.recv].depth);
+        if (d > (uint32_t)kMaxLevel) {
+          jp.L = kMaxLevel;
+          jp.s_unmet = 1;
+        } else {
+          jp.L = std::max(2, (int)d);
+        }
       }
     }
-    for (auto& sp : sets) sp.Lb = 0;
-    for (auto& jp : jobs) {
-      sets[jp.src].Lb = std::max(sets[jp.src].Lb, jp.L);
-      sets[jp.recv].Lb = std::max(sets[jp.recv].Lb, jp.L);
+  }
+  for (auto& sp : sets) sp.Lb = 0;
+  for (auto& jp : jobs) {
+    sets[jp.src].Lb = std::max(sets[jp.src].Lb, jp.L);
+    sets[jp.recv].Lb = std::max(sets[jp.recv].Lb, jp.L);
+  }
+  // A set paired with a deeper one needs its order to that depth.
+  std::vector<SetPlan*> resort;
+  for (auto& sp : sets)
+    if (sp.Lb > sp.Ls) {
+      sp.Ls = std::max(sort_level(sp.n, sp.Lb), sp.Lb);
+      resort.push_back(&sp);
     }
-    // A set paired with a deeper one needs its order to that depth.
-    std::vector<SetPlan*> resort;
-    for (auto& sp : sets)
-      if (sp.Lb > sp.Ls) {
-        sp.Ls = std::max(sort_level(sp.n, sp.Lb), sp.Lb);
-        resort.push_back(&sp);
-      }
-    if (!resort.empty()) {
-      SortMem sr;
-      FMM_TRY(sort_sets(c, resort, false, wait_ns, &sr));
-    }
+  if (!resort.empty()) {
+    SortMem sr;
+    FMM_TRY(sort_sets(c, resort, false, wait_ns, &sr));
   }
 
   Readback rb;
@@ -1160,7 +1182,7 @@ int fmm_build(fmm_ctx* c, const float* src_xyz, uint32_t N, const float* recv_xy
   DeviceGuard g(c->device);
   c->stream = static_cast<cudaStream_t>(stream);
   const uint64_t l0 = c->launches;
-  const PairIn pin{src_xyz, N, recv_xyz, M};
+  const PairIn pin{src_xyz, N, recv_xyz, M, -1};
   return finish_call(c, do_builds(c, &pin, 1, params, out), l0);
 }
 
@@ -1169,14 +1191,17 @@ int fmm_build_batched(fmm_ctx* c, const fmm_set* sets, uint32_t nsets, fmm_param
   if (!c || (nsets > 0 && (!sets || !outs))) return FMM_ERR_ARG;
   FMM_TRY(check_params(params));
   if (params.flags & FMM_FLAG_TEST_STALL) return FMM_ERR_ARG;
-  for (uint32_t k = 0; k < nsets; ++k)
+  for (uint32_t k = 0; k < nsets; ++k) {
     if ((sets[k].N > 0 && !sets[k].src) || (sets[k].M > 0 && !sets[k].recv)) return FMM_ERR_ARG;
+    if (sets[k].L < FMM_SET_PARAMS_L || sets[k].L > kMaxLevel) return FMM_ERR_LEVEL;
+  }
   if (nsets == 0) return FMM_OK;
   DeviceGuard g(c->device);
   c->stream = static_cast<cudaStream_t>(stream);
   const uint64_t l0 = c->launches;
   std::vector<PairIn> pins(nsets);
-  for (uint32_t k = 0; k < nsets; ++k) pins[k] = {sets[k].src, sets[k].N, sets[k].recv, sets[k].M};
+  for (uint32_t k = 0; k < nsets; ++k)
+    pins[k] = {sets[k].src, sets[k].N, sets[k].recv, sets[k].M, sets[k].L};
   return finish_call(c, do_builds(c, pins.data(), nsets, params, outs), l0);
 }
 

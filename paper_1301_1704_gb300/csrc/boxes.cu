@@ -358,12 +358,13 @@ uint32_t coarse_tiles(uint32_t cap) {
 void launch_finish_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
                          DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
   if (units == 0) return;
-  static bool attr = false;
-  if (!attr) {
+  // once per process (thread-safe static initialisation)
+  static const bool attr = [] {
     cudaFuncSetAttribute(finish_boxes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBoxSmem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   finish_boxes_kernel<<<units, kBoxThreads, kBoxSmem, s>>>(segs, slots, nslots, st, wait_ns);
 }
 

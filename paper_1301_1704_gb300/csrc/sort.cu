@@ -293,14 +293,15 @@ void launch_onesweep_pass(int pass, const float* xyz, const uint64_t* keys_in,
                           uint64_t* status, uint32_t* counter, DevStatus* st, uint64_t wait_ns,
                           int stall_tile, cudaStream_t s) {
   if (n == 0) return;
-  static bool attr = false;
-  if (!attr) {
+  // once per process (thread-safe static initialisation)
+  static const bool attr = [] {
     cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kSortSmem);
     cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kSortSmem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int shift = p.lo + pass * p.bits;
   if (pass == 0)
     onesweep_kernel<true><<<p.ntiles, kSortThreads, kSortSmem, s>>>(
@@ -629,21 +630,19 @@ void launch_rts_scatter(int pass, const TileRec* recs, uint32_t ntiles, const ui
                         const uint32_t* offsets, bool stable, bool bulk, DevStatus* st,
                         uint64_t wait_ns, cudaStream_t s) {
   if (ntiles == 0) return;
-  static bool attr = false;
-  static int sms = 0;
-  if (!attr) {
+  // once per process (thread-safe static initialisation)
+  static const int sms = [] {
     cudaFuncSetAttribute(rts_scatter_kernel<true, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
     cudaFuncSetAttribute(rts_scatter_kernel<true, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
     cudaFuncSetAttribute(rts_scatter_kernel<false, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
-    int dev = 0;
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-    attr = true;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 152;
+  }();
   uint32_t grid = (uint32_t)sms * 2u;
   if (grid > ntiles) grid = ntiles;
   if (pass == 0) {

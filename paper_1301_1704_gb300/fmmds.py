@@ -50,14 +50,18 @@ class TreeC(C.Structure):
 
 
 class SetC(C.Structure):
-    _fields_ = [("src", C.c_void_p), ("N", C.c_uint32), ("recv", C.c_void_p), ("M", C.c_uint32)]
+    _fields_ = [("src", C.c_void_p), ("N", C.c_uint32), ("recv", C.c_void_p), ("M", C.c_uint32),
+                ("L", C.c_int32)]
 
 
 class Batch:
-    """fmm_set array (and result array) of a list of (src, recv) tensor pairs."""
+    """fmm_set array (and result array) of a list of (src, recv) tensor pairs,
+    with optional per-pair depths ``levels`` (None or -1: the call's L or s)."""
 
-    def __init__(self, sets):
+    def __init__(self, sets, levels=None):
         self.k = len(sets)
+        if levels is not None and len(levels) != self.k:
+            raise ValueError("one level per set")
         self.arr = (SetC * max(self.k, 1))()
         self.outs = (TreeC * max(self.k, 1))()
         self.sizes = []
@@ -66,9 +70,31 @@ class Batch:
             for t in (a, b):
                 if t.dtype.itemsize != 4 or (t.numel() and not t.is_contiguous()):
                     raise ValueError("points must be contiguous float32 [n, 3]")
+            lv = -1 if levels is None or levels[i] is None else int(levels[i])
             self.arr[i] = SetC(a.data_ptr() if a.shape[0] else 0, a.shape[0],
-                               b.data_ptr() if b.shape[0] else 0, b.shape[0])
+                               b.data_ptr() if b.shape[0] else 0, b.shape[0], lv)
             self.sizes.append((a.shape[0], b.shape[0]))
+
+
+class ServerParams(C.Structure):
+    _fields_ = [("workers", C.c_uint32), ("max_batch", C.c_uint32), ("mem_budget", C.c_uint64),
+                ("flags", C.c_uint32)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("system", C.c_uint32), ("status", C.c_uint32),
+                ("step", C.c_uint64), ("t_arrival", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double), ("batch_size", C.c_uint32), ("worker", C.c_uint32),
+                ("points", C.c_uint64), ("nnz_e2", C.c_uint64), ("nnz_e4", C.c_uint64),
+                ("digest", C.c_uint64)]
+
+
+FMM_SERVER_DIGEST = 0x1
+_INFO_FIELDS = [f for f, _ in RequestInfo._fields_]
+
+
+def _info_dict(x: RequestInfo) -> dict:
+    return {f: getattr(x, f) for f in _INFO_FIELDS}
 
 
 class KernelTime(C.Structure):
@@ -84,6 +110,9 @@ EXPORTS = (
     "fmm_query_workspace",
     "fmm_set_tuning", "fmm_get_tuning", "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing",
     "fmm_last_launch_count", "fmm_status_string", "fmm_exclusive_scan_noalloc",
+    "fmm_displace", "fmm_server_create", "fmm_server_destroy", "fmm_server_add_system",
+    "fmm_server_submit", "fmm_server_wait", "fmm_server_run_trace", "fmm_server_points",
+    "fmm_server_tree",
 )
 FMM_NOALLOC_SCAN_MAX = 1 << 26
 
@@ -143,6 +172,27 @@ def _load():
     lib.fmm_exclusive_scan_noalloc.restype = C.c_int
     lib.fmm_status_string.argtypes = [C.c_int]
     lib.fmm_status_string.restype = C.c_char_p
+    lib.fmm_displace.argtypes = [C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_float,
+                                 C.c_void_p]
+    lib.fmm_displace.restype = C.c_int
+    lib.fmm_server_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(ServerParams)]
+    lib.fmm_server_create.restype = C.c_int
+    lib.fmm_server_destroy.argtypes = [C.c_void_p]
+    lib.fmm_server_destroy.restype = C.c_int
+    lib.fmm_server_add_system.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_int, C.c_int,
+                                          C.c_float, C.c_uint64, C.POINTER(C.c_uint32)]
+    lib.fmm_server_add_system.restype = C.c_int
+    lib.fmm_server_submit.argtypes = [C.c_void_p, C.c_uint32, _u64p]
+    lib.fmm_server_submit.restype = C.c_int
+    lib.fmm_server_wait.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(RequestInfo)]
+    lib.fmm_server_wait.restype = C.c_int
+    lib.fmm_server_run_trace.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32,
+                                         C.POINTER(RequestInfo)]
+    lib.fmm_server_run_trace.restype = C.c_int
+    lib.fmm_server_points.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p]
+    lib.fmm_server_points.restype = C.c_int
+    lib.fmm_server_tree.argtypes = [C.c_void_p, C.c_uint32, C.POINTER(TreeC)]
+    lib.fmm_server_tree.restype = C.c_int
     _lib = lib
     return lib
 
@@ -308,23 +358,27 @@ class Context:
             return tc
         return _tree_from(tc, n, m)
 
-    def batch(self, sets) -> "Batch":
+    def batch(self, sets, levels=None) -> "Batch":
         """The fmm_set array of a list of (src, recv) pairs of float32 [n, 3]
         CUDA tensors, built once for repeated fmm_build_batched calls on the
         same tensors (the tensors must stay alive and in place)."""
-        return Batch(sets)
+        return Batch(sets, levels)
 
     def build_batched(self, sets, L: int | None = None, s: int | None = None, stream=None,
-                      flags: int = 0, raw: bool = False):
+                      flags: int = 0, raw: bool = False, levels=None):
         """fmm_build_batched.  ``sets``: list of (src, recv) pairs of float32
         [n, 3] CUDA tensors (the same tensor twice for an aliased set), or a
-        :class:`Batch` of them.  Returns one :class:`Tree` per set (or the
-        raw ``TreeC`` array)."""
+        :class:`Batch` of them; ``levels``: optional per-set depths that
+        override L / s.  Returns one :class:`Tree` per set (or the raw
+        ``TreeC`` array)."""
         lib = _load()
+        b = sets if isinstance(sets, Batch) else Batch(sets, levels)
+        if L is None and s is None and levels is not None and all(
+                v is not None and v >= 0 for v in levels):
+            L = 0  # every set carries its own depth
         if (L is None) == (s is None):
             raise ValueError("give exactly one of L or s")
         p = Params(L if L is not None else -1, s if s is not None else 0, flags, 0)
-        b = sets if isinstance(sets, Batch) else Batch(sets)
         st = lib.fmm_build_batched(self._h, b.arr, b.k, p, b.outs, C.c_void_p(self._stream(stream)))
         if st != FMM_OK:
             raise FmmError(st, "fmm_build_batched")
@@ -402,3 +456,104 @@ def query_workspace(N: int, M: int, L: int | None = None, s: int | None = None, 
 
 def status_string(code: int) -> str:
     return _load().fmm_status_string(code).decode()
+
+
+def displace(xyz, seed: int, step: int, sigma: float, stream=None) -> None:
+    """fmm_displace: one time step of the float32 [n, 3] CUDA tensor in place."""
+    import torch
+    lib = _load()
+    if xyz.dtype != torch.float32 or not xyz.is_contiguous() or not xyz.is_cuda:
+        raise ValueError("points must be a contiguous float32 CUDA tensor [n, 3]")
+    n = xyz.shape[0]
+    h = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    st = lib.fmm_displace(C.c_void_p(xyz.data_ptr() if n else 0), n, seed, step, sigma,
+                          C.c_void_p(h))
+    if st != FMM_OK:
+        raise FmmError(st, "fmm_displace")
+
+
+class Server:
+    """Served dynamic rebuilds (fmm_server_*): resident time-stepped systems,
+    continuous batching over ``workers`` concurrent batched builds."""
+
+    def __init__(self, device: int = 0, workers: int = 2, max_batch: int = 8,
+                 mem_budget: int = 0, digest: bool = False):
+        lib = _load()
+        self._h = C.c_void_p()
+        prm = ServerParams(workers, max_batch, mem_budget, FMM_SERVER_DIGEST if digest else 0)
+        st = lib.fmm_server_create(C.byref(self._h), device, C.byref(prm))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_server_create")
+        self.sizes = []
+
+    def add_system(self, xyz, L: int, sigma_scale: float = 0.1, seed: int = 0) -> int:
+        """Copies the points (numpy float32 [n, 3], or a CUDA tensor) in."""
+        lib = _load()
+        sid = C.c_uint32()
+        if isinstance(xyz, np.ndarray):
+            a = np.ascontiguousarray(xyz, dtype=np.float32)
+            ptr, host, n = a.ctypes.data, 1, a.shape[0]
+        else:
+            a = xyz.contiguous()
+            ptr, host, n = a.data_ptr(), 0, a.shape[0]
+        st = lib.fmm_server_add_system(self._h, C.c_void_p(ptr if n else 0), n, host, L,
+                                       sigma_scale, seed, C.byref(sid))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_server_add_system")
+        self.sizes.append(n)
+        return sid.value
+
+    def submit(self, system: int) -> int:
+        rid = C.c_uint64()
+        st = _load().fmm_server_submit(self._h, system, C.byref(rid))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_server_submit")
+        return rid.value
+
+    def wait(self, request_id: int) -> dict:
+        inf = RequestInfo()
+        st = _load().fmm_server_wait(self._h, request_id, C.byref(inf))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_server_wait")
+        return _info_dict(inf)
+
+    def step(self, system: int) -> dict:
+        return self.wait(self.submit(system))
+
+    def run_trace(self, arrival_s, systems) -> list:
+        t = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        y = np.ascontiguousarray(systems, dtype=np.uint32)
+        k = t.shape[0]
+        out = (RequestInfo * max(k, 1))()
+        st = _load().fmm_server_run_trace(self._h, C.c_void_p(t.ctypes.data),
+                                          C.c_void_p(y.ctypes.data), k, out)
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_server_run_trace")
+        return [_info_dict(out[i]) for i in range(k)]
+
+    def points(self, system: int) -> np.ndarray:
+        n = self.sizes[system]
+        a = np.empty((n, 3), np.float32)
+        st = _load().fmm_server_points(self._h, system, C.c_void_p(a.ctypes.data))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_server_points")
+        return a
+
+    def tree(self, system: int) -> "Tree":
+        tc = TreeC()
+        st = _load().fmm_server_tree(self._h, system, C.byref(tc))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_server_tree")
+        n = self.sizes[system]
+        return _tree_from(tc, n, n)
+
+    def close(self):
+        if self._h:
+            _load().fmm_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

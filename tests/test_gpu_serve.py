@@ -1,0 +1,145 @@
+"""Served dynamic rebuilds on the GPU: the time step against the oracle's,
+each served step's tree against the oracle built from the served points, and
+every result the same alone and in the mix (continuous batching)."""
+import numpy as np
+import pytest
+
+from oracle import displace as D
+from paper_1301_1704_gb300 import workloads
+from tests.test_gpu_parity import compare_full
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# float32 step (logf, sincospif, fma) against the float64 oracle: the draws
+# agree to a few float32 ulps of z, the sum to half an ulp of x (2^-24 near
+# 1), so 4e-7 bounds the difference for sigma <= 0.1.
+DISPLACE_TOL = 4e-7
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1301_1704_gb300 import build, fmmds
+    build.build()
+    return fmmds
+
+
+def test_displace_matches_oracle(lib):
+    rng = np.random.default_rng(21)
+    p = rng.random((100003, 3)).astype(np.float32)
+    p[:300] = rng.choice(np.array([0.0, 1.0, 1e-7, 1 - 1e-7], np.float32), size=(300, 3))
+    for seed, step, sigma in ((7, 0, 0.05), (2 ** 40 + 3, 2 ** 33 + 5, 1e-3), (0, 17, 0.1)):
+        d = torch.from_numpy(p).cuda()
+        lib.displace(d, seed, step, np.float32(sigma))
+        got = d.cpu().numpy().astype(np.float64)
+        want = D.displace(p.astype(np.float64), seed, step, float(np.float32(sigma)))
+        assert np.all((got >= 0) & (got <= 1))
+        err = np.abs(got - want)
+        assert err.max() <= DISPLACE_TOL, (seed, step, err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def _systems(seed=3):
+    sizes = [1500, 20000, 120000]
+    return [workloads.clumps(n, seed * 10 + i, nclumps=8, sigma=0.02) for i, n in enumerate(sizes)]
+
+
+def _levels(lib, pts, s=64):
+    ctx = lib.Context(0)
+    try:
+        return [ctx.build(torch.from_numpy(p).cuda(), torch.from_numpy(p).cuda(), s=s).L for p in pts]
+    finally:
+        ctx.close()
+
+
+def test_served_steps_match_oracle(lib, orc):
+    pts = _systems()
+    Ls = _levels(lib, pts)
+    srv = lib.Server(0, workers=2, max_batch=8)
+    try:
+        ids = [srv.add_system(p, L, 0.1, seed=100 + k) for k, (p, L) in enumerate(zip(pts, Ls))]
+        prev = [p.astype(np.float64) for p in pts]
+        for step in range(3):
+            rids = [srv.submit(i) for i in ids]
+            infos = [srv.wait(r) for r in rids]
+            for k, (i, inf) in enumerate(zip(ids, infos)):
+                assert inf["status"] == 0 and inf["step"] == step + 1
+                cur = srv.points(i)
+                want = D.displace(prev[k], 100 + k, step, D.sigma_of(Ls[k]))
+                assert np.abs(cur - want).max() <= DISPLACE_TOL
+                prev[k] = cur.astype(np.float64)
+                if step == 2:
+                    got = srv.tree(i).numpy()
+                    compare_full(got, orc.build_tree(cur, cur, L=Ls[k]), Ls[k])
+    finally:
+        srv.close()
+
+
+def _trace(nsys, steps, rate, seed):
+    rng = np.random.default_rng(seed)
+    per = [0] * nsys
+    t, arr, sys = 0.0, [], []
+    while min(per) < steps:
+        t += rng.exponential(1.0 / rate)
+        k = int(rng.integers(0, nsys))
+        arr.append(t)
+        sys.append(k)
+        per[k] += 1
+    return np.array(arr), np.array(sys, np.uint32)
+
+
+def test_same_alone_and_in_the_mix(lib):
+    pts = _systems(5)
+    Ls = _levels(lib, pts)
+    arr, sys = _trace(len(pts), 6, 20000.0, 9)  # arrivals far faster than builds: batches form
+
+    def run(workers, max_batch, budget=0):
+        srv = lib.Server(0, workers=workers, max_batch=max_batch, mem_budget=budget, digest=True)
+        try:
+            for k, (p, L) in enumerate(zip(pts, Ls)):
+                srv.add_system(p, L, 0.1, seed=7 + k)
+            infos = srv.run_trace(arr, sys)
+            final = [srv.points(k) for k in range(len(pts))]
+        finally:
+            srv.close()
+        return infos, final
+
+    mix, fmix = run(2, 8)
+    alone, falone = run(1, 1)
+    assert max(i["batch_size"] for i in mix) > 1       # systems were built together
+    assert max(i["batch_size"] for i in alone) == 1
+    dm = {(i["system"], i["step"]): i["digest"] for i in mix}
+    da = {(i["system"], i["step"]): i["digest"] for i in alone}
+    assert dm == da and all(v != 0 for v in dm.values())
+    for a, b in zip(fmix, falone):
+        assert np.array_equal(a, b)
+    for i in mix:
+        assert i["t_arrival"] <= i["t_start"] <= i["t_done"]
+    # a budget below any one system's estimate admits one system per batch
+    tight, _ = run(2, 8, budget=1)
+    assert max(i["batch_size"] for i in tight) == 1
+    assert {(i["system"], i["step"]): i["digest"] for i in tight} == da
+
+
+def test_server_argument_errors(lib):
+    srv = lib.Server(0, workers=1, max_batch=2)
+    try:
+        bad = workloads.uniform(100, 1)
+        bad[5, 2] = np.nan
+        with pytest.raises(lib.FmmError) as e:
+            srv.add_system(bad, 3)
+        assert e.value.code == lib.FMM_ERR_DOMAIN
+        with pytest.raises(lib.FmmError) as e:
+            srv.add_system(workloads.uniform(100, 1), 22)
+        assert e.value.code == lib.FMM_ERR_LEVEL
+        with pytest.raises(lib.FmmError):
+            srv.submit(0)  # no such system
+        k = srv.add_system(workloads.uniform(100, 2), 3)
+        with pytest.raises(lib.FmmError):
+            srv.tree(k)  # no result yet
+        assert srv.step(k)["status"] == 0
+        assert srv.tree(k).L == 3
+    finally:
+        srv.close()
