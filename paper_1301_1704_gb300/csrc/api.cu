@@ -438,9 +438,10 @@ int run_sort(fmm_ctx* c, std::vector<SetPlan*>& sets, SortMem& m, bool stall, ui
     uint64_t* kout = (p & 1) ? m.kb : m.ka;
     uint32_t* vout = (p & 1) ? m.vb : m.va;
     {
+      // pass 0 stores the keys in buffer b, which pass 0's scatter then reads
       Launch L(c, "tile_hist");
       launch_tile_hist(p, m.segs, m.pass_slots[p], m.pass_nslots[p], m.pass_tiles[p],
-                       m.pass_hist[p], kin, m.pass_recs[p], c->st, s);
+                       m.pass_hist[p], kin, p == 0 ? m.kb : nullptr, m.pass_recs[p], c->st, s);
     }
     {
       Launch L(c, "scan");

@@ -381,12 +381,15 @@ __host__ __device__ inline int passes_for(int Ls) { return (3 * Ls + kRadixBits 
 // aux0 = first histogram entry of the set, aux1 = scan-to-slot correction):
 // per-tile digit histograms, digit-major per set, set after set.
 // Per-tile digit counts of pass p, and the tiles' records for the scatter.
+// Pass 0 forms the keys from the coordinates and stores them to keys_out;
+// later passes read `keys`.
 void launch_tile_hist(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
-                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, TileRec* recs,
-                      DevStatus* st, cudaStream_t s);
-// Scatter of pass p from `in` (or the coordinates) to `out` (concatenated
-// arrays of `slots_total` entries).  stable = false only for a first pass
-// that a finishing sort follows.
+                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, uint64_t* keys_out,
+                      TileRec* recs, DevStatus* st, cudaStream_t s);
+// Scatter of pass p from (keys_in, vals_in) -- pass 0: the keys pass 0's
+// histogram stored, values = point indices -- to (keys_out, vals_out)
+// (concatenated arrays).  stable = false only for a first pass that a
+// finishing sort follows.
 void launch_rts_scatter(int pass, const TileRec* recs, uint32_t ntiles, const uint64_t* keys_in,
                         const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
                         const uint32_t* offsets, bool stable, bool bulk, DevStatus* st,

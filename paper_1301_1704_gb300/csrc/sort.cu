@@ -325,11 +325,15 @@ __device__ __forceinline__ void count_digit(uint64_t key, int shift, uint32_t* s
   atomicAdd(&sh[(uint32_t)(key >> shift) & (kRadixMax - 1u)], 1u);
 }
 
+// kFromXyz (first pass): the keys are formed here from the coordinates and
+// stored to keys_out (concatenated slots) for the scatter, which then reads 8
+// bytes a point instead of forming each key a second time.
 template <bool kFromXyz>
 __global__ void __launch_bounds__(256) tile_hist_kernel(const Seg* __restrict__ segs,
                                                         const Slot* __restrict__ slots,
                                                         uint32_t nslots, int pass,
                                                         const uint64_t* __restrict__ keys,
+                                                        uint64_t* __restrict__ keys_out,
                                                         uint32_t* __restrict__ hist,
                                                         TileRec* __restrict__ recs,
                                                         DevStatus* st) {
@@ -361,16 +365,24 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(const Seg* __restrict__ 
   bool bad = false;
   if (kFromXyz) {
     const float* xyz = sg.xyz;
+    uint64_t* ko = keys_out + sg.base + base;  // set bases: multiples of 4 slots
     uint32_t done = 0;
     if (((uintptr_t)xyz & 15u) == 0) {  // 4 points = 3 float4; tiles start at multiples of 4
       const float4* v = reinterpret_cast<const float4*>(xyz + 3 * base);
+      ulonglong2* o = reinterpret_cast<ulonglong2*>(ko);
       for (uint32_t g = threadIdx.x; g < cnt / 4; g += blockDim.x) {
         const float4 a = __ldcs(v + 3 * g), b = __ldcs(v + 3 * g + 1), c = __ldcs(v + 3 * g + 2);
         bool ok0, ok1, ok2, ok3;
-        count_digit(morton_key(a.x, a.y, a.z, &ok0), shift, sh);
-        count_digit(morton_key(a.w, b.x, b.y, &ok1), shift, sh);
-        count_digit(morton_key(b.z, b.w, c.x, &ok2), shift, sh);
-        count_digit(morton_key(c.y, c.z, c.w, &ok3), shift, sh);
+        const uint64_t k0 = morton_key(a.x, a.y, a.z, &ok0);
+        const uint64_t k1 = morton_key(a.w, b.x, b.y, &ok1);
+        const uint64_t k2 = morton_key(b.z, b.w, c.x, &ok2);
+        const uint64_t k3 = morton_key(c.y, c.z, c.w, &ok3);
+        count_digit(k0, shift, sh);
+        count_digit(k1, shift, sh);
+        count_digit(k2, shift, sh);
+        count_digit(k3, shift, sh);
+        o[2 * g] = make_ulonglong2(k0, k1);
+        o[2 * g + 1] = make_ulonglong2(k2, k3);
         bad |= !(ok0 && ok1 && ok2 && ok3);
       }
       done = cnt & ~3u;
@@ -378,7 +390,9 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(const Seg* __restrict__ 
     for (uint32_t j = done + threadIdx.x; j < cnt; j += blockDim.x) {
       const uint64_t i = base + j;
       bool ok;
-      count_digit(morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok), shift, sh);
+      const uint64_t k = morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], &ok);
+      count_digit(k, shift, sh);
+      ko[j] = k;
       bad |= !ok;
     }
   } else {
@@ -398,31 +412,31 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(const Seg* __restrict__ 
 }
 
 void launch_tile_hist(int pass, const Seg* segs, const Slot* slots, uint32_t nslots,
-                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, TileRec* recs,
-                      DevStatus* st, cudaStream_t s) {
+                      uint32_t ntiles, uint32_t* hist, const uint64_t* keys, uint64_t* keys_out,
+                      TileRec* recs, DevStatus* st, cudaStream_t s) {
   if (ntiles == 0) return;
   if (pass == 0)
-    tile_hist_kernel<true><<<ntiles, 256, 0, s>>>(segs, slots, nslots, 0, nullptr, hist, recs,
-                                                  st);
+    tile_hist_kernel<true><<<ntiles, 256, 0, s>>>(segs, slots, nslots, 0, nullptr, keys_out, hist,
+                                                  recs, st);
   else
-    tile_hist_kernel<false><<<ntiles, 256, 0, s>>>(segs, slots, nslots, pass, keys, hist, recs,
-                                                   st);
+    tile_hist_kernel<false><<<ntiles, 256, 0, s>>>(segs, slots, nslots, pass, keys, nullptr, hist,
+                                                   recs, st);
 }
 
 // Scatter of one pass, persistent: each block walks the tiles u = blockIdx.x,
 // + gridDim.x, ... of all sets and, while it ranks and scatters one tile, a
-// bulk copy (TMA) brings the next tile's input -- the coordinates in the
-// first pass, the (key, index) pairs in later ones -- into the other half of
-// a double buffer.  Partial tiles, and inputs that are not 16-byte aligned,
-// are read with plain loads.  Global output position of (set, digit, tile) =
-// scanned offset + the slot's correction (set base minus the points of the
-// sets before it in this pass).
-constexpr uint32_t kInBytes = kSortTile * 12;  // xyz of a tile, or its keys + indices
+// bulk copy (TMA) brings the next tile's input -- the keys the first pass's
+// histogram kernel stored, then the (key, index) pairs of later passes --
+// into the other half of a double buffer.  Partial tiles are read with plain
+// loads.  Global output position of (set, digit, tile) = scanned offset + the
+// slot's correction (set base minus the points of the sets before it in this
+// pass).
+constexpr uint32_t kInBytes = kSortTile * 12;  // a tile's keys + indices
 constexpr size_t kScatterSmem = 2 * (size_t)kInBytes;
 
-// kStable: keep the input order inside a digit (every pass but an unstable
-// first one).
-template <bool kFromXyz, bool kStable>
+// kFirst: the values are the points' indices (first pass); kStable: keep the
+// input order inside a digit (every pass but an unstable first one).
+template <bool kFirst, bool kStable>
 __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     const TileRec* __restrict__ recs, uint32_t ntiles, const uint64_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
@@ -430,6 +444,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     DevStatus* st, uint64_t wait_ns) {
   constexpr int W = kSortThreads / 32;
   constexpr uint32_t mask = kRadixMax - 1u;
+  constexpr uint32_t kCopyBytes = kFirst ? kSortTile * 8 : kInBytes;
   __shared__ uint32_t s_fail;
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_wcnt[W][kRadixMax];  // per-warp digit counts, then block slots
@@ -448,30 +463,24 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
   __syncthreads();
   if (s_fail) return;  // an earlier kernel failed (domain error): leave the outputs alone
 
-  // Whether a tile is full and read by bulk copy (its source 16-byte aligned).
-  auto is_bulk = [&](const TileRec& r) -> bool {
-    if (!bulk || r.cnt != kSortTile) return false;
-    return kFromXyz ? ((uintptr_t)r.xyz & 15u) == 0 : true;  // set bases: multiples of 4 slots
-  };
+  // Full tiles are read by bulk copy (set bases are multiples of 4 slots, so
+  // their keys and indices start 16-byte aligned).
+  auto is_bulk = [&](const TileRec& r) -> bool { return bulk && r.cnt == kSortTile; };
   auto issue = [&](const TileRec& r, int b) {  // thread 0 only
     unsigned char* dst = s_in + b * kInBytes;
-    mbar_expect_tx(&s_bar[b], kInBytes);
-    if (kFromXyz) {
-      bulk_load(dst, r.xyz, kInBytes, &s_bar[b]);
-    } else {
-      bulk_load(dst, keys_in + r.first, kSortTile * 8, &s_bar[b]);
-      bulk_load(dst + kSortTile * 8, vals_in + r.first, kSortTile * 4, &s_bar[b]);
-    }
+    mbar_expect_tx(&s_bar[b], kCopyBytes);
+    bulk_load(dst, keys_in + r.first, kSortTile * 8, &s_bar[b]);
+    if (!kFirst) bulk_load(dst + kSortTile * 8, vals_in + r.first, kSortTile * 4, &s_bar[b]);
   };
-  uint32_t phase[2] = {0u, 0u};
-  bool pending[2] = {false, false};
+  // bit b: parity of buffer b's barrier phase / a copy into buffer b is in flight
+  uint32_t phase = 0u, pending = 0u;
   uint32_t u = blockIdx.x;
   TileRec rec;
   if (u < ntiles) {
     rec = recs[u];
     if (is_bulk(rec)) {
       if (threadIdx.x == 0) issue(rec, 0);
-      pending[0] = true;
+      pending |= 1u;
     }
   }
   for (int it = 0; u < ntiles; u += gridDim.x, ++it) {
@@ -480,7 +489,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     const TileRec r = rec;
     const uint32_t cnt = r.cnt;
     const int shift = (int)r.shift;
-    const bool full = pending[b];
+    const bool full = (pending >> b) & 1u;
     {
       const uint32_t un = u + gridDim.x;
       if (un < ntiles) {
@@ -490,7 +499,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
             fence_proxy_async();
             issue(rec, b ^ 1);
           }
-          pending[b ^ 1] = true;
+          pending |= 1u << (b ^ 1);
         }
       }
     }
@@ -501,14 +510,14 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     for (int i = threadIdx.x; i < W * kRadixMax; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
     bool ok = true;
     if (full) {
-      ok = mbar_wait(&s_bar[b], phase[b], st, wait_ns);
-      phase[b] ^= 1u;
-      pending[b] = false;
+      ok = mbar_wait(&s_bar[b], (phase >> b) & 1u, st, wait_ns);
+      phase ^= 1u << b;
+      pending &= ~(1u << b);
     }
     if (__syncthreads_or(!ok)) {
       // a copy never completed: let any other copy land, then leave
       for (int k = 0; k < 2; ++k)
-        if (pending[k]) mbar_wait(&s_bar[k], phase[k], st, wait_ns);
+        if ((pending >> k) & 1u) mbar_wait(&s_bar[k], (phase >> k) & 1u, st, wait_ns);
       return;
     }
 
@@ -523,17 +532,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
       key[k] = 0;
       val[k] = r.local + j;
       if (j < cnt) {
-        if (kFromXyz) {
-          const float* f = full ? reinterpret_cast<const float*>(buf) + 3 * j : r.xyz + 3 * j;
-          bool okk;
-          key[k] = morton_key(f[0], f[1], f[2], &okk);
-        } else if (full) {
-          key[k] = reinterpret_cast<const uint64_t*>(buf)[j];
-          val[k] = reinterpret_cast<const uint32_t*>(buf + kSortTile * 8)[j];
-        } else {
-          key[k] = keys_in[r.first + j];
-          val[k] = vals_in[r.first + j];
-        }
+        key[k] = full ? reinterpret_cast<const uint64_t*>(buf)[j] : keys_in[r.first + j];
+        if (!kFirst)
+          val[k] = full ? reinterpret_cast<const uint32_t*>(buf + kSortTile * 8)[j]
+                        : vals_in[r.first + j];
       }
     }
     uint32_t pos[kSortItems];
@@ -548,16 +550,27 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
         pos[k] = valid ? atomicAdd(&s_wcnt[0][(uint32_t)(key[k] >> shift) & mask], 1u) : 0u;
       }
     } else {
+      // Stable rank inside the warp's run of items: the lanes holding the
+      // same digit ("peers") come from one ballot per digit bit (a warp
+      // multisplit, which keeps the slow match unit out of the loop); the
+      // lowest peer adds their number to the warp's counter for the digit and
+      // hands the old count to the others.  A warp takes its items in input
+      // order, so count + peers below = rank among equal digits.
 #pragma unroll
       for (int k = 0; k < kSortItems; ++k) {
         const bool valid = (uint32_t)warp * (kSortItems * 32) + k * 32 + lane < cnt;
-        const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & mask : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = valid ? s_wcnt[warp][d] : 0u;
-        __syncwarp();
-        if (valid && (peers & lt) == 0) s_wcnt[warp][d] = before + __popc(peers);
-        __syncwarp();
-        pos[k] = before + __popc(peers & lt);
+        const uint32_t d = (uint32_t)(key[k] >> shift) & mask;
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < kRadixBits; ++b) {
+          const bool bit = ((d >> b) & 1u) != 0u;
+          const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+          peers &= bit ? bb : ~bb;
+        }
+        const int leader = valid ? __ffs(peers) - 1 : lane;
+        uint32_t old = 0;
+        if (valid && lane == leader) old = atomicAdd(&s_wcnt[warp][d], (uint32_t)__popc(peers));
+        pos[k] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
       }
     }
     __syncthreads();
@@ -648,10 +661,10 @@ void launch_rts_scatter(int pass, const TileRec* recs, uint32_t ntiles, const ui
   if (pass == 0) {
     if (stable)
       rts_scatter_kernel<true, true><<<grid, kSortThreads, kScatterSmem, s>>>(
-          recs, ntiles, nullptr, nullptr, keys_out, vals_out, offsets, bulk, st, wait_ns);
+          recs, ntiles, keys_in, nullptr, keys_out, vals_out, offsets, bulk, st, wait_ns);
     else
       rts_scatter_kernel<true, false><<<grid, kSortThreads, kScatterSmem, s>>>(
-          recs, ntiles, nullptr, nullptr, keys_out, vals_out, offsets, bulk, st, wait_ns);
+          recs, ntiles, keys_in, nullptr, keys_out, vals_out, offsets, bulk, st, wait_ns);
   } else {
     rts_scatter_kernel<false, true><<<grid, kSortThreads, kScatterSmem, s>>>(
         recs, ntiles, keys_in, vals_in, keys_out, vals_out, offsets, bulk, st, wait_ns);
