@@ -109,6 +109,22 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, dist, device: str = "cuda") -> float:
+    """The slowest rank's time (replicas: the job ends when the last one does)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, ms: float, world: int) -> float:
+    """Whole-job throughput in units per second: every rank's units over the
+    max-over-ranks time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def _algorithmic_bytes(tree) -> dict:
     """Compulsory traffic of one build: inputs read once, outputs written once."""
     n, m = tree.src.n, tree.recv.n
@@ -474,13 +490,10 @@ def main():
     ktimes = ctx.timing()
     tree = ctx.build(src, recv, L=level, stream=stream)
     torch.cuda.synchronize()
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
 
     pts_per_step = npts * 2
-    value = pts_per_step * args.steps * ws / (total_ms / 1e3) / 1e6
+    value = replica_throughput(pts_per_step * args.steps, total_ms, ws) / 1e6
     p50 = step_ms[len(step_ms) // 2]
     p99 = step_ms[min(len(step_ms) - 1, int(np.ceil(0.99 * len(step_ms))) - 1)]
 
@@ -528,11 +541,9 @@ def main():
     e1.record(stream)
     barrier()
     e2e_ms = max(e0.elapsed_time(e1), 1e-9)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = pts_per_step * args.e2e_steps * ws / (e2e_ms / 1e3) / 1e6 if args.e2e_steps else None
+    e2e_ms = max_over_ranks(e2e_ms, dist)
+    e2e_val = (replica_throughput(pts_per_step * args.e2e_steps, e2e_ms, ws) / 1e6
+               if args.e2e_steps else None)
     batched = None
     if not args.no_batched:
         batched = batched_section(ctx, stream, args.steps, args.warmup, args.plain_steps)
