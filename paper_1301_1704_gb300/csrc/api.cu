@@ -826,13 +826,8 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     }
     {
       Launch Lk(c, "scan");
-      launch_scan_u32(lvls[l].work2, nullptr, (uint32_t)work_len[l], st2, cnt, lvls[l].total,
-                      c->st, wait_ns, s);
-    }
-    {
-      Launch Lk(c, "scan");
-      launch_scan_u32(lvls[l].work4, nullptr, (uint32_t)work_len[l], st4, cnt + 1,
-                      lvls[l].total + 1, c->st, wait_ns, s);
+      launch_scan_u32_pair(lvls[l].work2, st2, lvls[l].total, lvls[l].work4, st4,
+                           lvls[l].total + 1, (uint32_t)work_len[l], cnt, c->st, wait_ns, s);
     }
     {
       Launch Lk(c, "list_fill");

@@ -21,10 +21,11 @@ uint32_t boxes_tiles(uint32_t n) {
 }
 
 constexpr int kWin = kBoxTile + kBoxHalo;  // points held per tile
-// Shared memory: keys [kWin + 1] (u64), then the per-point first differing
-// levels [kWin] (u8, 16-byte aligned for vector reads), then the indices
-// [kWin] (u32).
-constexpr size_t kBoxDdOff = (sizeof(uint64_t) * (kWin + 1) + 15) & ~(size_t)15;
+// Shared memory: keys [kWin + 2] (u64: the two points before the tile, then
+// the window, so that a bulk copy can start 16-byte aligned), then the
+// per-point first differing levels [kWin] (u8, 16-byte aligned for vector
+// reads), then the indices [kWin] (u32).
+constexpr size_t kBoxDdOff = (sizeof(uint64_t) * (kWin + 2) + 15) & ~(size_t)15;
 constexpr size_t kBoxValOff = kBoxDdOff + kWin;
 constexpr size_t kBoxSmem = kBoxValOff + sizeof(uint32_t) * kWin;
 static_assert(kWin % 16 == 0 && kBoxValOff % 16 == 0, "shared layout alignment");
@@ -43,7 +44,9 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __
   constexpr int W = kBoxThreads / 32;
   __shared__ uint32_t s_tile, s_abort, s_ttot, s_texcl;
   __shared__ uint32_t s_wtot[W];
-  extern __shared__ __align__(16) uint64_t s_key[];  // s_key[j + 1] = key of point t0 + j
+  __shared__ __align__(8) uint64_t s_bar;
+  extern __shared__ __align__(16) uint64_t s_key[];  // s_key[j + 2] = key of point t0 + j
+  uint64_t* const sk = s_key + 1;                     // sk[j + 1] = key of point t0 + j
   uint8_t* s_dd = reinterpret_cast<uint8_t*>(s_key) + kBoxDdOff;  // first differing level
   uint32_t* s_val = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(s_key) + kBoxValOff);
 
@@ -60,6 +63,8 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __
   if (threadIdx.x == 0) {
     s_tile = atomicAdd(&sg.tickets[0], 1u);
     s_abort = failed(st) ? 1u : 0u;
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
   }
   __syncthreads();
   if (s_abort) return;  // an earlier kernel failed: leave the outputs alone
@@ -67,19 +72,34 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __
   const int64_t t0 = (int64_t)tile * kBoxTile;
   const int64_t nn = n;
   const int jend = (int)((nn - t0) < kWin ? (nn - t0) : kWin);  // valid window points
-  for (int j = threadIdx.x; j < kWin + 1; j += kBoxThreads) {
-    const int64_t i = t0 - 1 + j;
-    s_key[j] = (i >= 0 && i < nn) ? __ldcs(keys + i) : 0ull;
+  {
+    // The window by bulk copy (TMA): keys of points [t0 - 2, t0 + jend) and
+    // indices of [t0, t0 + jend).  Set bases are multiples of 4 slots and t0
+    // of 4096, so both sources start 16-byte aligned; an odd key and up to
+    // three indices at the end come by plain loads.  Slots outside the data
+    // are never read (every use is bounded by jend).
+    const int64_t g0 = t0 >= 2 ? t0 - 2 : 0;
+    const uint32_t nk = (uint32_t)(t0 + jend - g0), nk_bulk = nk & ~1u;
+    const uint32_t nv = (uint32_t)jend, nv_bulk = nv & ~3u;
+    uint64_t* kdst = s_key + (g0 - (t0 - 2));
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&s_bar, nk_bulk * 8u + nv_bulk * 4u);
+      if (nk_bulk) bulk_load(kdst, keys + g0, nk_bulk * 8u, &s_bar);
+      if (nv_bulk) bulk_load(s_val, vals + t0, nv_bulk * 4u, &s_bar);
+    }
+    if (threadIdx.x == 32 && (nk & 1u)) kdst[nk - 1] = keys[g0 + nk - 1];
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + (nv - nv_bulk))
+      s_val[nv_bulk + threadIdx.x - 64] = vals[t0 + nv_bulk + threadIdx.x - 64];
+    const bool ok = mbar_wait(&s_bar, 0, st, wait_ns);
+    if (__syncthreads_or(!ok)) {
+      mbar_wait(&s_bar, 0, st, wait_ns);  // let the copy land before the block leaves
+      return;
+    }
   }
-  for (int j = threadIdx.x; j < kWin; j += kBoxThreads) {
-    const int64_t i = t0 + j;
-    s_val[j] = i < nn ? __ldcs(vals + i) : 0u;
-  }
-  __syncthreads();
   // dd[j]: the point opens a box at every level >= dd[j].  Past the end of
   // the data every slot reads 0, which ends every box walk there.
   for (int j = threadIdx.x; j < kWin; j += kBoxThreads)
-    s_dd[j] = (j >= jend || t0 + j == 0) ? 0u : (uint8_t)first_diff_level(s_key[j + 1], s_key[j]);
+    s_dd[j] = (j >= jend || t0 + j == 0) ? 0u : (uint8_t)first_diff_level(sk[j + 1], sk[j]);
   __syncthreads();
 
   // Level-Lb box starts among this thread's points 8t .. 8t+7.
@@ -164,10 +184,10 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __
       uint32_t r = 0;
       if (b - a > 1) {
         // within a box the top bits agree: order by (low key bits, index)
-        const uint64_t mine = s_key[j + 1] & lowmask;
+        const uint64_t mine = sk[j + 1] & lowmask;
         const uint32_t vj = s_val[j];
         for (int q = a; q < b; ++q) {
-          const uint64_t kq = s_key[q + 1] & lowmask;
+          const uint64_t kq = sk[q + 1] & lowmask;
           r += (kq < mine) || (kq == mine && s_val[q] < vj);
         }
       }
@@ -206,7 +226,7 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __
     mask &= mask - 1;
     const int j = threadIdx.x * kBoxItems + k;
     if (rank < cap) {
-      lv.key[Lb][rank] = Lb == 0 ? 0ull : s_key[j + 1] >> shift;
+      lv.key[Lb][rank] = Lb == 0 ? 0ull : sk[j + 1] >> shift;
       lv.off[Lb][rank] = (uint32_t)(t0 + j);
     }
     ++rank;

@@ -186,12 +186,19 @@ __device__ __forceinline__ uint64_t lookback_warp(const uint64_t* status, uint32
   return excl;
 }
 
-// Store with a per-lane predicate as one predicated instruction (streaming
+// Store v when `word` is non-zero, as one predicated instruction (streaming
 // cache hint): no branch around it.
-__device__ __forceinline__ void st_cs_if(uint32_t* p, uint32_t v, bool pred) {
+__device__ __forceinline__ void st_cs_if(uint32_t* p, uint32_t v, uint32_t word) {
   asm volatile(
       "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.cs.u32 [%0], %1;\n\t}"
-      ::"l"(p), "r"(v), "r"((uint32_t)pred)
+      ::"l"(p), "r"(v), "r"(word)
+      : "memory");
+}
+// ... and when `word` is zero.
+__device__ __forceinline__ void st_cs_if_zero(uint32_t* p, uint32_t v, uint32_t word) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.eq.u32 q, %2, 0;\n\t@q st.global.cs.u32 [%0], %1;\n\t}"
+      ::"l"(p), "r"(v), "r"(word)
       : "memory");
 }
 
@@ -438,6 +445,10 @@ uint32_t coarse_tiles(uint32_t cap);
 void launch_scan_u32(uint32_t* data, const uint32_t* count_dev, uint32_t cap, uint64_t* status,
                      uint32_t* counter, uint64_t* total64, DevStatus* st, uint64_t wait_ns,
                      cudaStream_t s);
+// The same for two arrays of cap entries each, in one launch.
+void launch_scan_u32_pair(uint32_t* data0, uint64_t* status0, uint64_t* total0, uint32_t* data1,
+                          uint64_t* status1, uint64_t* total1, uint32_t cap, uint32_t* counter,
+                          DevStatus* st, uint64_t wait_ns, cudaStream_t s);
 uint32_t scan_tiles(uint32_t cap);
 
 // Lists of level l for every job.  jprefix of the level is computed first

@@ -20,6 +20,8 @@
 // One warp handles one parent box p: lane k takes the k-th entry Q_k of
 // E2(p) (at most 27), and the warp serves every receiver child r of p.
 // Counting and filling are two kernels around a prefix sum of the counts.
+#include <type_traits>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -226,12 +228,21 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(const Seg* __r
     const uint32_t p = g - jstart;
     const Neighbour q = load_neighbour(a, l, p, lane);
     uint32_t lo = 0, hi = 0;  // byte rho: popc(occ & mask(delta, rho))
+    {
+      // mask(delta, rho) factors by axis into masks chosen by rho's bits
+      const uint32_t mx0 = axis_mask(q.dx, 0u, 0x55u, 0xaau), mx1 = axis_mask(q.dx, 1u, 0x55u, 0xaau);
+      const uint32_t my0 = axis_mask(q.dy, 0u, 0x33u, 0xccu), my1 = axis_mask(q.dy, 1u, 0x33u, 0xccu);
+      const uint32_t mz0 = axis_mask(q.dz, 0u, 0x0fu, 0xf0u), mz1 = axis_mask(q.dz, 1u, 0x0fu, 0xf0u);
 #pragma unroll
-    for (uint32_t rho = 0; rho < 4; ++rho)
-      lo |= (uint32_t)__popc(q.occ & e2_child_mask(q.dx, q.dy, q.dz, rho)) << (8 * rho);
-#pragma unroll
-    for (uint32_t rho = 4; rho < 8; ++rho)
-      hi |= (uint32_t)__popc(q.occ & e2_child_mask(q.dx, q.dy, q.dz, rho)) << (8 * (rho - 4));
+      for (uint32_t rho = 0; rho < 8; ++rho) {
+        const uint32_t m = ((rho & 1) ? mx1 : mx0) & ((rho & 2) ? my1 : my0) & ((rho & 4) ? mz1 : mz0);
+        const uint32_t cnt = (uint32_t)__popc(q.occ & m);
+        if (rho < 4)
+          lo |= cnt << (8 * rho);
+        else
+          hi |= cnt << (8 * (rho - 4));
+      }
+    }
     const uint32_t tot = warp_sum(__popc(q.occ));
     lo = warp_sum(lo);
     hi = warp_sum(hi);
@@ -353,13 +364,20 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
     uint32_t e = warp_excl(nc, lane);
     const uint32_t total = __shfl_sync(0xffffffffu, e + nc, 31);
     {
-      uint32_t bits = q.occ, rank = q.child;
-      while (bits) {
-        const uint32_t o = __ffs(bits) - 1;
-        bits &= bits - 1;
-        crank[e] = rank++;
-        csib[e] = (uint8_t)e2_child_mask(-q.dx, -q.dy, -q.dz, o);
-        ++e;
+      // The sibling byte of child o of this neighbour factors by axis: bit
+      // rho is set iff axis_mask(-delta, o's bit, ...) holds on every axis.
+      // Branch-free over the eight octants (predicated stores).
+      const uint32_t mx0 = axis_mask(-q.dx, 0u, 0x55u, 0xaau), mx1 = axis_mask(-q.dx, 1u, 0x55u, 0xaau);
+      const uint32_t my0 = axis_mask(-q.dy, 0u, 0x33u, 0xccu), my1 = axis_mask(-q.dy, 1u, 0x33u, 0xccu);
+      const uint32_t mz0 = axis_mask(-q.dz, 0u, 0x0fu, 0xf0u), mz1 = axis_mask(-q.dz, 1u, 0x0fu, 0xf0u);
+      uint32_t rank = q.child;
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        if ((q.occ >> o) & 1u) {
+          crank[e] = rank++;
+          csib[e] = (uint8_t)(((o & 1) ? mx1 : mx0) & ((o & 2) ? my1 : my0) & ((o & 4) ? mz1 : mz0));
+          ++e;
+        }
       }
     }
     __syncwarp();
@@ -380,36 +398,49 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
     uint32_t sbit[8], w2[8], w4[8];
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
-      sbit[jj] = (uint32_t)jj < nsib ? 1u << __shfl_sync(0xffffffffu, my_rho, jj) : 0u;
+      sbit[jj] = 1u << __shfl_sync(0xffffffffu, my_rho, jj);
       w2[jj] = __shfl_sync(0xffffffffu, my_o2, jj);
       w4[jj] = __shfl_sync(0xffffffffu, my_o4, jj);
     }
-    // E2 of sibling jj: the near candidates whose byte has bit rho_jj.
-    for (uint32_t c = 0; c < nnear; c += 32) {
-      const uint32_t i = c + lane;
-      const uint32_t v = i < nnear ? nrank[i] : 0u;
-      const uint32_t sb = i < nnear ? nsibm[i] : 0u;
+    // E2 of sibling jj: the near candidates whose byte has bit rho_jj; E4:
+    // the candidates without it.  A parent with all eight children runs the
+    // eight siblings as straight-line code; otherwise absent siblings (the
+    // same for the whole warp) are skipped.
+    auto emit = [&](auto all_tag) {
+      constexpr bool kAll = decltype(all_tag)::value;
+      for (uint32_t c = 0; c < nnear; c += 32) {
+        const uint32_t i = c + lane;
+        const uint32_t v = i < nnear ? nrank[i] : 0u;
+        const uint32_t sb = i < nnear ? nsibm[i] : 0u;
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {  // absent siblings have sbit 0: nothing stored
-        const bool in2 = (sb & sbit[jj]) != 0u;
-        const uint32_t b2 = __ballot_sync(0xffffffffu, in2);
-        st_cs_if(idx2 + w2[jj] + __popc(b2 & lt), v, in2);
-        w2[jj] += __popc(b2);
+        for (int jj = 0; jj < 8; ++jj) {
+          if (kAll || (uint32_t)jj < nsib) {
+            const uint32_t hit = sb & sbit[jj];
+            const uint32_t b2 = __ballot_sync(0xffffffffu, hit != 0u);
+            st_cs_if(idx2 + w2[jj] + __popc(b2 & lt), v, hit);
+            w2[jj] += __popc(b2);
+          }
+        }
       }
-    }
-    // E4 of sibling jj: the candidates without bit rho_jj.
-    for (uint32_t c = 0; c < total; c += 32) {
-      const uint32_t i = c + lane;
-      const uint32_t v = i < total ? crank[i] : 0u;
-      const uint32_t sb = i < total ? csib[i] : 0xffu;  // past the end: never stored
+      for (uint32_t c = 0; c < total; c += 32) {
+        const uint32_t i = c + lane;
+        const uint32_t v = i < total ? crank[i] : 0u;
+        const uint32_t sb = i < total ? csib[i] : 0xffu;  // past the end: never stored
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {  // absent siblings: in4 is false everywhere
-        const bool in4 = (sb & sbit[jj]) == 0u && (uint32_t)jj < nsib;
-        const uint32_t b4 = __ballot_sync(0xffffffffu, in4);
-        st_cs_if(idx4 + w4[jj] + __popc(b4 & lt), v, in4);
-        w4[jj] += __popc(b4);
+        for (int jj = 0; jj < 8; ++jj) {
+          if (kAll || (uint32_t)jj < nsib) {
+            const uint32_t hit = sb & sbit[jj];
+            const uint32_t b4 = __ballot_sync(0xffffffffu, hit == 0u);
+            st_cs_if_zero(idx4 + w4[jj] + __popc(b4 & lt), v, hit);
+            w4[jj] += __popc(b4);
+          }
+        }
       }
-    }
+    };
+    if (nsib == 8)
+      emit(std::true_type{});
+    else
+      emit(std::false_type{});
     __syncwarp();
   }
 }
@@ -434,10 +465,18 @@ __host__ __device__ inline uint32_t scan_tiles_of(uint32_t cap) {
 
 uint32_t scan_tiles(uint32_t cap) { return scan_tiles_of(cap); }
 
-__global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(uint32_t* data,
+// Up to two arrays of the same length in one launch (the E2 and E4 counts of
+// a level): tickets [0, need) scan the first, [need, 2 need) the second, each
+// with its own look-back words and total.
+struct ScanArray {
+  uint32_t* data;
+  uint64_t* status;
+  uint64_t* total64;
+};
+
+__global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(ScanArray a0, ScanArray a1,
                                                                const uint32_t* count_dev,
-                                                               uint32_t cap, uint64_t* status,
-                                                               uint32_t* counter, uint64_t* total64,
+                                                               uint32_t cap, uint32_t* counter,
                                                                DevStatus* st, uint64_t wait_ns) {
   constexpr int W = kScanThreads / 32;
   __shared__ uint32_t s_tile;
@@ -447,8 +486,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(uint32_t* data,
   const uint32_t need = scan_tiles_of(count);
   if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
   __syncthreads();
-  const uint32_t tile = s_tile;
-  if (tile >= need) return;
+  const uint32_t ticket = s_tile;
+  const bool second = ticket >= need;
+  if (second && (a1.data == nullptr || ticket >= 2 * need)) return;
+  const uint32_t tile = second ? ticket - need : ticket;
+  uint32_t* const data = second ? a1.data : a0.data;
+  uint64_t* const status = second ? a1.status : a0.status;
+  uint64_t* const total64 = second ? a1.total64 : a0.total64;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t i0 = (uint64_t)tile * kScanTile + (uint64_t)threadIdx.x * kScanItems;
   uint32_t v[kScanItems];
@@ -506,8 +550,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(uint32_t* data,
 void launch_scan_u32(uint32_t* data, const uint32_t* count_dev, uint32_t cap, uint64_t* status,
                      uint32_t* counter, uint64_t* total64, DevStatus* st, uint64_t wait_ns,
                      cudaStream_t s) {
-  scan_u32_kernel<<<scan_tiles(cap), kScanThreads, 0, s>>>(data, count_dev, cap, status, counter,
-                                                           total64, st, wait_ns);
+  scan_u32_kernel<<<scan_tiles(cap), kScanThreads, 0, s>>>(ScanArray{data, status, total64},
+                                                           ScanArray{nullptr, nullptr, nullptr},
+                                                           count_dev, cap, counter, st, wait_ns);
+}
+
+void launch_scan_u32_pair(uint32_t* data0, uint64_t* status0, uint64_t* total0, uint32_t* data1,
+                          uint64_t* status1, uint64_t* total1, uint32_t cap, uint32_t* counter,
+                          DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+  scan_u32_kernel<<<2 * scan_tiles(cap), kScanThreads, 0, s>>>(
+      ScanArray{data0, status0, total0}, ScanArray{data1, status1, total1}, nullptr, cap, counter,
+      st, wait_ns);
 }
 
 }  // namespace fmm
