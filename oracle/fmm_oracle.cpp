@@ -146,6 +146,17 @@ void sort_points(Side* s) {
   }
 }
 
+// The order variant that sorts only by the box (Sec. 2.1: the order of the
+// points inside a box is irrelevant): ascending (level-L key, original
+// index).  The boxes of levels 0..L are the same as in the full-key order.
+void box_key_order(Side* s, int L) {
+  const int shift = 3 * (kMaxLevel - L);
+  std::vector<std::pair<uint64_t, uint32_t>> pairs(s->n);
+  for (uint32_t i = 0; i < s->n; ++i) pairs[i] = std::make_pair(s->point_key[i] >> shift, i);
+  std::sort(pairs.begin(), pairs.end());
+  for (uint32_t j = 0; j < s->n; ++j) s->perm[j] = pairs[j].second;
+}
+
 // Alg. 3 for every level 0..Lmax: the distinct level-l keys along the sorted
 // order are the non-empty boxes; the first occurrence is the bookmark.
 void make_boxes(Side* s, int Lmax) {
@@ -320,11 +331,14 @@ void orc_decode(uint64_t key, int bits, int64_t* c3) { deinterleave(key, bits, c
 
 // Builds the whole structure.  L in [0, 21] (L mode) or L = -1 and s >= 1
 // (cluster-size mode).  mode: 0 = stencil lists, 1 = brute-force lists,
-// 2 = no lists (keys, order and boxes only).
+// 2 = no lists (keys, order and boxes only); plus 16 for the box-key order
+// of the points.
 int orc_build(const float* src, uint32_t N, const float* recv, uint32_t M, int L,
               uint32_t s, int mode, void** out) {
   if (!out) return ORC_ERR_ARG;
   *out = nullptr;
+  const bool box_order = (mode & 16) != 0;
+  mode &= ~16;
   if ((N > 0 && !src) || (M > 0 && !recv) || mode < 0 || mode > 2) return ORC_ERR_ARG;
   if (L > kMaxLevel || L < -1 || (L == -1 && s == 0)) return ORC_ERR_LEVEL;
   Tree* t = new Tree();
@@ -357,6 +371,8 @@ int orc_build(const float* src, uint32_t N, const float* recv, uint32_t M, int L
     }
     for (int k = 0; k < 2; ++k) truncate_levels(&t->side[k], t->L);
   }
+  if (box_order)
+    for (int k = 0; k < 2; ++k) box_key_order(&t->side[k], t->L);
   if (mode != 2) make_lists(t, mode);
   *out = t;
   return ORC_OK;

@@ -25,6 +25,7 @@ _lib = None
 
 ORC_OK, ORC_ERR_ARG, ORC_ERR_DOMAIN, ORC_ERR_LEVEL = 0, 1, 2, 3
 MODE_STENCIL, MODE_BRUTE, MODE_NOLISTS = 0, 1, 2
+ORDER_KEY, ORDER_BOX = 0, 16  # point order: (full key, index) or (level-L key, index)
 
 
 class OracleError(RuntimeError):
@@ -123,20 +124,23 @@ def decode(key: int, bits: int = 21) -> tuple:
     return (int(c[0]), int(c[1]), int(c[2]))
 
 
-def build_tree(src, recv, L: int = -1, s: int = 0, mode: int = MODE_STENCIL) -> dict:
+def build_tree(src, recv, L: int = -1, s: int = 0, mode: int = MODE_STENCIL,
+               order: int = ORDER_KEY) -> dict:
     """The whole structure as a dict of numpy arrays.
 
     Keys: ``L``, ``s_unmet``; per side (``"src"``, ``"recv"``): ``perm``,
     ``sorted_keys``, ``key[l]``, ``off[l]``, ``parent[l]`` (l >= 1),
     ``child[l]`` (l < L); lists: ``e2_off[l]``, ``e2_idx[l]``, ``e4_off[l]``,
     ``e4_idx[l]`` for l in 2..L (absent with ``mode=MODE_NOLISTS``).
+    ``order=ORDER_BOX`` orders the points by (level-L key, index) instead of
+    (full key, index); only ``perm`` differs.
     """
     lib = _load()
     a, b = _f32(src), _f32(recv)
     h = C.c_void_p()
     fp = C.POINTER(C.c_float)
     st = lib.orc_build(a.ctypes.data_as(fp), a.shape[0], b.ctypes.data_as(fp), b.shape[0], L, s,
-                       mode, C.byref(h))
+                       mode | order, C.byref(h))
     if st != ORC_OK:
         raise OracleError(st, "build")
     try:

@@ -131,3 +131,40 @@ def test_cluster_size_unmet(orc):
     same = np.repeat(np.array([[0.3, 0.3, 0.3]], np.float32), 10, axis=0)
     t = orc.build_tree(same, same, L=-1, s=4, mode=orc.MODE_NOLISTS)
     assert t["L"] == 21 and t["s_unmet"] == 1
+
+
+@pytest.mark.parametrize("L", [0, 1, 3, 5])
+def test_box_key_order(orc, L):
+    """(level-L key, index) order: a stable argsort of the level-L keys (a
+    different sort), ascending indices inside every level-L box, the same
+    boxes as the full-key order, and permuted points that stay inside the
+    boxes the full-key order gives them."""
+    from paper_1301_1704_gb300 import workloads
+    src = workloads.clumps(6000, 51, nclumps=5, sigma=0.03)
+    recv = workloads.uniform(3000, 52)
+    full = orc.build_tree(src, recv, L=L)
+    box = orc.build_tree(src, recv, L=L, order=orc.ORDER_BOX)
+    for side, pts in (("src", src), ("recv", recv)):
+        k = orc.keys(pts) >> np.uint64(3 * (21 - L))
+        assert np.array_equal(box[side]["perm"], np.argsort(k, kind="stable"))
+        off = box[side]["off"][L]
+        for b in range(len(off) - 1):
+            seg = box[side]["perm"][off[b]:off[b + 1]]
+            assert np.all(np.diff(seg.astype(np.int64)) > 0)
+            assert set(seg) == set(full[side]["perm"][off[b]:off[b + 1]])
+        for l in range(L + 1):
+            for nm in ("key", "off", "parent", "child"):
+                assert np.array_equal(box[side][nm][l], full[side][nm][l])
+    for l in range(2, L + 1):
+        for nm in ("e2_off", "e2_idx", "e4_off", "e4_idx"):
+            assert np.array_equal(box[nm][l], full[nm][l])
+
+
+def test_box_key_order_cluster_size(orc):
+    from paper_1301_1704_gb300 import workloads
+    p = workloads.clumps(5000, 53, nclumps=3, sigma=0.02)
+    box = orc.build_tree(p, p, L=-1, s=16, order=orc.ORDER_BOX)
+    full = orc.build_tree(p, p, L=-1, s=16)
+    assert box["L"] == full["L"]
+    k = orc.keys(p) >> np.uint64(3 * (21 - box["L"]))
+    assert np.array_equal(box["src"]["perm"], np.argsort(k, kind="stable"))
