@@ -191,3 +191,33 @@ def box_lists(src_keys_l, level: int, recv_key: int, mode: int = MODE_STENCIL):
     if st != ORC_OK:
         raise OracleError(st, "box_lists")
     return e2[: n2.value].copy(), e4[: n4.value].copy()
+
+
+def sorted_points(xyz, perm) -> np.ndarray:
+    """SortedSrc / SortedRecv (Sec. 2.1): the points in the build's order,
+    point j = xyz[perm[j]]."""
+    return np.ascontiguousarray(np.asarray(xyz, dtype=np.float32)[np.asarray(perm, dtype=np.int64)])
+
+
+def gather_e2(tree: dict, src_xyz, level: int):
+    """Alg. 2 (Access-Source-E2-neighborhood) for every receiver box of
+    `level`, in receiver order: for box i, the entries j of its neighbour
+    list give source boxes v, and the source points of v are read from
+    SortedSrc[SrcBookmark[v] .. SrcBookmark[v+1]).  Returns (offsets [nbox+1],
+    points [total, 3]); box i's points are points[offsets[i]:offsets[i+1]]."""
+    sorted_src = sorted_points(src_xyz, tree["src"]["perm"])
+    book = tree["src"]["off"][level].astype(np.int64)
+    nb_off = tree["e2_off"][level].astype(np.int64)
+    nb_list = tree["e2_idx"][level].astype(np.int64)
+    nrecv = len(nb_off) - 1
+    out, offsets = [], [0]
+    for i in range(nrecv):
+        temp = []
+        for j in range(nb_off[i], nb_off[i + 1]):
+            v = nb_list[j]
+            for k in range(book[v], book[v + 1]):
+                temp.append(sorted_src[k])
+        out.extend(temp)
+        offsets.append(offsets[-1] + len(temp))
+    pts = np.array(out, dtype=np.float32).reshape(-1, 3)
+    return np.array(offsets, dtype=np.uint64), pts
