@@ -71,6 +71,13 @@ typedef void (*fmm_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 #define FMM_FLAG_HOST_INPUT 0x1u   /* src/recv point to host memory (pinned or
                                       pageable); the call copies them to the
                                       device on its stream */
+#define FMM_FLAG_BOX_ORDER 0x2u    /* order the points by (level-L box key,
+                                      original index) instead of (full key,
+                                      original index): the order inside a box
+                                      that Sec. 2.1 leaves free, taken as input
+                                      order; only the permutations differ */
+#define FMM_FLAG_SORTED_XYZ 0x4u   /* also return the points in sorted
+                                      order (fmm_tree.sorted_src/_recv) */
 #define FMM_FLAG_TEST_STALL 0x80000000u /* test only: one tile of the first
                                       sort pass never publishes, so the
                                       bounded wait must end with
@@ -123,6 +130,10 @@ typedef struct fmm_tree {
   const uint32_t* e2_idx[FMM_LEVELS];
   const uint32_t* e4_off[FMM_LEVELS];
   const uint32_t* e4_idx[FMM_LEVELS];
+  /* SortedSrc / SortedRecv (Sec. 2.1): float32 [n][3], point j = input
+   * point perm[j]; only with FMM_FLAG_SORTED_XYZ, else NULL. */
+  const float* sorted_src;
+  const float* sorted_recv;
 } fmm_tree;
 
 typedef struct fmm_ctx fmm_ctx;
@@ -237,6 +248,31 @@ int fmm_last_launch_count(fmm_ctx* ctx, uint64_t* launches);
 #define FMM_NOALLOC_SCAN_MAX (1u << 26)
 int fmm_exclusive_scan_noalloc(const uint32_t* counts, uint32_t n, uint32_t* offsets,
                                uint64_t* total, void* stream);
+
+/* ---- Alg. 2: the source points of every receiver box's E2 neighbourhood.
+ *
+ * For receiver box i of `level` (2..tree->L), Alg. 2 walks its neighbour
+ * list NeighborList[NeighborBookmark[i] .. NeighborBookmark[i+1]) and, for
+ * each source box v there, copies SortedSrc[SrcBookmark[v] ..
+ * SrcBookmark[v+1]).  These two calls do it for all receiver boxes at once:
+ *
+ * fmm_e2_source_offsets writes off[i] = number of E2 source points of the
+ * receiver boxes before i (off [nbox_recv[level] + 1], device, caller-owned;
+ * off[nbox] = the total) and *total (host) = the total; FMM_ERR_CAPACITY if
+ * it reaches 2^32.  Synchronises `stream`.
+ *
+ * fmm_gather_e2_sources then copies the points: box i's occupy out[off[i] ..
+ * off[i+1]) ([total][3] float32, device, caller-owned), neighbour boxes in
+ * list order, points inside a box in sorted order.  sorted_src is the tree's
+ * sorted_src (FMM_FLAG_SORTED_XYZ) or any [N][3] float32 array in that
+ * order.  Asynchronous on `stream`.
+ *
+ * The tree must come from the last build of `ctx` (its arrays live in the
+ * arena); FMM_ERR_LEVEL for a level outside 2..L. */
+int fmm_e2_source_offsets(fmm_ctx* ctx, const fmm_tree* tree, int level, uint32_t* off,
+                          uint64_t* total, void* stream);
+int fmm_gather_e2_sources(fmm_ctx* ctx, const fmm_tree* tree, int level, const float* sorted_src,
+                          const uint32_t* off, float* out, void* stream);
 
 /* ---- Served dynamic rebuilds ---------------------------------------------
  *

@@ -255,6 +255,8 @@ struct SetPlan {
   uint32_t n = 0;
   int Lb = 0, Ls = 0;
   bool full = false;      // sort all 63 bits (the order needs no finishing window)
+  bool exact = false;     // box-key order: exactly the top 3*Ls bits, stable passes
+  bool want_sorted = false;  // also the points in sorted order
   bool need_occ = false;  // used as a source
   uint32_t depth = 0;     // cluster-size mode: 1 + deepest level shared by points i, i + s
   Seg dev{};              // the device descriptor
@@ -387,9 +389,13 @@ SortTables plan_sort(const std::vector<SetPlan*>& sets) {
 int run_sort(fmm_ctx* c, std::vector<SetPlan*>& sets, SortMem& m, bool stall, uint64_t wait_ns) {
   cudaStream_t s = c->stream;
   int err = FMM_OK;
-  bool any_full = false;  // a set sorted in full keeps every pass stable
-  for (auto* sp : sets) any_full |= sp->full;
-  const bool onesweep = stall || c->tuning.sort_kind == FMM_SORT_ONESWEEP;
+  bool any_full = false;  // a set sorted in full (or exactly) keeps every pass stable
+  bool any_exact = false;
+  for (auto* sp : sets) {
+    any_full |= sp->full || sp->exact;
+    any_exact |= sp->exact;
+  }
+  const bool onesweep = stall || (c->tuning.sort_kind == FMM_SORT_ONESWEEP && !any_exact);
   if (onesweep) {
     // One set at a time, one kernel per pass (decoupled look-back).
     for (auto* sp : sets) {
@@ -473,8 +479,11 @@ int sort_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, bool stall, uint64_t wait
     d.n = sp->n;
     d.base = (uint32_t)slots_total;
     d.Ls = sp->Ls;
-    d.passes = sp->n ? passes_for(sp->Ls) : 0;
+    // an exact sort of 0 bits still takes one pass: it forms the keys, and
+    // its digit (bits 63..70 of a 63-bit key) is zero for every point
+    d.passes = sp->n ? std::max(passes_for(sp->Ls), sp->exact ? 1 : 0) : 0;
     d.lo = 63 - 3 * sp->Ls;
+    d.exact = sp->exact ? 1 : 0;
     d.ntiles = (uint32_t)(((uint64_t)sp->n + kSortTile - 1) / kSortTile);
     slots_total += ((uint64_t)sp->n + 3) & ~3ull;  // set bases stay 16-byte aligned
     if (slots_total >= (1ull << 32)) return FMM_ERR_ARG;
@@ -603,6 +612,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     d.nbox = d.tickets + 2;
     d.seg_long = d.nbox + kLevels;
     d.perm = arena_get<uint32_t>(c, sp.n, &err);
+    d.sorted = sp.want_sorted ? arena_get<float>(c, 3ull * sp.n, &err) : nullptr;
     std::memset(&d.lv, 0, sizeof(d.lv));
     for (int l = 0; l <= sp.Lb; ++l) {
       d.lv.cap[l] = sp.cap[l];
@@ -743,6 +753,12 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     Launch L(c, "finish_boxes");
     launch_finish_boxes(m.segs, m.fin_slots, (uint32_t)fin.size(), m.fin_units, c->st, wait_ns, s);
   }
+  bool any_sorted = false;
+  for (auto& sp : sets) any_sorted |= sp.want_sorted;
+  if (any_sorted) {
+    Launch L(c, "sorted_xyz");
+    launch_sorted_xyz(m.segs, m.fin_slots, (uint32_t)fin.size(), m.fin_units, c->st, s);
+  }
   if (m.crs_units) {
     Launch L(c, "coarse_boxes");
     launch_coarse_boxes(m.segs, m.crs_slots, (uint32_t)crs.size(), m.crs_units, c->st, wait_ns,
@@ -865,9 +881,15 @@ int full_sort_perms(fmm_ctx* c, std::vector<SetPlan>& sets, const std::vector<ui
   // Every pass of a full sort is stable: the values of the last pass are the
   // order by (key, index).
   cudaStream_t s = c->stream;
-  for (size_t k = 0; k < ids.size(); ++k)
-    FMM_CUDA(cudaMemcpyAsync(sets[ids[k]].dev.perm, sub[k].dev.svals,
-                             sizeof(uint32_t) * sub[k].n, cudaMemcpyDeviceToDevice, s));
+  for (size_t k = 0; k < ids.size(); ++k) {
+    const Seg& d = sets[ids[k]].dev;
+    FMM_CUDA(cudaMemcpyAsync(d.perm, sub[k].dev.svals, sizeof(uint32_t) * sub[k].n,
+                             cudaMemcpyDeviceToDevice, s));
+    if (d.sorted) {
+      Launch L(c, "sorted_xyz");
+      launch_sorted_xyz_one(d.perm, d.xyz, sub[k].n, d.sorted, s);
+    }
+  }
   FMM_CUDA(cudaStreamSynchronize(s));
   return FMM_OK;
 }
@@ -893,6 +915,7 @@ void fill_tree(const std::vector<SetPlan>& sets, const JobPlan& J, const Readbac
     const uint32_t** opar = k ? out->parent_recv : out->parent_src;
     const uint32_t** ochi = k ? out->child_recv : out->child_src;
     (k ? out->perm_recv : out->perm_src) = d.perm;
+    (k ? out->sorted_recv : out->sorted_src) = d.sorted;
     for (int l = 0; l <= L; ++l) {
       onb[l] = nb[l];
       okey[l] = d.lv.key[l];
@@ -929,6 +952,7 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
   int err = FMM_OK;
   const bool stall = (prm.flags & FMM_FLAG_TEST_STALL) != 0;
   const bool host_in = (prm.flags & FMM_FLAG_HOST_INPUT) != 0;
+  const bool box_order = (prm.flags & FMM_FLAG_BOX_ORDER) != 0;
   const uint64_t wait_ns = wait_ns_of(prm);
 
   uint64_t expect = 0;
@@ -970,7 +994,10 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
     }
   }
   std::vector<SetPlan*> all;
-  for (auto& sp : sets) all.push_back(&sp);
+  for (auto& sp : sets) {
+    sp.want_sorted = (prm.flags & FMM_FLAG_SORTED_XYZ) != 0;
+    all.push_back(&sp);
+  }
 
   // Jobs of fixed depth (their own, or the call's L) and cluster-size jobs
   // (L = -1).  Sort depth: at least every fixed depth the set serves, and deep
@@ -993,7 +1020,12 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
   for (uint32_t i = 0; i < sets.size(); ++i) {
     SetPlan& sp = sets[i];
     const int lb = std::max(fixed_lb[i], in_smode[i] ? 2 : 0);
-    sp.Ls = std::max(sort_level(sp.n, lb), lb);
+    if (box_order && !in_smode[i]) {
+      sp.Ls = lb;  // exactly the box bits
+      sp.exact = true;
+    } else {
+      sp.Ls = std::max(sort_level(sp.n, lb), lb);
+    }
   }
   {
     SortMem sm;
@@ -1040,13 +1072,22 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
     sets[jp.src].Lb = std::max(sets[jp.src].Lb, jp.L);
     sets[jp.recv].Lb = std::max(sets[jp.recv].Lb, jp.L);
   }
-  // A set paired with a deeper one needs its order to that depth.
+  // A set paired with a deeper one needs its order to that depth; in the
+  // box-key order every set is sorted on exactly its box bits.
   std::vector<SetPlan*> resort;
-  for (auto& sp : sets)
-    if (sp.Lb > sp.Ls) {
+  for (auto& sp : sets) {
+    if (box_order) {
+      if (!sp.exact || sp.Ls != sp.Lb) {
+        sp.Ls = sp.Lb;
+        sp.exact = true;
+        sp.full = false;
+        resort.push_back(&sp);
+      }
+    } else if (sp.Lb > sp.Ls) {
       sp.Ls = std::max(sort_level(sp.n, sp.Lb), sp.Lb);
       resort.push_back(&sp);
     }
+  }
   if (!resort.empty()) {
     SortMem sr;
     FMM_TRY(sort_sets(c, resort, false, wait_ns, &sr));
@@ -1100,7 +1141,9 @@ struct DeviceGuard {
 };
 
 int check_params(const fmm_params& p) {
-  if (p.flags & ~(FMM_FLAG_HOST_INPUT | FMM_FLAG_TEST_STALL)) return FMM_ERR_ARG;
+  if (p.flags & ~(FMM_FLAG_HOST_INPUT | FMM_FLAG_TEST_STALL | FMM_FLAG_BOX_ORDER |
+                  FMM_FLAG_SORTED_XYZ))
+    return FMM_ERR_ARG;
   if (p.L > kMaxLevel || p.L < -1 || (p.L == -1 && p.s == 0)) return FMM_ERR_LEVEL;
   return FMM_OK;
 }
@@ -1199,6 +1242,61 @@ int fmm_build_batched(fmm_ctx* c, const fmm_set* sets, uint32_t nsets, fmm_param
   for (uint32_t k = 0; k < nsets; ++k)
     pins[k] = {sets[k].src, sets[k].N, sets[k].recv, sets[k].M, sets[k].L};
   return finish_call(c, do_builds(c, pins.data(), nsets, params, outs), l0);
+}
+
+int fmm_e2_source_offsets(fmm_ctx* c, const fmm_tree* t, int level, uint32_t* off,
+                          uint64_t* total, void* stream) {
+  if (!c || !t || !off || !total) return FMM_ERR_ARG;
+  if (level < 2 || level > t->L) return FMM_ERR_LEVEL;
+  DeviceGuard g(c->device);
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaStream_t s = c->stream;
+  const uint32_t nrecv = t->nbox_recv[level];
+  int err = FMM_OK;
+  const size_t zb = align_up(sizeof(uint64_t) * scan_tiles(nrecv)) + align_up(sizeof(uint64_t)) +
+                    align_up(sizeof(uint32_t));
+  char* z = arena_get<char>(c, zb, &err);
+  if (err) return err;
+  uint64_t* status = reinterpret_cast<uint64_t*>(z);
+  uint64_t* total64 = reinterpret_cast<uint64_t*>(z + align_up(sizeof(uint64_t) * scan_tiles(nrecv)));
+  uint32_t* counter = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(total64) +
+                                                  align_up(sizeof(uint64_t)));
+  FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
+  FMM_CUDA(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
+  {
+    Launch L(c, "e2_count");
+    launch_e2_count(t->e2_off[level], t->e2_idx[level], t->off_src[level], nrecv, off, c->st, s);
+  }
+  {
+    Launch L(c, "scan");
+    launch_scan_u32(off, nullptr, nrecv, status, counter, total64, c->st, wait_ns_of(fmm_params{}),
+                    s);
+  }
+  char* h = static_cast<char*>(c->rb_buf);
+  FMM_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(cudaMemcpyAsync(h + 64, total64, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(cudaStreamSynchronize(s));
+  if (c->timing) collect_times(c);
+  DevStatus st;
+  std::memcpy(&st, h, sizeof(st));
+  std::memcpy(total, h + 64, sizeof(uint64_t));
+  if (st.code) return (int)st.code;
+  return (*total >> 32) ? FMM_ERR_CAPACITY : FMM_OK;
+}
+
+int fmm_gather_e2_sources(fmm_ctx* c, const fmm_tree* t, int level, const float* sorted_src,
+                          const uint32_t* off, float* out, void* stream) {
+  if (!c || !t || !off || (!sorted_src && t->n_src > 0)) return FMM_ERR_ARG;
+  if (level < 2 || level > t->L) return FMM_ERR_LEVEL;
+  DeviceGuard g(c->device);
+  c->stream = static_cast<cudaStream_t>(stream);
+  {
+    Launch L(c, "e2_gather");
+    launch_e2_gather(t->e2_off[level], t->e2_idx[level], t->off_src[level], sorted_src, off,
+                     t->nbox_recv[level], out, c->stream);
+  }
+  FMM_CUDA(cudaGetLastError());
+  return FMM_OK;
 }
 
 int fmm_morton_keys(fmm_ctx* c, const float* xyz, uint32_t n, uint64_t* keys, void* stream) {

@@ -142,9 +142,9 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __
   // points; box bounds inside the warp come from one ballot of box starts.
   // This runs between publishing the aggregate and reading the earlier
   // tiles' words, which gives them time to publish.
-  if (Ls >= kMaxLevel) {
-    // Sorted on all 63 key bits with stable passes: the order is already
-    // (key, index).
+  if (Ls >= kMaxLevel || sg.exact) {
+    // Sorted with stable passes on all 63 key bits, or on exactly the bits
+    // that the order asks for: the order is already final.
     const int own = jend < kBoxTile ? jend : kBoxTile;
     for (int j = threadIdx.x; j < own; j += kBoxThreads) perm[t0 + j] = s_val[j];
   } else {

@@ -281,9 +281,13 @@ struct Seg {
   uint32_t base;      // first slot of this set in the concatenated sort arrays
   int Ls, Lb;         // sort depth (top 3*Ls key bits), box depth
   int passes, lo;     // radix passes of 8 bits, lowest sorted key bit
+  int exact;          // sorted on exactly the top 3*Ls bits with stable passes: the
+                      // order is final, no finishing sort (box-key order)
+  int pad_;
   uint32_t ntiles;    // sort tiles
   uint32_t btiles;    // finishing / finest-box tiles
   uint32_t* perm;
+  float* sorted;          // SortedSrc / SortedRecv [n][3], or null
   const uint64_t* skeys;  // this set's keys after the last pass (concatenated array + base)
   const uint32_t* svals;  // ... and point indices (local to the set)
   LevelArrays lv;
@@ -427,6 +431,17 @@ void launch_coarse_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, ui
                          DevStatus* st, uint64_t wait_ns, cudaStream_t s);
 // Child-occupancy bytes (sets flagged in `which`, grid y = set) and largest
 // occupancy per level.
+// Sorted points (xyz[perm[j]]) of the sets with `sorted` set; units: finishing tiles.
+void launch_sorted_xyz(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
+                       DevStatus* st, cudaStream_t s);
+void launch_sorted_xyz_one(const uint32_t* perm, const float* xyz, uint32_t n, float* out,
+                           cudaStream_t s);
+// Alg. 2 over all receiver boxes of a level: E2 source-point counts, then the copy.
+void launch_e2_count(const uint32_t* e2_off, const uint32_t* e2_idx, const uint32_t* src_off,
+                     uint32_t nrecv, uint32_t* out, DevStatus* st, cudaStream_t s);
+void launch_e2_gather(const uint32_t* e2_off, const uint32_t* e2_idx, const uint32_t* src_off,
+                      const float* sorted_src, const uint32_t* off, uint32_t nrecv, float* out,
+                      cudaStream_t s);
 // Child-occupancy bytes of the slots' sets (slot aux0 = the set's units).
 void launch_occupancy(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
                       DevStatus* st, cudaStream_t s);

@@ -23,6 +23,8 @@ FMM_OK, FMM_ERR_ARG, FMM_ERR_DOMAIN, FMM_ERR_LEVEL = 0, 1, 2, 3
 FMM_ERR_OOM, FMM_ERR_TIMEOUT, FMM_ERR_CUDA, FMM_ERR_CAPACITY = 4, 5, 6, 7
 
 FMM_FLAG_HOST_INPUT = 0x1
+FMM_FLAG_BOX_ORDER = 0x2
+FMM_FLAG_SORTED_XYZ = 0x4
 FMM_FLAG_TEST_STALL = 0x80000000
 
 _u32p = C.POINTER(C.c_uint32)
@@ -46,6 +48,7 @@ class TreeC(C.Structure):
         ("nnz_e2", C.c_uint64 * _L), ("nnz_e4", C.c_uint64 * _L),
         ("e2_off", C.c_void_p * _L), ("e2_idx", C.c_void_p * _L),
         ("e4_off", C.c_void_p * _L), ("e4_idx", C.c_void_p * _L),
+        ("sorted_src", C.c_void_p), ("sorted_recv", C.c_void_p),
     ]
 
 
@@ -110,6 +113,7 @@ EXPORTS = (
     "fmm_query_workspace",
     "fmm_set_tuning", "fmm_get_tuning", "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing",
     "fmm_last_launch_count", "fmm_status_string", "fmm_exclusive_scan_noalloc",
+    "fmm_e2_source_offsets", "fmm_gather_e2_sources",
     "fmm_displace", "fmm_server_create", "fmm_server_destroy", "fmm_server_add_system",
     "fmm_server_submit", "fmm_server_wait", "fmm_server_run_trace", "fmm_server_points",
     "fmm_server_tree",
@@ -172,6 +176,12 @@ def _load():
     lib.fmm_exclusive_scan_noalloc.restype = C.c_int
     lib.fmm_status_string.argtypes = [C.c_int]
     lib.fmm_status_string.restype = C.c_char_p
+    lib.fmm_e2_source_offsets.argtypes = [C.c_void_p, C.POINTER(TreeC), C.c_int, C.c_void_p,
+                                          _u64p, C.c_void_p]
+    lib.fmm_e2_source_offsets.restype = C.c_int
+    lib.fmm_gather_e2_sources.argtypes = [C.c_void_p, C.POINTER(TreeC), C.c_int, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.fmm_gather_e2_sources.restype = C.c_int
     lib.fmm_displace.argtypes = [C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_float,
                                  C.c_void_p]
     lib.fmm_displace.restype = C.c_int
@@ -243,6 +253,9 @@ class Tree:
     e2_idx: dict
     e4_off: dict
     e4_idx: dict
+    sorted_src: object = None   # float32 [N, 3] with FMM_FLAG_SORTED_XYZ
+    sorted_recv: object = None
+    raw: object = None          # the fmm_tree struct (for calls that take it)
 
     def numpy(self) -> dict:
         """Host copy with the oracle's layout (uint32 / uint64 numpy arrays)."""
@@ -261,6 +274,10 @@ class Tree:
             }
         for nm in ("e2_off", "e2_idx", "e4_off", "e4_idx"):
             out[nm] = {l: u32(t) for l, t in getattr(self, nm).items()}
+        for nm in ("sorted_src", "sorted_recv"):
+            t = getattr(self, nm)
+            if t is not None:
+                out[nm] = t.cpu().numpy().copy()
         return out
 
 
@@ -281,6 +298,12 @@ def _tree_from(tc: TreeC, n: int, m: int) -> Tree:
     tree = Tree(L=Lr, s_unmet=tc.s_unmet, src=_side(tc, "src", Lr, n),
                 recv=_side(tc, "recv", Lr, m), nnz_e2=list(tc.nnz_e2), nnz_e4=list(tc.nnz_e4),
                 e2_off={}, e2_idx={}, e4_off={}, e4_idx={})
+    import torch
+    for nm, cnt in (("sorted_src", n), ("sorted_recv", m)):
+        ptr = getattr(tc, nm)
+        if ptr:
+            setattr(tree, nm, _view(ptr, 3 * cnt, "<i4").view(torch.float32).view(cnt, 3))
+    tree.raw = tc
     for l in range(2, Lr + 1):
         nr = tc.nbox_recv[l]
         tree.e2_off[l] = _view(tc.e2_off[l], nr + 1, "<i4")
@@ -385,6 +408,33 @@ class Context:
         if raw:
             return b.outs
         return [_tree_from(b.outs[i], b.sizes[i][0], b.sizes[i][1]) for i in range(b.k)]
+
+    def gather_e2(self, tree: "Tree", level: int, sorted_src=None, stream=None):
+        """Alg. 2 for every receiver box of `level` (fmm_e2_source_offsets +
+        fmm_gather_e2_sources): returns (offsets int32-carrying-uint32 [nbox+1],
+        points float32 [total, 3]) on the device."""
+        import torch
+        lib = _load()
+        if sorted_src is None:
+            sorted_src = tree.sorted_src
+        if sorted_src is None:
+            raise ValueError("build with FMM_FLAG_SORTED_XYZ or pass sorted_src")
+        nb = tree.recv.nbox[level]
+        off = torch.empty(nb + 1, dtype=torch.int32, device="cuda")
+        total = C.c_uint64()
+        h = C.c_void_p(self._stream(stream))
+        st = lib.fmm_e2_source_offsets(self._h, C.byref(tree.raw), level, C.c_void_p(off.data_ptr()),
+                                       C.byref(total), h)
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_e2_source_offsets")
+        out = torch.empty((int(total.value), 3), dtype=torch.float32, device="cuda")
+        st = lib.fmm_gather_e2_sources(self._h, C.byref(tree.raw), level,
+                                       C.c_void_p(sorted_src.data_ptr() if sorted_src.numel() else 0),
+                                       C.c_void_p(off.data_ptr()),
+                                       C.c_void_p(out.data_ptr() if out.numel() else 0), h)
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_gather_e2_sources")
+        return off, out
 
     def morton_keys(self, xyz, out=None, stream=None):
         """fmm_morton_keys: int64 CUDA tensor carrying the uint64 keys."""

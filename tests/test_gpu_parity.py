@@ -243,3 +243,63 @@ def test_full_size_configs(ctx, orc, cfg):
             for nm in ("key", "off", "parent", "child"):
                 assert np.array_equal(got[side][nm][l], want[side][nm][l]), (side, nm, l)
     _sampled_lists(ctx, orc, got, want, L, seed=cfg)
+
+
+# ---------------------------------------------------------------------------
+# Box-key order (FMM_FLAG_BOX_ORDER): points ordered by (level-L key, index).
+
+@pytest.mark.parametrize("L", [0, 1, 2, 5, 7, 12, 21])
+def test_box_key_order_fixed_level(ctx, orc, L):
+    from paper_1301_1704_gb300 import fmmds
+    src = workloads.clumps(60000, 60 + L, nclumps=6, sigma=0.02)
+    recv = workloads.uniform(40001, 61)
+    got = ctx.build(_dev(src), _dev(recv), L=L, flags=fmmds.FMM_FLAG_BOX_ORDER).numpy()
+    compare_full(got, orc.build_tree(src, recv, L=L, order=orc.ORDER_BOX), L)
+
+
+def test_box_key_order_cluster_size_and_batched(ctx, orc):
+    from paper_1301_1704_gb300 import fmmds
+    pts = [workloads.clumps(30000, 70, nclumps=4, sigma=0.02), workloads.uniform(5000, 71),
+           np.repeat(np.array([[0.5, 0.5, 0.5]], np.float32), 300, axis=0)]
+    got = ctx.build(_dev(pts[0]), _dev(pts[1]), s=32, flags=fmmds.FMM_FLAG_BOX_ORDER).numpy()
+    want = orc.build_tree(pts[0], pts[1], L=-1, s=32, order=orc.ORDER_BOX)
+    assert got["L"] == want["L"]
+    compare_full(got, want, want["L"])
+    devs = [_dev(p) for p in pts]
+    trees = ctx.build_batched([(d, d) for d in devs], s=16, flags=fmmds.FMM_FLAG_BOX_ORDER)
+    for p, t in zip(pts, trees):
+        want = orc.build_tree(p, p, L=-1, s=16, order=orc.ORDER_BOX)
+        g = t.numpy()
+        assert (g["L"], g["s_unmet"]) == (want["L"], want["s_unmet"])
+        compare_full(g, want, want["L"])
+
+
+# ---------------------------------------------------------------------------
+# Sorted points (FMM_FLAG_SORTED_XYZ) and Alg. 2 over whole levels.
+
+def test_sorted_points_and_e2_gather(ctx, orc):
+    from paper_1301_1704_gb300 import fmmds
+    src = workloads.clumps(40000, 90, nclumps=6, sigma=0.03)
+    recv = workloads.uniform(9000, 91)
+    L = 5
+    tree = ctx.build(_dev(src), _dev(recv), L=L, flags=fmmds.FMM_FLAG_SORTED_XYZ)
+    got = tree.numpy()
+    want = orc.build_tree(src, recv, L=L)
+    compare_full(got, want, L)
+    assert np.array_equal(got["sorted_src"], orc.sorted_points(src, want["src"]["perm"]))
+    assert np.array_equal(got["sorted_recv"], orc.sorted_points(recv, want["recv"]["perm"]))
+    for level in (2, 4, L):
+        off, pts = ctx.gather_e2(tree, level)
+        woff, wpts = orc.gather_e2(want, src, level)
+        assert np.array_equal(off.cpu().numpy().view(np.uint32).astype(np.uint64), woff)
+        assert np.array_equal(pts.cpu().numpy(), wpts)
+
+
+def test_sorted_points_aliased_and_long_boxes(ctx, orc):
+    from paper_1301_1704_gb300 import fmmds
+    rng = np.random.default_rng(92)
+    p = (0.25 + 0.01 * rng.random((30000, 3))).astype(np.float32)  # boxes past the window
+    t = ctx.build(_dev(p), _dev(p), L=3, flags=fmmds.FMM_FLAG_SORTED_XYZ).numpy()
+    w = orc.build_tree(p, p, L=3)
+    compare_full(t, w, 3)
+    assert np.array_equal(t["sorted_src"], orc.sorted_points(p, w["src"]["perm"]))
