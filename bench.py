@@ -544,6 +544,25 @@ def main():
     e2e_ms = max_over_ranks(e2e_ms, dist)
     e2e_val = (replica_throughput(pts_per_step * args.e2e_steps, e2e_ms, ws) / 1e6
                if args.e2e_steps else None)
+    # The same build with each way of ordering the points (radix passes in
+    # reduce-then-scan or onesweep form, the paper's Fixed-Grid pseudo-sort).
+    sort_kinds = {}
+    if (npts, level) == (N_PTS, LEVEL):
+        base_kind = ctx.tuning()["sort_kind"]
+        for kind, name in ((fmmds.FMM_SORT_RTS, "radix_rts"), (fmmds.FMM_SORT_ONESWEEP, "radix_onesweep"),
+                           (fmmds.FMM_SORT_FIXED_GRID, "fixed_grid")):
+            ctx.set_tuning(kind)
+            for _ in range(2):
+                ctx.build(src, recv, L=level, stream=stream, raw=True)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(5)]
+            for a, b in evs:
+                a.record(stream)
+                ctx.build(src, recv, L=level, stream=stream, raw=True)
+                b.record(stream)
+            torch.cuda.synchronize()
+            sort_kinds[name] = _pct([a.elapsed_time(b) for a, b in evs], 0.5)
+        ctx.set_tuning(base_kind)
     batched = None
     if not args.no_batched:
         batched = batched_section(ctx, stream, args.steps, args.warmup, args.plain_steps)
@@ -575,6 +594,8 @@ def main():
         }
         if not args.no_cpu_baseline and ws == 1 and (npts, level) == (N_PTS, LEVEL):
             line["cpu_baseline"] = cpu_baseline()
+        if sort_kinds:
+            line["p50_ms_by_sort_kind"] = sort_kinds
         if batched is not None:
             line["batched"] = batched
         if served is not None:

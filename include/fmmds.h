@@ -190,15 +190,23 @@ int fmm_morton_keys(fmm_ctx* ctx, const float* xyz, uint32_t n, uint64_t* keys, 
 /* Upper bound of the arena bytes one build of this size needs. */
 int fmm_query_workspace(uint32_t N, uint32_t M, fmm_params params, uint64_t* bytes);
 
-/* Tuning of a context (the autotuner's knobs).  sort_kind selects how each
- * radix pass finds its output positions:
- *   FMM_SORT_RTS       per-tile digit histograms, one prefix sum, then a
- *                      scatter with no waiting between tiles (default);
- *   FMM_SORT_ONESWEEP  one kernel per pass, each tile finds its offsets by
- *                      decoupled look-back over the earlier tiles.
- * Both give the same result.  FMM_ERR_ARG for an unknown kind. */
+/* Tuning of a context (the autotuner's knobs).  sort_kind selects how the
+ * points are ordered before the finishing sort inside the boxes:
+ *   FMM_SORT_RTS         LSD radix passes, each: per-tile digit histograms,
+ *                        one prefix sum, then a scatter with no waiting
+ *                        between tiles (default);
+ *   FMM_SORT_ONESWEEP    radix passes, one kernel each, every tile finding
+ *                        its offsets by decoupled look-back over the earlier
+ *                        tiles;
+ *   FMM_SORT_FIXED_GRID  the paper's Fixed-Grid pseudo-sort (Alg. 1): a dense
+ *                        histogram of the level-Ls cells with atomic ranks,
+ *                        its prefix sum as the bookmarks (Alg. 3), one move;
+ *                        used when every set's sort depth is at most 8 and
+ *                        the histograms hold at most 2^28 cells (else RTS).
+ * All give the same result.  FMM_ERR_ARG for an unknown kind. */
 #define FMM_SORT_RTS 0u
 #define FMM_SORT_ONESWEEP 1u
+#define FMM_SORT_FIXED_GRID 2u
 typedef struct fmm_tuning {
   uint32_t sort_kind;
 } fmm_tuning;

@@ -463,6 +463,68 @@ int run_sort(fmm_ctx* c, std::vector<SetPlan*>& sets, SortMem& m, bool stall, ui
   return FMM_OK;
 }
 
+// The Fixed-Grid pseudo-sort of `sets` (Alg. 1, 3): keys, cells and atomic
+// ranks into (kb, vb), one prefix sum over all sets' histograms, the move
+// into (ka, va).  The order inside a level-Ls cell is left to the finishing
+// sort.
+int fixed_grid_sort(fmm_ctx* c, std::vector<SetPlan*>& sets, SortMem& m, uint64_t cells,
+                    uint64_t wait_ns) {
+  cudaStream_t s = c->stream;
+  int err = FMM_OK;
+  std::vector<Slot> slots;
+  uint32_t tiles = 0, compact = 0, bin0 = 0;
+  for (uint32_t id = 0; id < sets.size(); ++id) {
+    SetPlan& sp = *sets[id];
+    Seg& d = sp.dev;
+    d.passes = sp.n ? 1 : 0;
+    d.skeys = m.ka + d.base;
+    d.svals = m.va + d.base;
+    if (sp.n == 0) continue;
+    slots.push_back(Slot{id, tiles, bin0, d.base - compact});
+    tiles += d.ntiles;
+    compact += sp.n;
+    bin0 += 1u << (3 * sp.Ls);
+  }
+  const size_t zb = align_up(sizeof(uint32_t) * (cells + 1)) +
+                    align_up(sizeof(uint64_t) * scan_tiles((uint32_t)cells)) +
+                    align_up(sizeof(uint32_t) * 4);
+  char* z = arena_get<char>(c, zb, &err);
+  if (err) return err;
+  uint32_t* bins = reinterpret_cast<uint32_t*>(z);
+  uint64_t* status = reinterpret_cast<uint64_t*>(z + align_up(sizeof(uint32_t) * (cells + 1)));
+  uint32_t* counter = reinterpret_cast<uint32_t*>(
+      reinterpret_cast<char*>(status) + align_up(sizeof(uint64_t) * scan_tiles((uint32_t)cells)));
+  Upload up;
+  std::vector<Seg> segs_host(sets.size());
+  for (size_t i = 0; i < sets.size(); ++i) segs_host[i] = sets[i]->dev;
+  const size_t o_segs = up.add(segs_host.data(), segs_host.size());
+  const size_t o_slots = up.add(slots.data(), slots.size());
+  char* dev = upload(c, up, &err);
+  if (err) return err;
+  m.segs = reinterpret_cast<Seg*>(dev + o_segs);
+  // the depth stage walks the sort's tiles through pass 0's slot table
+  m.max_passes = 1;
+  m.pass_slots[0] = reinterpret_cast<Slot*>(dev + o_slots);
+  m.pass_nslots[0] = (uint32_t)slots.size();
+  m.pass_tiles[0] = tiles;
+  FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
+  {
+    Launch L(c, "fg_count");
+    launch_fg_count(m.segs, m.pass_slots[0], m.pass_nslots[0], tiles, bins, m.kb, m.vb, c->st, s);
+  }
+  {
+    Launch L(c, "scan");
+    launch_scan_u32(bins, nullptr, (uint32_t)cells, status, counter, nullptr, c->st, wait_ns, s);
+  }
+  {
+    Launch L(c, "fg_move");
+    launch_fg_move(m.segs, m.pass_slots[0], m.pass_nslots[0], tiles, bins, m.kb, m.vb, m.ka, m.va,
+                   c->st, s);
+  }
+  FMM_CUDA(cudaGetLastError());
+  return FMM_OK;
+}
+
 // Sort stage: orders the points of `sets` by the top 3 * Ls bits of their
 // keys (all 63 for full sets) into fresh concatenated arrays and points each
 // set's skeys / svals there.  Only the sort fields of the descriptors change.
@@ -495,6 +557,19 @@ int sort_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, bool stall, uint64_t wait
   m.kb = arena_get<uint64_t>(c, nslot, &err);
   m.vb = arena_get<uint32_t>(c, nslot, &err);
   if (err) return err;
+
+  // The Fixed-Grid pseudo-sort, when chosen and every set's dense histogram
+  // (8^Ls cells) fits.
+  if (c->tuning.sort_kind == FMM_SORT_FIXED_GRID && !stall) {
+    bool ok = true;
+    uint64_t cells = 0;
+    for (auto* sp : sets) {
+      ok &= !sp->full && !sp->exact && sp->Ls <= 8;
+      if (sp->n) cells += 1ull << (3 * std::min(sp->Ls, 8));
+    }
+    if (ok && cells <= (1ull << 28)) return fixed_grid_sort(c, sets, m, cells, wait_ns);
+  }
+
   for (auto* sp : sets) {
     Seg& d = sp->dev;
     const int last = d.passes > 0 ? (d.passes - 1) & 1 : 0;
@@ -1317,7 +1392,7 @@ int fmm_morton_keys(fmm_ctx* c, const float* xyz, uint32_t n, uint64_t* keys, vo
 }
 
 int fmm_set_tuning(fmm_ctx* c, const fmm_tuning* t) {
-  if (!c || !t || t->sort_kind > FMM_SORT_ONESWEEP) return FMM_ERR_ARG;
+  if (!c || !t || t->sort_kind > FMM_SORT_FIXED_GRID) return FMM_ERR_ARG;
   c->tuning = *t;
   return FMM_OK;
 }

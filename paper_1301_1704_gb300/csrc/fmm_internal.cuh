@@ -442,6 +442,15 @@ void launch_e2_count(const uint32_t* e2_off, const uint32_t* e2_idx, const uint3
 void launch_e2_gather(const uint32_t* e2_off, const uint32_t* e2_idx, const uint32_t* src_off,
                       const float* sorted_src, const uint32_t* off, uint32_t nrecv, float* out,
                       cudaStream_t s);
+// Fixed-Grid pseudo-sort (Alg. 1, 3): keys, cells and atomic ranks per tile
+// (slot aux0: the set's first histogram entry), then the move to bookmark +
+// rank (slot aux1: the set's base minus the points of earlier sets).
+void launch_fg_count(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t ntiles,
+                     uint32_t* bins, uint64_t* keys_out, uint32_t* ranks_out, DevStatus* st,
+                     cudaStream_t s);
+void launch_fg_move(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t ntiles,
+                    const uint32_t* bins, const uint64_t* keys_in, const uint32_t* ranks_in,
+                    uint64_t* keys_out, uint32_t* vals_out, DevStatus* st, cudaStream_t s);
 // Child-occupancy bytes of the slots' sets (slot aux0 = the set's units).
 void launch_occupancy(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
                       DevStatus* st, cudaStream_t s);

@@ -122,6 +122,7 @@ FMM_NOALLOC_SCAN_MAX = 1 << 26
 
 FMM_SORT_RTS = 0
 FMM_SORT_ONESWEEP = 1
+FMM_SORT_FIXED_GRID = 2
 
 
 class Tuning(C.Structure):

@@ -63,7 +63,7 @@ def test_morton_keys_match_oracle(ctx, orc):
         assert np.array_equal(got, orc.keys(p))
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_sort_kinds_agree(ctx, orc, kind):
     from paper_1301_1704_gb300 import fmmds
     src = workloads.clumps(150000, 30, nclumps=10, sigma=0.03)
