@@ -265,6 +265,8 @@ def batched_section(ctx, stream, steps: int, warmup: int, plain_steps: int) -> d
     pairs = [(d, d) for d in devs]
     npts = int(sum(len(p) for p in sets))  # aliased: each point counted once
     batch = ctx.batch(pairs)
+    saved = ctx.tuning()
+    tuned = ctx.autotune(batch, s=64, trials=2, stream=stream)
 
     def timed(fn, k):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -331,6 +333,8 @@ def batched_section(ctx, stream, steps: int, warmup: int, plain_steps: int) -> d
     out["nnz"] = {"e2": int(nnz2), "e4": int(nnz4)}
     out["levels"] = {"min": int(min(levels)), "max": int(max(levels)),
                      "mean": float(np.mean(levels))}
+    out["batched"]["tuning"] = tuned
+    ctx.set_tuning(saved["sort_kind"], saved["sort_items"])
     out["workload"] = ("512 aliased sets, sizes log-uniform in [1e3, 1e6], uniform / sphere / "
                        "clumps with p = 1/3, s = 64 (per-set L); batched = one fmm_build_batched "
                        "call, plain = one fmm_build call per set")
@@ -415,7 +419,10 @@ def main():
     ap.add_argument("--points", type=int, default=N_PTS,
                     help="points per set (default 2^24; smaller values only for profiling)")
     ap.add_argument("--level", type=int, default=LEVEL)
-    ap.add_argument("--sort-kind", type=int, default=None, help="0 reduce-then-scan, 1 onesweep")
+    ap.add_argument("--sort-kind", type=int, default=None,
+                    help="0 radix reduce-then-scan, 1 radix onesweep, 2 Fixed-Grid (else autotuned)")
+    ap.add_argument("--sort-items", type=int, default=0, help="points per thread of a sort tile")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="steps of the per-instance comparison of the batched workload")
@@ -449,9 +456,13 @@ def main():
     src = torch.from_numpy(src_h).cuda()
     recv = torch.from_numpy(recv_h).cuda()
     ctx = fmmds.Context(local)
-    if args.sort_kind is not None:
-        ctx.set_tuning(args.sort_kind)
     stream = torch.cuda.current_stream()
+    autotuned = None
+    if args.sort_kind is not None:
+        ctx.set_tuning(args.sort_kind, args.sort_items)
+    elif not args.no_autotune:
+        # the library's autotuner picks the sort kind and tile size on these inputs
+        autotuned = ctx.autotune([(src, recv)], L=level, trials=3, stream=stream)
 
     for _ in range(args.warmup):
         ctx.build(src, recv, L=level, stream=stream, raw=True)
@@ -548,7 +559,7 @@ def main():
     # reduce-then-scan or onesweep form, the paper's Fixed-Grid pseudo-sort).
     sort_kinds = {}
     if (npts, level) == (N_PTS, LEVEL):
-        base_kind = ctx.tuning()["sort_kind"]
+        base = ctx.tuning()
         for kind, name in ((fmmds.FMM_SORT_RTS, "radix_rts"), (fmmds.FMM_SORT_ONESWEEP, "radix_onesweep"),
                            (fmmds.FMM_SORT_FIXED_GRID, "fixed_grid")):
             ctx.set_tuning(kind)
@@ -562,7 +573,7 @@ def main():
                 b.record(stream)
             torch.cuda.synchronize()
             sort_kinds[name] = _pct([a.elapsed_time(b) for a, b in evs], 0.5)
-        ctx.set_tuning(base_kind)
+        ctx.set_tuning(base["sort_kind"], base["sort_items"])
     batched = None
     if not args.no_batched:
         batched = batched_section(ctx, stream, args.steps, args.warmup, args.plain_steps)
@@ -575,7 +586,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "tuning": ctx.tuning(),
+            "tuning": dict(ctx.tuning(), autotuned=autotuned is not None),
             "config": {"workload": WORKLOAD if (npts, level) == (N_PTS, LEVEL) else
                        f"profiling case N=M={npts} uniform, L={level}", "N": npts, "M": npts, "L": level,
                        "seeds": list(SEEDS), "l2": "inputs larger than L2 (402 MB of xyz)",

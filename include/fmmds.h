@@ -207,12 +207,27 @@ int fmm_query_workspace(uint32_t N, uint32_t M, fmm_params params, uint64_t* byt
 #define FMM_SORT_RTS 0u
 #define FMM_SORT_ONESWEEP 1u
 #define FMM_SORT_FIXED_GRID 2u
+/* sort_items: points per thread of a radix tile (4, 6 or 8; 0 = 6): the tile
+ * of the histogram, scatter, depth and Fixed-Grid kernels is 512 x sort_items
+ * points.  Larger tiles mean fewer tiles and histogram entries but one
+ * resident scatter block per SM instead of two at 8. */
 typedef struct fmm_tuning {
   uint32_t sort_kind;
+  uint32_t sort_items;
 } fmm_tuning;
 
 int fmm_set_tuning(fmm_ctx* ctx, const fmm_tuning* tuning);
 int fmm_get_tuning(fmm_ctx* ctx, fmm_tuning* tuning);
+
+/* The autotuner: times `trials` builds of `sets` (as fmm_build_batched with
+ * `params`) for every sort kind x items-per-thread choice, after one warm-up
+ * build each, with CUDA events on `stream`; keeps the one with the smallest
+ * median time as the context's tuning and returns it in *best (and its median
+ * in *best_ms).  Every candidate gives the same result, so the choice only
+ * changes speed.  The context's arena holds the last candidate's outputs
+ * afterwards. */
+int fmm_autotune(fmm_ctx* ctx, const fmm_set* sets, uint32_t nsets, fmm_params params,
+                 uint32_t trials, fmm_tuning* best, double* best_ms, void* stream);
 
 /* Per-kernel timing with CUDA events on the build's stream (off by
  * default).  Each entry: kernel name, launches and summed milliseconds since

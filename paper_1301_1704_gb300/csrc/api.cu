@@ -61,7 +61,7 @@ struct fmm_ctx {
   std::vector<TimeAcc> acc;
   uint64_t launches = 0;
   uint64_t last_launches = 0;
-  fmm_tuning tuning{FMM_SORT_RTS};
+  fmm_tuning tuning{FMM_SORT_RTS, 6};
 };
 
 namespace {
@@ -457,8 +457,8 @@ int run_sort(fmm_ctx* c, std::vector<SetPlan*>& sets, SortMem& m, bool stall, ui
     // The first pass may leave equal digits in any order when a finishing
     // sort follows; sets sorted in full keep every pass stable.
     Launch L(c, "rts_scatter");
-    launch_rts_scatter(p, m.pass_recs[p], m.pass_tiles[p], kin, vin, kout, vout, m.pass_hist[p],
-                       any_full || p > 0, true, c->st, wait_ns, s);
+    launch_rts_scatter(p, c->tuning.sort_items, m.pass_recs[p], m.pass_tiles[p], kin, vin, kout,
+                       vout, m.pass_hist[p], any_full || p > 0, true, c->st, wait_ns, s);
   }
   return FMM_OK;
 }
@@ -546,7 +546,8 @@ int sort_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, bool stall, uint64_t wait
     d.passes = sp->n ? std::max(passes_for(sp->Ls), sp->exact ? 1 : 0) : 0;
     d.lo = 63 - 3 * sp->Ls;
     d.exact = sp->exact ? 1 : 0;
-    d.ntiles = (uint32_t)(((uint64_t)sp->n + kSortTile - 1) / kSortTile);
+    d.tile = kSortThreads * c->tuning.sort_items;
+    d.ntiles = (uint32_t)(((uint64_t)sp->n + d.tile - 1) / d.tile);
     slots_total += ((uint64_t)sp->n + 3) & ~3ull;  // set bases stay 16-byte aligned
     if (slots_total >= (1ull << 32)) return FMM_ERR_ARG;
     m.max_passes = std::max(m.max_passes, d.passes);
@@ -1192,8 +1193,9 @@ int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes
     const uint64_t n = ns[k];
     if (p.flags & FMM_FLAG_HOST_INPUT) total += align_up(12 * n);
     total += 2 * align_up(12 * n + 48) + align_up(4 * n) + (16 << 10);
-    total += (n / kSortTile + 1) * kRadixMax * 4 * 3 + (n / kBoxTile + 1) * 8 * (1 + kLevels);
-    total += (n / kSortTile + 1) * sizeof(TileRec) * 8 + 8 * 256;  // tile records, 8 passes
+    const uint64_t tiles = n / (kSortThreads * 4) + 1;  // the smallest tile
+    total += tiles * kRadixMax * 4 * 3 + (n / kBoxTile + 1) * 8 * (1 + kLevels);
+    total += tiles * sizeof(TileRec) * 8 + 8 * 256;  // tile records, 8 passes
     for (int l = 0; l <= L; ++l) total += align_up(21ull * level_cap(ns[k], l) + 8) + 1024;
   }
   for (int l = 2; l <= L; ++l)
@@ -1393,7 +1395,64 @@ int fmm_morton_keys(fmm_ctx* c, const float* xyz, uint32_t n, uint64_t* keys, vo
 
 int fmm_set_tuning(fmm_ctx* c, const fmm_tuning* t) {
   if (!c || !t || t->sort_kind > FMM_SORT_FIXED_GRID) return FMM_ERR_ARG;
+  const uint32_t items = t->sort_items ? t->sort_items : 6;
+  if (items != 4 && items != 6 && items != 8) return FMM_ERR_ARG;
   c->tuning = *t;
+  c->tuning.sort_items = items;
+  return FMM_OK;
+}
+
+int fmm_autotune(fmm_ctx* c, const fmm_set* sets, uint32_t nsets, fmm_params params,
+                 uint32_t trials, fmm_tuning* best, double* best_ms, void* stream) {
+  if (!c || !best || nsets == 0 || !sets || trials == 0) return FMM_ERR_ARG;
+  FMM_TRY(check_params(params));
+  if (params.flags & FMM_FLAG_TEST_STALL) return FMM_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<fmm_tree> outs(nsets);
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    return FMM_ERR_CUDA;
+  }
+  const fmm_tuning saved = c->tuning;
+  fmm_tuning win = saved;
+  double win_ms = 1e300;
+  int st = FMM_OK;
+  const uint32_t kinds[3] = {FMM_SORT_RTS, FMM_SORT_ONESWEEP, FMM_SORT_FIXED_GRID};
+  const uint32_t items[3] = {4, 6, 8};
+  for (uint32_t kind : kinds) {
+    for (uint32_t it : items) {
+      if (kind == FMM_SORT_ONESWEEP && it != 6) continue;  // onesweep keeps its own tile
+      c->tuning = fmm_tuning{kind, it};
+      std::vector<double> ms;
+      for (uint32_t r = 0; r <= trials && st == FMM_OK; ++r) {
+        cudaEventRecord(a, s);
+        st = fmm_build_batched(c, sets, nsets, params, outs.data(), stream);
+        cudaEventRecord(b, s);
+        if (st == FMM_OK && cudaEventSynchronize(b) != cudaSuccess) st = FMM_ERR_CUDA;
+        float t = 0.f;
+        if (st == FMM_OK && r > 0) {  // the first build of a choice warms up
+          cudaEventElapsedTime(&t, a, b);
+          ms.push_back(t);
+        }
+      }
+      if (st != FMM_OK) break;
+      std::sort(ms.begin(), ms.end());
+      const double med = ms[ms.size() / 2];
+      if (med < win_ms) {
+        win_ms = med;
+        win = c->tuning;
+      }
+    }
+    if (st != FMM_OK) break;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->tuning = st == FMM_OK ? win : saved;
+  if (st != FMM_OK) return st;
+  *best = win;
+  if (best_ms) *best_ms = win_ms;
   return FMM_OK;
 }
 

@@ -447,12 +447,12 @@ __global__ void __launch_bounds__(256) depth_kernel(const Seg* __restrict__ segs
   const uint32_t k = find_slot(slots, nslots, blockIdx.x);
   const uint32_t set = slots[k].seg;
   const Seg& sg = segs[set];
-  const uint64_t t0 = (uint64_t)(blockIdx.x - slots[k].unit0) * kSortTile;
+  const uint64_t t0 = (uint64_t)(blockIdx.x - slots[k].unit0) * sg.tile;
   const uint64_t npairs = sg.n > s ? (uint64_t)sg.n - s : 0;
   const uint64_t* keys = sg.skeys;
   const uint32_t cap = (uint32_t)sg.Ls;
   uint32_t m = 0;
-  for (uint64_t i = t0 + threadIdx.x; i < t0 + kSortTile && i < npairs; i += blockDim.x) {
+  for (uint64_t i = t0 + threadIdx.x; i < t0 + sg.tile && i < npairs; i += blockDim.x) {
     const uint32_t shared = first_diff_level(keys[i], keys[i + s]) - 1u;  // 0..21
     const uint32_t v = (shared < cap ? shared : cap) + 1u;
     m = v > m ? v : m;

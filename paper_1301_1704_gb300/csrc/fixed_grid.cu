@@ -27,8 +27,8 @@ __global__ void __launch_bounds__(256) fg_count_kernel(const Seg* __restrict__ s
                                                        DevStatus* st) {
   const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
   const Seg& sg = segs[sl.seg];
-  const uint64_t base = (uint64_t)(blockIdx.x - sl.unit0) * kSortTile;
-  const uint32_t cnt = (uint32_t)((sg.n - base) < (uint64_t)kSortTile ? (sg.n - base) : kSortTile);
+  const uint64_t base = (uint64_t)(blockIdx.x - sl.unit0) * sg.tile;
+  const uint32_t cnt = (uint32_t)((sg.n - base) < (uint64_t)sg.tile ? (sg.n - base) : sg.tile);
   const int shift = 63 - 3 * sg.Ls;
   uint32_t* const bin = bins + sl.aux0;
   uint64_t* const ko = keys_out + sg.base + base;
@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(256) fg_move_kernel(const Seg* __restrict__ se
   if (failed(st)) return;
   const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
   const Seg& sg = segs[sl.seg];
-  const uint64_t base = (uint64_t)(blockIdx.x - sl.unit0) * kSortTile;
-  const uint32_t cnt = (uint32_t)((sg.n - base) < (uint64_t)kSortTile ? (sg.n - base) : kSortTile);
+  const uint64_t base = (uint64_t)(blockIdx.x - sl.unit0) * sg.tile;
+  const uint32_t cnt = (uint32_t)((sg.n - base) < (uint64_t)sg.tile ? (sg.n - base) : sg.tile);
   const int shift = 63 - 3 * sg.Ls;
   const uint32_t* const bin = bins + sl.aux0;
   const uint32_t lo = sg.base, hi = sg.base + sg.n;

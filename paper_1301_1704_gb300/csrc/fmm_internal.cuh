@@ -283,7 +283,7 @@ struct Seg {
   int passes, lo;     // radix passes of 8 bits, lowest sorted key bit
   int exact;          // sorted on exactly the top 3*Ls bits with stable passes: the
                       // order is final, no finishing sort (box-key order)
-  int pad_;
+  uint32_t tile;      // points of a sort tile (kSortThreads x items per thread)
   uint32_t ntiles;    // sort tiles
   uint32_t btiles;    // finishing / finest-box tiles
   uint32_t* perm;
@@ -401,10 +401,10 @@ void launch_tile_hist(int pass, const Seg* segs, const Slot* slots, uint32_t nsl
 // histogram stored, values = point indices -- to (keys_out, vals_out)
 // (concatenated arrays).  stable = false only for a first pass that a
 // finishing sort follows.
-void launch_rts_scatter(int pass, const TileRec* recs, uint32_t ntiles, const uint64_t* keys_in,
-                        const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                        const uint32_t* offsets, bool stable, bool bulk, DevStatus* st,
-                        uint64_t wait_ns, cudaStream_t s);
+void launch_rts_scatter(int pass, uint32_t items, const TileRec* recs, uint32_t ntiles,
+                        const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                        uint32_t* vals_out, const uint32_t* offsets, bool stable, bool bulk,
+                        DevStatus* st, uint64_t wait_ns, cudaStream_t s);
 
 // Onesweep pass over one set (keys_in / keys_out point at the set's slots).
 struct SortPlan {

@@ -344,8 +344,9 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(const Seg* __restrict__ 
   const uint32_t t = blockIdx.x - sl.unit0;  // tile of the set
   const uint32_t n = sg.n;
   const int shift = sg.lo + kRadixBits * pass;
-  const uint64_t base = (uint64_t)t * kSortTile;
-  const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)kSortTile ? (n - base) : kSortTile);
+  const uint32_t tile = sg.tile;
+  const uint64_t base = (uint64_t)t * tile;
+  const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)tile ? (n - base) : tile);
   if (threadIdx.x == 0) {
     TileRec r;
     r.xyz = sg.xyz ? sg.xyz + 3 * base : nullptr;
@@ -431,20 +432,25 @@ void launch_tile_hist(int pass, const Seg* segs, const Slot* slots, uint32_t nsl
 // loads.  Global output position of (set, digit, tile) = scanned offset + the
 // slot's correction (set base minus the points of the sets before it in this
 // pass).
-constexpr uint32_t kInBytes = kSortTile * 12;  // a tile's keys + indices
-constexpr size_t kScatterSmem = 2 * (size_t)kInBytes;
+// ITEMS: items per thread (the tile is kSortThreads * ITEMS points, a tuning
+// knob); kFirst: the values are the points' indices (first pass); kStable:
+// keep the input order inside a digit (every pass but an unstable first one).
+template <int ITEMS>
+constexpr size_t scatter_smem() {
+  return 2 * (size_t)kSortThreads * ITEMS * 12;  // two buffers of keys + indices
+}
 
-// kFirst: the values are the points' indices (first pass); kStable: keep the
-// input order inside a digit (every pass but an unstable first one).
-template <bool kFirst, bool kStable>
-__global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
+template <int ITEMS, bool kFirst, bool kStable>
+__global__ void __launch_bounds__(kSortThreads, ITEMS <= 6 ? 2 : 1) rts_scatter_kernel(
     const TileRec* __restrict__ recs, uint32_t ntiles, const uint64_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ offsets, bool bulk,
     DevStatus* st, uint64_t wait_ns) {
   constexpr int W = kSortThreads / 32;
   constexpr uint32_t mask = kRadixMax - 1u;
-  constexpr uint32_t kCopyBytes = kFirst ? kSortTile * 8 : kInBytes;
+  constexpr uint32_t kTile = kSortThreads * ITEMS;
+  constexpr uint32_t kInBytes = kTile * 12;
+  constexpr uint32_t kCopyBytes = kFirst ? kTile * 8 : kInBytes;
   __shared__ uint32_t s_fail;
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_wcnt[W][kRadixMax];  // per-warp digit counts, then block slots
@@ -465,12 +471,12 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
 
   // Full tiles are read by bulk copy (set bases are multiples of 4 slots, so
   // their keys and indices start 16-byte aligned).
-  auto is_bulk = [&](const TileRec& r) -> bool { return bulk && r.cnt == kSortTile; };
+  auto is_bulk = [&](const TileRec& r) -> bool { return bulk && r.cnt == kTile; };
   auto issue = [&](const TileRec& r, int b) {  // thread 0 only
     unsigned char* dst = s_in + b * kInBytes;
     mbar_expect_tx(&s_bar[b], kCopyBytes);
-    bulk_load(dst, keys_in + r.first, kSortTile * 8, &s_bar[b]);
-    if (!kFirst) bulk_load(dst + kSortTile * 8, vals_in + r.first, kSortTile * 4, &s_bar[b]);
+    bulk_load(dst, keys_in + r.first, kTile * 8, &s_bar[b]);
+    if (!kFirst) bulk_load(dst + kTile * 8, vals_in + r.first, kTile * 4, &s_bar[b]);
   };
   // bit b: parity of buffer b's barrier phase / a copy into buffer b is in flight
   uint32_t phase = 0u, pending = 0u;
@@ -521,32 +527,32 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
       return;
     }
 
-    // Items, warp-striped: item k of lane j is tile slot 32 * (kSortItems *
+    // Items, warp-striped: item k of lane j is tile slot 32 * (ITEMS *
     // warp + k) + j, so (k, lane) order is the input order.  Values are point
     // indices local to the set.
-    uint64_t key[kSortItems];
-    uint32_t val[kSortItems];
+    uint64_t key[ITEMS];
+    uint32_t val[ITEMS];
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-      const uint32_t j = (uint32_t)warp * (kSortItems * 32) + k * 32 + lane;
+    for (int k = 0; k < ITEMS; ++k) {
+      const uint32_t j = (uint32_t)warp * (ITEMS * 32) + k * 32 + lane;
       key[k] = 0;
       val[k] = r.local + j;
       if (j < cnt) {
         key[k] = full ? reinterpret_cast<const uint64_t*>(buf)[j] : keys_in[r.first + j];
         if (!kFirst)
-          val[k] = full ? reinterpret_cast<const uint32_t*>(buf + kSortTile * 8)[j]
+          val[k] = full ? reinterpret_cast<const uint32_t*>(buf + kTile * 8)[j]
                         : vals_in[r.first + j];
       }
     }
-    uint32_t pos[kSortItems];
+    uint32_t pos[ITEMS];
     if (!kStable) {
       // First pass: there is no earlier order to keep, so the rank inside a
       // digit needs no stability -- one shared-memory atomic per item (the
       // paper's Alg. 1 takes box ranks the same way).  Counts go to warp 0's
       // row; the finishing sort orders points inside a box by (key, index).
 #pragma unroll
-      for (int k = 0; k < kSortItems; ++k) {
-        const bool valid = (uint32_t)warp * (kSortItems * 32) + k * 32 + lane < cnt;
+      for (int k = 0; k < ITEMS; ++k) {
+        const bool valid = (uint32_t)warp * (ITEMS * 32) + k * 32 + lane < cnt;
         pos[k] = valid ? atomicAdd(&s_wcnt[0][(uint32_t)(key[k] >> shift) & mask], 1u) : 0u;
       }
     } else {
@@ -557,8 +563,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
       // hands the old count to the others.  A warp takes its items in input
       // order, so count + peers below = rank among equal digits.
 #pragma unroll
-      for (int k = 0; k < kSortItems; ++k) {
-        const bool valid = (uint32_t)warp * (kSortItems * 32) + k * 32 + lane < cnt;
+      for (int k = 0; k < ITEMS; ++k) {
+        const bool valid = (uint32_t)warp * (ITEMS * 32) + k * 32 + lane < cnt;
         const uint32_t d = (uint32_t)(key[k] >> shift) & mask;
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
@@ -611,11 +617,11 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     __syncthreads();
     // Reorder the tile by digit into the (now consumed) input buffer.
     uint64_t* r_keys = reinterpret_cast<uint64_t*>(buf);
-    uint32_t* r_vals = reinterpret_cast<uint32_t*>(buf + kSortTile * 8);
+    uint32_t* r_vals = reinterpret_cast<uint32_t*>(buf + kTile * 8);
     const int row = kStable ? warp : 0;
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-      if ((uint32_t)warp * (kSortItems * 32) + k * 32 + lane < cnt) {
+    for (int k = 0; k < ITEMS; ++k) {
+      if ((uint32_t)warp * (ITEMS * 32) + k * 32 + lane < cnt) {
         const uint32_t p = pos[k] + s_wcnt[row][(uint32_t)(key[k] >> shift) & mask];
         r_keys[p] = key[k];
         r_vals[p] = val[k];
@@ -623,7 +629,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
     }
     __syncthreads();
 #pragma unroll 2
-    for (int j = 0; j < kSortItems; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
       const uint32_t p = threadIdx.x + j * kSortThreads;
       if (p < cnt) {
         const uint64_t kk = r_keys[p];
@@ -638,37 +644,58 @@ __global__ void __launch_bounds__(kSortThreads, 2) rts_scatter_kernel(
   }
 }
 
-void launch_rts_scatter(int pass, const TileRec* recs, uint32_t ntiles, const uint64_t* keys_in,
-                        const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                        const uint32_t* offsets, bool stable, bool bulk, DevStatus* st,
-                        uint64_t wait_ns, cudaStream_t s) {
-  if (ntiles == 0) return;
-  // once per process (thread-safe static initialisation)
+namespace {
+
+template <int ITEMS>
+void scatter_items(int pass, const TileRec* recs, uint32_t ntiles, const uint64_t* keys_in,
+                   const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                   const uint32_t* offsets, bool stable, bool bulk, DevStatus* st,
+                   uint64_t wait_ns, cudaStream_t s) {
+  constexpr size_t smem = scatter_smem<ITEMS>();
+  // once per process and instantiation (thread-safe static initialisation)
   static const int sms = [] {
-    cudaFuncSetAttribute(rts_scatter_kernel<true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
-    cudaFuncSetAttribute(rts_scatter_kernel<true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
-    cudaFuncSetAttribute(rts_scatter_kernel<false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    cudaFuncSetAttribute(rts_scatter_kernel<ITEMS, true, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(rts_scatter_kernel<ITEMS, true, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(rts_scatter_kernel<ITEMS, false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
     return v > 0 ? v : 152;
   }();
-  uint32_t grid = (uint32_t)sms * 2u;
+  uint32_t grid = (uint32_t)sms * (ITEMS <= 6 ? 2u : 1u);  // persistent: the resident blocks
   if (grid > ntiles) grid = ntiles;
   if (pass == 0) {
     if (stable)
-      rts_scatter_kernel<true, true><<<grid, kSortThreads, kScatterSmem, s>>>(
+      rts_scatter_kernel<ITEMS, true, true><<<grid, kSortThreads, smem, s>>>(
           recs, ntiles, keys_in, nullptr, keys_out, vals_out, offsets, bulk, st, wait_ns);
     else
-      rts_scatter_kernel<true, false><<<grid, kSortThreads, kScatterSmem, s>>>(
+      rts_scatter_kernel<ITEMS, true, false><<<grid, kSortThreads, smem, s>>>(
           recs, ntiles, keys_in, nullptr, keys_out, vals_out, offsets, bulk, st, wait_ns);
   } else {
-    rts_scatter_kernel<false, true><<<grid, kSortThreads, kScatterSmem, s>>>(
+    rts_scatter_kernel<ITEMS, false, true><<<grid, kSortThreads, smem, s>>>(
         recs, ntiles, keys_in, vals_in, keys_out, vals_out, offsets, bulk, st, wait_ns);
   }
+}
+
+}  // namespace
+
+void launch_rts_scatter(int pass, uint32_t items, const TileRec* recs, uint32_t ntiles,
+                        const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                        uint32_t* vals_out, const uint32_t* offsets, bool stable, bool bulk,
+                        DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+  if (ntiles == 0) return;
+  if (items == 4)
+    scatter_items<4>(pass, recs, ntiles, keys_in, vals_in, keys_out, vals_out, offsets, stable,
+                     bulk, st, wait_ns, s);
+  else if (items == 8)
+    scatter_items<8>(pass, recs, ntiles, keys_in, vals_in, keys_out, vals_out, offsets, stable,
+                     bulk, st, wait_ns, s);
+  else
+    scatter_items<6>(pass, recs, ntiles, keys_in, vals_in, keys_out, vals_out, offsets, stable,
+                     bulk, st, wait_ns, s);
 }
 
 }  // namespace fmm

@@ -113,7 +113,7 @@ EXPORTS = (
     "fmm_query_workspace",
     "fmm_set_tuning", "fmm_get_tuning", "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing",
     "fmm_last_launch_count", "fmm_status_string", "fmm_exclusive_scan_noalloc",
-    "fmm_e2_source_offsets", "fmm_gather_e2_sources",
+    "fmm_autotune", "fmm_e2_source_offsets", "fmm_gather_e2_sources",
     "fmm_displace", "fmm_server_create", "fmm_server_destroy", "fmm_server_add_system",
     "fmm_server_submit", "fmm_server_wait", "fmm_server_run_trace", "fmm_server_points",
     "fmm_server_tree",
@@ -126,7 +126,7 @@ FMM_SORT_FIXED_GRID = 2
 
 
 class Tuning(C.Structure):
-    _fields_ = [("sort_kind", C.c_uint32)]
+    _fields_ = [("sort_kind", C.c_uint32), ("sort_items", C.c_uint32)]
 
 _lib = None
 
@@ -177,6 +177,9 @@ def _load():
     lib.fmm_exclusive_scan_noalloc.restype = C.c_int
     lib.fmm_status_string.argtypes = [C.c_int]
     lib.fmm_status_string.restype = C.c_char_p
+    lib.fmm_autotune.argtypes = [C.c_void_p, C.POINTER(SetC), C.c_uint32, Params, C.c_uint32,
+                                 C.POINTER(Tuning), C.POINTER(C.c_double), C.c_void_p]
+    lib.fmm_autotune.restype = C.c_int
     lib.fmm_e2_source_offsets.argtypes = [C.c_void_p, C.POINTER(TreeC), C.c_int, C.c_void_p,
                                           _u64p, C.c_void_p]
     lib.fmm_e2_source_offsets.restype = C.c_int
@@ -451,8 +454,8 @@ class Context:
             raise FmmError(st, "fmm_morton_keys")
         return out
 
-    def set_tuning(self, sort_kind: int):
-        t = Tuning(sort_kind)
+    def set_tuning(self, sort_kind: int, sort_items: int = 0):
+        t = Tuning(sort_kind, sort_items)
         st = _load().fmm_set_tuning(self._h, C.byref(t))
         if st != FMM_OK:
             raise FmmError(st, "fmm_set_tuning")
@@ -460,7 +463,25 @@ class Context:
     def tuning(self) -> dict:
         t = Tuning()
         _load().fmm_get_tuning(self._h, C.byref(t))
-        return {"sort_kind": int(t.sort_kind)}
+        return {"sort_kind": int(t.sort_kind), "sort_items": int(t.sort_items)}
+
+    def autotune(self, sets, L: int | None = None, s: int | None = None, trials: int = 3,
+                 flags: int = 0, stream=None) -> dict:
+        """fmm_autotune over (sort kind, items per thread) on the given pairs
+        (a list of (src, recv) CUDA tensors, or a Batch); keeps the fastest."""
+        lib = _load()
+        b = sets if isinstance(sets, Batch) else Batch(sets)
+        if (L is None) == (s is None):
+            raise ValueError("give exactly one of L or s")
+        p = Params(L if L is not None else -1, s if s is not None else 0, flags, 0)
+        best = Tuning()
+        ms = C.c_double()
+        st = lib.fmm_autotune(self._h, b.arr, b.k, p, trials, C.byref(best), C.byref(ms),
+                              C.c_void_p(self._stream(stream)))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_autotune")
+        return {"sort_kind": int(best.sort_kind), "sort_items": int(best.sort_items),
+                "median_ms": ms.value}
 
     def set_timing(self, on: bool):
         _load().fmm_set_timing(self._h, 1 if on else 0)

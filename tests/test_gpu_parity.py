@@ -303,3 +303,43 @@ def test_sorted_points_aliased_and_long_boxes(ctx, orc):
     w = orc.build_tree(p, p, L=3)
     compare_full(t, w, 3)
     assert np.array_equal(t["sorted_src"], orc.sorted_points(p, w["src"]["perm"]))
+
+
+@pytest.mark.parametrize("items", [4, 8])
+def test_sort_tile_sizes_agree(ctx, orc, items):
+    """The tile-size knob (points per thread of a radix tile) changes no result."""
+    from paper_1301_1704_gb300 import fmmds
+    src = workloads.clumps(100003, 95, nclumps=10, sigma=0.03)
+    recv = workloads.uniform(70001, 96)
+    try:
+        for kind in (fmmds.FMM_SORT_RTS, fmmds.FMM_SORT_FIXED_GRID):
+            ctx.set_tuning(kind, items)
+            assert ctx.tuning() == {"sort_kind": kind, "sort_items": items}
+            got, want = run_both(ctx, orc, src, recv, 6)
+            compare_full(got, want, 6)
+        ctx.set_tuning(fmmds.FMM_SORT_RTS, items)
+        got = ctx.build(_dev(src), _dev(recv), s=40).numpy()
+        want = orc.build_tree(src, recv, L=-1, s=40)
+        compare_full(got, want, want["L"])
+    finally:
+        ctx.set_tuning(fmmds.FMM_SORT_RTS, 6)
+
+
+def test_autotune_picks_a_candidate(ctx, orc):
+    from paper_1301_1704_gb300 import fmmds
+    pts = [workloads.uniform(200000, 97), workloads.clumps(50000, 98, nclumps=4, sigma=0.02)]
+    devs = [_dev(p) for p in pts]
+    try:
+        best = ctx.autotune([(d, d) for d in devs], s=64, trials=2)
+        assert (best["sort_kind"], best["sort_items"]) in {
+            (0, 4), (0, 6), (0, 8), (1, 6), (2, 4), (2, 6), (2, 8)}
+        assert best["median_ms"] > 0
+        assert ctx.tuning() == {"sort_kind": best["sort_kind"], "sort_items": best["sort_items"]}
+        trees = ctx.build_batched([(d, d) for d in devs], s=64)
+        for p, t in zip(pts, trees):
+            want = orc.build_tree(p, p, L=-1, s=64)
+            compare_full(t.numpy(), want, want["L"])
+    finally:
+        ctx.set_tuning(fmmds.FMM_SORT_RTS, 6)
+    with pytest.raises(fmmds.FmmError):
+        ctx.set_tuning(fmmds.FMM_SORT_RTS, 5)
