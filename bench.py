@@ -423,6 +423,8 @@ def main():
                     help="0 radix reduce-then-scan, 1 radix onesweep, 2 Fixed-Grid (else autotuned)")
     ap.add_argument("--sort-items", type=int, default=0, help="points per thread of a sort tile")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the comparison of the sort kinds")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="steps of the per-instance comparison of the batched workload")
@@ -558,7 +560,7 @@ def main():
     # The same build with each way of ordering the points (radix passes in
     # reduce-then-scan or onesweep form, the paper's Fixed-Grid pseudo-sort).
     sort_kinds = {}
-    if (npts, level) == (N_PTS, LEVEL):
+    if (npts, level) == (N_PTS, LEVEL) and not args.no_compare:
         base = ctx.tuning()
         for kind, name in ((fmmds.FMM_SORT_RTS, "radix_rts"), (fmmds.FMM_SORT_ONESWEEP, "radix_onesweep"),
                            (fmmds.FMM_SORT_FIXED_GRID, "fixed_grid")):

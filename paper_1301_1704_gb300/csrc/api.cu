@@ -836,9 +836,11 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     launch_sorted_xyz(m.segs, m.fin_slots, (uint32_t)fin.size(), m.fin_units, c->st, s);
   }
   if (m.crs_units) {
+    int max_lb = 0;
+    for (auto& sp : sets) max_lb = std::max(max_lb, sp.Lb);
     Launch L(c, "coarse_boxes");
-    launch_coarse_boxes(m.segs, m.crs_slots, (uint32_t)crs.size(), m.crs_units, c->st, wait_ns,
-                        s);
+    launch_coarse_boxes(m.segs, m.crs_slots, (uint32_t)crs.size(), m.crs_units, max_lb, c->st,
+                        wait_ns, s);
   }
   if (m.occ_units) {
     Launch L(c, "occupancy");

@@ -237,6 +237,9 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __
 // boxes: box b opens a level-l box exactly when its key differs from box
 // b-1's in the level-l prefix.  A multi-level prefix sum over the boxes (one
 // decoupled look-back chain per level) gives each start its rank.
+// NL: a bound on the sets' box depths (Lb <= NL), so that the per-level
+// loops, unrolled, cover only the levels in use.
+template <int NL>
 __global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(const Seg* __restrict__ segs,
                                                                    const Slot* __restrict__ slots,
                                                                    uint32_t nslots, DevStatus* st,
@@ -279,9 +282,9 @@ __global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(const Seg* __
     const int64_t b = t0 + j;
     dd[k] = b >= (int64_t)nb ? 0xffu : (b == 0 ? 0u : first_diff_level(s_key[j + 1], s_key[j]));
   }
-  uint32_t lex[kLevels];
+  uint32_t lex[NL];
 #pragma unroll
-  for (int l = 0; l < kLevels; ++l) {
+  for (int l = 0; l < NL; ++l) {
     lex[l] = 0;
     if (l < Lb) {
       uint32_t c = 0;
@@ -329,9 +332,9 @@ __global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(const Seg* __
       if (c <= lv.cap[l]) lv.child[l][c] = l + 1 < Lb ? s_texcl[l + 1] + s_ttot[l + 1] : nb;
     }
   }
-  uint32_t run[kLevels];
+  uint32_t run[NL];
 #pragma unroll
-  for (int l = 0; l < kLevels; ++l) run[l] = (l < Lb) ? s_texcl[l] + s_wtot[warp][l] + lex[l] : 0u;
+  for (int l = 0; l < NL; ++l) run[l] = (l < Lb) ? s_texcl[l] + s_wtot[warp][l] + lex[l] : 0u;
 #pragma unroll
   for (int k = 0; k < kBoxItems; ++k) {
     const int j = threadIdx.x * kBoxItems + k;
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(const Seg* __
     if (Lb >= 1) {
       uint32_t pr = 0;
 #pragma unroll
-      for (int l = 0; l < kLevels; ++l)
+      for (int l = 0; l < NL; ++l)
         if (l == Lb - 1) pr = dk <= (uint32_t)l ? run[l] : run[l] - 1u;
       lv.parent[Lb][b] = pr;
       if (dk <= (uint32_t)(Lb - 1) && pr < lv.cap[Lb - 1]) lv.child[Lb - 1][pr] = (uint32_t)b;
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(const Seg* __
     if (dk < (uint32_t)Lb) {
       const uint32_t off = lv.off[Lb][b];
 #pragma unroll
-      for (int l = 0; l < kLevels; ++l) {
+      for (int l = 0; l < NL; ++l) {
         if (l < Lb && (uint32_t)l >= dk && run[l] < lv.cap[l]) {
           const uint32_t rk = run[l];
           lv.key[l][rk] = l == 0 ? 0ull : key >> (63 - 3 * l);
@@ -365,7 +368,7 @@ __global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(const Seg* __
       }
     }
 #pragma unroll
-    for (int l = 0; l < kLevels; ++l)
+    for (int l = 0; l < NL; ++l)
       if (l < Lb && (uint32_t)l >= dk) ++run[l];
   }
 }
@@ -389,9 +392,16 @@ void launch_finish_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, ui
 }
 
 void launch_coarse_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
-                         DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
+                         int max_lb, DevStatus* st, uint64_t wait_ns, cudaStream_t s) {
   if (units == 0) return;
-  coarse_boxes_kernel<<<units, kBoxThreads, 0, s>>>(segs, slots, nslots, st, wait_ns);
+  if (max_lb <= 8)
+    coarse_boxes_kernel<8><<<units, kBoxThreads, 0, s>>>(segs, slots, nslots, st, wait_ns);
+  else if (max_lb <= 12)
+    coarse_boxes_kernel<12><<<units, kBoxThreads, 0, s>>>(segs, slots, nslots, st, wait_ns);
+  else if (max_lb <= 16)
+    coarse_boxes_kernel<16><<<units, kBoxThreads, 0, s>>>(segs, slots, nslots, st, wait_ns);
+  else
+    coarse_boxes_kernel<kLevels><<<units, kBoxThreads, 0, s>>>(segs, slots, nslots, st, wait_ns);
 }
 
 // ---------------------------------------------------------------------------

@@ -428,7 +428,7 @@ void launch_finish_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, ui
 // Levels 0..Lb-1, parents of level Lb, children of level Lb-1 (units =
 // coarse tiles by capacity).
 void launch_coarse_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
-                         DevStatus* st, uint64_t wait_ns, cudaStream_t s);
+                         int max_lb, DevStatus* st, uint64_t wait_ns, cudaStream_t s);
 // Child-occupancy bytes (sets flagged in `which`, grid y = set) and largest
 // occupancy per level.
 // Sorted points (xyz[perm[j]]) of the sets with `sorted` set; units: finishing tiles.
