@@ -804,6 +804,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
       LV.total = reinterpret_cast<uint64_t*>(z);
       LV.idx2 = arena_get<uint32_t>(c, i2[l], &err);
       LV.idx4 = arena_get<uint32_t>(c, i4[l], &err);
+      LV.code2 = l < Lmax ? arena_get<uint8_t>(c, i2[l], &err) : nullptr;
       LV.jprefix = arena_get<uint32_t>(c, (size_t)njobs + 1, &err);
       for (auto& jp : jobs) {
         if (jp.L < l) continue;
@@ -925,7 +926,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     }
     {
       Launch Lk(c, "list_fill");
-      launch_list_fill(m.segs, m.jobs, njobs, l, m.lvls, c->st, s);
+      launch_list_fill(m.segs, m.jobs, njobs, l, m.lvls, lvls[l].code2 != nullptr, c->st, s);
     }
   }
   FMM_CUDA(cudaGetLastError());

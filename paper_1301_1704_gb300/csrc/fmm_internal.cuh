@@ -356,6 +356,8 @@ struct ListLevel {
   uint32_t* work4;
   uint32_t* idx2;    // list entries (all jobs)
   uint32_t* idx4;
+  uint8_t* code2;    // per E2 entry: (dx+1) + 3(dy+1) + 9(dz+1), the source box's offset
+                     // from the receiver box; for the next level (null at the last one)
   uint32_t* jprefix; // [njobs + 1] parents (receiver boxes at l-1) before each job
   uint64_t* base;    // [njobs][2] first E2 / E4 entry of each job
   uint64_t* nnz;     // [njobs][2] E2 / E4 entries of each job
@@ -484,7 +486,7 @@ void launch_job_prefix(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
 void launch_list_count(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
                        const ListLevel* lvls, DevStatus* st, cudaStream_t s);
 void launch_list_fill(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
-                      const ListLevel* lvls, DevStatus* st, cudaStream_t s);
+                      const ListLevel* lvls, bool codes, DevStatus* st, cudaStream_t s);
 
 // Morton keys of n points (public fmm_morton_keys).
 void launch_keys(const float* xyz, uint32_t n, uint64_t* keys, DevStatus* st, cudaStream_t s);

@@ -63,6 +63,7 @@ struct ListCtx {
   const uint64_t* rkey;        // receiver keys, level l
   const uint32_t* e2_off_up;   // the job's E2 row starts, level l-1 (rebased)
   const uint32_t* e2_idx_up;   // the job's E2 entries, level l-1
+  const uint8_t* e2_code_up;   // ... and their offset codes (see list_fill), or null
   const uint64_t* skey_up;     // source keys, level l-1
   const uint32_t* schild_up;   // source children, level l-1
   const uint8_t* socc_up;      // source child occupancy, level l-1
@@ -82,6 +83,8 @@ __device__ __forceinline__ ListCtx make_ctx(const Seg* segs, const Job& J, int l
   c.rkey = R.lv.key[l];
   c.e2_off_up = l >= 3 ? J.out2[l - 1] : nullptr;
   c.e2_idx_up = l >= 3 ? lvls[l - 1].idx2 + lvls[l - 1].base[2 * jidx] : nullptr;
+  c.e2_code_up = (l >= 3 && lvls[l - 1].code2) ? lvls[l - 1].code2 + lvls[l - 1].base[2 * jidx]
+                                               : nullptr;
   c.skey_up = S.lv.key[l - 1];
   c.schild_up = S.lv.child[l - 1];
   c.socc_up = S.lv.occ[l - 1];
@@ -110,11 +113,20 @@ __device__ __forceinline__ Neighbour load_neighbour(const ListCtx& a, int l, uin
   }
   if ((uint32_t)lane < m) {
     const uint32_t Q = (l == 2) ? (uint32_t)lane : a.e2_idx_up[first + lane];
-    const uint64_t pk = a.rkey_up[p];
-    const uint64_t qk = a.skey_up[Q];
-    q.dx = (int)compact3(qk) - (int)compact3(pk);
-    q.dy = (int)compact3(qk >> 1) - (int)compact3(pk >> 1);
-    q.dz = (int)compact3(qk >> 2) - (int)compact3(pk >> 2);
+    if (a.e2_code_up) {
+      // the offset of Q from p, written with the entry: (dx+1) + 3(dy+1) + 9(dz+1)
+      const uint32_t code = a.e2_code_up[first + lane];
+      const uint32_t z = code / 9u, rem = code - 9u * z, y = rem / 3u;
+      q.dx = (int)(rem - 3u * y) - 1;
+      q.dy = (int)y - 1;
+      q.dz = (int)z - 1;
+    } else {
+      const uint64_t pk = a.rkey_up[p];
+      const uint64_t qk = a.skey_up[Q];
+      q.dx = (int)compact3(qk) - (int)compact3(pk);
+      q.dy = (int)compact3(qk >> 1) - (int)compact3(pk >> 1);
+      q.dz = (int)compact3(qk >> 2) - (int)compact3(pk >> 2);
+    }
     q.occ = a.socc_up[Q];
     q.child = a.schild_up[Q];
   }
@@ -278,15 +290,19 @@ struct WarpJob {
   uint32_t j, jstart, jend;
 };
 
+// kCodes: also write the E2 entries' offset codes for the next level (every
+// level but the last).
+template <bool kCodes>
 __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* __restrict__ segs,
                                                                 const Job* __restrict__ jobs,
                                                                 uint32_t njobs, int l,
                                                                 const ListLevel* lvls,
                                                                 DevStatus* st) {
   __shared__ uint32_t s_rank[kListWarps][kCand];
-  __shared__ uint8_t s_sib[kListWarps][kCand];
+  // per candidate: its sibling byte, and above it (lane of its neighbour) * 8 + octant
+  __shared__ uint16_t s_sib[kListWarps][kCand];
   __shared__ uint32_t s_nrank[kListWarps][kNear];
-  __shared__ uint8_t s_nsib[kListWarps][kNear];
+  __shared__ uint16_t s_nsib[kListWarps][kNear];
   __shared__ WarpJob s_job[kListWarps];
   if (failed(st)) return;  // set before this launch: the same for every thread
   const ListLevel& LV = lvls[l];
@@ -303,9 +319,10 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   uint32_t* crank = s_rank[warp];
-  uint8_t* csib = s_sib[warp];
+  uint16_t* csib = s_sib[warp];
   uint32_t* nrank = s_nrank[warp];
-  uint8_t* nsibm = s_nsib[warp];
+  uint16_t* nsibm = s_nsib[warp];
+  uint8_t* const code2 = LV.code2;
   const uint32_t npar = jprefix[njobs];
   const BlockRange br = block_range(npar);
   // The warp's current job lives in shared memory, not in registers: the
@@ -357,6 +374,8 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
     }
     const Neighbour q = load_neighbour(J.a, l, p, lane);
     const uint32_t nsib = c1 - c0;
+    // this lane's neighbour's part of the position sum P (see the E2 loop)
+    const int pbase = (2 * q.dx + 1) + 3 * (2 * q.dy + 1) + 9 * (2 * q.dz + 1);
 
     // Candidates C (children of p's neighbours, ascending rank) and the near
     // candidates (those in some sibling's E2), each with its sibling byte.
@@ -371,11 +390,13 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
       const uint32_t my0 = axis_mask(-q.dy, 0u, 0x33u, 0xccu), my1 = axis_mask(-q.dy, 1u, 0x33u, 0xccu);
       const uint32_t mz0 = axis_mask(-q.dz, 0u, 0x0fu, 0xf0u), mz1 = axis_mask(-q.dz, 1u, 0x0fu, 0xf0u);
       uint32_t rank = q.child;
+      const uint32_t lane8 = (uint32_t)lane << 11;  // (lane * 8) << 8
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         if ((q.occ >> o) & 1u) {
           crank[e] = rank++;
-          csib[e] = (uint8_t)(((o & 1) ? mx1 : mx0) & ((o & 2) ? my1 : my0) & ((o & 4) ? mz1 : mz0));
+          csib[e] = (uint16_t)((((o & 1) ? mx1 : mx0) & ((o & 2) ? my1 : my0) & ((o & 4) ? mz1 : mz0)) |
+                               lane8 | ((uint32_t)o << 8));
           ++e;
         }
       }
@@ -384,12 +405,13 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
     uint32_t nnear = 0;
     for (uint32_t c = 0; c < total; c += 32) {
       const uint32_t i = c + lane;
-      const uint32_t sb = i < total ? csib[i] : 0u;
-      const uint32_t bn = __ballot_sync(0xffffffffu, sb != 0u);
-      if (sb) {
+      const uint32_t sb16 = i < total ? csib[i] : 0u;
+      const bool near = (sb16 & 0xffu) != 0u;
+      const uint32_t bn = __ballot_sync(0xffffffffu, near);
+      if (near) {
         const uint32_t k = nnear + __popc(bn & lt);
         nrank[k] = crank[i];
-        nsibm[k] = (uint8_t)sb;
+        nsibm[k] = (uint16_t)sb16;
       }
       nnear += __popc(bn);
     }
@@ -411,13 +433,30 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
       for (uint32_t c = 0; c < nnear; c += 32) {
         const uint32_t i = c + lane;
         const uint32_t v = i < nnear ? nrank[i] : 0u;
-        const uint32_t sb = i < nnear ? nsibm[i] : 0u;
+        const uint32_t sb16 = i < nnear ? nsibm[i] : 0u;
+        const uint32_t sb = sb16 & 0xffu;
+        // Position of the candidate, child o of the neighbour at delta, among
+        // the parent's children: p = 2 delta + o per axis; P = sum over axes of
+        // 3^axis (p + 1).  Minus the sibling's (rx + 3 ry + 9 rz) it is the
+        // entry's offset code (dx+1) + 3(dy+1) + 9(dz+1) from that sibling.
+        uint32_t P = 0;
+        if (kCodes) {
+          const uint32_t cq = sb16 >> 8, o = cq & 7u;
+          P = (uint32_t)__shfl_sync(0xffffffffu, pbase, (int)(cq >> 3)) + (o & 1u) +
+              3u * ((o >> 1) & 1u) + 9u * (o >> 2);
+        }
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) {
           if (kAll || (uint32_t)jj < nsib) {
             const uint32_t hit = sb & sbit[jj];
             const uint32_t b2 = __ballot_sync(0xffffffffu, hit != 0u);
-            st_cs_if(idx2 + w2[jj] + __popc(b2 & lt), v, hit);
+            const uint32_t at = w2[jj] + __popc(b2 & lt);
+            st_cs_if(idx2 + at, v, hit);
+            if (kCodes) {
+              const uint32_t rho = __ffs(sbit[jj]) - 1u;
+              const uint32_t R = (rho & 1u) + 3u * ((rho >> 1) & 1u) + 9u * (rho >> 2);
+              if (hit) code2[at] = (uint8_t)(P - R);
+            }
             w2[jj] += __popc(b2);
           }
         }
@@ -425,7 +464,7 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
       for (uint32_t c = 0; c < total; c += 32) {
         const uint32_t i = c + lane;
         const uint32_t v = i < total ? crank[i] : 0u;
-        const uint32_t sb = i < total ? csib[i] : 0xffu;  // past the end: never stored
+        const uint32_t sb = i < total ? (csib[i] & 0xffu) : 0xffu;  // past the end: never stored
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) {
           if (kAll || (uint32_t)jj < nsib) {
@@ -451,8 +490,11 @@ void launch_list_count(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
 }
 
 void launch_list_fill(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
-                      const ListLevel* lvls, DevStatus* st, cudaStream_t s) {
-  list_fill_kernel<<<152u * 8u, kListThreads, 0, s>>>(segs, jobs, njobs, l, lvls, st);
+                      const ListLevel* lvls, bool codes, DevStatus* st, cudaStream_t s) {
+  if (codes)
+    list_fill_kernel<true><<<152u * 8u, kListThreads, 0, s>>>(segs, jobs, njobs, l, lvls, st);
+  else
+    list_fill_kernel<false><<<152u * 8u, kListThreads, 0, s>>>(segs, jobs, njobs, l, lvls, st);
 }
 
 // ---------------------------------------------------------------------------
