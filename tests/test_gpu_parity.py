@@ -163,6 +163,18 @@ def test_host_input_flag(ctx, orc):
     hr = torch.from_numpy(recv).pin_memory()
     got = ctx.build(hs, hr, L=5, flags=fmmds.FMM_FLAG_HOST_INPUT).numpy()
     compare_full(got, orc.build_tree(src, recv, L=5), 5)
+    # pageable host memory too; and with the sorted points and onesweep passes
+    got = ctx.build(torch.from_numpy(src), torch.from_numpy(recv), L=5,
+                    flags=fmmds.FMM_FLAG_HOST_INPUT).numpy()
+    compare_full(got, orc.build_tree(src, recv, L=5), 5)
+    try:
+        ctx.set_tuning(fmmds.FMM_SORT_ONESWEEP)
+        t = ctx.build(hs, hr, L=5, flags=fmmds.FMM_FLAG_HOST_INPUT | fmmds.FMM_FLAG_SORTED_XYZ).numpy()
+        want = orc.build_tree(src, recv, L=5)
+        compare_full(t, want, 5)
+        assert np.array_equal(t["sorted_src"], orc.sorted_points(src, want["src"]["perm"]))
+    finally:
+        ctx.set_tuning(fmmds.FMM_SORT_RTS)
 
 
 @pytest.mark.parametrize("s", [1, 8, 64, 300])
