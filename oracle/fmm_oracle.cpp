@@ -119,18 +119,28 @@ struct Tree {
   std::vector<std::vector<uint32_t>> e2_off, e2_idx, e4_off, e4_idx;
 };
 
-// Keys of every point of one set, in input order.
+// Keys of every point of one set, in input order.  (Compiled with OpenMP,
+// the loop runs on all cores; the first error of any point is returned.)
 int make_keys(const float* xyz, uint32_t n, std::vector<uint64_t>* keys) {
   keys->assign(n, 0);
-  for (uint32_t i = 0; i < n; ++i) {
+  int err = ORC_OK;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+  for (int64_t i = 0; i < (int64_t)n; ++i) {
     uint32_t q[3];
-    for (int d = 0; d < 3; ++d) {
-      int st = quantize(xyz[3 * (size_t)i + d], &q[d]);
-      if (st != ORC_OK) return st;
+    int st = ORC_OK;
+    for (int d = 0; d < 3 && st == ORC_OK; ++d) st = quantize(xyz[3 * (size_t)i + d], &q[d]);
+    if (st != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+      err = st;
+      continue;
     }
     (*keys)[i] = interleave(q[0], q[1], q[2], kMaxLevel);
   }
-  return ORC_OK;
+  return err;
 }
 
 // Alg. 1, deterministic: ascending (key, original index).
@@ -284,19 +294,41 @@ void make_lists(Tree* t, int mode) {
   t->e4_idx.assign(L + 1, {});
   const Side& src = t->side[0];
   const Side& recv = t->side[1];
-  std::vector<uint32_t> e2, e4;
   for (int l = 2; l <= L; ++l) {
     t->e2_off[l].push_back(0);
     t->e4_off[l].push_back(0);
-    for (uint64_t rk : recv.key[l]) {
-      if (mode == 1)
-        brute_lists(view_of(src.key[l]), l, rk, &e2, &e4);
-      else
-        stencil_lists(view_of(src.key[l]), l, rk, &e2, &e4);
-      t->e2_idx[l].insert(t->e2_idx[l].end(), e2.begin(), e2.end());
-      t->e4_idx[l].insert(t->e4_idx[l].end(), e4.begin(), e4.end());
-      t->e2_off[l].push_back((uint32_t)t->e2_idx[l].size());
-      t->e4_off[l].push_back((uint32_t)t->e4_idx[l].size());
+    // Receiver boxes in blocks; each block's lists are appended in box order.
+    // (Compiled with OpenMP, the blocks of a round run on all cores.)
+    const std::vector<uint64_t>& rkeys = recv.key[l];
+    const int64_t nr = (int64_t)rkeys.size(), blk = 4096;
+    const int64_t nblk = (nr + blk - 1) / blk, round = 64;
+    for (int64_t b0 = 0; b0 < nblk; b0 += round) {
+      const int64_t b1 = std::min(nblk, b0 + round);
+      std::vector<std::vector<uint32_t>> e2b(b1 - b0), e4b(b1 - b0), c2b(b1 - b0), c4b(b1 - b0);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+      for (int64_t b = b0; b < b1; ++b) {
+        std::vector<uint32_t> e2, e4;
+        for (int64_t r = b * blk; r < std::min(nr, (b + 1) * blk); ++r) {
+          if (mode == 1)
+            brute_lists(view_of(src.key[l]), l, rkeys[r], &e2, &e4);
+          else
+            stencil_lists(view_of(src.key[l]), l, rkeys[r], &e2, &e4);
+          e2b[b - b0].insert(e2b[b - b0].end(), e2.begin(), e2.end());
+          e4b[b - b0].insert(e4b[b - b0].end(), e4.begin(), e4.end());
+          c2b[b - b0].push_back((uint32_t)e2.size());
+          c4b[b - b0].push_back((uint32_t)e4.size());
+        }
+      }
+      for (int64_t b = b0; b < b1; ++b) {
+        t->e2_idx[l].insert(t->e2_idx[l].end(), e2b[b - b0].begin(), e2b[b - b0].end());
+        t->e4_idx[l].insert(t->e4_idx[l].end(), e4b[b - b0].begin(), e4b[b - b0].end());
+        for (size_t k = 0; k < c2b[b - b0].size(); ++k) {
+          t->e2_off[l].push_back(t->e2_off[l].back() + c2b[b - b0][k]);
+          t->e4_off[l].push_back(t->e4_off[l].back() + c4b[b - b0][k]);
+        }
+      }
     }
   }
 }

@@ -34,22 +34,34 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle_fmm.so`` (plain -O2, one core)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+_LIB_OMP = os.path.join(_HERE, "liboracle_fmm_omp.so")
+_lib_omp = None
+
+
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle_fmm.so`` (plain -O2, one
+    core), or with ``parallel`` the same source with OpenMP and libstdc++'s
+    parallel mode (all cores: key loop, sort, per-box list blocks) into
+    ``oracle/liboracle_fmm_omp.so``.  Both compute the same result."""
+    lib = _LIB_OMP if parallel else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
         cxx = os.environ.get("CXX", "g++")
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call([cxx, "-std=c++17", "-O2", "-fPIC", "-shared", _SRC, "-o", tmp])
-        os.replace(tmp, _LIB)
-    return _LIB
+        tmp = lib + f".tmp{os.getpid()}"
+        extra = ["-fopenmp", "-D_GLIBCXX_PARALLEL"] if parallel else []
+        subprocess.check_call([cxx, "-std=c++17", "-O2", "-fPIC", "-shared", *extra, _SRC,
+                               "-o", tmp])
+        os.replace(tmp, lib)
+    return lib
 
 
-def _load():
-    global _lib
+def _load(parallel: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is not None:
+        if parallel and _lib_omp is not None:
+            return _lib_omp
+        if not parallel and _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        lib = C.CDLL(build(parallel=parallel))
         u32p, u64p, f32p = C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_float)
         lib.orc_keys.argtypes = [f32p, C.c_uint32, u64p]
         lib.orc_keys.restype = C.c_int
@@ -87,7 +99,10 @@ def _load():
         lib.orc_box_lists.argtypes = [u64p, C.c_uint32, C.c_int, C.c_uint64, C.c_int, u32p, u32p,
                                       u32p, u32p]
         lib.orc_box_lists.restype = C.c_int
-        _lib = lib
+        if parallel:
+            _lib_omp = lib
+        else:
+            _lib = lib
         return lib
 
 
@@ -125,7 +140,7 @@ def decode(key: int, bits: int = 21) -> tuple:
 
 
 def build_tree(src, recv, L: int = -1, s: int = 0, mode: int = MODE_STENCIL,
-               order: int = ORDER_KEY) -> dict:
+               order: int = ORDER_KEY, parallel: bool = False) -> dict:
     """The whole structure as a dict of numpy arrays.
 
     Keys: ``L``, ``s_unmet``; per side (``"src"``, ``"recv"``): ``perm``,
@@ -133,9 +148,10 @@ def build_tree(src, recv, L: int = -1, s: int = 0, mode: int = MODE_STENCIL,
     ``child[l]`` (l < L); lists: ``e2_off[l]``, ``e2_idx[l]``, ``e4_off[l]``,
     ``e4_idx[l]`` for l in 2..L (absent with ``mode=MODE_NOLISTS``).
     ``order=ORDER_BOX`` orders the points by (level-L key, index) instead of
-    (full key, index); only ``perm`` differs.
+    (full key, index); only ``perm`` differs.  ``parallel`` runs the OpenMP
+    build of the same source on all host cores.
     """
-    lib = _load()
+    lib = _load(parallel)
     a, b = _f32(src), _f32(recv)
     h = C.c_void_p()
     fp = C.POINTER(C.c_float)

@@ -168,3 +168,26 @@ def test_box_key_order_cluster_size(orc):
     assert box["L"] == full["L"]
     k = orc.keys(p) >> np.uint64(3 * (21 - box["L"]))
     assert np.array_equal(box["src"]["perm"], np.argsort(k, kind="stable"))
+
+
+def test_parallel_build_equals_serial(orc):
+    """The OpenMP build of the oracle (key loop, parallel sort, list blocks)
+    gives exactly the single-threaded result."""
+    from paper_1301_1704_gb300 import workloads
+    src = workloads.clumps(60000, 57, nclumps=8, sigma=0.03)
+    recv = workloads.uniform(50000, 58)
+    a = orc.build_tree(src, recv, L=5)
+    b = orc.build_tree(src, recv, L=5, parallel=True)
+    assert a["L"] == b["L"]
+    for side in ("src", "recv"):
+        assert np.array_equal(a[side]["perm"], b[side]["perm"])
+        for nm in ("key", "off", "parent", "child"):
+            for x, y in zip(a[side][nm], b[side][nm]):
+                assert np.array_equal(x, y)
+    for nm in ("e2_off", "e2_idx", "e4_off", "e4_idx"):
+        for l in a[nm]:
+            assert np.array_equal(a[nm][l], b[nm][l])
+    bad = src.copy()
+    bad[777, 1] = np.nan
+    with pytest.raises(orc.OracleError):
+        orc.build_tree(bad, recv, L=3, parallel=True)

@@ -34,7 +34,7 @@ def _rank(rank, world, port, out):
 
 def test_replica_timing_two_gloo_ranks():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a threaded test process
     out = mgr.dict()
     mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
     assert out[0] == out[1]
