@@ -187,10 +187,11 @@ def _traffic_for(kernel: str):
     return e.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(sub: int = 2) -> dict:
+def cpu_baseline(sub: int = 1) -> dict:
     """The oracle on the points of the workload that fall in the sub-cube
-    [0, 1/sub)^3 (same level, same density, 1/sub^3 of the work): its OpenMP
-    build on all host cores, and the plain build on one core."""
+    [0, 1/sub)^3 (same level, same density, 1/sub^3 of the work; the whole
+    workload by default, about 25 s on one core): its OpenMP build on all
+    host cores, and the plain build on one core."""
     from oracle import oracle
     from paper_1301_1704_gb300 import workloads
     src = workloads.uniform(N_PTS, SEEDS[0])
