@@ -525,12 +525,12 @@ def main():
     peak, peak_kind = _peaks()
     alg = _algorithmic_bytes(tree)
     def alg_of(name):
-        # A radix pass reads and writes 12 bytes per point: the coordinates,
-        # then (u64 key, u32 index).  rts_scatter sorts both sets in one launch
-        # per pass, onesweep one set per launch.
+        # A radix pass reads and writes (u64 key, u32 index) per point;
+        # rts_scatter sorts both sets in one launch per pass, onesweep one set
+        # per launch (and forms the keys from the coordinates in its pass 0).
         per_build = ktimes[name][0] / args.steps
-        if name == "rts_scatter":
-            return 24 * pts_per_step * per_build
+        if name == "rts_scatter":  # pass 0 reads the stored 8-byte keys: 20 bytes a point
+            return pts_per_step * (20 + 24 * (per_build - 1))
         if name == "onesweep":
             return 24 * pts_per_step * per_build / 2
         if name == "tile_hist":  # first pass reads the coordinates, later ones the keys
