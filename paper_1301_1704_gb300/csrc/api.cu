@@ -911,7 +911,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     uint64_t* st2 = reinterpret_cast<uint64_t*>(zs);
     uint64_t* st4 = reinterpret_cast<uint64_t*>(zs + sw);
     uint32_t* cnt = reinterpret_cast<uint32_t*>(zs + 2 * sw);
-    {
+    if (!job_prefix_in_count(njobs)) {
       Launch Lk(c, "job_prefix");
       launch_job_prefix(m.segs, m.jobs, njobs, l, m.lvls, c->st, s);
     }

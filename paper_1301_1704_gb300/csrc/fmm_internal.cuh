@@ -483,6 +483,9 @@ uint32_t scan_tiles(uint32_t cap);
 // are read).
 void launch_job_prefix(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
                        const ListLevel* lvls, DevStatus* st, cudaStream_t s);
+// Whether list_count computes the per-job prefix itself (small builds), so
+// that no job_prefix launch is needed.
+bool job_prefix_in_count(uint32_t njobs);
 void launch_list_count(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
                        const ListLevel* lvls, DevStatus* st, cudaStream_t s);
 void launch_list_fill(const Seg* segs, const Job* jobs, uint32_t njobs, int l,

@@ -26,6 +26,10 @@
 
 namespace fmm {
 
+constexpr int kListWarps = kListThreads / 32;
+// Builds of at most this many jobs get their per-job prefix inside list_count.
+constexpr uint32_t kLocalJobs = 1024;
+
 __device__ __forceinline__ uint32_t axis_mask(int delta, uint32_t rho_bit, uint32_t lo_oct,
                                               uint32_t hi_oct) {
   // lo_oct / hi_oct: octants with child bit 0 / 1 on this axis.
@@ -196,6 +200,8 @@ void launch_job_prefix(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
   job_prefix_kernel<<<1, 1024, 0, s>>>(segs, jobs, njobs, l, lvls, st);
 }
 
+bool job_prefix_in_count(uint32_t njobs) { return njobs <= kLocalJobs; }
+
 // Each block takes a contiguous run of the level's parents (over all jobs),
 // dealt round-robin to its warps: a warp changes jobs only where the run
 // crosses a job boundary, and the warps of a block work on neighbouring
@@ -210,6 +216,62 @@ __device__ __forceinline__ BlockRange block_range(uint32_t total) {
   return BlockRange{(uint32_t)(a < total ? a : total), (uint32_t)(b < total ? b : total)};
 }
 
+// Parents before each job at level l, computed by the whole block into s_jp
+// (njobs <= kLocalJobs; s_jp[kLocalJobs] = the level's total).  Block 0 also
+// publishes them in `jprefix_out` for the fill kernel and starts the rows of
+// jobs with no receiver box at level l, as job_prefix_kernel does for larger
+// builds.
+
+__device__ void block_job_prefix(const Seg* __restrict__ segs, const Job* __restrict__ jobs,
+                                 uint32_t njobs, int l, uint32_t* s_jp, uint32_t* s_wsum,
+                                 uint32_t* jprefix_out) {
+  constexpr int kPer = kLocalJobs / kListThreads;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t v[kPer], sum = 0;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const uint32_t j = threadIdx.x * kPer + k;
+    v[k] = 0;
+    if (j < njobs && jobs[j].L >= l) {
+      const Seg& R = segs[jobs[j].recv];
+      v[k] = R.nbox[l - 1];
+      if (blockIdx.x == 0 && R.nbox[l] == 0) {
+        jobs[j].out2[l][0] = 0;
+        jobs[j].out4[l][0] = 0;
+      }
+    }
+    sum += v[k];
+  }
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wsum[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < kListWarps; ++w) {
+      const uint32_t c = s_wsum[w];
+      s_wsum[w] = run;
+      run += c;
+    }
+    s_jp[kLocalJobs] = run;
+  }
+  __syncthreads();
+  uint32_t off = s_wsum[warp] + x - sum;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    s_jp[threadIdx.x * kPer + k] = off;
+    off += v[k];
+  }
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (uint32_t j = threadIdx.x; j <= njobs; j += blockDim.x)
+      jprefix_out[j] = j < kLocalJobs ? s_jp[j] : s_jp[kLocalJobs];
+}
+
 // Counts: per receiver child r of parent p, |E2(r)| = sum over the parent's
 // neighbours Q of popc(occ(Q) & mask(delta_Q, rho_r)), and |E2| + |E4| = the
 // number of non-empty children of all Q.  The eight possible sibling octants
@@ -219,14 +281,20 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(const Seg* __r
                                                                  uint32_t njobs, int l,
                                                                  const ListLevel* lvls,
                                                                  DevStatus* st) {
+  __shared__ uint32_t s_jp[kLocalJobs + 1];
+  __shared__ uint32_t s_wsum[kListWarps];
   if (failed(st)) return;  // set before this launch: the same for every thread
   const int lane = threadIdx.x & 31;
   // The level's arrays in registers: stores through them must not force
   // reloads of the descriptor.
-  const uint32_t* const jprefix = lvls[l].jprefix;
   uint32_t* const work2 = lvls[l].work2;
   uint32_t* const work4 = lvls[l].work4;
-  const uint32_t total = jprefix[njobs];
+  const uint32_t* jprefix = lvls[l].jprefix;
+  if (njobs <= kLocalJobs) {  // the per-job prefix here, not in its own launch
+    block_job_prefix(segs, jobs, njobs, l, s_jp, s_wsum, lvls[l].jprefix);
+    jprefix = s_jp;
+  }
+  const uint32_t total = njobs <= kLocalJobs ? s_jp[kLocalJobs] : jprefix[njobs];
   const BlockRange br = block_range(total);
   uint32_t j = 0, jstart = 0, jend = 0;
   ListCtx a{};
@@ -279,7 +347,6 @@ __global__ void __launch_bounds__(kListThreads) list_count_kernel(const Seg* __r
 // Row starts are written rebased to the job's own lists.
 constexpr int kCand = 27 * 8;  // at most 27 neighbours x 8 children
 constexpr int kNear = 64;      // candidates in some sibling's E2: the 4x4x4 block
-constexpr int kListWarps = kListThreads / 32;
 
 // A warp's current job in the fill kernel.
 struct WarpJob {

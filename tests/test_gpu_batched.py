@@ -115,3 +115,15 @@ def test_batched_workload_full_size_sampled(ctx, orc):
                     for nm in ("key", "off", "parent", "child"):
                         assert np.array_equal(got[side][nm][l], want[side][nm][l]), (i, side, nm, l)
             _sampled_lists(ctx, orc, got, want, L, per_level=100, seed=i)
+
+
+def test_batched_more_jobs_than_one_block_holds(ctx, orc):
+    """Above 1024 jobs the per-job parent prefix has its own launch; below,
+    the count kernel computes it: both routes against the oracle."""
+    rng = np.random.default_rng(23)
+    for k in (1000, 1100):
+        pts = [workloads.uniform(int(rng.integers(0, 60)), 5000 + i) for i in range(k)]
+        devs = [_dev(p) for p in pts]
+        trees = ctx.build_batched([(d, d) for d in devs], L=3)
+        for i in list(range(0, k, 97)) + [k - 1]:
+            compare_full(trees[i].numpy(), orc.build_tree(pts[i], pts[i], L=3), 3)
