@@ -297,6 +297,33 @@ int fmm_e2_source_offsets(fmm_ctx* ctx, const fmm_tree* tree, int level, uint32_
 int fmm_gather_e2_sources(fmm_ctx* ctx, const fmm_tree* tree, int level, const float* sorted_src,
                           const uint32_t* off, float* out, void* stream);
 
+/* ---- Alg. 6: source-box types for node J of a partition (Sec. 3.2).
+ *
+ * The space is split among nodes at level lpar (2..L): owner[b] is the node
+ * of source box b of that level (device, [nbox_src[lpar]]).  With the
+ * critical level lcrit = max(lpar - 1, 2), every source box of levels 2..L
+ * gets a type (types[l] device, [nbox_src[l]], caller-owned, for l = 2..L):
+ *   levels < lcrit: DOMESTIC;
+ *   lcrit: IMPORT if none of its descendants at lpar is owned by J, else ROOT
+ *          if some is not, else EXPORT if an M2L neighbour (E4 entry) has a
+ *          descendant at lpar not owned by J, else DOMESTIC;
+ *   deeper: a box "on J" (its ancestor at lpar owned by J) is EXPORT if an
+ *          M2L neighbour is not on J, else DOMESTIC; a box not on J is IMPORT
+ *          if an M2L neighbour is on J, else OTHERS.
+ * (Readings: ownership is read at lpar, and the IMPORT marks the printed
+ * algorithm sets from other boxes' threads are kept.)  The tree must be a
+ * build of the sources against themselves (the same array as src and recv,
+ * with lists), the last build of ctx.  Asynchronous on `stream`; scratch
+ * from the arena.  FMM_ERR_LEVEL for lpar outside 2..L, FMM_ERR_ARG for a
+ * tree that is not built against itself. */
+#define FMM_BOX_DOMESTIC 0
+#define FMM_BOX_EXPORT 1
+#define FMM_BOX_IMPORT 2
+#define FMM_BOX_ROOT 3
+#define FMM_BOX_OTHERS 4
+int fmm_box_types(fmm_ctx* ctx, const fmm_tree* tree, int lpar, const uint32_t* owner,
+                  uint32_t node, uint8_t* const* types, void* stream);
+
 /* ---- Served dynamic rebuilds ---------------------------------------------
  *
  * Dynamic problems rebuild the structure every time step (Sec. 1).  The

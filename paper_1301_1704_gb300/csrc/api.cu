@@ -1364,6 +1364,53 @@ int fmm_e2_source_offsets(fmm_ctx* c, const fmm_tree* t, int level, uint32_t* of
   return (*total >> 32) ? FMM_ERR_CAPACITY : FMM_OK;
 }
 
+int fmm_box_types(fmm_ctx* c, const fmm_tree* t, int lpar, const uint32_t* owner, uint32_t node,
+                  uint8_t* const* types, void* stream) {
+  if (!c || !t || !types) return FMM_ERR_ARG;
+  if (lpar < 2 || lpar > t->L) return FMM_ERR_LEVEL;
+  if (t->perm_src != t->perm_recv || (t->nbox_src[lpar] > 0 && !owner)) return FMM_ERR_ARG;
+  for (int l = 2; l <= t->L; ++l)
+    if (!types[l] && t->nbox_src[l] > 0) return FMM_ERR_ARG;
+  DeviceGuard g(c->device);
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaStream_t s = c->stream;
+  int err = FMM_OK;
+  const int L = t->L, lcrit = std::max(lpar - 1, 2);
+  std::vector<uint8_t*> on(kLevels, nullptr);
+  for (int l = lpar; l <= L; ++l) {
+    on[l] = arena_get<uint8_t>(c, t->nbox_src[l], &err);
+    if (err) return err;
+    Launch Lk(c, "box_types");
+    launch_on_node(l == lpar ? owner : nullptr, t->parent_src[l], on[l - 1], t->nbox_src[l], node,
+                   on[l], s);
+  }
+  uint8_t* sides = nullptr;
+  if (lcrit < lpar) {
+    sides = arena_get<uint8_t>(c, t->nbox_src[lcrit], &err);
+    if (err) return err;
+    Launch Lk(c, "box_types");
+    launch_child_sides(t->child_src[lcrit], on[lpar], t->nbox_src[lcrit], sides, s);
+  }
+  for (int l = 2; l <= L; ++l) {
+    Launch Lk(c, "box_types");
+    if (l < lcrit) {
+      launch_box_type(nullptr, nullptr, nullptr, nullptr, t->nbox_src[l], 0, types[l], s);
+    } else if (l == lcrit && lcrit < lpar) {
+      launch_box_type(t->e4_off[l], t->e4_idx[l], sides, nullptr, t->nbox_src[l], 1, types[l], s);
+    } else if (l == lcrit) {  // lcrit = lpar = 2: a box's own ownership decides
+      // its descendants at lpar are itself: bit 0 on J, bit 1 off J
+      uint8_t* sd = arena_get<uint8_t>(c, t->nbox_src[l], &err);
+      if (err) return err;
+      launch_child_sides(nullptr, on[l], t->nbox_src[l], sd, s);
+      launch_box_type(t->e4_off[l], t->e4_idx[l], sd, nullptr, t->nbox_src[l], 1, types[l], s);
+    } else {
+      launch_box_type(t->e4_off[l], t->e4_idx[l], nullptr, on[l], t->nbox_src[l], 2, types[l], s);
+    }
+  }
+  FMM_CUDA(cudaGetLastError());
+  return FMM_OK;
+}
+
 int fmm_gather_e2_sources(fmm_ctx* c, const fmm_tree* t, int level, const float* sorted_src,
                           const uint32_t* off, float* out, void* stream) {
   if (!c || !t || !off || (!sorted_src && t->n_src > 0)) return FMM_ERR_ARG;

@@ -453,6 +453,15 @@ void launch_fg_count(const Seg* segs, const Slot* slots, uint32_t nslots, uint32
 void launch_fg_move(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t ntiles,
                     const uint32_t* bins, const uint64_t* keys_in, const uint32_t* ranks_in,
                     uint64_t* keys_out, uint32_t* vals_out, DevStatus* st, cudaStream_t s);
+// Alg. 6 box types (box_types.cu): on-J flags of a level (from the owners
+// at lpar, or through the parents), the child sides of the lcrit boxes, and
+// the types of a level (mode 0: DOMESTIC; 1: lcrit; 2: deeper).
+void launch_on_node(const uint32_t* owner, const uint32_t* parent, const uint8_t* on_up,
+                    uint32_t nbox, uint32_t node, uint8_t* on, cudaStream_t s);
+void launch_child_sides(const uint32_t* child, const uint8_t* on_par, uint32_t nbox,
+                        uint8_t* sides, cudaStream_t s);
+void launch_box_type(const uint32_t* e4_off, const uint32_t* e4_idx, const uint8_t* sides,
+                     const uint8_t* on, uint32_t nbox, int mode, uint8_t* type, cudaStream_t s);
 // Child-occupancy bytes of the slots' sets (slot aux0 = the set's units).
 void launch_occupancy(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
                       DevStatus* st, cudaStream_t s);

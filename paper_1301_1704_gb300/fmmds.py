@@ -113,7 +113,7 @@ EXPORTS = (
     "fmm_query_workspace",
     "fmm_set_tuning", "fmm_get_tuning", "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing",
     "fmm_last_launch_count", "fmm_status_string", "fmm_exclusive_scan_noalloc",
-    "fmm_autotune", "fmm_e2_source_offsets", "fmm_gather_e2_sources",
+    "fmm_autotune", "fmm_e2_source_offsets", "fmm_gather_e2_sources", "fmm_box_types",
     "fmm_displace", "fmm_server_create", "fmm_server_destroy", "fmm_server_add_system",
     "fmm_server_submit", "fmm_server_wait", "fmm_server_run_trace", "fmm_server_points",
     "fmm_server_tree",
@@ -180,6 +180,9 @@ def _load():
     lib.fmm_autotune.argtypes = [C.c_void_p, C.POINTER(SetC), C.c_uint32, Params, C.c_uint32,
                                  C.POINTER(Tuning), C.POINTER(C.c_double), C.c_void_p]
     lib.fmm_autotune.restype = C.c_int
+    lib.fmm_box_types.argtypes = [C.c_void_p, C.POINTER(TreeC), C.c_int, C.c_void_p, C.c_uint32,
+                                  C.POINTER(C.c_void_p), C.c_void_p]
+    lib.fmm_box_types.restype = C.c_int
     lib.fmm_e2_source_offsets.argtypes = [C.c_void_p, C.POINTER(TreeC), C.c_int, C.c_void_p,
                                           _u64p, C.c_void_p]
     lib.fmm_e2_source_offsets.restype = C.c_int
@@ -412,6 +415,24 @@ class Context:
         if raw:
             return b.outs
         return [_tree_from(b.outs[i], b.sizes[i][0], b.sizes[i][1]) for i in range(b.k)]
+
+    def box_types(self, tree: "Tree", lpar: int, owner, node: int, stream=None) -> dict:
+        """fmm_box_types (Alg. 6): uint8 CUDA tensors per level 2..L of the
+        source boxes' types for `node`; `owner`: uint32-valued CUDA tensor of
+        the owners of the source boxes at level `lpar`.  The tree must come
+        from a build of the sources against themselves."""
+        import torch
+        types = {l: torch.empty(tree.src.nbox[l], dtype=torch.uint8, device="cuda")
+                 for l in range(2, tree.L + 1)}
+        arr = (C.c_void_p * FMM_LEVELS)()
+        for l, t in types.items():
+            arr[l] = t.data_ptr() if t.numel() else 0
+        st = _load().fmm_box_types(self._h, C.byref(tree.raw), lpar,
+                                   C.c_void_p(owner.data_ptr() if owner.numel() else 0), node, arr,
+                                   C.c_void_p(self._stream(stream)))
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_box_types")
+        return types
 
     def gather_e2(self, tree: "Tree", level: int, sorted_src=None, stream=None):
         """Alg. 2 for every receiver box of `level` (fmm_e2_source_offsets +

@@ -355,3 +355,26 @@ def test_autotune_picks_a_candidate(ctx, orc):
         ctx.set_tuning(fmmds.FMM_SORT_RTS, 6)
     with pytest.raises(fmmds.FmmError):
         ctx.set_tuning(fmmds.FMM_SORT_RTS, 5)
+
+
+# ---------------------------------------------------------------------------
+# Alg. 6 source-box types.
+
+@pytest.mark.parametrize("lpar", [2, 3, 4])
+def test_box_types_match_oracle(ctx, orc, lpar):
+    from oracle import box_types as BT
+    p = workloads.clumps(50000, 100 + lpar, nclumps=8, sigma=0.06)
+    L = 6
+    d = _dev(p)
+    tree = ctx.build(d, d, L=L)
+    want_tree = orc.build_tree(p, p, L=L)
+    compare_full(tree.numpy(), want_tree, L)
+    rng = np.random.default_rng(lpar)
+    nparts = 3
+    owner = rng.integers(0, nparts, size=tree.src.nbox[lpar]).astype(np.uint32)
+    od = torch.from_numpy(owner.view(np.int32)).cuda()
+    for node in range(nparts):
+        got = ctx.box_types(tree, lpar, od, node)
+        want = BT.box_types(want_tree, lpar, owner, node)
+        for l in range(2, L + 1):
+            assert np.array_equal(got[l].cpu().numpy(), want[l]), (lpar, node, l)
