@@ -275,8 +275,10 @@ __device__ void block_job_prefix(const Seg* __restrict__ segs, const Job* __rest
 // Counts: per receiver child r of parent p, |E2(r)| = sum over the parent's
 // neighbours Q of popc(occ(Q) & mask(delta_Q, rho_r)), and |E2| + |E4| = the
 // number of non-empty children of all Q.  The eight possible sibling octants
-// are counted at once: byte rho of a packed pair of words.
-__global__ void __launch_bounds__(kListThreads) list_count_kernel(const Seg* __restrict__ segs,
+// are counted at once: byte rho of a packed pair of words.  The kernel waits
+// on chains of dependent loads (row start, entry, occupancy): eight blocks an
+// SM keep more parents in flight.
+__global__ void __launch_bounds__(kListThreads, 8) list_count_kernel(const Seg* __restrict__ segs,
                                                                  const Job* __restrict__ jobs,
                                                                  uint32_t njobs, int l,
                                                                  const ListLevel* lvls,
@@ -606,11 +608,25 @@ __global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(ScanArray a0, Sc
   const uint64_t i0 = (uint64_t)tile * kScanTile + (uint64_t)threadIdx.x * kScanItems;
   uint32_t v[kScanItems];
   uint32_t sum = 0;
+  // A thread's items are consecutive: four 16-byte loads (and stores) when
+  // the array is 16-byte aligned and all of them are in range.
+  const bool vec = ((reinterpret_cast<uintptr_t>(data) & 15u) == 0) && i0 + kScanItems <= count;
+  if (vec) {
+    const uint4* p4 = reinterpret_cast<const uint4*>(data + i0);
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    v[k] = (i0 + k < count) ? data[i0 + k] : 0u;
-    sum += v[k];
+    for (int k = 0; k < kScanItems / 4; ++k) {
+      const uint4 q = p4[k];
+      v[4 * k] = q.x;
+      v[4 * k + 1] = q.y;
+      v[4 * k + 2] = q.z;
+      v[4 * k + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) v[k] = (i0 + k < count) ? data[i0 + k] : 0u;
   }
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) sum += v[k];
   uint32_t x = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -649,10 +665,27 @@ __global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(ScanArray a0, Sc
   }
   __syncthreads();
   uint64_t off = s_prev + s_wsum[warp] + (x - sum);
+  if (vec) {
+    uint4* p4 = reinterpret_cast<uint4*>(data + i0);
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    if (i0 + k < count) data[i0 + k] = (uint32_t)off;
-    off += v[k];
+    for (int k = 0; k < kScanItems / 4; ++k) {
+      uint4 q;
+      q.x = (uint32_t)off;
+      off += v[4 * k];
+      q.y = (uint32_t)off;
+      off += v[4 * k + 1];
+      q.z = (uint32_t)off;
+      off += v[4 * k + 2];
+      q.w = (uint32_t)off;
+      off += v[4 * k + 3];
+      p4[k] = q;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (i0 + k < count) data[i0 + k] = (uint32_t)off;
+      off += v[k];
+    }
   }
 }
 
