@@ -245,6 +245,24 @@ int fmm_reset_timing(fmm_ctx* ctx);
 /* Number of kernels launched by the last fmm_build on this context. */
 int fmm_last_launch_count(fmm_ctx* ctx, uint64_t* launches);
 
+/* Graph mode (off by default).  When enabled, every build on the context
+ * after its first one records its stream work into CUDA graphs: the work
+ * between two host synchronisations of the build (one at the end of a
+ * fixed-depth build; also one after the sort in cluster-size mode, and after
+ * a full-key re-sort) is captured, updates the executable graph kept for the
+ * same segment of the previous build -- or replaces it when the work changed
+ * shape -- and is launched as one graph.  A time-stepping caller that
+ * rebuilds from the same device buffers with new coordinates therefore
+ * launches a few graphs per build instead of some thirty kernels.  Results are
+ * identical to the eager build.  Builds with per-kernel timing, with
+ * FMM_FLAG_HOST_INPUT or with the stall test flag run eagerly.  Disabling
+ * frees the kept graphs.  Errors: FMM_ERR_ARG for a null context. */
+int fmm_set_graphs(fmm_ctx* ctx, int enable);
+
+/* Graphs launched and graphs instantiated (not just updated) by builds on
+ * this context since its creation. */
+int fmm_graph_stats(fmm_ctx* ctx, uint64_t* launches, uint64_t* instantiations);
+
 /* Exclusive prefix sum of n uint32 counts that allocates nothing.  The paper
  * has no counterpart: this serves callers that must not allocate device
  * memory while they run -- for example a time-stepping loop that reserved
@@ -401,9 +419,12 @@ int fmm_server_run_trace(fmm_server* srv, const double* arrival_s, const uint32_
 /* Copies a system's current points to host memory (xyz [n][3]); the system
  * must have no request queued or running (FMM_ERR_ARG otherwise). */
 int fmm_server_points(fmm_server* srv, uint32_t system, float* host_xyz);
-/* The system's latest tree (device arrays in a worker's arena): valid while
- * no request runs, until that worker's next build.  FMM_ERR_ARG if the system
- * has no result yet or has a request queued or running. */
+/* The system's latest tree: the served build's own output while the worker
+ * that built it has not taken another batch, else a rebuild of the same
+ * points on a context of the server's own (a build depends on the points and
+ * L alone).  The device arrays stay valid until the next request is submitted
+ * or the next fmm_server_tree call.  FMM_ERR_ARG if the system has no result
+ * yet or has a request queued or running. */
 int fmm_server_tree(fmm_server* srv, uint32_t system, fmm_tree* out);
 
 /* Static description of a status code. */

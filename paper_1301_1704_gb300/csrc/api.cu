@@ -11,6 +11,9 @@
 // The host synchronises once at the end, and also: in cluster-size mode after
 // the sort (to learn each set's depth) and after the full-key sort of the sets
 // that need one; when the list capacity bound is too large, after the boxes.
+// In graph mode (fmm_set_graphs) the stream work between two host
+// synchronisations is captured into a CUDA graph, which updates the
+// executable graph kept for that segment of the build and is launched.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -62,6 +65,19 @@ struct fmm_ctx {
   uint64_t launches = 0;
   uint64_t last_launches = 0;
   fmm_tuning tuning{FMM_SORT_RTS, 6};
+  // graph mode
+  bool graphs = false;         // capture builds (after the first) into CUDA graphs
+  bool warm = false;           // a build has run eagerly on this context
+  bool graph_build = false;    // the build in progress captures its stream work
+  bool capturing = false;      // the stream is being captured
+  uint32_t seg = 0;            // next segment of the build in progress
+  std::vector<cudaGraphExec_t> gexec;  // executable graph per segment
+  uint64_t graph_launches = 0, graph_instantiations = 0;
+  // The legacy default stream cannot be captured: graph builds called on it
+  // run on this stream, after an event that orders them behind the caller's
+  // earlier work.
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gevent = nullptr;
 };
 
 namespace {
@@ -73,13 +89,106 @@ constexpr uint64_t kAsyncListBytes = 16ull << 30;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
-void* raw_alloc(fmm_ctx* c, size_t bytes) {
-  if (c->alloc) return c->alloc(bytes, (void*)c->stream, c->user);
-  void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+// ---- graph mode: segments of a build's stream work.
+int cap_begin(fmm_ctx* c) {
+  if (!c->graph_build || c->capturing) return FMM_OK;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    c->graph_build = false;  // the rest of the build runs eagerly
+    return FMM_OK;
   }
+  c->capturing = true;
+  return FMM_OK;
+}
+
+// Ends the segment being captured, if any: its graph updates the executable
+// graph of the same segment of the previous build (or replaces it when the
+// shape changed) and is launched.
+int cap_end(fmm_ctx* c) {
+  if (!c->capturing) return FMM_OK;
+  c->capturing = false;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess || g == nullptr) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    return FMM_ERR_CUDA;
+  }
+  size_t nodes = 0;
+  int st = FMM_OK;
+  if (cudaGraphGetNodes(g, nullptr, &nodes) != cudaSuccess) {
+    cudaGetLastError();
+    st = FMM_ERR_CUDA;
+  } else if (nodes > 0) {
+    const uint32_t k = c->seg++;
+    if (c->gexec.size() <= k) c->gexec.resize(k + 1, nullptr);
+    cudaGraphExec_t& ex = c->gexec[k];
+    if (ex) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(ex, g, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(ex);
+        ex = nullptr;
+      }
+    }
+    if (!ex) {
+      if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        ex = nullptr;
+        st = FMM_ERR_CUDA;
+      } else {
+        ++c->graph_instantiations;
+      }
+    }
+    if (ex) {
+      if (cudaGraphLaunch(ex, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        st = FMM_ERR_CUDA;
+      } else {
+        ++c->graph_launches;
+      }
+    }
+  }
+  cudaGraphDestroy(g);
+  return st;
+}
+
+// Drops the segment being captured (a build that fails): its work never runs.
+void cap_abort(fmm_ctx* c) {
+  c->graph_build = false;
+  if (!c->capturing) return;
+  c->capturing = false;
+  cudaGraph_t g = nullptr;
+  cudaStreamEndCapture(c->stream, &g);
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+}
+
+// A host synchronisation inside a build: the segment captured so far is
+// launched first; capture resumes after it when `resume`.
+int build_sync(fmm_ctx* c, bool resume = true) {
+  const bool was = c->capturing;
+  const int st = cap_end(c);
+  if (st != FMM_OK) return st;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return FMM_ERR_CUDA;
+  }
+  if (was && resume) return cap_begin(c);
+  return FMM_OK;
+}
+
+void* raw_alloc(fmm_ctx* c, size_t bytes) {
+  // no allocation inside a captured segment: launch it, allocate, resume
+  const bool was = c->capturing;
+  if (was && cap_end(c) != FMM_OK) return nullptr;
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(bytes, (void*)c->stream, c->user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (was) cap_begin(c);
   return p;
 }
 
@@ -328,16 +437,15 @@ char* upload(fmm_ctx* c, const Upload& up, int* err) {
   if (*err) return nullptr;
   if (c->up_cursor + need > c->up_bytes) {
     // every earlier copy from the staging buffer must have landed
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
-      cudaGetLastError();
-      *err = FMM_ERR_CUDA;
-      return nullptr;
-    }
+    *err = build_sync(c, false);
+    if (*err) return nullptr;
     c->up_cursor = 0;
     if (need > c->up_bytes) {
       *err = pinned_reserve(&c->up_buf, &c->up_bytes, 2 * need);
       if (*err) return nullptr;
     }
+    *err = cap_begin(c);
+    if (*err) return nullptr;
   }
   char* h = static_cast<char*>(c->up_buf) + c->up_cursor;
   std::memcpy(h, up.bytes.data(), need);
@@ -633,12 +741,13 @@ int depth_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, const SortMem& m, uint32
                  c->st, s);
   }
   const size_t need = 64 + sizeof(uint32_t) * nsets;
-  FMM_CUDA(cudaStreamSynchronize(s));  // the read-back buffer may be replaced
+  FMM_TRY(build_sync(c, false));  // the read-back buffer may be replaced
   FMM_TRY(pinned_reserve(&c->rb_buf, &c->rb_bytes, need));
+  FMM_TRY(cap_begin(c));
   char* h = static_cast<char*>(c->rb_buf);
   FMM_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   FMM_CUDA(cudaMemcpyAsync(h + 64, dout, sizeof(uint32_t) * nsets, cudaMemcpyDeviceToHost, s));
-  FMM_CUDA(cudaStreamSynchronize(s));
+  FMM_TRY(build_sync(c));
   std::memcpy(st_out, h, sizeof(DevStatus));
   const uint32_t* hd = reinterpret_cast<const uint32_t*>(h + 64);
   for (size_t i = 0; i < nsets; ++i) sets[i]->depth = hd[i];
@@ -852,8 +961,9 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   auto read_sets = [&](bool lists) -> int {
     const size_t list_words = lists ? 4 * (size_t)njobs * kLevels : 0;
     const size_t need = 64 + sizeof(uint32_t) * nsets * per_set + 16 + sizeof(uint64_t) * list_words;
-    FMM_CUDA(cudaStreamSynchronize(s));  // the read-back buffer may be replaced
+    FMM_TRY(build_sync(c, false));  // the read-back buffer may be replaced
     FMM_TRY(pinned_reserve(&c->rb_buf, &c->rb_bytes, need));
+    FMM_TRY(cap_begin(c));
     char* h = static_cast<char*>(c->rb_buf);
     FMM_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     uint32_t* hn = reinterpret_cast<uint32_t*>(h + 64);
@@ -869,7 +979,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
         FMM_CUDA(cudaMemcpyAsync(hl + (size_t)l * njobs * 4 + 2 * njobs, lvls[l].nnz,
                                  sizeof(uint64_t) * 2 * njobs, cudaMemcpyDeviceToHost, s));
       }
-    FMM_CUDA(cudaStreamSynchronize(s));
+    FMM_TRY(build_sync(c));
     std::memcpy(&rb->st, h, sizeof(DevStatus));
     rb->nbox.assign((size_t)nsets * kLevels, 0);
     rb->seg_long.assign(nsets, 0);
@@ -969,7 +1079,7 @@ int full_sort_perms(fmm_ctx* c, std::vector<SetPlan>& sets, const std::vector<ui
       launch_sorted_xyz_one(d.perm, d.xyz, sub[k].n, d.sorted, s);
     }
   }
-  FMM_CUDA(cudaStreamSynchronize(s));
+  FMM_TRY(build_sync(c));
   return FMM_OK;
 }
 
@@ -1025,8 +1135,8 @@ struct PairIn {
 int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes);
 
 // The build of one or many (Src, Recv) pairs, outputs in outs[].
-int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params& prm,
-              fmm_tree* outs) {
+int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params& prm,
+                 fmm_tree* outs) {
   cudaStream_t s = c->stream;
   int err = FMM_OK;
   const bool stall = (prm.flags & FMM_FLAG_TEST_STALL) != 0;
@@ -1044,6 +1154,8 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
   }
   FMM_TRY(arena_reset(c, c->peak_request > expect ? c->peak_request : expect));
   c->up_cursor = 0;
+  c->seg = 0;
+  FMM_TRY(cap_begin(c));
   FMM_CUDA(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
 
   // Sets (the same array given as a pair's sources and receivers is one set)
@@ -1182,10 +1294,49 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
   FMM_TRY(full_sort_perms(c, sets, longs, prm));
 
   for (uint32_t j = 0; j < npairs; ++j) fill_tree(sets, jobs[j], rb, j, npairs, &outs[j]);
+  FMM_TRY(cap_end(c));  // nothing is left to capture after the last read-back
+  c->graph_build = false;
+  c->warm = true;
   size_t used = 0;
   for (size_t i = 0; i < c->chunks.size(); ++i) used += c->chunks[i].bytes;
   c->peak_request = std::max(c->peak_request, used);
   return FMM_OK;
+}
+
+// A build, in graph mode when the context asks for it: from the second build
+// of a context on (the first one grows the arena and the staging buffers),
+// and not with timing, the stall test or copies from the caller's host
+// memory.
+int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params& prm,
+              fmm_tree* outs) {
+  const uint32_t f = prm.flags;
+  c->graph_build = c->graphs && c->warm && !c->timing && !(f & FMM_FLAG_TEST_STALL) &&
+                   !(f & FMM_FLAG_HOST_INPUT);
+  const cudaStream_t caller = c->stream;
+  bool moved = false;
+  if (c->graph_build && (caller == nullptr || caller == cudaStreamLegacy)) {
+    if (!c->gstream &&
+        (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->gevent, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      if (c->gstream) cudaStreamDestroy(c->gstream);
+      c->gstream = nullptr;
+      c->graph_build = false;
+    }
+    if (c->graph_build) {
+      FMM_CUDA(cudaEventRecord(c->gevent, caller));
+      FMM_CUDA(cudaStreamWaitEvent(c->gstream, c->gevent, 0));
+      c->stream = c->gstream;
+      moved = true;
+    }
+  }
+  const int st = do_builds_on(c, pairs, npairs, prm, outs);
+  cap_abort(c);  // a build that failed inside a captured segment
+  if (moved) {
+    if (st != FMM_OK) cudaStreamSynchronize(c->stream);
+    c->stream = caller;
+  }
+  return st;
 }
 
 int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes) {
@@ -1229,6 +1380,7 @@ int check_params(const fmm_params& p) {
 }
 
 int finish_call(fmm_ctx* c, int st, uint64_t l0) {
+  cap_abort(c);  // a build that failed inside a captured segment
   if (st != FMM_OK) {
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
@@ -1280,6 +1432,10 @@ int fmm_destroy(fmm_ctx* c) {
     cudaEventDestroy(p.b);
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  for (auto ex : c->gexec)
+    if (ex) cudaGraphExecDestroy(ex);
+  if (c->gevent) cudaEventDestroy(c->gevent);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   cudaFree(c->st);
   if (c->up_buf) cudaFreeHost(c->up_buf);
   if (c->rb_buf) cudaFreeHost(c->rb_buf);
@@ -1540,6 +1696,25 @@ int fmm_get_timing(fmm_ctx* c, fmm_kernel_time* out, int max_entries, int* n_ent
 int fmm_last_launch_count(fmm_ctx* c, uint64_t* launches) {
   if (!c || !launches) return FMM_ERR_ARG;
   *launches = c->last_launches;
+  return FMM_OK;
+}
+
+int fmm_set_graphs(fmm_ctx* c, int enable) {
+  if (!c) return FMM_ERR_ARG;
+  DeviceGuard g(c->device);
+  c->graphs = enable != 0;
+  if (!c->graphs) {
+    for (auto& ex : c->gexec)
+      if (ex) cudaGraphExecDestroy(ex);
+    c->gexec.clear();
+  }
+  return FMM_OK;
+}
+
+int fmm_graph_stats(fmm_ctx* c, uint64_t* launches, uint64_t* instantiations) {
+  if (!c || !launches || !instantiations) return FMM_ERR_ARG;
+  *launches = c->graph_launches;
+  *instantiations = c->graph_instantiations;
   return FMM_OK;
 }
 

@@ -170,12 +170,15 @@ struct System {
   std::deque<uint64_t> queue;  // waiting request ids, arrival order
   fmm_tree last{};
   bool has_last = false;
+  uint32_t last_worker = 0;  // the worker whose arena holds `last` ...
+  uint64_t last_gen = 0;     // ... while its batch count is still this
 };
 
 struct Worker {
   fmm_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
   unsigned long long* digest = nullptr;  // device accumulators, one per batch slot
+  uint64_t gen = 0;                      // batches taken (each one reuses the arena)
   std::thread th;
 };
 
@@ -193,6 +196,9 @@ struct fmm_server {
   std::deque<fmm::System> systems;  // stable references: workers hold one outside the lock
   std::vector<std::unique_ptr<fmm::Request>> reqs;  // by id
   std::vector<fmm::Worker> workers;
+  // fmm_server_tree's rebuilds of systems whose worker has built again
+  fmm_ctx* qctx = nullptr;
+  cudaStream_t qstream = nullptr;
 };
 
 namespace fmm {
@@ -251,6 +257,7 @@ void worker_main(fmm_server* S, uint32_t w) {
       S->work_cv.wait(lk, [&] { return S->stop || any_ready(S); });
       if (!any_ready(S)) return;  // stopping, nothing left that this worker can take
       take_batch(S, &sys, &ids);
+      ++W.gen;  // the trees of this worker's previous batch are about to be overwritten
     }
     const uint32_t k = (uint32_t)sys.size();
     int st = FMM_OK;
@@ -290,6 +297,8 @@ void worker_main(fmm_server* S, uint32_t w) {
         y.busy = false;
         y.last = outs[j];
         y.has_last = st == FMM_OK;
+        y.last_worker = w;
+        y.last_gen = W.gen;
         inf.status = (uint32_t)st;
         inf.step = y.step;
         inf.t_done = t;
@@ -404,6 +413,8 @@ int fmm_server_destroy(fmm_server* S) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(S->device);
+  if (S->qctx) fmm_destroy(S->qctx);
+  if (S->qstream) cudaStreamDestroy(S->qstream);
   for (auto& W : S->workers) {
     if (W.stream) cudaStreamSynchronize(W.stream);
     if (W.ctx) fmm_destroy(W.ctx);
@@ -542,8 +553,31 @@ int fmm_server_tree(fmm_server* S, uint32_t system, fmm_tree* out) {
   if (system >= S->systems.size()) return FMM_ERR_ARG;
   const System& y = S->systems[system];
   if (!y.has_last || y.busy || !y.queue.empty()) return FMM_ERR_ARG;
-  *out = y.last;
-  return FMM_OK;
+  if (S->workers[y.last_worker].gen == y.last_gen) {
+    *out = y.last;  // still in the arena of the worker that built it
+    return FMM_OK;
+  }
+  // That worker has built another batch since: build the same points again
+  // (a build is a function of the points and L alone).
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(S->device);
+  int st = FMM_OK;
+  if (!S->qctx) {
+    st = fmm_create(&S->qctx, S->device, nullptr, nullptr, nullptr);
+    if (st == FMM_OK && cudaStreamCreateWithFlags(&S->qstream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      fmm_destroy(S->qctx);
+      S->qctx = nullptr;
+      st = FMM_ERR_CUDA;
+    }
+  }
+  if (st == FMM_OK) {
+    fmm_params p{y.L, 0, 0, 0};
+    st = fmm_build(S->qctx, y.xyz, y.n, y.xyz, y.n, p, out, S->qstream);
+  }
+  cudaSetDevice(prev);
+  return st;
 }
 
 }  // extern "C"

@@ -116,7 +116,7 @@ EXPORTS = (
     "fmm_autotune", "fmm_e2_source_offsets", "fmm_gather_e2_sources", "fmm_box_types",
     "fmm_displace", "fmm_server_create", "fmm_server_destroy", "fmm_server_add_system",
     "fmm_server_submit", "fmm_server_wait", "fmm_server_run_trace", "fmm_server_points",
-    "fmm_server_tree",
+    "fmm_server_tree", "fmm_set_graphs", "fmm_graph_stats",
 )
 FMM_NOALLOC_SCAN_MAX = 1 << 26
 
@@ -172,6 +172,10 @@ def _load():
     lib.fmm_get_timing.restype = C.c_int
     lib.fmm_last_launch_count.argtypes = [C.c_void_p, _u64p]
     lib.fmm_last_launch_count.restype = C.c_int
+    lib.fmm_set_graphs.argtypes = [C.c_void_p, C.c_int]
+    lib.fmm_set_graphs.restype = C.c_int
+    lib.fmm_graph_stats.argtypes = [C.c_void_p, _u64p, _u64p]
+    lib.fmm_graph_stats.restype = C.c_int
     lib.fmm_exclusive_scan_noalloc.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
                                                C.c_void_p]
     lib.fmm_exclusive_scan_noalloc.restype = C.c_int
@@ -522,6 +526,20 @@ class Context:
         v = C.c_uint64()
         _load().fmm_last_launch_count(self._h, C.byref(v))
         return int(v.value)
+
+    def set_graphs(self, on: bool):
+        """Graph mode: builds after the first record their stream work into
+        CUDA graphs that are updated and launched (see fmm_set_graphs)."""
+        st = _load().fmm_set_graphs(self._h, 1 if on else 0)
+        if st != 0:
+            raise FmmError(st, "fmm_set_graphs")
+
+    def graph_stats(self) -> dict:
+        a, b = C.c_uint64(), C.c_uint64()
+        st = _load().fmm_graph_stats(self._h, C.byref(a), C.byref(b))
+        if st != 0:
+            raise FmmError(st, "fmm_graph_stats")
+        return {"launches": int(a.value), "instantiations": int(b.value)}
 
 
 def exclusive_scan_noalloc(counts, offsets, total=None, stream=None) -> None:
