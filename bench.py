@@ -437,6 +437,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the comparison of the sort kinds")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-graphs", action="store_true", help="skip the graph-mode timings")
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="steps of the per-instance comparison of the batched workload")
     ap.add_argument("--serve-steps", type=int, default=1000,
@@ -512,6 +513,25 @@ def main():
     torch.cuda.synchronize()
     ctx.set_timing(False)
     ktimes = ctx.timing()
+
+    # Graph mode (fmm_set_graphs): the same builds with their stream work
+    # recorded into CUDA graphs that are updated and launched every build.
+    graphs = None
+    if not args.no_graphs:
+        ctx.set_graphs(True)
+        for _ in range(max(3, args.warmup)):
+            ctx.build(src, recv, L=level, stream=stream, raw=True)
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            starts[i].record(stream)
+            ctx.build(src, recv, L=level, stream=stream, raw=True)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        g_ms = sorted(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+        graphs = {"p50_ms": g_ms[len(g_ms) // 2], "p99_ms": g_ms[-1],
+                  "value": 2 * npts / (g_ms[len(g_ms) // 2] / 1e3) / 1e6, "unit": "Mpts/s",
+                  "steps": args.steps, "graph_stats": ctx.graph_stats()}
+        ctx.set_graphs(False)
     tree = ctx.build(src, recv, L=level, stream=stream)
     torch.cuda.synchronize()
     total_ms = max_over_ranks(total_ms, dist)
@@ -620,6 +640,8 @@ def main():
             line["cpu_baseline"] = cpu_baseline()
         if sort_kinds:
             line["p50_ms_by_sort_kind"] = sort_kinds
+        if graphs is not None:
+            line["graph_mode"] = graphs
         if batched is not None:
             line["batched"] = batched
         if served is not None:

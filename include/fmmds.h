@@ -245,18 +245,18 @@ int fmm_reset_timing(fmm_ctx* ctx);
 /* Number of kernels launched by the last fmm_build on this context. */
 int fmm_last_launch_count(fmm_ctx* ctx, uint64_t* launches);
 
-/* Graph mode (off by default).  When enabled, every build on the context
- * after its first one records its stream work into CUDA graphs: the work
- * between two host synchronisations of the build (one at the end of a
- * fixed-depth build; also one after the sort in cluster-size mode, and after
- * a full-key re-sort) is captured, updates the executable graph kept for the
- * same segment of the previous build -- or replaces it when the work changed
- * shape -- and is launched as one graph.  A time-stepping caller that
- * rebuilds from the same device buffers with new coordinates therefore
- * launches a few graphs per build instead of some thirty kernels.  Results are
- * identical to the eager build.  Builds with per-kernel timing, with
- * FMM_FLAG_HOST_INPUT or with the stall test flag run eagerly.  Disabling
- * frees the kept graphs.  Errors: FMM_ERR_ARG for a null context. */
+/* Graph mode (off by default).  When enabled, every fixed-depth build on the
+ * context after its first one records its launches up to its first host
+ * synchronisation -- sort, boxes and lists, everything but the read-back of
+ * the sizes (and the rare full-key re-sort of over-full boxes) -- into one
+ * CUDA graph, which updates the executable graph kept from the previous build
+ * (or replaces it when the work changed shape) and is launched.  A
+ * time-stepping caller that rebuilds from the same device buffers with new
+ * coordinates launches one graph per build instead of some thirty kernels.
+ * Results are identical to the eager build.  Cluster-size builds, builds with
+ * per-kernel timing, with FMM_FLAG_HOST_INPUT or with the stall test flag run
+ * eagerly.  Disabling frees the kept graph.  Errors: FMM_ERR_ARG for a null
+ * context. */
 int fmm_set_graphs(fmm_ctx* ctx, int enable);
 
 /* Graphs launched and graphs instantiated (not just updated) by builds on

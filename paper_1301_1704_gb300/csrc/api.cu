@@ -11,9 +11,9 @@
 // The host synchronises once at the end, and also: in cluster-size mode after
 // the sort (to learn each set's depth) and after the full-key sort of the sets
 // that need one; when the list capacity bound is too large, after the boxes.
-// In graph mode (fmm_set_graphs) the stream work between two host
-// synchronisations is captured into a CUDA graph, which updates the
-// executable graph kept for that segment of the build and is launched.
+// In graph mode (fmm_set_graphs) the launches of a fixed-depth build up to its
+// first host synchronisation are captured into a CUDA graph, which updates
+// the executable graph kept from the previous build and is launched.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -164,23 +164,27 @@ void cap_abort(fmm_ctx* c) {
 }
 
 // A host synchronisation inside a build: the segment captured so far is
-// launched first; capture resumes after it when `resume`.
-int build_sync(fmm_ctx* c, bool resume = true) {
-  const bool was = c->capturing;
+// launched first.  What follows the first one (read-backs, the rare re-sorts)
+// runs eagerly.
+int build_sync(fmm_ctx* c) {
   const int st = cap_end(c);
+  c->graph_build = false;
   if (st != FMM_OK) return st;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
     cudaGetLastError();
     return FMM_ERR_CUDA;
   }
-  if (was && resume) return cap_begin(c);
   return FMM_OK;
 }
 
 void* raw_alloc(fmm_ctx* c, size_t bytes) {
-  // no allocation inside a captured segment: launch it, allocate, resume
-  const bool was = c->capturing;
-  if (was && cap_end(c) != FMM_OK) return nullptr;
+  // no allocation inside a captured segment: it is launched first, and the
+  // rest of the build runs eagerly
+  if (c->capturing) {
+    const int st = cap_end(c);
+    c->graph_build = false;
+    if (st != FMM_OK) return nullptr;
+  }
   void* p = nullptr;
   if (c->alloc) {
     p = c->alloc(bytes, (void*)c->stream, c->user);
@@ -188,7 +192,6 @@ void* raw_alloc(fmm_ctx* c, size_t bytes) {
     cudaGetLastError();
     p = nullptr;
   }
-  if (was) cap_begin(c);
   return p;
 }
 
@@ -437,15 +440,13 @@ char* upload(fmm_ctx* c, const Upload& up, int* err) {
   if (*err) return nullptr;
   if (c->up_cursor + need > c->up_bytes) {
     // every earlier copy from the staging buffer must have landed
-    *err = build_sync(c, false);
+    *err = build_sync(c);
     if (*err) return nullptr;
     c->up_cursor = 0;
     if (need > c->up_bytes) {
       *err = pinned_reserve(&c->up_buf, &c->up_bytes, 2 * need);
       if (*err) return nullptr;
     }
-    *err = cap_begin(c);
-    if (*err) return nullptr;
   }
   char* h = static_cast<char*>(c->up_buf) + c->up_cursor;
   std::memcpy(h, up.bytes.data(), need);
@@ -741,9 +742,8 @@ int depth_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, const SortMem& m, uint32
                  c->st, s);
   }
   const size_t need = 64 + sizeof(uint32_t) * nsets;
-  FMM_TRY(build_sync(c, false));  // the read-back buffer may be replaced
+  FMM_TRY(build_sync(c));  // the read-back buffer may be replaced
   FMM_TRY(pinned_reserve(&c->rb_buf, &c->rb_bytes, need));
-  FMM_TRY(cap_begin(c));
   char* h = static_cast<char*>(c->rb_buf);
   FMM_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   FMM_CUDA(cudaMemcpyAsync(h + 64, dout, sizeof(uint32_t) * nsets, cudaMemcpyDeviceToHost, s));
@@ -961,9 +961,8 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   auto read_sets = [&](bool lists) -> int {
     const size_t list_words = lists ? 4 * (size_t)njobs * kLevels : 0;
     const size_t need = 64 + sizeof(uint32_t) * nsets * per_set + 16 + sizeof(uint64_t) * list_words;
-    FMM_TRY(build_sync(c, false));  // the read-back buffer may be replaced
+    FMM_TRY(build_sync(c));  // the read-back buffer may be replaced
     FMM_TRY(pinned_reserve(&c->rb_buf, &c->rb_bytes, need));
-    FMM_TRY(cap_begin(c));
     char* h = static_cast<char*>(c->rb_buf);
     FMM_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     uint32_t* hn = reinterpret_cast<uint32_t*>(h + 64);
@@ -1303,15 +1302,19 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   return FMM_OK;
 }
 
-// A build, in graph mode when the context asks for it: from the second build
-// of a context on (the first one grows the arena and the staging buffers),
-// and not with timing, the stall test or copies from the caller's host
-// memory.
+// A build, in graph mode when the context asks for it: a fixed-depth build
+// (no cluster-size job), from the second build of a context on (the first
+// one grows the arena and the staging buffers), and not with timing, the
+// stall test or copies from the caller's host memory.  Its launches up to the
+// first host synchronisation -- the whole build but the read-back, unless
+// the list capacity is too large to reserve up front -- are one graph.
 int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params& prm,
               fmm_tree* outs) {
   const uint32_t f = prm.flags;
-  c->graph_build = c->graphs && c->warm && !c->timing && !(f & FMM_FLAG_TEST_STALL) &&
-                   !(f & FMM_FLAG_HOST_INPUT);
+  bool fixed = true;
+  for (uint32_t k = 0; k < npairs; ++k) fixed &= (pairs[k].L >= 0 ? pairs[k].L : prm.L) >= 0;
+  c->graph_build = c->graphs && c->warm && fixed && !c->timing &&
+                   !(f & FMM_FLAG_TEST_STALL) && !(f & FMM_FLAG_HOST_INPUT);
   const cudaStream_t caller = c->stream;
   bool moved = false;
   if (c->graph_build && (caller == nullptr || caller == cudaStreamLegacy)) {

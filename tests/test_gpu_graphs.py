@@ -1,9 +1,9 @@
-"""Graph mode (fmm_set_graphs): builds after a context's first one record
-their stream work into CUDA graphs that are updated and launched.  Every
-result must equal the oracle's, bit for bit, including time steps that
+"""Graph mode (fmm_set_graphs): fixed-depth builds after a context's first
+one record their launches into a CUDA graph that is updated and launched.
+Every result must equal the oracle's, bit for bit, including time steps that
 rebuild from the same device buffers with new coordinates, changes of shape,
-the cluster-size mode (a host read-back between two captured segments), the
-full-key re-sort of long boxes, and a failing build in the middle."""
+batched builds, cluster-size builds (which run eagerly), the full-key re-sort
+of long boxes after the graph, and a failing build in the middle."""
 import numpy as np
 import pytest
 
@@ -65,7 +65,7 @@ def test_shape_changes_and_batched_fixed_levels(gctx, orc):
             compare_full(t.numpy(), orc.build_tree(p, p, L=L), L)
 
 
-def test_cluster_size_mode_between_segments(gctx, orc):
+def test_cluster_size_builds_run_eagerly(gctx, orc):
     sets = [workloads.clumps(25000, 601, nclumps=6, sigma=0.02), workloads.uniform(9000, 602)]
     devs = [_dev(p) for p in sets]
     for step in range(3):
@@ -73,7 +73,9 @@ def test_cluster_size_mode_between_segments(gctx, orc):
             for p, d in zip(sets, devs):
                 p[:] = np.clip(p + np.float32(1e-3) * step, 0.0, 1.0)
                 d.copy_(torch.from_numpy(p))
+        before = gctx.graph_stats()["launches"]
         trees = gctx.build_batched([(d, d) for d in devs], s=48)
+        assert gctx.graph_stats()["launches"] == before
         for p, t in zip(sets, trees):
             w = orc.build_tree(p, p, L=-1, s=48)
             assert t.L == w["L"]
