@@ -54,21 +54,31 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    INTERVAL_MS = 100
+
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def start(self):
+        """Starts sampling and returns once nvidia-smi delivers samples, so
+        that the timed region that follows is covered from its start."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
         except (FileNotFoundError, OSError):
             self.proc = None
+            return
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0:
+            time.sleep(0.01)
+        self.first = len(self.lines)  # samples from here on fall in the timed region
 
     def _read(self):
         for line in self.proc.stdout:
@@ -85,7 +95,9 @@ class ClockSampler:
         self._t.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # the samples taken during the timed region (else the last one before it)
+        during = self.lines[self.first:] or self.lines[-1:]
+        for ln in during:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -422,7 +434,7 @@ def served_section(ctx, steps: int) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -78,6 +78,9 @@ struct fmm_ctx {
   // earlier work.
   cudaStream_t gstream = nullptr;
   cudaEvent_t gevent = nullptr;
+  // host-input copies of a pipelined build (see do_builds_on)
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t cevent = nullptr;
 };
 
 namespace {
@@ -303,6 +306,41 @@ struct Launch {
   }
 };
 
+// Small transfers of a build done by the SMs, not the copy engines: on the
+// copy engines they would queue behind a large host copy of another set's
+// coordinates (a pipelined host-input build) and stall the stage they feed.
+__global__ void __launch_bounds__(256) zero_words_kernel(uint32_t* __restrict__ p, uint64_t words) {
+  const uint64_t n16 = words / 4;
+  uint4* q = reinterpret_cast<uint4*>(p);  // p is 16-byte aligned
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n16; i += stride)
+    q[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (blockIdx.x == 0 && threadIdx.x < words - 4 * n16) p[4 * n16 + threadIdx.x] = 0u;
+}
+
+__global__ void __launch_bounds__(256) copy_words_kernel(const uint32_t* __restrict__ src,
+                                                          uint32_t* __restrict__ dst,
+                                                          uint64_t words) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words; i += stride)
+    dst[i] = src[i];
+}
+
+uint32_t small_grid(uint64_t items) {
+  const uint64_t g = (items + 255) / 256;
+  return (uint32_t)(g == 0 ? 1 : (g > 152u * 4u ? 152u * 4u : g));
+}
+
+// Zeroes `bytes` (a multiple of 4) at p (16-byte aligned) on the build's stream.
+int dev_zero(fmm_ctx* c, void* p, size_t bytes) {
+  if (bytes == 0) return FMM_OK;
+  if (bytes % 4 != 0 || (reinterpret_cast<uintptr_t>(p) & 15) != 0) return FMM_ERR_ARG;
+  Launch L(c, "zero");
+  const uint64_t words = bytes / 4;
+  zero_words_kernel<<<small_grid(words / 4), 256, 0, c->stream>>>(static_cast<uint32_t*>(p), words);
+  return cudaGetLastError() == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
+}
+
 void collect_times(fmm_ctx* c) {
   for (auto& p : c->pending) {
     float ms = 0.f;
@@ -450,8 +488,21 @@ char* upload(fmm_ctx* c, const Upload& up, int* err) {
   }
   char* h = static_cast<char*>(c->up_buf) + c->up_cursor;
   std::memcpy(h, up.bytes.data(), need);
-  if (cudaMemcpyAsync(dev, h, need, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+  // the device reads the pinned staging buffer directly (see copy_words_kernel)
+  void* hd = nullptr;
+  if (cudaHostGetDevicePointer(&hd, h, 0) != cudaSuccess) {
     cudaGetLastError();
+    *err = FMM_ERR_CUDA;
+    return nullptr;
+  }
+  {
+    Launch L(c, "upload");
+    const uint64_t words = (need + 3) / 4;  // the staging buffer and the arena block hold the rounding
+    copy_words_kernel<<<small_grid(words), 256, 0, c->stream>>>(static_cast<const uint32_t*>(hd),
+                                                                 reinterpret_cast<uint32_t*>(dev),
+                                                                 words);
+  }
+  if (cudaGetLastError() != cudaSuccess) {
     *err = FMM_ERR_CUDA;
     return nullptr;
   }
@@ -517,7 +568,7 @@ int run_sort(fmm_ctx* c, std::vector<SetPlan*>& sets, SortMem& m, bool stall, ui
                         align_up(sizeof(uint32_t) * 16);
       char* z = arena_get<char>(c, zb, &err);
       if (err) return err;
-      FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
+      FMM_TRY(dev_zero(c, z, zb));
       uint32_t* hist = reinterpret_cast<uint32_t*>(z);
       uint64_t* sstatus =
           reinterpret_cast<uint64_t*>(z + align_up(sizeof(uint32_t) * 8 * kRadixMax));
@@ -616,7 +667,7 @@ int fixed_grid_sort(fmm_ctx* c, std::vector<SetPlan*>& sets, SortMem& m, uint64_
   m.pass_slots[0] = reinterpret_cast<Slot*>(dev + o_slots);
   m.pass_nslots[0] = (uint32_t)slots.size();
   m.pass_tiles[0] = tiles;
-  FMM_CUDA(cudaMemsetAsync(z, 0, zb, s));
+  FMM_TRY(dev_zero(c, z, zb));
   {
     Launch L(c, "fg_count");
     launch_fg_count(m.segs, m.pass_slots[0], m.pass_nslots[0], tiles, bins, m.kb, m.vb, c->st, s);
@@ -638,7 +689,6 @@ int fixed_grid_sort(fmm_ctx* c, std::vector<SetPlan*>& sets, SortMem& m, uint64_
 // keys (all 63 for full sets) into fresh concatenated arrays and points each
 // set's skeys / svals there.  Only the sort fields of the descriptors change.
 int sort_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, bool stall, uint64_t wait_ns, SortMem* out) {
-  cudaStream_t s = c->stream;
   int err = FMM_OK;
   SortMem& m = *out;
   m = SortMem{};
@@ -722,7 +772,7 @@ int sort_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, bool stall, uint64_t wait
   m.segs = reinterpret_cast<Seg*>(dev + o_segs);
   for (int p = 0; p < m.max_passes; ++p)
     m.pass_slots[p] = reinterpret_cast<Slot*>(dev + o_pass[p]);
-  FMM_CUDA(cudaMemsetAsync(zero, 0, zero_bytes, s));
+  FMM_TRY(dev_zero(c, zero, zero_bytes));
   return run_sort(c, sets, m, stall, wait_ns);
 }
 
@@ -735,7 +785,7 @@ int depth_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, const SortMem& m, uint32
   const size_t nsets = sets.size();
   uint32_t* dout = arena_get<uint32_t>(c, nsets, &err);
   if (err) return err;
-  FMM_CUDA(cudaMemsetAsync(dout, 0, sizeof(uint32_t) * nsets, s));
+  FMM_TRY(dev_zero(c, dout, sizeof(uint32_t) * nsets));
   {
     Launch L(c, "depth");
     launch_depth(m.segs, m.pass_slots[0], m.pass_nslots[0], m.pass_tiles[0], s_cluster, dout,
@@ -931,8 +981,8 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     FMM_TRY(plan_lists());
   }
   FMM_TRY(upload_all(async_lists));
-  FMM_CUDA(cudaMemsetAsync(zero, 0, zero_bytes, s));
-  if (async_lists && list_zero_bytes) FMM_CUDA(cudaMemsetAsync(list_zero, 0, list_zero_bytes, s));
+  FMM_TRY(dev_zero(c, zero, zero_bytes));
+  if (async_lists) FMM_TRY(dev_zero(c, list_zero, list_zero_bytes));
 
   // ---- boxes, occupancy.
   {
@@ -1010,7 +1060,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
       for (int l = 2; l <= jp.L; ++l) jp.cap[l] = rb->nbox[(size_t)jp.recv * kLevels + l];
     FMM_TRY(plan_lists());
     FMM_TRY(upload_all(true));
-    if (list_zero_bytes) FMM_CUDA(cudaMemsetAsync(list_zero, 0, list_zero_bytes, s));
+    FMM_TRY(dev_zero(c, list_zero, list_zero_bytes));
   }
 
   // ---- lists, levels 2..Lmax.
@@ -1155,7 +1205,7 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   c->up_cursor = 0;
   c->seg = 0;
   FMM_TRY(cap_begin(c));
-  FMM_CUDA(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
+  FMM_TRY(dev_zero(c, c->st, sizeof(DevStatus)));
 
   // Sets (the same array given as a pair's sources and receivers is one set)
   // and jobs.
@@ -1174,13 +1224,34 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
     jobs[k].recv = aliased ? jobs[k].src : add_set(pairs[k].recv, pairs[k].M);
     sets[jobs[k].src].need_occ = true;
   }
+  // Host input: the coordinates are copied to the arena.  A fixed-depth
+  // build of a few sets copies them one set at a time on a copy stream and
+  // sorts each set as soon as it has landed, so that the next set's copy runs
+  // under that sort; otherwise every copy precedes the build.
+  bool all_fixed = true;
+  for (uint32_t k = 0; k < npairs; ++k) all_fixed &= (pairs[k].L >= 0 ? pairs[k].L : prm.L) >= 0;
+  const bool pipelined = host_in && !stall && all_fixed && sets.size() >= 2 && sets.size() <= 4;
+  std::vector<const float*> host_xyz(sets.size(), nullptr);
+  if (pipelined && !c->cstream) {
+    if (cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->cevent, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return FMM_ERR_CUDA;
+    }
+  }
   if (host_in) {
-    for (auto& sp : sets) {
+    for (size_t i = 0; i < sets.size(); ++i) {
+      SetPlan& sp = sets[i];
       float* d = arena_get<float>(c, (size_t)sp.n * 3, &err);
       if (err) return err;
-      if (sp.n)
+      host_xyz[i] = sp.xyz;
+      if (sp.n && !pipelined)
         FMM_CUDA(cudaMemcpyAsync(d, sp.xyz, sizeof(float) * 3 * sp.n, cudaMemcpyHostToDevice, s));
       sp.xyz = d;
+    }
+    if (pipelined) {  // the copies start after the build stream's earlier work
+      FMM_CUDA(cudaEventRecord(c->cevent, s));
+      FMM_CUDA(cudaStreamWaitEvent(c->cstream, c->cevent, 0));
     }
   }
   std::vector<SetPlan*> all;
@@ -1219,7 +1290,23 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   }
   {
     SortMem sm;
-    FMM_TRY(sort_sets(c, all, stall, wait_ns, &sm));
+    if (pipelined) {
+      // set i's copy, then its sort behind an event; copy i+1 is issued after
+      // sort i's launches (a pageable copy holds the host meanwhile)
+      for (size_t i = 0; i < sets.size(); ++i) {
+        SetPlan& sp = sets[i];
+        if (sp.n)
+          FMM_CUDA(cudaMemcpyAsync(const_cast<float*>(sp.xyz), host_xyz[i],
+                                   sizeof(float) * 3 * sp.n, cudaMemcpyHostToDevice, c->cstream));
+        FMM_CUDA(cudaEventRecord(c->cevent, c->cstream));
+        FMM_CUDA(cudaStreamWaitEvent(s, c->cevent, 0));
+        std::vector<SetPlan*> one{&sp};
+        SortMem si;
+        FMM_TRY(sort_sets(c, one, false, wait_ns, &si));
+      }
+    } else {
+      FMM_TRY(sort_sets(c, all, stall, wait_ns, &sm));
+    }
     if (any_smode) {
       // Cluster-size mode (Sec. 2.1): the deepest level at which s + 1 sorted
       // points still share a box, per set; sets whose boxes are still too
@@ -1439,6 +1526,8 @@ int fmm_destroy(fmm_ctx* c) {
     if (ex) cudaGraphExecDestroy(ex);
   if (c->gevent) cudaEventDestroy(c->gevent);
   if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->cevent) cudaEventDestroy(c->cevent);
+  if (c->cstream) cudaStreamDestroy(c->cstream);
   cudaFree(c->st);
   if (c->up_buf) cudaFreeHost(c->up_buf);
   if (c->rb_buf) cudaFreeHost(c->rb_buf);
