@@ -207,10 +207,10 @@ int fmm_query_workspace(uint32_t N, uint32_t M, fmm_params params, uint64_t* byt
 #define FMM_SORT_RTS 0u
 #define FMM_SORT_ONESWEEP 1u
 #define FMM_SORT_FIXED_GRID 2u
-/* sort_items: points per thread of a radix tile (4, 6 or 8; 0 = 6): the tile
- * of the histogram, scatter, depth and Fixed-Grid kernels is 512 x sort_items
- * points.  Larger tiles mean fewer tiles and histogram entries but one
- * resident scatter block per SM instead of two at 8. */
+/* sort_items: points per thread of a radix tile (4, 6, 7 or 8; 0 = 6): the
+ * tile of the histogram, scatter, depth and Fixed-Grid kernels is 512 x
+ * sort_items points.  Larger tiles mean fewer tiles and histogram entries but
+ * one resident scatter block per SM instead of two at 8. */
 typedef struct fmm_tuning {
   uint32_t sort_kind;
   uint32_t sort_items;

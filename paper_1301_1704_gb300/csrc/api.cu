@@ -1318,13 +1318,20 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
       DevStatus st{};
       FMM_TRY(depth_sets(c, all, sm, prm.s, &st));
       if (st.code) return (int)st.code;
-      std::vector<SetPlan*> deep;
-      for (auto* sp : ss)
-        if (!sp->full && sp->depth > (uint32_t)sp->Ls) {
-          sp->full = true;
-          deep.push_back(sp);
-        }
-      if (!deep.empty()) {
+      // A set still too full at its sort depth is sorted three levels deeper
+      // (one or two more radix passes) and measured again; only if that is not
+      // deep enough either, on all key bits.
+      for (int round = 0; round < 2; ++round) {
+        std::vector<SetPlan*> deep;
+        for (auto* sp : ss)
+          if (!sp->full && sp->depth > (uint32_t)sp->Ls) {
+            if (round == 0 && sp->Ls + 3 < kMaxLevel)
+              sp->Ls += 3;
+            else
+              sp->full = true;
+            deep.push_back(sp);
+          }
+        if (deep.empty()) break;
         SortMem sd;
         FMM_TRY(sort_sets(c, deep, false, wait_ns, &sd));
         FMM_TRY(depth_sets(c, deep, sd, prm.s, &st));
@@ -1694,7 +1701,7 @@ int fmm_morton_keys(fmm_ctx* c, const float* xyz, uint32_t n, uint64_t* keys, vo
 int fmm_set_tuning(fmm_ctx* c, const fmm_tuning* t) {
   if (!c || !t || t->sort_kind > FMM_SORT_FIXED_GRID) return FMM_ERR_ARG;
   const uint32_t items = t->sort_items ? t->sort_items : 6;
-  if (items != 4 && items != 6 && items != 8) return FMM_ERR_ARG;
+  if (items != 4 && items != 6 && items != 7 && items != 8) return FMM_ERR_ARG;
   c->tuning = *t;
   c->tuning.sort_items = items;
   return FMM_OK;
@@ -1718,7 +1725,7 @@ int fmm_autotune(fmm_ctx* c, const fmm_set* sets, uint32_t nsets, fmm_params par
   double win_ms = 1e300;
   int st = FMM_OK;
   const uint32_t kinds[3] = {FMM_SORT_RTS, FMM_SORT_ONESWEEP, FMM_SORT_FIXED_GRID};
-  const uint32_t items[3] = {4, 6, 8};
+  const uint32_t items[4] = {4, 6, 7, 8};
   for (uint32_t kind : kinds) {
     for (uint32_t it : items) {
       if (kind == FMM_SORT_ONESWEEP && it != 6) continue;  // onesweep keeps its own tile

@@ -441,7 +441,7 @@ constexpr size_t scatter_smem() {
 }
 
 template <int ITEMS, bool kFirst, bool kStable>
-__global__ void __launch_bounds__(kSortThreads, ITEMS <= 6 ? 2 : 1) rts_scatter_kernel(
+__global__ void __launch_bounds__(kSortThreads, ITEMS <= 7 ? 2 : 1) rts_scatter_kernel(
     const TileRec* __restrict__ recs, uint32_t ntiles, const uint64_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ offsets, bool bulk,
@@ -665,7 +665,7 @@ void scatter_items(int pass, const TileRec* recs, uint32_t ntiles, const uint64_
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
     return v > 0 ? v : 152;
   }();
-  uint32_t grid = (uint32_t)sms * (ITEMS <= 6 ? 2u : 1u);  // persistent: the resident blocks
+  uint32_t grid = (uint32_t)sms * (ITEMS <= 7 ? 2u : 1u);  // persistent: the resident blocks
   if (grid > ntiles) grid = ntiles;
   if (pass == 0) {
     if (stable)
@@ -689,6 +689,9 @@ void launch_rts_scatter(int pass, uint32_t items, const TileRec* recs, uint32_t 
   if (ntiles == 0) return;
   if (items == 4)
     scatter_items<4>(pass, recs, ntiles, keys_in, vals_in, keys_out, vals_out, offsets, stable,
+                     bulk, st, wait_ns, s);
+  else if (items == 7)
+    scatter_items<7>(pass, recs, ntiles, keys_in, vals_in, keys_out, vals_out, offsets, stable,
                      bulk, st, wait_ns, s);
   else if (items == 8)
     scatter_items<8>(pass, recs, ntiles, keys_in, vals_in, keys_out, vals_out, offsets, stable,

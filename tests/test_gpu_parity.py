@@ -317,7 +317,7 @@ def test_sorted_points_aliased_and_long_boxes(ctx, orc):
     assert np.array_equal(t["sorted_src"], orc.sorted_points(p, w["src"]["perm"]))
 
 
-@pytest.mark.parametrize("items", [4, 8])
+@pytest.mark.parametrize("items", [4, 7, 8])
 def test_sort_tile_sizes_agree(ctx, orc, items):
     """The tile-size knob (points per thread of a radix tile) changes no result."""
     from paper_1301_1704_gb300 import fmmds
@@ -344,7 +344,7 @@ def test_autotune_picks_a_candidate(ctx, orc):
     try:
         best = ctx.autotune([(d, d) for d in devs], s=64, trials=2)
         assert (best["sort_kind"], best["sort_items"]) in {
-            (0, 4), (0, 6), (0, 8), (1, 6), (2, 4), (2, 6), (2, 8)}
+            (0, 4), (0, 6), (0, 7), (0, 8), (1, 6), (2, 4), (2, 6), (2, 7), (2, 8)}
         assert best["median_ms"] > 0
         assert ctx.tuning() == {"sort_kind": best["sort_kind"], "sort_items": best["sort_items"]}
         trees = ctx.build_batched([(d, d) for d in devs], s=64)
