@@ -375,7 +375,7 @@ constexpr int kRadixMax = 1 << kRadixBits;
 constexpr int kBoxThreads = 512;
 constexpr int kBoxItems = 8;
 constexpr int kBoxTile = kBoxThreads * kBoxItems;  // 4096
-constexpr int kBoxHalo = 512;  // a box the finishing sort handles ends within it
+constexpr int kBoxHalo = 256;  // a box the finishing sort handles ends within it
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
