@@ -149,9 +149,12 @@ int fmm_destroy(fmm_ctx* ctx);
 /* Alg. 5 for one (Src, Recv) pair.  src_xyz [N][3] and recv_xyz [M][3] are
  * device pointers (host pointers with FMM_FLAG_HOST_INPUT), caller-owned and
  * read-only; they must stay valid until the call returns.  src_xyz may equal
- * recv_xyz (N == M).  N or M may be 0.  Work runs on `stream`
- * (cudaStream_t, NULL = legacy default stream); the call returns after the
- * stream has finished the build, with *out filled. */
+ * recv_xyz (N == M).  N or M may be 0.  N and M, each rounded up to a
+ * multiple of 4 (once when the sets are the same array), must add up to less
+ * than 2^32; FMM_ERR_ARG otherwise (in a batched build: over all distinct
+ * sets).  Work runs on `stream` (cudaStream_t, NULL = legacy default
+ * stream); the call returns after the stream has finished the build, with
+ * *out filled. */
 int fmm_build(fmm_ctx* ctx, const float* src_xyz, uint32_t N, const float* recv_xyz,
               uint32_t M, fmm_params params, fmm_tree* out, void* stream);
 

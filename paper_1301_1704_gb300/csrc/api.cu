@@ -1193,6 +1193,16 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   const bool box_order = (prm.flags & FMM_FLAG_BOX_ORDER) != 0;
   const uint64_t wait_ns = wait_ns_of(prm);
 
+  // The sort stage concatenates every distinct set (each rounded up to 4
+  // points) and indexes the result with 32-bit offsets.
+  uint64_t points = 0;
+  for (uint32_t k = 0; k < npairs; ++k) {
+    const bool aliased = pairs[k].src == pairs[k].recv && pairs[k].N == pairs[k].M;
+    points += ((uint64_t)pairs[k].N + 3) & ~3ull;
+    if (!aliased) points += ((uint64_t)pairs[k].M + 3) & ~3ull;
+  }
+  if (points >= (1ull << 32)) return FMM_ERR_ARG;
+
   uint64_t expect = 0;
   for (uint32_t k = 0; k < npairs; ++k) {
     uint64_t b = 0;

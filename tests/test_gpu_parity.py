@@ -220,6 +220,13 @@ def test_bad_arguments(ctx):
     assert e.value.code == fmmds.FMM_ERR_LEVEL
     with pytest.raises(ValueError):
         ctx.build(p, p)
+    # more points than 32-bit offsets can index: refused before any work
+    import ctypes as C
+    lib = fmmds._load()
+    tc = fmmds.TreeC()
+    st = lib.fmm_build(ctx._h, C.c_void_p(p.data_ptr()), 1 << 31, C.c_void_p(p.data_ptr() + 4),
+                       1 << 31, fmmds.Params(5, 0, 0, 0), C.byref(tc), C.c_void_p(0))
+    assert st == fmmds.FMM_ERR_ARG
 
 
 # ---------------------------------------------------------------------------
