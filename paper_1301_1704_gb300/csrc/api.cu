@@ -264,7 +264,8 @@ int pinned_reserve(void** buf, size_t* have, size_t bytes) {
   if (*buf) cudaFreeHost(*buf);
   *buf = nullptr;
   *have = 0;
-  const size_t want = std::max<size_t>(bytes, 1 << 20);
+  // whole 256-byte blocks: the upload kernel reads whole words past a size
+  const size_t want = align_up(std::max<size_t>(bytes, 1 << 20));
   if (cudaMallocHost(buf, want) != cudaSuccess) {
     cudaGetLastError();
     return FMM_ERR_OOM;
