@@ -127,3 +127,28 @@ def test_batched_more_jobs_than_one_block_holds(ctx, orc):
         trees = ctx.build_batched([(d, d) for d in devs], L=3)
         for i in list(range(0, k, 97)) + [k - 1]:
             compare_full(trees[i].numpy(), orc.build_tree(pts[i], pts[i], L=3), 3)
+
+
+def test_batched_host_input(ctx, orc):
+    """Host-input batched builds: two to four sets are copied set by set and
+    sorted as they land; more sets, or cluster-size mode, copy everything
+    first.  Every set must match the oracle either way."""
+    from paper_1301_1704_gb300 import fmmds
+    a, b, c = (workloads.uniform(9000, 71), workloads.sphere(7000, 72),
+               workloads.clumps(11000, 73, nclumps=3, sigma=0.02))
+    ha, hb, hc = (torch.from_numpy(x).pin_memory() for x in (a, b, c))
+    # three distinct sets, fixed depth: pipelined copies
+    trees = ctx.build_batched([(ha, hb), (hc, hc)], L=5, flags=fmmds.FMM_FLAG_HOST_INPUT)
+    compare_full(trees[0].numpy(), orc.build_tree(a, b, L=5), 5)
+    compare_full(trees[1].numpy(), orc.build_tree(c, c, L=5), 5)
+    # six sets (pageable memory): copies first
+    pairs = [(torch.from_numpy(x), torch.from_numpy(y)) for x, y in ((a, b), (b, c), (c, a))]
+    trees = ctx.build_batched(pairs, L=4, flags=fmmds.FMM_FLAG_HOST_INPUT)
+    for (x, y), t in zip(((a, b), (b, c), (c, a)), trees):
+        compare_full(t.numpy(), orc.build_tree(x, y, L=4), 4)
+    # cluster-size mode with host input
+    trees = ctx.build_batched([(ha, ha), (hb, hb)], s=40, flags=fmmds.FMM_FLAG_HOST_INPUT)
+    for x, t in zip((a, b), trees):
+        w = orc.build_tree(x, x, L=-1, s=40)
+        assert t.L == w["L"]
+        compare_full(t.numpy(), w, w["L"])
