@@ -239,8 +239,10 @@ __global__ void __launch_bounds__(kBoxThreads) finish_boxes_kernel(const Seg* __
 // decoupled look-back chain per level) gives each start its rank.
 // NL: a bound on the sets' box depths (Lb <= NL), so that the per-level
 // loops, unrolled, cover only the levels in use.
+// Four blocks an SM for trees up to level 8 (a few spilled registers): its
+// look-back waits hide better; deeper trees keep their registers.
 template <int NL>
-__global__ void __launch_bounds__(kBoxThreads) coarse_boxes_kernel(const Seg* __restrict__ segs,
+__global__ void __launch_bounds__(kBoxThreads, NL <= 8 ? 4 : 1) coarse_boxes_kernel(const Seg* __restrict__ segs,
                                                                    const Slot* __restrict__ slots,
                                                                    uint32_t nslots, DevStatus* st,
                                                                    uint64_t wait_ns) {
