@@ -200,6 +200,51 @@ def test_domain_error_then_recovery(ctx, orc):
     compare_full(got, want, 4)
 
 
+def test_allocator_failure_then_recovery(orc):
+    """An allocator that returns NULL makes the build fail with FMM_ERR_OOM
+    before any work; once it allocates again, the same context builds
+    correctly."""
+    import ctypes as C
+    from paper_1301_1704_gb300 import fmmds
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lib = fmmds._load()
+    state = {"fail": True, "live": {}}
+
+    def _alloc(nbytes, stream, user):
+        if state["fail"]:
+            return None
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        state["live"][t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(ptr, nbytes, stream, user):
+        state["live"].pop(ptr, None)
+
+    a_cb, f_cb = fmmds.ALLOC_FN(_alloc), fmmds.FREE_FN(_free)
+    h = C.c_void_p()
+    assert lib.fmm_create(C.byref(h), 0, a_cb, f_cb, None) == fmmds.FMM_OK
+    try:
+        p, q = workloads.uniform(5000, 3), workloads.uniform(4000, 4)
+        dp, dq = _dev(p), _dev(q)
+        torch.cuda.synchronize()
+
+        def build():
+            tc = fmmds.TreeC()
+            st = lib.fmm_build(h, C.c_void_p(dp.data_ptr()), len(p), C.c_void_p(dq.data_ptr()),
+                               len(q), fmmds.Params(4, 0, 0, 0), C.byref(tc), C.c_void_p(0))
+            return st, tc
+
+        st, _ = build()
+        assert st == fmmds.FMM_ERR_OOM
+        state["fail"] = False
+        st, tc = build()
+        assert st == fmmds.FMM_OK
+        compare_full(fmmds._tree_from(tc, len(p), len(q)).numpy(), orc.build_tree(p, q, L=4), 4)
+    finally:
+        lib.fmm_destroy(h)
+
+
 def test_bounded_wait_reports_timeout(ctx, orc):
     """One sort tile never publishes (test flag): the bounded look-back must
     give up with FMM_ERR_TIMEOUT, and the context must stay usable."""
