@@ -6,6 +6,9 @@
 // data structures for fast multipole methods", arXiv:1301.1704).  Only the
 // tests, __graft_entry__.smoke() and the cpu_baseline leg of bench.py may load
 // it.  It shares no code, header, table or helper with the CUDA path.
+// Built a second time with OpenMP (for the timed CPU baseline only), the key
+// loop and the per-box list loop run on all cores; the test
+// test_parallel_build_equals_serial pins that build to this one.
 //
 // What it computes, in the paper's order:
 //   * box index of a point at the finest grid and its Morton key
