@@ -54,7 +54,7 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    INTERVAL_MS = 100
+    INTERVAL_MS = 50
 
     def __init__(self, index: int):
         self.index = index
@@ -153,28 +153,6 @@ def _algorithmic_bytes(tree) -> dict:
     return b
 
 
-def _kernel_alg_bytes(name: str, tree) -> float | None:
-    """Algorithmic bytes of ALL launches of one kernel in one build (None if
-    the kernel has no compulsory traffic of its own)."""
-    n, m = tree.src.n, tree.recv.n
-    if name == "list_fill":  # writes the E2 and E4 index lists (offsets come from the scans)
-        return 4 * sum(tree.nnz_e2[l] + tree.nnz_e4[l] for l in range(2, tree.L + 1))
-    if name in ("onesweep", "rts_scatter"):  # one LSD pass reads and writes (u64 key, u32 index)
-        return None  # filled in by the caller from the pass count
-    if name == "tile_hist":  # reads the keys (or the coordinates in the first pass)
-        return None
-    if name == "finish_boxes":  # reads (key, index), writes the permutation and every box level
-        bx = 0
-        for sd in (tree.src, tree.recv):
-            for l in range(tree.L + 1):
-                nb = sd.nbox[l]
-                bx += 8 * nb + 4 * (nb + 1) + 4 * nb + (4 * (nb + 1) if l < tree.L else 0)
-        return 16 * (n + m) + bx
-    if name == "upfront_hist":  # reads the coordinates
-        return 12 * (n + m)
-    return None
-
-
 def _src_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1301_1704_gb300", "csrc")
@@ -184,53 +162,53 @@ def _src_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic_for(kernel: str):
-    """ncu DRAM bytes per launch of `kernel`, if captured from the current source."""
+def _traffic_record() -> dict:
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
-        return None
+        return {}
     try:
-        d = json.load(open(p))
+        return json.load(open(p))
     except ValueError:
-        return None
-    e = d.get(kernel)
+        return {}
+
+
+def _build_traffic(workload: str):
+    """ncu DRAM bytes (read + write) of all kernels of one build of
+    `workload`, if they were captured from the current sources."""
+    e = _traffic_record().get(workload)
     if not e or e.get("src_hash") != _src_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get("dram_bytes_per_build")
 
 
-def cpu_baseline(sub: int = 1) -> dict:
-    """The oracle on the points of the workload that fall in the sub-cube
-    [0, 1/sub)^3 (same level, same density, 1/sub^3 of the work; the whole
-    workload by default, about 25 s on one core): its OpenMP build on all
-    host cores, and the plain build on one core."""
+def cpu_baseline() -> dict:
+    """The oracle on the whole benchmark workload (config 2): its OpenMP
+    build on all host cores (about 3 s on 16 Grace cores), and the plain build
+    on one core (about 25 s)."""
     from oracle import oracle
     from paper_1301_1704_gb300 import workloads
     src = workloads.uniform(N_PTS, SEEDS[0])
     recv = workloads.uniform(N_PTS, SEEDS[1])
-    lim = np.float32(1.0 / sub)
-    s = np.ascontiguousarray(src[np.all(src < lim, axis=1)])
-    r = np.ascontiguousarray(recv[np.all(recv < lim, axis=1)])
-    pts = len(s) + len(r)
+    pts = len(src) + len(recv)
     out = {}
     for parallel in (True, False):
         oracle.build(parallel=parallel)
-        t0 = time.perf_counter()
-        oracle.build_tree(s, r, L=LEVEL, mode=oracle.MODE_STENCIL, parallel=parallel)
-        out[parallel] = time.perf_counter() - t0
+        out[parallel] = oracle.time_build(src, recv, L=LEVEL, mode=oracle.MODE_STENCIL,
+                                          parallel=parallel)
     cores = os.cpu_count() or 1
     return {"value": pts / out[True] / 1e6, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
-            "sample": f"points of the benchmark inputs inside [0,1/{sub})^3 ({len(s)} src + {len(r)} recv),"
-                      f" L={LEVEL}, stencil lists; the oracle's OpenMP build on {cores} threads:"
-                      f" {out[True]:.1f} s",
+            "sample": f"the whole benchmark workload ({len(src)} src + {len(recv)} recv), L={LEVEL},"
+                      f" stencil lists; the oracle's OpenMP build on {cores} threads:"
+                      f" {out[True]:.2f} s",
             "single_thread": {"value": pts / out[False] / 1e6, "cores": 1,
                               "seconds": out[False]}}
 
 
 def reference_arm(args) -> None:
-    """`--impl reference`: the CPU oracle (its OpenMP build, all host cores),
-    each step one bounded sample of the workload (points inside one of the 64
-    sub-cubes of side 1/4, in turn)."""
+    """`--impl reference`: the CPU oracle (its OpenMP build, all host cores)
+    on the benchmark's own workload, one whole config-2 build (2^24 + 2^24
+    points, L = 7, every list) per step -- about 3 s a step on 16 Grace
+    cores."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
@@ -238,34 +216,27 @@ def reference_arm(args) -> None:
     from paper_1301_1704_gb300 import workloads
     oracle.build(parallel=True)
     cores = os.cpu_count() or 1
-    src = workloads.uniform(N_PTS, SEEDS[0])
-    recv = workloads.uniform(N_PTS, SEEDS[1])
-    cs, cr = (src * 4).astype(np.int64).clip(0, 3), (recv * 4).astype(np.int64).clip(0, 3)
-    ids = cs[:, 0] + 4 * cs[:, 1] + 16 * cs[:, 2]
-    idr = cr[:, 0] + 4 * cr[:, 1] + 16 * cr[:, 2]
-    times, pts = [], []
+    npts = args.points
+    src = workloads.uniform(npts, SEEDS[0])
+    recv = workloads.uniform(npts, SEEDS[1])
+    times = []
     for step in range(args.warmup + args.steps):
-        sub = step % 64
-        s = np.ascontiguousarray(src[ids == sub])
-        r = np.ascontiguousarray(recv[idr == sub])
-        t0 = time.perf_counter()
-        oracle.build_tree(s, r, L=LEVEL, mode=oracle.MODE_STENCIL, parallel=True)
-        dt = time.perf_counter() - t0
+        dt = oracle.time_build(src, recv, L=args.level, mode=oracle.MODE_STENCIL, parallel=True)
         if step >= args.warmup:
             times.append(dt)
-            pts.append(len(s) + len(r))
     total = sum(times)
-    val = sum(pts) / total / 1e6
+    val = 2 * npts * len(times) / total / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "Mpts/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "one 1/64 sub-cube of the inputs per step"},
+        "config": {"workload": WORKLOAD if (npts, args.level) == (N_PTS, LEVEL) else
+                   f"N=M={npts} uniform, L={args.level}", "N": npts, "M": npts, "L": args.level,
+                   "seeds": list(SEEDS)},
         "cpu_baseline": {"value": val, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
-                         "sample": "per step: the points of the benchmark inputs inside one of the"
-                                   " 64 sub-cubes of side 1/4 (about 2^18 per set), L=7; the"
-                                   f" oracle's OpenMP build on {cores} threads"},
+                         "sample": f"per step one whole build of the workload; the oracle's "
+                                   f"OpenMP build on {cores} threads"},
         "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -386,13 +357,35 @@ def serve_trace(nsys: int, steps: int, rate: float, seed: int):
     return np.array(arr), np.array(sys_, np.uint32)
 
 
+def _serve_run(fmmds, pts, levels, seed, arr, sys_, workers, batch) -> dict:
+    srv = fmmds.Server(0, workers=workers, max_batch=batch)
+    try:
+        for k, (p, L) in enumerate(zip(pts, levels)):
+            srv.add_system(p, L, 0.1, seed=seed * 1000 + k)
+        infos = srv.run_trace(arr, sys_)
+    finally:
+        srv.close()
+    lat = np.array([(i["t_done"] - i["t_arrival"]) * 1e3 for i in infos])
+    span = max(i["t_done"] for i in infos) - min(i["t_arrival"] for i in infos)
+    npts = sum(i["points"] for i in infos)
+    return {"value": npts / span / 1e6, "unit": "Mpts/s",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "requests": len(infos), "span_s": span,
+            "mean_batch": float(np.mean([i["batch_size"] for i in infos])),
+            "failed": int(sum(i["status"] != 0 for i in infos))}
+
+
 def served_section(ctx, steps: int) -> dict:
     """Served dynamic rebuilds: 8 resident clump systems (two each of 1e4,
     1e5, 1e6, 1e7 points), depth fixed from the initial state at s = 64,
-    Poisson requests at 2000/s, each advancing one random system by one step
-    (Gaussian steps of 0.1 h_L, wall reflection) and rebuilding it.  Served =
+    Poisson requests, each advancing one random system by one step (Gaussian
+    steps of 0.1 h_L, wall reflection) and rebuilding it.  Served =
     continuous batching over 2 concurrent workers; plain = one worker, one
-    system per build (per-instance launches)."""
+    system per build (per-instance launches).  Two offered loads: the
+    required 2000 requests/s (more points per second than the GPU builds, so
+    queues grow over the trace and latency measures the backlog), and 60 % of
+    the served throughput measured there (below capacity: latency is the
+    service time)."""
     import torch
     from paper_1301_1704_gb300 import fmmds, workloads
     seed = workloads.CONFIG_SEEDS[5]
@@ -403,32 +396,137 @@ def served_section(ctx, steps: int) -> dict:
         levels.append(ctx.build(d, d, s=64).L)
         del d
     torch.cuda.synchronize()
+    mean_pts = float(np.mean(SERVE_SIZES))
+    out = {"offered_2000": {}, "below_capacity": {}}
     arr, sys_ = serve_trace(len(pts), steps, SERVE_RATE, seed)
-    out = {}
     for name, workers, batch in (("served", 2, 8), ("plain", 1, 1)):
-        srv = fmmds.Server(0, workers=workers, max_batch=batch)
-        try:
-            for k, (p, L) in enumerate(zip(pts, levels)):
-                srv.add_system(p, L, 0.1, seed=seed * 1000 + k)
-            infos = srv.run_trace(arr, sys_)
-        finally:
-            srv.close()
-        lat = np.array([(i["t_done"] - i["t_arrival"]) * 1e3 for i in infos])
-        span = max(i["t_done"] for i in infos) - min(i["t_arrival"] for i in infos)
-        npts = sum(i["points"] for i in infos)
-        out[name] = {"value": npts / span / 1e6, "unit": "Mpts/s",
-                     "p50_ms": float(np.percentile(lat, 50)),
-                     "p99_ms": float(np.percentile(lat, 99)),
-                     "requests": len(infos), "span_s": span,
-                     "mean_batch": float(np.mean([i["batch_size"] for i in infos])),
-                     "failed": int(sum(i["status"] != 0 for i in infos))}
+        out["offered_2000"][name] = _serve_run(fmmds, pts, levels, seed, arr, sys_, workers, batch)
+    out["offered_2000"]["offered_mpts_s"] = SERVE_RATE * mean_pts / 1e6
+    # below capacity: 60 % of the served throughput just measured
+    rate = 0.6 * out["offered_2000"]["served"]["value"] * 1e6 / mean_pts
+    low_steps = max(20, steps // 5)
+    arr2, sys2 = serve_trace(len(pts), low_steps, rate, seed + 1)
+    for name, workers, batch in (("served", 2, 8), ("plain", 1, 1)):
+        out["below_capacity"][name] = _serve_run(fmmds, pts, levels, seed, arr2, sys2, workers,
+                                                 batch)
+    out["below_capacity"]["rate_per_s"] = rate
+    out["below_capacity"]["offered_mpts_s"] = rate * mean_pts / 1e6
+    out["below_capacity"]["steps_per_system"] = low_steps
+    # Kernel breakdown of one batched build of all 8 systems (what a full
+    # served batch runs, without the time step) and of the 1e7 system alone.
+    devs = [torch.from_numpy(p).cuda() for p in pts]
+    bd = {}
+    for name, idx in (("batch_of_8", list(range(len(pts)))), ("one_1e7", [6])):
+        b = ctx.batch([(devs[i], devs[i]) for i in idx], levels=[levels[i] for i in idx])
+        for _ in range(3):
+            ctx.build_batched(b, L=7, raw=True)
+        torch.cuda.synchronize()
+        ctx.reset_timing()
+        ctx.set_timing(True)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            ctx.build_batched(b, L=7, raw=True)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / 5 * 1e3
+        ctx.set_timing(False)
+        kt = ctx.timing()
+        npt = sum(len(pts[i]) for i in idx)
+        bd[name] = {"points": npt, "wall_ms": wall, "value": npt / (wall / 1e3) / 1e6,
+                    "kernel_ms": {k: v[1] / 5 for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])},
+                    "kernel_sum_ms": sum(v[1] for v in kt.values()) / 5}
+    out["batch_breakdown"] = bd
+    del devs
     out["workload"] = ("8 resident clump systems (2 x 1e4, 1e5, 1e6, 1e7 points), L from the "
-                       f"initial state at s = 64 ({levels}), Poisson {SERVE_RATE:.0f}/s requests "
-                       f"until every system has {steps} steps; served = continuous batching "
-                       "(2 workers, up to 8 systems per batched build), plain = 1 worker, "
+                       f"initial state at s = 64 ({levels}), Poisson requests each for a uniformly "
+                       f"chosen system: {SERVE_RATE:.0f}/s until every system has {steps} steps, and "
+                       f"{rate:.0f}/s until every system has {low_steps} steps; served = continuous "
+                       "batching (2 workers, up to 8 systems per batched build), plain = 1 worker, "
                        "1 system per build")
-    out["speedup_vs_plain"] = out["served"]["value"] / out["plain"]["value"]
+    out["speedup_vs_plain"] = out["offered_2000"]["served"]["value"] / out["offered_2000"]["plain"]["value"]
     return out
+
+
+def _timed(fn, steps: int, stream):
+    """Per-step CUDA-event times (ms) of `steps` calls of fn on `stream`, the
+    whole region's time, and the kernel launches fn reports."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for a, b in ev:
+        a.record(stream)
+        launches += fn()
+        b.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], t0.elapsed_time(t1), launches
+
+
+def small_config_section(ctx, stream, steps: int) -> dict:
+    """Config 1: N = M = 16384 uniform, L = 4 (a few MB: launch-latency
+    bound, so microseconds per build, eagerly and in graph mode; a roofline
+    fraction would mean nothing here)."""
+    import torch
+    from paper_1301_1704_gb300 import workloads
+    src_h, recv_h, L = workloads.config_inputs(1)
+    src, recv = torch.from_numpy(src_h).cuda(), torch.from_numpy(recv_h).cuda()
+    out = {"workload": "config 1: N=M=16384 uniform [0,1)^3 float32, L=4, lists at levels 2..4"}
+    for mode in ("eager", "graph"):
+        ctx.set_graphs(mode == "graph")
+
+        def one():
+            ctx.build(src, recv, L=L, stream=stream, raw=True)
+            return ctx.last_launch_count()
+
+        for _ in range(5):
+            one()
+        t, _, nl = _timed(one, steps, stream)
+        out[mode] = {"p50_us": 1e3 * _pct(t, 0.5), "p99_us": 1e3 * _pct(t, 0.99),
+                     "value": 2 * len(src_h) / (_pct(t, 0.5) / 1e3) / 1e6, "unit": "Mpts/s",
+                     "steps": steps, "gpu_launches_per_step": nl / steps}
+    ctx.set_graphs(False)
+    out["graph_stats"] = ctx.graph_stats()
+    return out
+
+
+def sparse_config_section(ctx, stream, steps: int, warmup: int, autotune: bool) -> dict:
+    """Config 3: N = M = 2^24, half on a sphere surface, half in 64 clumps,
+    L = 9 (most boxes empty): Mpoints/s, p50/p99, and the whole build's
+    fraction of the HBM roofline on its compulsory bytes."""
+    import torch
+    from paper_1301_1704_gb300 import workloads
+    src_h, recv_h, L = workloads.config_inputs(3)
+    src, recv = torch.from_numpy(src_h).cuda(), torch.from_numpy(recv_h).cuda()
+    saved = ctx.tuning()
+    tuned = ctx.autotune([(src, recv)], L=L, trials=2, stream=stream) if autotune else None
+
+    def one():
+        ctx.build(src, recv, L=L, stream=stream, raw=True)
+        return ctx.last_launch_count()
+
+    for _ in range(warmup):
+        one()
+    t, total, nl = _timed(one, steps, stream)
+    tree = ctx.build(src, recv, L=L, stream=stream)
+    torch.cuda.synchronize()
+    alg = _algorithmic_bytes(tree)
+    peak, peak_kind = _peaks()
+    ms = total / steps
+    ctx.set_tuning(saved["sort_kind"], saved["sort_items"])
+    return {"workload": "config 3: N=M=2^24, half on a sphere surface (r=0.4, jitter 1e-3), "
+                        "half in 64 Gaussian clumps (sigma 0.01), L=9, lists at levels 2..9",
+            "value": 2 * len(src_h) / (ms / 1e3) / 1e6, "unit": "Mpts/s", "ms_per_step": ms,
+            "p50_ms": _pct(t, 0.5), "p99_ms": _pct(t, 0.99), "steps": steps,
+            "gpu_launches_per_step": nl / steps, "tuning": tuned,
+            "roofline": {"bound": "hbm", "alg_bytes": alg["total"],
+                         "achieved": alg["total"] / (ms / 1e3) / 1e9, "peak": peak,
+                         "frac": alg["total"] / (ms / 1e3) / 1e9 / peak,
+                         "peak_kind": peak_kind, "unit": "GB/s"},
+            "boxes": {"finest_src": int(tree.src.nbox[L]), "finest_recv": int(tree.recv.nbox[L])},
+            "nnz": {"e2": int(sum(tree.nnz_e2)), "e4": int(sum(tree.nnz_e4))}}
 
 
 def main():
@@ -443,13 +541,17 @@ def main():
                     help="points per set (default 2^24; smaller values only for profiling)")
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--sort-kind", type=int, default=None,
-                    help="0 radix reduce-then-scan, 1 radix onesweep, 2 Fixed-Grid (else autotuned)")
+                    help="sort kind (see fmm_set_tuning; else autotuned)")
     ap.add_argument("--sort-items", type=int, default=0, help="points per thread of a sort tile")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the comparison of the sort kinds")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-graphs", action="store_true", help="skip the graph-mode timings")
+    ap.add_argument("--no-configs", action="store_true", help="skip the config 1 and 3 timings")
+    ap.add_argument("--clock-window", type=float, default=1.0,
+                    help="seconds of untimed builds, under the clock sampler, before the timed "
+                         "region")
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="steps of the per-instance comparison of the batched workload")
     ap.add_argument("--serve-steps", type=int, default=1000,
@@ -477,6 +579,7 @@ def main():
         torch.cuda.synchronize()
 
     npts, level = args.points, args.level
+    full = (npts, level) == (N_PTS, LEVEL)
     src_h = workloads.uniform(npts, SEEDS[0])
     recv_h = workloads.uniform(npts, SEEDS[1])
     src = torch.from_numpy(src_h).cuda()
@@ -490,38 +593,39 @@ def main():
         # the library's autotuner picks the sort kind and tile size on these inputs
         autotuned = ctx.autotune([(src, recv)], L=level, trials=3, stream=stream)
 
-    for _ in range(args.warmup):
+    def one():
         ctx.build(src, recv, L=level, stream=stream, raw=True)
+        return ctx.last_launch_count()
+
+    for _ in range(args.warmup):
+        one()
     torch.cuda.synchronize()
 
-    # Timed region: K builds through the C ABI (raw result struct: no Python
-    # wrapping of the outputs), CUDA events on the build's stream.
+    # Clock record: the sampler runs over `--clock-window` seconds of untimed
+    # builds right before the timed region and over the timed region itself
+    # (a timed region of a few dozen builds lasts only a few sampling periods).
     clocks = ClockSampler(local)
     clocks.start()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    launches = 0
+    t_end = time.time() + args.clock_window
+    while time.time() < t_end:
+        for _ in range(20):
+            one()
+        torch.cuda.synchronize()
+    # Timed region: K builds through the C ABI (raw result struct: no Python
+    # wrapping of the outputs), CUDA events on the build's stream.
     barrier()
-    t_all0 = torch.cuda.Event(enable_timing=True)
-    t_all1 = torch.cuda.Event(enable_timing=True)
-    t_all0.record(stream)
-    for i in range(args.steps):
-        starts[i].record(stream)
-        ctx.build(src, recv, L=level, stream=stream, raw=True)
-        ends[i].record(stream)
-        launches += ctx.last_launch_count()
-    t_all1.record(stream)
+    step_ms, total_ms, launches = _timed(one, args.steps, stream)
     barrier()
     clk = clocks.stop()
-    total_ms = t_all0.elapsed_time(t_all1)
-    step_ms = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
+    clk["window"] = f"{args.clock_window:.1f} s of back-to-back builds, then the timed region"
+    step_ms = sorted(step_ms)
 
     # Kernel durations: the same K builds again with the library's per-launch
     # events on (they add a little time, so they are kept out of `value`).
     ctx.reset_timing()
     ctx.set_timing(True)
-    for i in range(args.steps):
-        ctx.build(src, recv, L=level, stream=stream, raw=True)
+    for _ in range(args.steps):
+        one()
     torch.cuda.synchronize()
     ctx.set_timing(False)
     ktimes = ctx.timing()
@@ -532,16 +636,10 @@ def main():
     if not args.no_graphs:
         ctx.set_graphs(True)
         for _ in range(max(3, args.warmup)):
-            ctx.build(src, recv, L=level, stream=stream, raw=True)
-        torch.cuda.synchronize()
-        for i in range(args.steps):
-            starts[i].record(stream)
-            ctx.build(src, recv, L=level, stream=stream, raw=True)
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-        g_ms = sorted(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
-        graphs = {"p50_ms": g_ms[len(g_ms) // 2], "p99_ms": g_ms[-1],
-                  "value": 2 * npts / (g_ms[len(g_ms) // 2] / 1e3) / 1e6, "unit": "Mpts/s",
+            one()
+        g_ms, g_total, _ = _timed(one, args.steps, stream)
+        graphs = {"p50_ms": _pct(g_ms, 0.5), "p99_ms": _pct(g_ms, 0.99),
+                  "value": 2 * npts * args.steps / (g_total / 1e3) / 1e6, "unit": "Mpts/s",
                   "steps": args.steps, "graph_stats": ctx.graph_stats()}
         ctx.set_graphs(False)
     tree = ctx.build(src, recv, L=level, stream=stream)
@@ -550,75 +648,60 @@ def main():
 
     pts_per_step = npts * 2
     value = replica_throughput(pts_per_step * args.steps, total_ms, ws) / 1e6
-    p50 = step_ms[len(step_ms) // 2]
-    p99 = step_ms[min(len(step_ms) - 1, int(np.ceil(0.99 * len(step_ms))) - 1)]
+    ms_per_step = total_ms / args.steps
 
-    # Roofline of the dominant kernel (largest summed time in the timed region).
+    # Roofline of the whole build (the unit one step processes): compulsory
+    # bytes -- inputs read once, outputs written once -- over the measured
+    # time per build, against the measured copy bandwidth.
     peak, peak_kind = _peaks()
     alg = _algorithmic_bytes(tree)
-    def alg_of(name):
-        # A radix pass reads and writes (u64 key, u32 index) per point;
-        # rts_scatter sorts both sets in one launch per pass, onesweep one set
-        # per launch (and forms the keys from the coordinates in its pass 0).
-        per_build = ktimes[name][0] / args.steps
-        if name == "rts_scatter":  # pass 0 reads the stored 8-byte keys: 20 bytes a point
-            return pts_per_step * (20 + 24 * (per_build - 1))
-        if name == "onesweep":
-            return 24 * pts_per_step * per_build / 2
-        if name == "tile_hist":  # first pass reads the coordinates, later ones the keys
-            return pts_per_step * (12 + 8 * (per_build - 1))
-        return _kernel_alg_bytes(name, tree)
-
-    measured = {k: v for k, v in ktimes.items() if alg_of(k) is not None}
-    dom_name, (dom_launches, dom_ms) = max(measured.items(), key=lambda kv: kv[1][1])
-    per_build_launches = dom_launches / args.steps
-    avg_ms = dom_ms / dom_launches
-    bytes_per_launch = alg_of(dom_name) / per_build_launches
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    achieved = alg["total"] / (ms_per_step / 1e3) / 1e9
+    wl_key = "plain_uniform_2p24_L7" if full else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": _traffic_for(dom_name),
-                "kernel": dom_name, "peak_kind": peak_kind,
-                "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms}
-    kernel_frac = {k: alg_of(k) / (v[1] / args.steps / 1e3) / 1e9 / peak
-                   for k, v in measured.items()}
-    build_frac = alg["total"] / (p50 / 1e3) / 1e9 / peak
+                "frac": achieved / peak,
+                "traffic": _build_traffic(wl_key) if wl_key else None,
+                "kernel": "whole build (every kernel of one fmm_build)", "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg["total"], "alg_bytes": alg,
+                "avg_launch_ms": ms_per_step,
+                "frac_of_nominal_8000": achieved / 8000.0}
+    per_kernel = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
+                      "share": v[1] / sum(x[1] for x in ktimes.values())}
+                  for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][1])}
 
     # End to end through the C ABI: pinned host inputs, copies inside the call.
     hs = torch.from_numpy(src_h).pin_memory()
     hr = torch.from_numpy(recv_h).pin_memory()
+
+    def one_e2e():
+        ctx.build(hs, hr, L=level, flags=fmmds.FMM_FLAG_HOST_INPUT, stream=stream, raw=True)
+        return 0
+
     for _ in range(min(2, args.e2e_steps)):
-        ctx.build(hs, hr, L=level, flags=fmmds.FMM_FLAG_HOST_INPUT, stream=stream, raw=True)
+        one_e2e()
     barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.e2e_steps):
-        ctx.build(hs, hr, L=level, flags=fmmds.FMM_FLAG_HOST_INPUT, stream=stream, raw=True)
-    e1.record(stream)
-    barrier()
-    e2e_ms = max(e0.elapsed_time(e1), 1e-9)
-    e2e_ms = max_over_ranks(e2e_ms, dist)
-    e2e_val = (replica_throughput(pts_per_step * args.e2e_steps, e2e_ms, ws) / 1e6
-               if args.e2e_steps else None)
-    # The same build with each way of ordering the points (radix passes in
-    # reduce-then-scan or onesweep form, the paper's Fixed-Grid pseudo-sort).
+    e2e_val = None
+    if args.e2e_steps:
+        _, e2e_ms, _ = _timed(one_e2e, args.e2e_steps, stream)
+        e2e_ms = max_over_ranks(max(e2e_ms, 1e-9), dist)
+        e2e_val = replica_throughput(pts_per_step * args.e2e_steps, e2e_ms, ws) / 1e6
+    # The same build with each way of ordering the points.
     sort_kinds = {}
-    if (npts, level) == (N_PTS, LEVEL) and not args.no_compare:
+    if full and not args.no_compare:
         base = ctx.tuning()
-        for kind, name in ((fmmds.FMM_SORT_RTS, "radix_rts"), (fmmds.FMM_SORT_ONESWEEP, "radix_onesweep"),
+        for kind, name in ((fmmds.FMM_SORT_RTS, "radix_rts"),
+                           (fmmds.FMM_SORT_ONESWEEP, "radix_onesweep"),
                            (fmmds.FMM_SORT_FIXED_GRID, "fixed_grid")):
             ctx.set_tuning(kind)
             for _ in range(2):
-                ctx.build(src, recv, L=level, stream=stream, raw=True)
-            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(5)]
-            for a, b in evs:
-                a.record(stream)
-                ctx.build(src, recv, L=level, stream=stream, raw=True)
-                b.record(stream)
-            torch.cuda.synchronize()
-            sort_kinds[name] = _pct([a.elapsed_time(b) for a, b in evs], 0.5)
+                one()
+            t, _, _ = _timed(one, 5, stream)
+            sort_kinds[name] = _pct(t, 0.5)
         ctx.set_tuning(base["sort_kind"], base["sort_items"])
+    configs = {}
+    if not args.no_configs and rank == 0:
+        configs["config1"] = small_config_section(ctx, stream, max(args.steps, 200))
+        configs["config3"] = sparse_config_section(ctx, stream, args.steps, args.warmup,
+                                                   not args.no_autotune)
     batched = None
     if not args.no_batched:
         batched = batched_section(ctx, stream, args.steps, args.warmup, args.plain_steps)
@@ -629,31 +712,29 @@ def main():
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "tuning": dict(ctx.tuning(), autotuned=autotuned is not None),
-            "config": {"workload": WORKLOAD if (npts, level) == (N_PTS, LEVEL) else
+            "config": {"workload": WORKLOAD if full else
                        f"profiling case N=M={npts} uniform, L={level}", "N": npts, "M": npts, "L": level,
                        "seeds": list(SEEDS), "l2": "inputs larger than L2 (402 MB of xyz)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "p50_ms": p50, "p99_ms": p99,
+            "p50_ms": _pct(step_ms, 0.5), "p99_ms": _pct(step_ms, 0.99),
             "gpu_launches": launches,
             "clocks": clk,
             "roofline": roofline,
-            "build_roofline": {"alg_bytes": alg, "frac_of_peak": build_frac, "peak": peak,
-                               "note": "whole build, compulsory bytes / p50 step time"},
-            "kernel_ms_per_step": {k: v[1] / args.steps for k, v in sorted(ktimes.items())},
-            "kernel_hbm_frac": kernel_frac,
+            "kernels": per_kernel,
             "nnz": {"e2": int(sum(tree.nnz_e2)), "e4": int(sum(tree.nnz_e4))},
             "e2e": {"value": e2e_val, "unit": "Mpts/s", "h2d_bytes_per_step": 12 * pts_per_step,
                     "d2h_bytes_per_step": D2H_BYTES, "steps": args.e2e_steps},
         }
-        if not args.no_cpu_baseline and ws == 1 and (npts, level) == (N_PTS, LEVEL):
+        if not args.no_cpu_baseline and ws == 1 and full:
             line["cpu_baseline"] = cpu_baseline()
         if sort_kinds:
             line["p50_ms_by_sort_kind"] = sort_kinds
         if graphs is not None:
             line["graph_mode"] = graphs
+        line.update(configs)
         if batched is not None:
             line["batched"] = batched
         if served is not None:

@@ -58,7 +58,8 @@ typedef enum fmm_status {
   FMM_ERR_OOM = 4,      /* the allocator returned NULL */
   FMM_ERR_TIMEOUT = 5,  /* a bounded device-side wait expired */
   FMM_ERR_CUDA = 6,     /* a CUDA runtime call failed */
-  FMM_ERR_CAPACITY = 7  /* a list of one level holds 2^32 or more entries */
+  FMM_ERR_CAPACITY = 7, /* a list of one level holds 2^32 or more entries */
+  FMM_PENDING = 8       /* fmm_server_poll only: the request is not done yet */
 } fmm_status;
 
 /* Device allocator used for the context's arena (for instance PyTorch's
@@ -193,6 +194,21 @@ int fmm_morton_keys(fmm_ctx* ctx, const float* xyz, uint32_t n, uint64_t* keys, 
 /* Upper bound of the arena bytes one build of this size needs. */
 int fmm_query_workspace(uint32_t N, uint32_t M, fmm_params params, uint64_t* bytes);
 
+/* Sizes of one build known before it runs (Alg. 5's outputs, Sec. 2.1):
+ * the arena bound of fmm_query_workspace, and per level l the largest
+ * possible number of non-empty boxes, min(n, 8^l), of each set and the
+ * largest possible list sizes, 27 and 189 entries per receiver box (E2
+ * includes the box itself; E4 = the 6^3 children of the parent's neighbours
+ * less the 3^3 of E2).  With L = -1 (cluster-size mode) the level bounds are
+ * given for every level 0..21.  The tree a build returns holds the exact
+ * sizes (nbox_*, nnz_*). */
+typedef struct fmm_sizes {
+  uint64_t workspace_bytes;
+  uint32_t max_nbox_src[FMM_LEVELS], max_nbox_recv[FMM_LEVELS];
+  uint64_t max_nnz_e2[FMM_LEVELS], max_nnz_e4[FMM_LEVELS];  /* 0 at levels 0, 1 */
+} fmm_sizes;
+int fmm_query_sizes(uint32_t N, uint32_t M, fmm_params params, fmm_sizes* out);
+
 /* Tuning of a context (the autotuner's knobs).  sort_kind selects how the
  * points are ordered before the finishing sort inside the boxes:
  *   FMM_SORT_RTS         LSD radix passes, each: per-tile digit histograms,
@@ -274,9 +290,13 @@ int fmm_graph_stats(fmm_ctx* ctx, uint64_t* launches, uint64_t* instantiations);
  * counts (the role of NeighborBookmark).
  *
  *   counts  [n] device, read-only; offsets [n + 1] device: offsets[i] = sum
- *   of counts[0..i), offsets[n] = the total (low 32 bits); total: optional
- *   device uint64 receiving the full total (all ones if a bounded device-side
- *   wait gave up).  Both buffers are the caller's.
+ *   of counts[0..i) (low 32 bits), offsets[n] = the total (low 32 bits);
+ *   total: optional device uint64 receiving the full 64-bit total.  All
+ *   buffers are the caller's.  If a bounded device-side wait gives up (the
+ *   GPU did not schedule an earlier tile within 2 s), offsets[n] is set to
+ *   0xffffffff and *total to all ones; only `total` tells that apart from a
+ *   real total, so a caller that must detect the failure passes `total`
+ *   (a real total is below 2^58).
  *
  * n must not exceed FMM_NOALLOC_SCAN_MAX (FMM_ERR_ARG otherwise).  The only
  * scratch is a fixed static device array (about 128 KiB) that every GPU
@@ -414,6 +434,9 @@ int fmm_server_add_system(fmm_server* srv, const float* xyz, uint32_t n, int hos
 int fmm_server_submit(fmm_server* srv, uint32_t system, uint64_t* request_id);
 /* Blocks until the request is done. */
 int fmm_server_wait(fmm_server* srv, uint64_t request_id, fmm_request_info* info);
+/* Does not block: FMM_PENDING while the request is queued or running (info
+ * untouched); once it is done, the same as fmm_server_wait. */
+int fmm_server_poll(fmm_server* srv, uint64_t request_id, fmm_request_info* info);
 /* Open-loop replay: request k arrives at (call time + arrival_s[k]) for
  * system[k] (arrival_s ascending); blocks until every request is done and
  * fills info[k]. */

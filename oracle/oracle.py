@@ -193,6 +193,26 @@ def build_tree(src, recv, L: int = -1, s: int = 0, mode: int = MODE_STENCIL,
         lib.orc_free(h)
 
 
+def time_build(src, recv, L: int = -1, s: int = 0, mode: int = MODE_STENCIL,
+               parallel: bool = False) -> float:
+    """Seconds the oracle takes to build the whole structure of (src, recv)
+    (what ``build_tree`` computes, without copying it out): the timed CPU
+    baseline."""
+    import time
+    lib = _load(parallel)
+    a, b = _f32(src), _f32(recv)
+    h = C.c_void_p()
+    fp = C.POINTER(C.c_float)
+    t0 = time.perf_counter()
+    st = lib.orc_build(a.ctypes.data_as(fp), a.shape[0], b.ctypes.data_as(fp), b.shape[0], L, s,
+                       mode, C.byref(h))
+    dt = time.perf_counter() - t0
+    if st != ORC_OK:
+        raise OracleError(st, "build")
+    lib.orc_free(h)
+    return dt
+
+
 def box_lists(src_keys_l, level: int, recv_key: int, mode: int = MODE_STENCIL):
     """E2 and E4 lists (ascending source ranks) of one receiver box."""
     lib = _load()

@@ -1559,6 +1559,23 @@ int fmm_query_workspace(uint32_t N, uint32_t M, fmm_params p, uint64_t* bytes) {
   return query_workspace(N, M, p, bytes);
 }
 
+int fmm_query_sizes(uint32_t N, uint32_t M, fmm_params p, fmm_sizes* out) {
+  if (!out) return FMM_ERR_ARG;
+  FMM_TRY(check_params(p));
+  std::memset(out, 0, sizeof(*out));
+  FMM_TRY(query_workspace(N, M, p, &out->workspace_bytes));
+  const int L = p.L >= 0 ? p.L : kMaxLevel;
+  for (int l = 0; l <= L; ++l) {
+    out->max_nbox_src[l] = level_cap(N, l);
+    out->max_nbox_recv[l] = level_cap(M, l);
+    if (l >= 2) {
+      out->max_nnz_e2[l] = 27ull * level_cap(M, l);
+      out->max_nnz_e4[l] = 189ull * level_cap(M, l);
+    }
+  }
+  return FMM_OK;
+}
+
 int fmm_build(fmm_ctx* c, const float* src_xyz, uint32_t N, const float* recv_xyz, uint32_t M,
               fmm_params params, fmm_tree* out, void* stream) {
   if (!c || !out) return FMM_ERR_ARG;
@@ -1838,6 +1855,7 @@ const char* fmm_status_string(int status) {
     case FMM_ERR_TIMEOUT: return "a bounded device-side wait expired";
     case FMM_ERR_CUDA: return "CUDA runtime error";
     case FMM_ERR_CAPACITY: return "a list holds 2^32 or more entries";
+    case FMM_PENDING: return "the request is not done yet";
     default: return "unknown status";
   }
 }

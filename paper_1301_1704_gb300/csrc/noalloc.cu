@@ -41,8 +41,10 @@ namespace fmm {
 namespace {
 
 // Out-of-place exclusive scan of counts[0..n) into offsets[0..n], with
-// offsets[n] = total (low 32 bits) and *total = the 64-bit total (all ones if
-// a bounded wait gave up).
+// offsets[n] = total (low 32 bits) and *total = the 64-bit total.  The sums
+// of a thread, a warp and a tile are kept in 64 bits, so a tile whose counts
+// add up past 2^32 still gives the exact total.  If a bounded wait gives up,
+// offsets[n] = 0xffffffff and *total = all ones (a real total is below 2^58).
 __global__ void __launch_bounds__(kScanThreads) scan_noalloc_kernel(const uint32_t* counts,
                                                                    uint32_t n, uint32_t* offsets,
                                                                    uint64_t* total,
@@ -50,7 +52,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_noalloc_kernel(const uint32
                                                                    uint64_t wait_ns) {
   constexpr int W = kScanThreads / 32;
   __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_wsum[W];
+  __shared__ uint64_t s_wsum[W];
   __shared__ uint64_t s_prev;
   const uint32_t ntiles = n == 0 ? 1u : (uint32_t)(((uint64_t)n + kScanTile - 1) / kScanTile);
   if (threadIdx.x == 0) s_tile = atomicAdd(&sc->counter, 1u);
@@ -59,25 +61,25 @@ __global__ void __launch_bounds__(kScanThreads) scan_noalloc_kernel(const uint32
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t i0 = (uint64_t)tile * kScanTile + (uint64_t)threadIdx.x * kScanItems;
   uint32_t v[kScanItems];
-  uint32_t sum = 0;
+  uint64_t sum = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     v[k] = (i0 + k < n) ? counts[i0 + k] : 0u;
     sum += v[k];
   }
-  uint32_t x = sum;
+  uint64_t x = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) s_wsum[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    uint32_t run = 0;
+    uint64_t run = 0;
     if (lane == 0) {
       for (int w = 0; w < W; ++w) {
-        const uint32_t c = s_wsum[w];
+        const uint64_t c = s_wsum[w];
         s_wsum[w] = run;
         run += c;
       }
@@ -94,9 +96,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_noalloc_kernel(const uint32
     if (lane == 0) {
       s_prev = prev;
       if (tile == ntiles - 1) {
+        const bool gave_up = ld_relaxed_u32(&sc->st.abort) != 0;
         const uint64_t t = prev + run;
-        offsets[n] = (uint32_t)t;
-        if (total) *total = ld_relaxed_u32(&sc->st.abort) ? ~0ull : t;
+        offsets[n] = gave_up ? 0xffffffffu : (uint32_t)t;
+        if (total) *total = gave_up ? ~0ull : t;
       }
     }
   }

@@ -263,9 +263,14 @@ void worker_main(fmm_server* S, uint32_t w) {
     int st = FMM_OK;
     sets.assign(k, fmm_set{});
     outs.assign(k, fmm_tree{});
+    // Systems whose time step was launched: only they move on a step, so
+    // that a system's points stay a function of (seed, step) even when a
+    // launch fails partway through the batch.
+    uint32_t moved = 0;
     for (uint32_t j = 0; j < k && st == FMM_OK; ++j) {
       System& y = S->systems[sys[j]];  // busy: only this worker touches it
       st = launch_displace(y.xyz, y.n, y.seed, y.step, y.sigma, W.stream);
+      if (st == FMM_OK) moved = j + 1;
       sets[j] = fmm_set{y.xyz, y.n, y.xyz, y.n, y.L};
     }
     if (st == FMM_OK) {
@@ -293,7 +298,7 @@ void worker_main(fmm_server* S, uint32_t w) {
       for (uint32_t j = 0; j < k; ++j) {
         System& y = S->systems[sys[j]];
         fmm_request_info& inf = S->reqs[ids[j]]->info;
-        y.step += 1;
+        if (j < moved) y.step += 1;
         y.busy = false;
         y.last = outs[j];
         y.has_last = st == FMM_OK;
@@ -492,6 +497,15 @@ int fmm_server_wait(fmm_server* S, uint64_t id, fmm_request_info* info) {
   std::unique_lock<std::mutex> lk(S->mu);
   if (id >= S->reqs.size()) return FMM_ERR_ARG;
   S->done_cv.wait(lk, [&] { return S->reqs[id]->done; });
+  if (info) *info = S->reqs[id]->info;
+  return (int)S->reqs[id]->info.status;
+}
+
+int fmm_server_poll(fmm_server* S, uint64_t id, fmm_request_info* info) {
+  if (!S) return FMM_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (id >= S->reqs.size()) return FMM_ERR_ARG;
+  if (!S->reqs[id]->done) return FMM_PENDING;
   if (info) *info = S->reqs[id]->info;
   return (int)S->reqs[id]->info.status;
 }

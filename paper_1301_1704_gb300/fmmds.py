@@ -21,6 +21,7 @@ FMM_MAX_LEVEL = 21
 
 FMM_OK, FMM_ERR_ARG, FMM_ERR_DOMAIN, FMM_ERR_LEVEL = 0, 1, 2, 3
 FMM_ERR_OOM, FMM_ERR_TIMEOUT, FMM_ERR_CUDA, FMM_ERR_CAPACITY = 4, 5, 6, 7
+FMM_PENDING = 8
 
 FMM_FLAG_HOST_INPUT = 0x1
 FMM_FLAG_BOX_ORDER = 0x2
@@ -50,6 +51,12 @@ class TreeC(C.Structure):
         ("e4_off", C.c_void_p * _L), ("e4_idx", C.c_void_p * _L),
         ("sorted_src", C.c_void_p), ("sorted_recv", C.c_void_p),
     ]
+
+
+class SizesC(C.Structure):
+    _fields_ = [("workspace_bytes", C.c_uint64),
+                ("max_nbox_src", C.c_uint32 * _L), ("max_nbox_recv", C.c_uint32 * _L),
+                ("max_nnz_e2", C.c_uint64 * _L), ("max_nnz_e4", C.c_uint64 * _L)]
 
 
 class SetC(C.Structure):
@@ -110,7 +117,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 # Every function declared in include/fmmds.h.
 EXPORTS = (
     "fmm_create", "fmm_destroy", "fmm_build", "fmm_build_batched", "fmm_morton_keys",
-    "fmm_query_workspace",
+    "fmm_query_workspace", "fmm_query_sizes", "fmm_server_poll",
     "fmm_set_tuning", "fmm_get_tuning", "fmm_set_timing", "fmm_get_timing", "fmm_reset_timing",
     "fmm_last_launch_count", "fmm_status_string", "fmm_exclusive_scan_noalloc",
     "fmm_autotune", "fmm_e2_source_offsets", "fmm_gather_e2_sources", "fmm_box_types",
@@ -160,6 +167,8 @@ def _load():
     lib.fmm_morton_keys.restype = C.c_int
     lib.fmm_query_workspace.argtypes = [C.c_uint32, C.c_uint32, Params, _u64p]
     lib.fmm_query_workspace.restype = C.c_int
+    lib.fmm_query_sizes.argtypes = [C.c_uint32, C.c_uint32, Params, C.POINTER(SizesC)]
+    lib.fmm_query_sizes.restype = C.c_int
     lib.fmm_set_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
     lib.fmm_set_tuning.restype = C.c_int
     lib.fmm_get_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
@@ -207,6 +216,8 @@ def _load():
     lib.fmm_server_submit.restype = C.c_int
     lib.fmm_server_wait.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(RequestInfo)]
     lib.fmm_server_wait.restype = C.c_int
+    lib.fmm_server_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(RequestInfo)]
+    lib.fmm_server_poll.restype = C.c_int
     lib.fmm_server_run_trace.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32,
                                          C.POINTER(RequestInfo)]
     lib.fmm_server_run_trace.restype = C.c_int
@@ -545,9 +556,21 @@ class Context:
 def exclusive_scan_noalloc(counts, offsets, total=None, stream=None) -> None:
     """fmm_exclusive_scan_noalloc: offsets[0..n] from counts[0..n) (CUDA
     tensors of 4-byte integers, offsets one longer); allocates nothing."""
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t in (("counts", counts), ("offsets", offsets)):
+        if (not t.is_cuda or t.device.index != dev or not t.is_contiguous()
+                or t.element_size() != 4 or t.dtype.is_floating_point):
+            raise ValueError(f"{name} must be a contiguous 4-byte integer CUDA tensor "
+                             "on the current device")
     n = counts.numel()
     if offsets.numel() != n + 1:
         raise ValueError("offsets needs n + 1 entries")
+    if total is not None and (not total.is_cuda or total.device.index != dev
+                              or total.dtype not in (torch.int64, torch.uint64)
+                              or total.numel() < 1):
+        raise ValueError("total must be an int64 CUDA tensor of at least one element "
+                         "on the current device")
     st = _load().fmm_exclusive_scan_noalloc(
         C.c_void_p(counts.data_ptr() if n else 0), n, C.c_void_p(offsets.data_ptr()),
         C.c_void_p(total.data_ptr() if total is not None else 0),
@@ -563,6 +586,20 @@ def query_workspace(N: int, M: int, L: int | None = None, s: int | None = None, 
     if st != FMM_OK:
         raise FmmError(st, "fmm_query_workspace")
     return int(v.value)
+
+
+def query_sizes(N: int, M: int, L: int | None = None, s: int | None = None,
+                flags: int = 0) -> dict:
+    """fmm_query_sizes: the workspace bound and the per-level box and list
+    size bounds of a build of N sources and M receivers."""
+    v = SizesC()
+    p = Params(L if L is not None else -1, s if s is not None else 0, flags, 0)
+    st = _load().fmm_query_sizes(N, M, p, C.byref(v))
+    if st != FMM_OK:
+        raise FmmError(st, "fmm_query_sizes")
+    return {"workspace_bytes": int(v.workspace_bytes),
+            "max_nbox_src": list(v.max_nbox_src), "max_nbox_recv": list(v.max_nbox_recv),
+            "max_nnz_e2": list(v.max_nnz_e2), "max_nnz_e4": list(v.max_nnz_e4)}
 
 
 def status_string(code: int) -> str:
@@ -626,6 +663,16 @@ class Server:
         st = _load().fmm_server_wait(self._h, request_id, C.byref(inf))
         if st != FMM_OK:
             raise FmmError(st, "fmm_server_wait")
+        return _info_dict(inf)
+
+    def poll(self, request_id: int):
+        """The request's info once it is done, else None (does not block)."""
+        inf = RequestInfo()
+        st = _load().fmm_server_poll(self._h, request_id, C.byref(inf))
+        if st == FMM_PENDING:
+            return None
+        if st != FMM_OK:
+            raise FmmError(st, "fmm_server_poll")
         return _info_dict(inf)
 
     def step(self, system: int) -> dict:

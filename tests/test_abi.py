@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings(lib):
     from paper_1301_1704_gb300 import fmmds
-    for code in range(8):
+    for code in range(9):
         s = fmmds.status_string(code)
         assert s and s != "unknown status"
     assert fmmds.status_string(99) == "unknown status"
@@ -60,6 +60,21 @@ def test_query_workspace_host_only(lib):
     assert e.value.code == fmmds.FMM_ERR_LEVEL
     with pytest.raises(fmmds.FmmError):
         fmmds.query_workspace(10, 10, s=0)
+
+
+def test_query_sizes_host_only(lib):
+    from paper_1301_1704_gb300 import fmmds
+    q = fmmds.query_sizes(1 << 24, 1000, L=7)
+    assert q["workspace_bytes"] == fmmds.query_workspace(1 << 24, 1000, L=7)
+    assert q["max_nbox_src"][:8] == [1, 8, 64, 512, 4096, 32768, 262144, 2097152]
+    assert q["max_nbox_recv"][:8] == [1, 8, 64, 512, 1000, 1000, 1000, 1000]
+    assert q["max_nbox_src"][8] == 0 and q["max_nnz_e2"][1] == 0
+    assert q["max_nnz_e2"][7] == 27 * 1000 and q["max_nnz_e4"][7] == 189 * 1000
+    assert q["max_nnz_e4"][2] == 189 * 64
+    q = fmmds.query_sizes(5, 5, s=1)  # cluster-size mode: bounds of every level
+    assert q["max_nbox_src"][21] == 5
+    with pytest.raises(fmmds.FmmError):
+        fmmds.query_sizes(10, 10, L=22)
 
 
 def test_binding_refuses_without_library(monkeypatch, tmp_path):

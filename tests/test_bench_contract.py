@@ -11,7 +11,8 @@ from tests.conftest import ROOT
 
 def test_reference_arm_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0"],
+                        "--steps", "1", "--warmup", "0", "--points", str(1 << 18),
+                        "--level", "5"],
                        capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]

@@ -143,3 +143,59 @@ def test_server_argument_errors(lib):
         assert srv.tree(k).L == 3
     finally:
         srv.close()
+
+
+@pytest.mark.slow
+def test_served_full_size_systems_match_oracle(lib, orc):
+    """Config 5's real sizes: the benchmark's 1e6- and 1e7-point clump
+    systems (same seeds), depth from the initial state at s = 64, served
+    together for three steps; every step's points against the float64
+    oracle step, and the last step's tree of each system, whole, against the
+    oracle built from the served points."""
+    seed = workloads.CONFIG_SEEDS[5]
+    picks = [(4, 1_000_000), (6, 10_000_000)]  # (system index in the workload, size)
+    pts = [workloads.clumps(n, seed * 1000 + k) for k, n in picks]
+    Ls = _levels(lib, pts)
+    srv = lib.Server(0, workers=2, max_batch=8)
+    try:
+        ids = [srv.add_system(p, L, 0.1, seed=seed * 1000 + k)
+               for (k, _), p, L in zip(picks, pts, Ls)]
+        prev = [p.astype(np.float64) for p in pts]
+        for step in range(3):
+            rids = [srv.submit(i) for i in ids]
+            infos = [srv.wait(r) for r in rids]
+            for j, (i, inf) in enumerate(zip(ids, infos)):
+                assert inf["status"] == 0 and inf["step"] == step + 1
+                cur = srv.points(i)
+                want = D.displace(prev[j], seed * 1000 + picks[j][0], step, D.sigma_of(Ls[j]))
+                assert np.abs(cur - want).max() <= DISPLACE_TOL
+                prev[j] = cur.astype(np.float64)
+                if step == 2:
+                    got = srv.tree(i).numpy()
+                    compare_full(got, orc.build_tree(cur, cur, L=Ls[j], parallel=True), Ls[j])
+    finally:
+        srv.close()
+
+
+def test_server_poll(lib):
+    """fmm_server_poll never blocks: FMM_PENDING (None here) until the
+    request is done, then the same info as fmm_server_wait."""
+    import time
+    pts = _systems()
+    Ls = _levels(lib, pts)
+    srv = lib.Server(0, workers=1, max_batch=8)
+    try:
+        ids = [srv.add_system(p, L, 0.1, seed=50 + k) for k, (p, L) in enumerate(zip(pts, Ls))]
+        rids = [srv.submit(i) for i in ids for _ in range(3)]
+        t0 = time.time()
+        last = None
+        while last is None and time.time() - t0 < 60:
+            last = srv.poll(rids[-1])
+        assert last is not None and last["status"] == 0 and last["step"] == 3
+        for r in rids:
+            a, b = srv.poll(r), srv.wait(r)
+            assert a == b
+        with pytest.raises(lib.FmmError):
+            srv.poll(10 ** 9)
+    finally:
+        srv.close()

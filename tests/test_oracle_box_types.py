@@ -72,3 +72,59 @@ def test_two_nodes_against_geometry(orc, lpar):
             assert (ty[0][lcrit][k] == BT.ROOT) == (sides == {0, 1})
     for l in range(2, lcrit):
         assert np.all(ty[0][l] == BT.DOMESTIC)
+
+
+@pytest.mark.parametrize("lpar,seed", [(3, 37), (4, 38), (5, 39)])
+def test_split_through_lcrit_boxes_against_geometry(orc, lpar, seed):
+    """Owner = whether a box's x cell at l_par is >= s with s odd, so the
+    split cuts the l_crit boxes of one x column in two and leaves the others
+    whole on one side.  Every type of every level l_crit..L, for both nodes,
+    is checked against geometry alone: a box's children on / off J are the
+    l_par cells of the source points inside it and the side each lies on; the
+    M2L neighbours of a box are the boxes whose parents are adjacent to its
+    parent (max-norm distance <= 1) and that are not adjacent to it.  At
+    l_crit: no child on J -> IMPORT; children on both sides -> ROOT; else
+    EXPORT when some M2L neighbour has a child off J, else DOMESTIC."""
+    p, t = _tree(orc, n=3000, L=6, seed=seed)
+    L = t["L"]
+    lcrit = lpar - 1
+    s = (1 << (lpar - 1)) + 1
+    cpar = np.array([orc.decode(int(k), lpar) for k in t["src"]["key"][lpar]])
+    own = (cpar[:, 0] >= s).astype(np.uint32)
+    ty = [BT.box_types(t, lpar, own, j) for j in (0, 1)]
+    # point sides (the node owning each point's l_par cell)
+    pside = (_cells(p, lpar)[:, 0] >= s).astype(int)
+    seen = set()
+    for l in range(lcrit, L + 1):
+        c = np.array([orc.decode(int(k), l) for k in t["src"]["key"][l]])
+        pcl = _cells(p, l)
+        # the boxes are exactly the cells that hold points
+        assert {tuple(r) for r in c} == {tuple(r) for r in pcl}
+        d = np.abs(c[:, None, :] - c[None, :, :]).max(axis=2)
+        dp = np.abs((c[:, None, :] >> 1) - (c[None, :, :] >> 1)).max(axis=2)
+        m2l = (dp <= 1) & (d >= 2)
+        for j in (0, 1):
+            if l == lcrit:
+                on = np.zeros(len(c), bool)
+                off = np.zeros(len(c), bool)
+                for k in range(len(c)):
+                    sides = pside[np.all(pcl == c[k], axis=1)]
+                    on[k] = (sides == j).any()
+                    off[k] = (sides != j).any()
+                exp = on & ~off & (m2l & off[None, :]).any(axis=1)
+                want = np.where(~on, BT.IMPORT, np.where(on & off, BT.ROOT,
+                                                         np.where(exp, BT.EXPORT, BT.DOMESTIC)))
+            else:
+                side = ((c[:, 0] >> (l - lpar)) >= s).astype(int)
+                mine = side == j
+                exp = mine & (m2l & (side[None, :] != j)).any(axis=1)
+                imp = ~mine & (m2l & (side[None, :] == j)).any(axis=1)
+                want = np.where(exp, BT.EXPORT, np.where(mine, BT.DOMESTIC,
+                                                        np.where(imp, BT.IMPORT, BT.OTHERS)))
+            assert np.array_equal(ty[j][l], want), (lpar, l, j)
+            if l == lcrit:
+                seen |= set(int(v) for v in want)
+    # the split exercises every branch at l_crit (at level 2 every box that
+    # is not adjacent is an M2L neighbour, so no box there is DOMESTIC)
+    want_seen = {BT.IMPORT, BT.ROOT, BT.EXPORT} | ({BT.DOMESTIC} if lcrit >= 3 else set())
+    assert seen == want_seen, seen
