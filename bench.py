@@ -702,19 +702,29 @@ def main():
         configs["config1"] = small_config_section(ctx, stream, max(args.steps, 200))
         configs["config3"] = sparse_config_section(ctx, stream, args.steps, args.warmup,
                                                    not args.no_autotune)
+    nnz = {"e2": int(sum(tree.nnz_e2)), "e4": int(sum(tree.nnz_e4))}
+    tuning_now = ctx.tuning()
     batched = None
     if not args.no_batched:
         batched = batched_section(ctx, stream, args.steps, args.warmup, args.plain_steps)
     served = None
     if args.serve_steps > 0 and rank == 0:
-        served = served_section(ctx, args.serve_steps)
+        # the served workload gets the device to itself: this context's arena
+        # and PyTorch's cached blocks are released first
+        del tree
+        ctx.close()
+        torch.cuda.empty_cache()
+        sctx = fmmds.Context(local)
+        served = served_section(sctx, args.serve_steps)
+        sctx.close()
+        ctx = None
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "tuning": dict(ctx.tuning(), autotuned=autotuned is not None),
+            "tuning": dict(tuning_now, autotuned=autotuned is not None),
             "config": {"workload": WORKLOAD if full else
                        f"profiling case N=M={npts} uniform, L={level}", "N": npts, "M": npts, "L": level,
                        "seeds": list(SEEDS), "l2": "inputs larger than L2 (402 MB of xyz)",
@@ -724,7 +734,7 @@ def main():
             "clocks": clk,
             "roofline": roofline,
             "kernels": per_kernel,
-            "nnz": {"e2": int(sum(tree.nnz_e2)), "e4": int(sum(tree.nnz_e4))},
+            "nnz": nnz,
             "e2e": {"value": e2e_val, "unit": "Mpts/s", "h2d_bytes_per_step": 12 * pts_per_step,
                     "d2h_bytes_per_step": D2H_BYTES, "steps": args.e2e_steps},
         }
@@ -740,7 +750,8 @@ def main():
         if served is not None:
             line["served"] = served
         print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 

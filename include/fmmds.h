@@ -213,7 +213,7 @@ int fmm_query_sizes(uint32_t N, uint32_t M, fmm_params params, fmm_sizes* out);
  * points are ordered before the finishing sort inside the boxes:
  *   FMM_SORT_RTS         LSD radix passes, each: per-tile digit histograms,
  *                        one prefix sum, then a scatter with no waiting
- *                        between tiles (default);
+ *                        between tiles;
  *   FMM_SORT_ONESWEEP    radix passes, one kernel each, every tile finding
  *                        its offsets by decoupled look-back over the earlier
  *                        tiles;
@@ -222,10 +222,20 @@ int fmm_query_sizes(uint32_t N, uint32_t M, fmm_params params, fmm_sizes* out);
  *                        its prefix sum as the bookmarks (Alg. 3), one move;
  *                        used when every set's sort depth is at most 8 and
  *                        the histograms hold at most 2^28 cells (else RTS).
+ *   FMM_SORT_BUCKET      fixed-depth builds: the points are bucketed on
+ *                        coarse cells (a histogram in shared memory and
+ *                        atomic ranks per tile, the cells' prefix sum as
+ *                        their bookmarks -- Alg. 1 and 3 at a coarse level),
+ *                        then each bucket is sorted in shared memory by one
+ *                        block, which also emits the boxes of every level;
+ *                        a set whose bucket is too full for one block, and
+ *                        every cluster-size build, takes FMM_SORT_RTS
+ *                        (default).
  * All give the same result.  FMM_ERR_ARG for an unknown kind. */
 #define FMM_SORT_RTS 0u
 #define FMM_SORT_ONESWEEP 1u
 #define FMM_SORT_FIXED_GRID 2u
+#define FMM_SORT_BUCKET 3u
 /* sort_items: points per thread of a radix tile (4, 6, 7 or 8; 0 = 6): the
  * tile of the histogram, scatter, depth and Fixed-Grid kernels is 512 x
  * sort_items points.  Larger tiles mean fewer tiles and histogram entries but

@@ -64,7 +64,7 @@ struct fmm_ctx {
   std::vector<TimeAcc> acc;
   uint64_t launches = 0;
   uint64_t last_launches = 0;
-  fmm_tuning tuning{FMM_SORT_RTS, 6};
+  fmm_tuning tuning{FMM_SORT_BUCKET, 6};
   // graph mode
   bool graphs = false;         // capture builds (after the first) into CUDA graphs
   bool warm = false;           // a build has run eagerly on this context
@@ -81,6 +81,9 @@ struct fmm_ctx {
   // host-input copies of a pipelined build (see do_builds_on)
   cudaStream_t cstream = nullptr;
   cudaEvent_t cevent = nullptr;
+  // sets of the build in progress kept off the bucket path (a bucket of
+  // theirs was too full for one block)
+  std::vector<uint8_t> no_bucket;
 };
 
 namespace {
@@ -410,6 +413,7 @@ struct SetPlan {
   bool want_sorted = false;  // also the points in sorted order
   bool need_occ = false;  // used as a source
   uint32_t depth = 0;     // cluster-size mode: 1 + deepest level shared by points i, i + s
+  bool bucket = false;    // ordered and boxed by the bucket path (bucket.cu)
   Seg dev{};              // the device descriptor
   uint32_t cap[kLevels] = {};
 };
@@ -456,6 +460,7 @@ struct BuildMem {
   Slot* fin_slots = nullptr;
   Slot* crs_slots = nullptr;
   Slot* occ_slots = nullptr;
+  Slot* sx_slots = nullptr;
   uint32_t fin_units = 0, crs_units = 0, occ_units = 0;
 };
 
@@ -805,10 +810,170 @@ int depth_sets(fmm_ctx* c, std::vector<SetPlan*>& sets, const SortMem& m, uint32
   return FMM_OK;
 }
 
+// ---- bucket path (bucket.cu) ----------------------------------------------
+
+// Device tables of the bucket path of a build.
+struct BucketMem {
+  BkSet* bsets = nullptr;            // descriptors, one per bucket set
+  std::vector<BkSet> host;           // ... and their host copies
+  Slot* tile_slots = nullptr;        // count / scatter units of all bucket sets
+  uint32_t tiles = 0;
+  Slot* one_slots = nullptr;         // per bucket set k: Slot{k, 0} (one-set launches)
+  Slot* split_slots = nullptr;       // bucket slots of all bucket sets
+  Slot* box_slots = nullptr;         // sub-cell slots (8 a bucket slot)
+  uint32_t units = 0;                // bucket slots
+  uint32_t* ticket = nullptr;
+  int max_bl = 0, max_lb = 0;
+  uint32_t count() const { return (uint32_t)host.size(); }
+};
+
+// Bucket parameters of a set of n points boxed to depth Lb; false when the
+// bucket path cannot take it (too many points for level-4 buckets, more box
+// levels below the sub-cells than an item keeps, or a box-key order whose
+// boxes would span several sub-cells).
+bool bucket_params(uint32_t n, int Lb, bool exact, BkSet* b) {
+  std::memset(b, 0, sizeof(*b));
+  if (n == 0) return false;
+  // the mean sub-cell at most 3/4 of what one block sorts
+  const uint64_t avg = (uint64_t)kBkCap * 3 / 4;
+  int bl = 0;
+  while (bl < kBkMaxLevel && (uint64_t)n > (avg << (3 * (bl + 1)))) ++bl;
+  if ((uint64_t)n > (avg << (3 * (bl + 1)))) return false;
+  const int ib = n <= 1 ? 1 : 32 - __builtin_clz(n - 1);
+  const int kept = 61 - ib;  // key bits an item keeps below the sub-cell
+  const int below = Lb - bl - 1;
+  if (below > 0 && 3 * below > kept) return false;
+  if (exact && below < 0) return false;
+  b->n = n;
+  b->bl = bl;
+  b->Lb = Lb;
+  b->ib = ib;
+  if (exact) {
+    b->keep = ~0ull << (64 - 3 * (Lb - bl));  // levels bl+1 .. Lb
+    b->D = std::min(kBkGroupBits, 3 * below);
+    b->trunc = 0;
+  } else {
+    b->keep = ~((1ull << ib) - 1ull);
+    b->D = std::min(kBkGroupBits, std::min(kept, 60 - 3 * bl));
+    b->trunc = 63 - 3 * bl > 64 - ib ? 1 : 0;
+  }
+  const uint32_t cells = 1u << (3 * bl);
+  b->tile = std::max<uint32_t>(16384u, cells * 64u);
+  b->ntiles = (uint32_t)(((uint64_t)n + b->tile - 1) / b->tile);
+  b->nslot = std::min<uint32_t>(cells, n);
+  return true;
+}
+
+// Allocates and uploads the bucket path's tables for the sets flagged
+// `bucket` (their BkSet parameters come from bucket_params).
+int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
+  int err = FMM_OK;
+  BucketMem& m = *bm;
+  std::vector<Slot> tile_slots, one, split_slots, box_slots;
+  size_t zero_bytes = align_up(sizeof(uint32_t) * 4);  // the ticket
+  std::vector<size_t> zoff;
+  for (uint32_t i = 0; i < sets.size(); ++i) {
+    SetPlan& sp = sets[i];
+    if (!sp.bucket) continue;
+    BkSet b;
+    bucket_params(sp.n, sp.Lb, sp.exact, &b);
+    b.xyz = sp.xyz;
+    b.seg = i;
+    const uint32_t k = (uint32_t)m.host.size();
+    tile_slots.push_back(Slot{k, m.tiles, 0, 0});
+    one.push_back(Slot{k, 0, 0, 0});
+    split_slots.push_back(Slot{k, m.units, 0, 0});
+    box_slots.push_back(Slot{k, 8 * m.units, 0, 0});
+    m.tiles += b.ntiles;
+    m.units += b.nslot;
+    m.max_bl = std::max(m.max_bl, b.bl);
+    m.max_lb = std::max(m.max_lb, b.Lb);
+    zoff.push_back(zero_bytes);
+    zero_bytes += align_up(sizeof(uint32_t) * 9 * (1u << (3 * b.bl))) + align_up(sizeof(uint32_t) * 4) +
+                  align_up(sizeof(uint64_t) * kLevels * 8 * b.nslot);
+    m.host.push_back(b);
+    // the set's Seg fields the later stages read
+    Seg& d = sp.dev;
+    d.xyz = sp.xyz;
+    d.n = sp.n;
+    d.Ls = sp.Lb;
+    d.exact = sp.exact ? 1 : 0;
+  }
+  if (m.host.empty()) return FMM_OK;
+  char* zero = arena_get<char>(c, zero_bytes, &err);
+  if (err) return err;
+  m.ticket = reinterpret_cast<uint32_t*>(zero);
+  for (uint32_t k = 0; k < m.count(); ++k) {
+    BkSet& b = m.host[k];
+    const uint32_t cells = 1u << (3 * b.bl);
+    char* z = zero + zoff[k];
+    b.cnt = reinterpret_cast<uint32_t*>(z);
+    b.sct = b.cnt + cells;
+    z += align_up(sizeof(uint32_t) * 9 * cells);
+    b.info = reinterpret_cast<uint32_t*>(z);
+    z += align_up(sizeof(uint32_t) * 4);
+    b.status = reinterpret_cast<uint64_t*>(z);
+    b.tbase = arena_get<uint32_t>(c, (size_t)b.ntiles * cells, &err);
+    b.coff = arena_get<uint32_t>(c, cells, &err);
+    b.bcell = arena_get<uint32_t>(c, b.nslot, &err);
+    b.boff = arena_get<uint32_t>(c, (size_t)b.nslot + 1, &err);
+    b.items = arena_get<uint64_t>(c, b.n, &err);
+    b.items2 = arena_get<uint64_t>(c, b.n, &err);
+    b.soff = arena_get<uint32_t>(c, 8ull * b.nslot, &err);
+    b.scnt = arena_get<uint32_t>(c, 8ull * b.nslot, &err);
+    if (err) return err;
+  }
+  Upload up;
+  const size_t o_b = up.add(m.host.data(), m.host.size());
+  const size_t o_t = up.add(tile_slots.data(), tile_slots.size());
+  const size_t o_o = up.add(one.data(), one.size());
+  const size_t o_s = up.add(split_slots.data(), split_slots.size());
+  const size_t o_x = up.add(box_slots.data(), box_slots.size());
+  char* dev = upload(c, up, &err);
+  if (err) return err;
+  m.bsets = reinterpret_cast<BkSet*>(dev + o_b);
+  m.tile_slots = reinterpret_cast<Slot*>(dev + o_t);
+  m.one_slots = reinterpret_cast<Slot*>(dev + o_o);
+  m.split_slots = reinterpret_cast<Slot*>(dev + o_s);
+  m.box_slots = reinterpret_cast<Slot*>(dev + o_x);
+  return dev_zero(c, zero, zero_bytes);
+}
+
+// count -> plan -> scatter of bucket set k, or of all bucket sets (k < 0).
+// A one-set launch runs the set's tiles from unit 0 (slot {k, 0}).
+int bucket_sort(fmm_ctx* c, const BucketMem& m, int k) {
+  cudaStream_t s = c->stream;
+  const Slot* slots = k < 0 ? m.tile_slots : m.one_slots + k;
+  const uint32_t nsl = k < 0 ? m.count() : 1u;
+  const uint32_t tiles = k < 0 ? m.tiles : m.host[k].ntiles;
+  const int max_bl = k < 0 ? m.max_bl : m.host[k].bl;
+  {
+    Launch L(c, "bucket_count");
+    launch_bucket_count(m.bsets, slots, nsl, tiles, max_bl, c->st, s);
+  }
+  {
+    Launch L(c, "bucket_plan");
+    launch_bucket_plan(k < 0 ? m.bsets : m.bsets + k, nsl, c->st, s);
+  }
+  {
+    Launch L(c, "bucket_scatter");
+    launch_bucket_scatter(m.bsets, slots, nsl, tiles, max_bl, c->st, s);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// split of every bucket set's buckets into sub-cells (after their sorts).
+int bucket_split(fmm_ctx* c, const BucketMem& m) {
+  if (!m.units) return FMM_OK;
+  Launch L(c, "bucket_split");
+  launch_bucket_split(m.bsets, m.split_slots, m.count(), m.units, c->st, c->stream);
+  return cuda_status(cudaGetLastError());
+}
+
 // Box and list stages of a build over sorted `sets` (SetPlan::Lb and
 // JobPlan::L fixed).
 int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs,
-              const fmm_params& prm, Readback* rb) {
+              const fmm_params& prm, const BucketMem& bm, Readback* rb) {
   cudaStream_t s = c->stream;
   int err = FMM_OK;
   const uint64_t wait_ns = wait_ns_of(prm);
@@ -861,12 +1026,18 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     if (err) return err;
   }
 
-  // Box-stage slots.
-  std::vector<Slot> fin, crs, occ;
+  // Box-stage slots (the bucket path emits its sets' boxes itself; every
+  // set's finishing tiles serve the sorted points).
+  std::vector<Slot> fin, crs, occ, sx;
+  uint32_t sx_units = 0;
   for (uint32_t i = 0; i < nsets; ++i) {
-    fin.push_back(Slot{i, m.fin_units, 0, 0});
-    m.fin_units += sets[i].dev.btiles;
-    if (sets[i].Lb >= 1) {
+    sx.push_back(Slot{i, sx_units, 0, 0});
+    sx_units += sets[i].dev.btiles;
+    if (!sets[i].bucket) {
+      fin.push_back(Slot{i, m.fin_units, 0, 0});
+      m.fin_units += sets[i].dev.btiles;
+    }
+    if (sets[i].Lb >= 1 && !sets[i].bucket) {
       crs.push_back(Slot{i, m.crs_units, 0, 0});
       m.crs_units += coarse_tiles(sets[i].cap[sets[i].Lb]);
     }
@@ -895,6 +1066,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     const size_t o_fin = up.add(fin.data(), fin.size());
     const size_t o_crs = up.add(crs.data(), crs.size());
     const size_t o_occ = up.add(occ.data(), occ.size());
+    const size_t o_sx = up.add(sx.data(), sx.size());
     size_t o_jobs = 0, o_lvls = 0;
     std::vector<Job> jobs_host(njobs);
     if (with_lists) {
@@ -908,6 +1080,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     m.fin_slots = reinterpret_cast<Slot*>(dev + o_fin);
     m.crs_slots = reinterpret_cast<Slot*>(dev + o_crs);
     m.occ_slots = reinterpret_cast<Slot*>(dev + o_occ);
+    m.sx_slots = reinterpret_cast<Slot*>(dev + o_sx);
     if (with_lists) {
       m.jobs = reinterpret_cast<Job*>(dev + o_jobs);
       m.lvls = reinterpret_cast<ListLevel*>(dev + o_lvls);
@@ -986,7 +1159,13 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   if (async_lists) FMM_TRY(dev_zero(c, list_zero, list_zero_bytes));
 
   // ---- boxes, occupancy.
-  {
+  FMM_TRY(bucket_split(c, bm));
+  if (bm.units) {
+    Launch L(c, "bucket_boxes");
+    launch_bucket_boxes(bm.bsets, m.segs, bm.box_slots, bm.count(), bm.units, bm.max_lb, bm.ticket,
+                        c->st, wait_ns, s);
+  }
+  if (m.fin_units) {
     Launch L(c, "finish_boxes");
     launch_finish_boxes(m.segs, m.fin_slots, (uint32_t)fin.size(), m.fin_units, c->st, wait_ns, s);
   }
@@ -994,7 +1173,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   for (auto& sp : sets) any_sorted |= sp.want_sorted;
   if (any_sorted) {
     Launch L(c, "sorted_xyz");
-    launch_sorted_xyz(m.segs, m.fin_slots, (uint32_t)fin.size(), m.fin_units, c->st, s);
+    launch_sorted_xyz(m.segs, m.sx_slots, (uint32_t)sx.size(), sx_units, c->st, s);
   }
   if (m.crs_units) {
     int max_lb = 0;
@@ -1183,6 +1362,8 @@ struct PairIn {
 };
 
 int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes);
+void workspace_parts(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes,
+                     uint64_t* list_bytes);
 
 // The build of one or many (Src, Recv) pairs, outputs in outs[].
 int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params& prm,
@@ -1204,14 +1385,19 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   }
   if (points >= (1ull << 32)) return FMM_ERR_ARG;
 
-  uint64_t expect = 0;
+  // Arena reserved up front: the lists' capacity bound only while it is
+  // reserved as such (above kAsyncListBytes the lists are sized from the box
+  // counts and the arena grows by what they need).
+  uint64_t expect = 0, list_expect = 0;
   for (uint32_t k = 0; k < npairs; ++k) {
-    uint64_t b = 0;
+    uint64_t b = 0, lb = 0;
     fmm_params pk = prm;
     if (pairs[k].L >= 0) pk.L = pairs[k].L;
-    query_workspace(pairs[k].N, pairs[k].M, pk, &b);
+    workspace_parts(pairs[k].N, pairs[k].M, pk, &b, &lb);
     expect += b;
+    list_expect += lb;
   }
+  expect += std::min<uint64_t>(list_expect, kAsyncListBytes);
   FMM_TRY(arena_reset(c, c->peak_request > expect ? c->peak_request : expect));
   c->up_cursor = 0;
   c->seg = 0;
@@ -1298,12 +1484,29 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
     } else {
       sp.Ls = std::max(sort_level(sp.n, lb), lb);
     }
+    // The bucket path (sort kind FMM_SORT_BUCKET) takes fixed-depth sets it
+    // can hold; the others, and every set after a bucket overflowed, take
+    // the radix passes.
+    BkSet probe;
+    sp.bucket = c->tuning.sort_kind == FMM_SORT_BUCKET && !stall && !in_smode[i] &&
+                !(i < c->no_bucket.size() && c->no_bucket[i]) &&
+                bucket_params(sp.n, lb, sp.exact, &probe);
+    if (sp.bucket) {
+      sp.Lb = lb;
+      sp.Ls = lb;
+    }
   }
+  std::vector<SetPlan*> lsd;
+  for (auto& sp : sets)
+    if (!sp.bucket) lsd.push_back(&sp);
+  BucketMem bm;
+  FMM_TRY(bucket_setup(c, sets, &bm));
   {
     SortMem sm;
     if (pipelined) {
       // set i's copy, then its sort behind an event; copy i+1 is issued after
       // sort i's launches (a pageable copy holds the host meanwhile)
+      uint32_t kb = 0;
       for (size_t i = 0; i < sets.size(); ++i) {
         SetPlan& sp = sets[i];
         if (sp.n)
@@ -1311,12 +1514,17 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
                                    sizeof(float) * 3 * sp.n, cudaMemcpyHostToDevice, c->cstream));
         FMM_CUDA(cudaEventRecord(c->cevent, c->cstream));
         FMM_CUDA(cudaStreamWaitEvent(s, c->cevent, 0));
-        std::vector<SetPlan*> one{&sp};
-        SortMem si;
-        FMM_TRY(sort_sets(c, one, false, wait_ns, &si));
+        if (sp.bucket) {
+          FMM_TRY(bucket_sort(c, bm, (int)kb++));
+        } else {
+          std::vector<SetPlan*> one{&sp};
+          SortMem si;
+          FMM_TRY(sort_sets(c, one, false, wait_ns, &si));
+        }
       }
     } else {
-      FMM_TRY(sort_sets(c, all, stall, wait_ns, &sm));
+      if (bm.count()) FMM_TRY(bucket_sort(c, bm, -1));
+      if (!lsd.empty()) FMM_TRY(sort_sets(c, lsd, stall, wait_ns, &sm));
     }
     if (any_smode) {
       // Cluster-size mode (Sec. 2.1): the deepest level at which s + 1 sorted
@@ -1327,7 +1535,7 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
         if (in_smode[i]) ss.push_back(&sets[i]);
       // (measured over all sorted sets: the sort's descriptors are in that order)
       DevStatus st{};
-      FMM_TRY(depth_sets(c, all, sm, prm.s, &st));
+      FMM_TRY(depth_sets(c, lsd, sm, prm.s, &st));
       if (st.code) return (int)st.code;
       // A set still too full at its sort depth is sorted three levels deeper
       // (one or two more radix passes) and measured again; only if that is not
@@ -1371,6 +1579,7 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   // box-key order every set is sorted on exactly its box bits.
   std::vector<SetPlan*> resort;
   for (auto& sp : sets) {
+    if (sp.bucket) continue;  // ordered to its box depth already
     if (box_order) {
       if (!sp.exact || sp.Ls != sp.Lb) {
         sp.Ls = sp.Lb;
@@ -1389,9 +1598,27 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   }
 
   Readback rb;
-  FMM_TRY(run_build(c, sets, jobs, prm, &rb));
-
-  // Boxes that outran the finishing window: redo those orders in full.
+  const int rs = run_build(c, sets, jobs, prm, bm, &rb);
+  // A bucket too full for one block (status kStatusBucketFull; the sets
+  // carry bit 2): the build stopped there; build again with those sets on
+  // the radix path.
+  if (rs == (int)kStatusBucketFull) {
+    if (c->no_bucket.size() < sets.size()) c->no_bucket.resize(sets.size(), 0);
+    bool any = false;
+    for (uint32_t i = 0; i < sets.size(); ++i)
+      if (rb.seg_long[i] & 2u) {
+        c->no_bucket[i] = 1;
+        any = true;
+      }
+    if (!any) return FMM_ERR_CUDA;  // (cannot happen: the status comes with the bit)
+    cap_abort(c);
+    c->graph_build = false;
+    return do_builds_on(c, pairs, npairs, prm, outs);
+  }
+  FMM_TRY(rs);
+  // Boxes that outran the finishing window, or runs of points tied in an
+  // item's key bits too long for one thread (bit 1): redo those orders in
+  // full.
   std::vector<uint32_t> longs;
   for (uint32_t i = 0; i < sets.size(); ++i)
     if (rb.seg_long[i]) longs.push_back(i);
@@ -1438,7 +1665,9 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
       moved = true;
     }
   }
+  c->no_bucket.clear();
   const int st = do_builds_on(c, pairs, npairs, prm, outs);
+  c->no_bucket.clear();
   cap_abort(c);  // a build that failed inside a captured segment
   if (moved) {
     if (st != FMM_OK) cudaStreamSynchronize(c->stream);
@@ -1447,7 +1676,10 @@ int do_builds(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_params
   return st;
 }
 
-int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes) {
+// Arena bytes of a build of N sources and M receivers: everything but the
+// lists (*bytes), and the lists' capacity bound (*list_bytes).
+void workspace_parts(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes,
+                     uint64_t* list_bytes) {
   const int L = p.L >= 0 ? p.L : std::max(sort_level(std::max(N, M), 2), 2);
   uint64_t total = 64 << 10;
   const uint32_t ns[2] = {N, M};
@@ -1460,9 +1692,16 @@ int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes
     total += tiles * sizeof(TileRec) * 8 + 8 * 256;  // tile records, 8 passes
     for (int l = 0; l <= L; ++l) total += align_up(21ull * level_cap(ns[k], l) + 8) + 1024;
   }
-  for (int l = 2; l <= L; ++l)
-    total += align_up(4ull * (4 + 27 + 189) * level_cap(M, l) + 64) + 4096;
+  uint64_t lists = 0;
+  for (int l = 2; l <= L; ++l) lists += align_up(4ull * (4 + 27 + 189) * level_cap(M, l) + 64) + 4096;
   *bytes = total;
+  *list_bytes = lists;
+}
+
+int query_workspace(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* bytes) {
+  uint64_t rest = 0, lists = 0;
+  workspace_parts(N, M, p, &rest, &lists);
+  *bytes = rest + lists;
   return FMM_OK;
 }
 
@@ -1727,7 +1966,7 @@ int fmm_morton_keys(fmm_ctx* c, const float* xyz, uint32_t n, uint64_t* keys, vo
 }
 
 int fmm_set_tuning(fmm_ctx* c, const fmm_tuning* t) {
-  if (!c || !t || t->sort_kind > FMM_SORT_FIXED_GRID) return FMM_ERR_ARG;
+  if (!c || !t || t->sort_kind > FMM_SORT_BUCKET) return FMM_ERR_ARG;
   const uint32_t items = t->sort_items ? t->sort_items : 6;
   if (items != 4 && items != 6 && items != 7 && items != 8) return FMM_ERR_ARG;
   c->tuning = *t;
@@ -1752,11 +1991,16 @@ int fmm_autotune(fmm_ctx* c, const fmm_set* sets, uint32_t nsets, fmm_params par
   fmm_tuning win = saved;
   double win_ms = 1e300;
   int st = FMM_OK;
-  const uint32_t kinds[3] = {FMM_SORT_RTS, FMM_SORT_ONESWEEP, FMM_SORT_FIXED_GRID};
+  const uint32_t kinds[4] = {FMM_SORT_BUCKET, FMM_SORT_RTS, FMM_SORT_ONESWEEP, FMM_SORT_FIXED_GRID};
   const uint32_t items[4] = {4, 6, 7, 8};
+  // a cluster-size build orders its points by the radix passes whatever the
+  // kind (the bucket path needs the depth before it sorts)
+  bool fixed = params.L >= 0;
+  for (uint32_t k = 0; k < nsets; ++k) fixed &= params.L >= 0 || sets[k].L >= 0;
   for (uint32_t kind : kinds) {
     for (uint32_t it : items) {
       if (kind == FMM_SORT_ONESWEEP && it != 6) continue;  // onesweep keeps its own tile
+      if (kind == FMM_SORT_BUCKET && (it != 6 || !fixed)) continue;  // no radix tile
       c->tuning = fmm_tuning{kind, it};
       std::vector<double> ms;
       for (uint32_t r = 0; r <= trials && st == FMM_OK; ++r) {

@@ -423,10 +423,11 @@ __global__ void __launch_bounds__(256) occupancy_kernel(const Seg* __restrict__ 
     const uint32_t nb = sg.nbox[l] < sg.lv.cap[l] ? sg.nbox[l] : sg.lv.cap[l];
     const uint32_t* ch = sg.lv.child[l];
     const uint64_t* ck = sg.lv.key[l + 1];
+    const uint32_t nbc = sg.nbox[l + 1] < sg.lv.cap[l + 1] ? sg.nbox[l + 1] : sg.lv.cap[l + 1];
     uint8_t* occ = sg.lv.occ[l];
     for (uint32_t b = u * blockDim.x + threadIdx.x; b < nb; b += units * blockDim.x) {
       uint32_t m = 0;
-      const uint32_t c1 = ch[b + 1];
+      const uint32_t c1 = ch[b + 1] < nbc ? ch[b + 1] : nbc;  // (never above nbc in a whole tree)
       for (uint32_t c = ch[b]; c < c1; ++c) m |= 1u << (uint32_t)(ck[c] & 7u);
       occ[b] = (uint8_t)m;
     }

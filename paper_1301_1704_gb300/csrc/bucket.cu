@@ -1,0 +1,904 @@
+// bucket.cu -- the point order and every box level of a fixed-depth build,
+// by bucketing the points on coarse cells (sort kind FMM_SORT_BUCKET).
+//
+// Alg. 1 orders the points with a histogram of the finest boxes, atomic
+// ranks and one move; Alg. 3 scans that histogram for the bookmarks.  Here
+// the same ideas are applied at coarse levels, where the histograms fit in
+// shared memory, and inside each sub-cell, where the rest of the order is
+// finished in shared memory by one block that also emits the boxes:
+//
+//   count    per tile of points: a histogram of the level-bl cells in shared
+//            memory; one atomic per (tile, non-empty cell) reserves the
+//            tile's range inside the cell (Alg. 1's atomic ranks, taken per
+//            tile and cell instead of per point);
+//   plan     per set: the prefix sum of the cell counts -- the cells'
+//            bookmarks (Alg. 3) -- and the list of non-empty cells, the
+//            "buckets";
+//   scatter  per tile, in chunks: each point becomes one 8-byte item -- the
+//            key bits below its cell, left-aligned, over the point index --
+//            the chunk is grouped by cell in shared memory and each cell's
+//            run is stored contiguously after the tile's earlier runs;
+//   split    per bucket: its items go to its 8 sub-cells (level bl + 1) as
+//            coalesced runs, one level down;
+//   boxes    per sub-cell, one block: a counting sort of its items on their
+//            next key bits, whose group counts also give the non-empty boxes
+//            of the next three levels with their ranks and bookmarks (Alg. 3
+//            inside the sub-cell); each point's rank inside its group by (key
+//            bits, index) -- the order (Morton key, original index) -- gives
+//            its permutation entry; one decoupled look-back over the sub-cells
+//            per level gives the sub-cell's first box ranks; deeper levels,
+//            if any, come from the first differing level of the sorted items.
+//
+// Traffic per point: coordinates read twice (12 + 12 bytes), the item
+// written and read twice (8 + 8, 8 + 8), the permutation written (4).
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+__device__ __forceinline__ uint32_t bk_cells(int bl) { return 1u << (3 * bl); }
+
+// Bit i of v (v < 32) moved to bit 3i: the cell of level <= 5 from the top
+// bits of the three cell coordinates.
+__device__ __forceinline__ uint32_t spread5(uint32_t v) {
+  return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6) | ((v & 16u) << 8);
+}
+
+// The spread of every 11-bit value (bit i -> bit 3i), built in shared
+// memory by each block that forms full keys: a key is then six table reads.
+constexpr int kLutBits = 11;
+__device__ __forceinline__ void build_lut(uint32_t* lut) {
+  for (uint32_t v = threadIdx.x; v < (1u << kLutBits); v += blockDim.x) {
+    uint32_t s = 0;
+    for (int i = 0; i < kLutBits; ++i) s |= ((v >> i) & 1u) << (3 * i);
+    lut[v] = s;
+  }
+}
+__device__ __forceinline__ uint64_t lut_spread(const uint32_t* lut, uint32_t q) {
+  return (uint64_t)lut[q & 0x7ffu] | ((uint64_t)lut[q >> 11] << 33);
+}
+// The same key as morton_key (same quantisation).
+__device__ __forceinline__ uint64_t lut_key(const uint32_t* lut, float x, float y, float z,
+                                            bool* ok) {
+  uint32_t qx, qy, qz;
+  const bool a = quantize21(x, &qx), b = quantize21(y, &qy), c = quantize21(z, &qz);
+  *ok = a && b && c;
+  return lut_spread(lut, qx) | (lut_spread(lut, qy) << 1) | (lut_spread(lut, qz) << 2);
+}
+
+// Cell of level bl (<= 5) of a point, and whether it lies in [0, 1]^3.
+__device__ __forceinline__ uint32_t cell_of(float x, float y, float z, int bl, bool* ok) {
+  uint32_t qx, qy, qz;
+  const bool a = quantize21(x, &qx), b = quantize21(y, &qy), c = quantize21(z, &qz);
+  *ok = a && b && c;
+  const int sh = 21 - bl;
+  return spread5(qx >> sh) | (spread5(qy >> sh) << 1) | (spread5(qz >> sh) << 2);
+}
+
+// Item of a point with Morton key `key`: the key bits below its level-bl
+// cell, left-aligned and masked by `keep`, over the point index.
+__device__ __forceinline__ uint64_t bk_item(uint64_t key, int bl, uint64_t keep, uint32_t idx) {
+  return ((key << (1 + 3 * bl)) & keep) | idx;
+}
+
+// First level at which two items of one sub-cell of level bl1 differ (22:
+// not within the kept key bits).  The top three item bits are level bl1 + 1.
+__device__ __forceinline__ uint32_t bk_diff_level(uint64_t a, uint64_t b, uint64_t keep, int bl1) {
+  const uint64_t z = (a ^ b) & keep;
+  if (z == 0) return 22u;
+  const uint32_t d = (uint32_t)bl1 + 1u + (uint32_t)__clzll((long long)z) / 3u;
+  return d < 22u ? d : 22u;
+}
+
+// Four 16-bit counters in a word: ones in fields a..b (b - a <= 3).
+__device__ __forceinline__ uint64_t fields(int a, int b) {
+  if (b < a) return 0ull;
+  const uint64_t ones = 0x0001000100010001ull;
+  return (ones >> (16 * (3 - (b - a)))) << (16 * a);
+}
+__device__ __forceinline__ uint32_t field(uint64_t w, int f) {
+  return (uint32_t)(w >> (16 * f)) & 0xffffu;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// count: per tile, the histogram of the sub-cells (level bl + 1), the
+// tile's base in every cell (level bl) and the sub-cells' totals.
+__global__ void __launch_bounds__(kBkTileThreads) bucket_count_kernel(
+    const BkSet* __restrict__ bsets, const Slot* __restrict__ slots, uint32_t nslots,
+    DevStatus* st) {
+  extern __shared__ uint32_t s_h[];
+  const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
+  const BkSet& S = bsets[sl.seg];
+  const uint32_t t = blockIdx.x - sl.unit0;
+  const int bl = S.bl, bl1 = bl + 1;
+  const uint32_t cells = bk_cells(bl), subs = 8 * cells;
+  for (uint32_t c = threadIdx.x; c < subs; c += blockDim.x) s_h[c] = 0;
+  __syncthreads();
+  const uint64_t base = (uint64_t)t * S.tile;
+  const uint32_t cnt = (uint32_t)((S.n - base) < (uint64_t)S.tile ? (S.n - base) : S.tile);
+  const float* xyz = S.xyz + 3 * base;
+  bool bad = false;
+  uint32_t done = 0;
+  if ((reinterpret_cast<uintptr_t>(S.xyz) & 15u) == 0) {
+    // 4 points = 3 float4; tiles start at multiples of 4 points
+    const float4* v = reinterpret_cast<const float4*>(xyz);
+    for (uint32_t g = threadIdx.x; g < cnt / 4; g += blockDim.x) {
+      const float4 a = __ldcs(v + 3 * g), b = __ldcs(v + 3 * g + 1), c = __ldcs(v + 3 * g + 2);
+      bool ok0, ok1, ok2, ok3;
+      const uint32_t c0 = cell_of(a.x, a.y, a.z, bl1, &ok0);
+      const uint32_t c1 = cell_of(a.w, b.x, b.y, bl1, &ok1);
+      const uint32_t c2 = cell_of(b.z, b.w, c.x, bl1, &ok2);
+      const uint32_t c3 = cell_of(c.y, c.z, c.w, bl1, &ok3);
+      atomicAdd(&s_h[c0], 1u);
+      atomicAdd(&s_h[c1], 1u);
+      atomicAdd(&s_h[c2], 1u);
+      atomicAdd(&s_h[c3], 1u);
+      bad |= !(ok0 && ok1 && ok2 && ok3);
+    }
+    done = cnt & ~3u;
+  }
+  for (uint32_t j = done + threadIdx.x; j < cnt; j += blockDim.x) {
+    bool ok;
+    atomicAdd(&s_h[cell_of(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], bl1, &ok)], 1u);
+    bad |= !ok;
+  }
+  __syncthreads();
+  uint32_t* tb = S.tbase + (uint64_t)t * cells;
+  for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t h = s_h[8 * c + q];
+      if (h) atomicAdd(&S.sct[8 * c + q], h);
+      v += h;
+    }
+    if (v) tb[c] = atomicAdd(&S.cnt[c], v);  // cells the tile does not touch are never read
+  }
+  if (bad) set_error(st, FMM_ERR_DOMAIN);
+}
+
+// ---------------------------------------------------------------------------
+// plan: per set (one block each), the cells' bookmarks and the buckets.
+__global__ void __launch_bounds__(kBkPlanThreads) bucket_plan_kernel(const BkSet* __restrict__ bsets,
+                                                                    DevStatus* st) {
+  constexpr int W = kBkPlanThreads / 32;
+  constexpr int kPer = kBkMaxCells / kBkPlanThreads;  // cells per thread, at most
+  __shared__ uint64_t s_w[W];
+  __shared__ uint32_t s_max[W];
+  if (failed(st)) return;
+  const BkSet& S = bsets[blockIdx.x];
+  const uint32_t cells = bk_cells(S.bl);
+  const uint32_t per = (cells + kBkPlanThreads - 1) / kBkPlanThreads;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t c0 = threadIdx.x * per;
+  uint32_t v[kPer];
+  uint64_t sum = 0;  // low 32 bits: points; high 32 bits: non-empty cells
+  uint32_t mx = 0;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    v[k] = ((uint32_t)k < per && c0 + k < cells) ? S.cnt[c0 + k] : 0u;
+    sum += (uint64_t)v[k] | ((uint64_t)(v[k] != 0) << 32);
+    mx = v[k] > mx ? v[k] : mx;
+  }
+  uint64_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if (lane == 31) s_w[warp] = x;
+  if (lane == 0) s_max[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t run = 0;
+    uint32_t m = 0;
+    for (int w = 0; w < W; ++w) {
+      const uint64_t c = s_w[w];
+      s_w[w] = run;
+      run += c;
+      m = s_max[w] > m ? s_max[w] : m;
+    }
+    const uint32_t nbk = (uint32_t)(run >> 32);
+    S.info[0] = nbk;
+    S.info[1] = m;
+    S.boff[nbk] = S.n;
+  }
+  __syncthreads();
+  uint64_t e = s_w[warp] + x - sum;
+  uint32_t off = (uint32_t)e, b = (uint32_t)(e >> 32);
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    if ((uint32_t)k < per && c0 + k < cells) {
+      S.coff[c0 + k] = off;
+      if (v[k]) {
+        S.bcell[b] = c0 + k;
+        S.boff[b] = off;
+        uint32_t so = off;  // the bucket's sub-cells, in octant order
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t n8 = S.sct[8 * (c0 + k) + q];
+          S.soff[8 * b + q] = so;
+          S.scnt[8 * b + q] = n8;
+          so += n8;
+        }
+        ++b;
+      }
+      off += v[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// scatter: per tile, in chunks of kBkChunk points, every point's item to its
+// place inside its cell, each cell's part of a chunk stored as one run.
+// Shared memory: the key table, per cell the tile's next slot and the
+// chunk's count / first staged slot, the staged items and their cells.
+constexpr int kScThreads = 512;  // two blocks an SM: one loads while the other stores
+constexpr int kBkChunk = kScThreads * 8;
+constexpr size_t kBkScatterSmem = sizeof(uint32_t) * ((1u << kLutBits) + 3 * kBkMaxCells) +
+                                  sizeof(uint64_t) * kBkChunk + sizeof(uint16_t) * kBkChunk;
+
+__global__ void __launch_bounds__(kScThreads, 2) bucket_scatter_kernel(
+    const BkSet* __restrict__ bsets, const Slot* __restrict__ slots, uint32_t nslots,
+    const DevStatus* st) {
+  constexpr int W = kScThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* s_item = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* lut = reinterpret_cast<uint32_t*>(s_item + kBkChunk);
+  uint32_t* s_at = lut + (1u << kLutBits);  // per cell: the tile's next slot
+  uint32_t* s_cc = s_at + kBkMaxCells;      // per cell: the chunk's count, then first staged slot
+  uint32_t* s_c0 = s_cc + kBkMaxCells;      // ... its first staged slot
+  uint16_t* s_cell = reinterpret_cast<uint16_t*>(s_c0 + kBkMaxCells);
+  __shared__ uint32_t s_wsum[W];
+  if (failed(st)) return;
+  const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
+  const BkSet& S = bsets[sl.seg];
+  const uint32_t t = blockIdx.x - sl.unit0;
+  const int bl = S.bl;
+  const uint32_t cells = bk_cells(bl);
+  const int sh = 63 - 3 * bl;
+  const uint64_t keep = S.keep;
+  const uint32_t* tb = S.tbase + (uint64_t)t * cells;
+  build_lut(lut);
+  for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) {
+    s_at[c] = S.coff[c] + tb[c];  // (garbage for cells the tile does not touch: never read)
+    s_cc[c] = 0;
+  }
+  __syncthreads();
+  const uint64_t base = (uint64_t)t * S.tile;
+  const uint32_t cnt = (uint32_t)((S.n - base) < (uint64_t)S.tile ? (S.n - base) : S.tile);
+  const float* xyz = S.xyz + 3 * base;
+  const bool vec = (reinterpret_cast<uintptr_t>(S.xyz) & 15u) == 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* items = S.items;
+  for (uint32_t c0 = 0; c0 < cnt; c0 += kBkChunk) {
+    const uint32_t m = cnt - c0 < (uint32_t)kBkChunk ? cnt - c0 : (uint32_t)kBkChunk;
+    // 1. items and cells of the chunk's points: thread takes points
+    //    4 (tid + kScThreads k) .. + 3, k = 0, 1
+    uint64_t it[8];
+    uint32_t ce[8], rk[8];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t j0 = 4 * (threadIdx.x + kScThreads * k);  // chunk-local
+      float p[12];
+      if (vec && j0 + 4 <= m) {
+        const float4* v = reinterpret_cast<const float4*>(xyz + 3 * (uint64_t)(c0 + j0));
+        const float4 a = __ldcs(v), b = __ldcs(v + 1), c = __ldcs(v + 2);
+        p[0] = a.x; p[1] = a.y; p[2] = a.z; p[3] = a.w; p[4] = b.x; p[5] = b.y;
+        p[6] = b.z; p[7] = b.w; p[8] = c.x; p[9] = c.y; p[10] = c.z; p[11] = c.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 12; ++q)
+          p[q] = (j0 + q / 3 < m) ? xyz[3 * (uint64_t)(c0 + j0) + q] : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * k + q;
+        bool ok;
+        const uint64_t key = lut_key(lut, p[3 * q], p[3 * q + 1], p[3 * q + 2], &ok);
+        ce[i] = (uint32_t)(key >> sh);
+        it[i] = bk_item(key, bl, keep, (uint32_t)(base + c0 + j0 + q));
+        rk[i] = (j0 + q < m) ? atomicAdd(&s_cc[ce[i]], 1u) : 0u;
+      }
+    }
+    __syncthreads();
+    // 2. first staged slot of each cell: a prefix sum of the chunk's counts
+    {
+      constexpr int kPer = kBkMaxCells / kScThreads;  // 8
+      uint32_t v[kPer], sum = 0;
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const uint32_t c = threadIdx.x * kPer + k;
+        v[k] = c < cells ? s_cc[c] : 0u;
+        sum += v[k];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_wsum[warp] = x;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        const uint32_t w = lane < W ? s_wsum[lane] : 0u;
+        uint32_t y = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+          if (lane >= o) y += z;
+        }
+        if (lane < W) s_wsum[lane] = y - w;
+      }
+      __syncthreads();
+      uint32_t e = s_wsum[warp] + x - sum;
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const uint32_t c = threadIdx.x * kPer + k;
+        if (c < cells) s_c0[c] = e;
+        e += v[k];
+      }
+    }
+    __syncthreads();
+    // 3. stage the chunk grouped by cell
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t j0 = 4 * (threadIdx.x + kScThreads * k);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * k + q;
+        if (j0 + q < m) {
+          const uint32_t at = s_c0[ce[i]] + rk[i];
+          s_item[at] = it[i];
+          s_cell[at] = (uint16_t)ce[i];
+        }
+      }
+    }
+    __syncthreads();
+    // 4. runs out: staged slot a of cell c goes to the tile's next slot of c
+    //    plus its place in the cell's run (slots beyond n would mean
+    //    coordinates that changed since the count)
+    for (uint32_t a = threadIdx.x; a < m; a += kScThreads) {
+      const uint32_t c = s_cell[a];
+      const uint32_t pos = s_at[c] + (a - s_c0[c]);
+      if (pos < S.n) items[pos] = s_item[a];
+    }
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < cells; c += kScThreads) {
+      s_at[c] += s_cc[c];
+      s_cc[c] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// split: one block per bucket.  The bucket's items are read once and stored
+// as the runs of its sub-cells (the next octant, level bl + 1; their sizes
+// come from the count), one level down (the sub-cell's octant shifted out of
+// the key bits): a streaming pass with coalesced runs.
+constexpr int kSplitThreads = 512;  // two or more blocks an SM
+constexpr int kSplitItems = 7;  // a warp's 224 items keep each octant count below 256
+constexpr int kSplitChunk = kSplitThreads * kSplitItems;
+
+__global__ void __launch_bounds__(kSplitThreads) bucket_split_kernel(
+    const BkSet* __restrict__ bsets, const Slot* __restrict__ slots, uint32_t nslots,
+    const DevStatus* st) {
+  constexpr int W = kSplitThreads / 32;
+  __shared__ uint64_t s_wt[W];     // per warp: its octant counts, 8-bit fields
+  __shared__ uint32_t s_wb[W][8];  // per warp and octant: first slot
+  __shared__ uint32_t s_base[8];   // per octant: the next free slot
+  if (failed(st)) return;
+  const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
+  const BkSet& S = bsets[sl.seg];
+  const uint32_t b = blockIdx.x - sl.unit0;
+  if (b >= S.info[0]) return;
+  const uint32_t off0 = S.boff[b], cnt = S.boff[b + 1] - off0;
+  const uint64_t* __restrict__ src = S.items + off0;
+  uint64_t* __restrict__ dst = S.items2 + off0;
+  const uint64_t keep = S.keep, imask = (1ull << S.ib) - 1ull;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  // The sub-cells' first slots, from the plan.
+  if (threadIdx.x < 8) s_base[threadIdx.x] = S.soff[8 * b + threadIdx.x] - off0;
+  __syncthreads();
+
+  // The move, a chunk at a time.  A thread takes kSplitItems consecutive
+  // items; its per-octant counts (8-bit fields of a 64-bit word) are scanned
+  // across the warp and the warps, so that each octant's items of the chunk
+  // land as one run, in chunk order.
+  for (uint32_t c0 = 0; c0 < cnt; c0 += kSplitChunk) {
+    uint64_t it[kSplitItems];
+    const uint32_t i0 = c0 + threadIdx.x * kSplitItems;
+#pragma unroll
+    for (int k = 0; k < kSplitItems; ++k) it[k] = i0 + k < cnt ? src[i0 + k] : 0ull;
+    uint64_t mine = 0;  // this thread's counts
+#pragma unroll
+    for (int k = 0; k < kSplitItems; ++k)
+      if (i0 + k < cnt) mine += 1ull << (8 * (uint32_t)(it[k] >> 61));
+    uint64_t x = mine;  // inclusive scan over the warp (fields stay below 256)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wt[warp] = x;
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      const uint32_t q = threadIdx.x;
+      uint32_t at = s_base[q];
+      for (int w = 0; w < W; ++w) {
+        s_wb[w][q] = at;
+        at += (uint32_t)(s_wt[w] >> (8 * q)) & 0xffu;
+      }
+      s_base[q] = at;
+    }
+    __syncthreads();
+    uint64_t run = x - mine;  // items of each octant before this thread's, in the warp
+#pragma unroll
+    for (int k = 0; k < kSplitItems; ++k) {
+      if (i0 + k < cnt) {
+        const uint64_t v = it[k];
+        const uint32_t q = (uint32_t)(v >> 61);
+        dst[s_wb[warp][q] + ((uint32_t)(run >> (8 * q)) & 0xffu)] = ((v & keep) << 3) | (v & imask);
+        run += 1ull << (8 * q);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// boxes: one block per sub-cell, in sub-cell order (tickets).
+
+// Block-wide sums of one packed word per thread: the exclusive prefix of
+// this thread (returned) and the total (*tot).
+template <int W>
+__device__ __forceinline__ uint64_t block_scan64(uint64_t v, uint64_t* s_w, uint64_t* tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t run = 0;
+    for (int w = 0; w < W; ++w) {
+      const uint64_t c = s_w[w];
+      s_w[w] = run;
+      run += c;
+    }
+    s_w[W] = run;
+  }
+  __syncthreads();
+  const uint64_t r = s_w[warp] + x - v;
+  *tot = s_w[W];
+  __syncthreads();  // s_w is reused by the next call
+  return r;
+}
+
+// Flags and exclusive ranks of the non-empty cells of the levels bl1 + m
+// (m = 1 .. kBkHistLevels) inside a sub-cell: level m at [(8^m - 8) / 7, ...).
+constexpr int kBkHistLevels = 3;
+constexpr int kBkHistCells = 8 + 64 + 512;
+__device__ __forceinline__ int hoff(int m) { return ((1 << (3 * m)) - 8) / 7; }
+
+__global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
+    const BkSet* __restrict__ bsets, const Seg* __restrict__ segs, const Slot* __restrict__ slots,
+    uint32_t nslots, uint32_t* ticket, DevStatus* st, uint64_t wait_ns) {
+  constexpr int W = kBkThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* A = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* B = A + kBkCap;
+  uint32_t* gs = reinterpret_cast<uint32_t*>(B + kBkCap);  // group counts, then starts [2^D + 1]
+  uint8_t* dd = reinterpret_cast<uint8_t*>(B);             // first differing levels (deep levels)
+  __shared__ uint32_t s_t, s_abort, s_tie;
+  __shared__ uint64_t s_w[W + 1];
+  __shared__ uint32_t s_R[kLevels], s_C[kLevels];
+  __shared__ __align__(8) uint8_t s_fl[kBkHistCells];  // non-empty flags
+  __shared__ uint16_t s_pre[kBkHistCells];              // exclusive ranks
+
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    s_t = atomicAdd(ticket, 1u);
+    s_abort = failed(st) ? 1u : 0u;
+    s_tie = 0;
+  }
+  __syncthreads();
+  if (s_abort) return;  // an earlier kernel failed: leave the outputs alone
+  const uint32_t t = s_t;
+  const Slot sl = slots[find_slot(slots, nslots, t)];
+  const BkSet& S = bsets[sl.seg];
+  const uint32_t u = t - sl.unit0;  // sub-cell slot of the set: bucket b, octant j
+  const uint32_t b = u >> 3, j = u & 7u;
+  const uint32_t nbk = S.info[0];
+  if (b >= nbk) return;  // past the set's last non-empty cell
+  const Seg& G = segs[S.seg];
+  const int bl = S.bl, bl1 = bl + 1, Lb = S.Lb, ib = S.ib, D = S.D;
+  const uint64_t imask = (1ull << ib) - 1ull, keep1 = S.keep << 3;
+  const uint32_t nsub = 8 * S.nslot;
+  uint64_t* const status = S.status;  // [kLevels][nsub]: one chain of sub-cells per level
+  const uint32_t n_j = S.scnt[u], offj = S.soff[u];
+  const uint32_t cell = S.bcell[b], cell1 = cell * 8 + j;
+  // a non-empty sub-cell precedes this one in the bucket
+  const bool sib = __syncthreads_or(tid < (int)j && S.scnt[8 * b + tid] > 0);
+  // The first point of the sub-cell opens a box at every level from the
+  // first one at which it differs from the point before it in the set.
+  uint32_t d0 = 0;
+  if (sib) {
+    d0 = (uint32_t)bl1;
+  } else if (b > 0) {
+    const uint32_t x = cell ^ S.bcell[b - 1];  // non-zero: distinct cells
+    d0 = (uint32_t)bl - (uint32_t)(31 - __clz((int)x)) / 3u;
+  }
+  if (n_j > (uint32_t)kBkCap) {
+    // More points than a block sorts: the host builds this set again by the
+    // radix path.  The build stops here (later kernels see the status and
+    // leave their outputs alone); empty counts are published so that later
+    // sub-cells do not wait.
+    if (tid == 0) {
+      atomicOr(G.seg_long, 2u);
+      atomicExch(&st->seg_long, 1u);
+      set_error(st, kStatusBucketFull);
+    }
+    for (int l = tid; l <= Lb; l += kBkThreads)
+      st_relaxed(status + (uint64_t)l * nsub + u, u == 0 ? kFlagIncl : kFlagAgg);
+    return;
+  }
+
+  // 1. The sub-cell's items (all loads in flight together).
+  {
+    const uint64_t* src = S.items2 + offj;
+    uint64_t v[kBkItems];
+#pragma unroll
+    for (int k = 0; k < kBkItems; ++k) {
+      const uint32_t p = tid + k * kBkThreads;
+      v[k] = p < n_j ? __ldcs(src + p) : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < kBkItems; ++k) {
+      const uint32_t p = tid + k * kBkThreads;
+      if (p < n_j) A[p] = v[k];
+    }
+  }
+  const uint32_t ng = 1u << D;
+  for (uint32_t q = tid; q <= ng; q += kBkThreads) gs[q] = 0;
+  __syncthreads();
+
+  // 2. Group counts (the top D item bits) with each point's rank in its
+  // group (an unstable counting sort), and the groups' starts.
+  const int gsh = 64 - D;
+  uint32_t rk[kBkItems];
+#pragma unroll
+  for (int k = 0; k < kBkItems; ++k) {
+    if (k * kBkThreads >= (int)n_j) break;
+    const uint32_t p = tid + k * kBkThreads;
+    if (p < n_j) rk[k] = atomicAdd(&gs[D ? (uint32_t)(A[p] >> gsh) : 0u], 1u);
+  }
+  __syncthreads();
+  {
+    constexpr int kPer = (1 << kBkGroupBits) / kBkThreads;  // 4 entries a thread
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t q = tid * kPer + k;
+      v[k] = q < ng ? gs[q] : 0u;
+      sum += v[k];
+    }
+    uint64_t tot;
+    uint32_t e = (uint32_t)block_scan64<W>(sum, s_w, &tot);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t q = tid * kPer + k;
+      if (q < ng) gs[q] = e;
+      e += v[k];
+    }
+    if (tid == 0) gs[ng] = n_j;
+  }
+  __syncthreads();
+
+  // 3. The boxes of levels bl1 + 1 .. lh from the group counts (Alg. 3 on
+  // the sub-cell): a level-lh cell holds the groups [c << gpc, (c + 1) <<
+  // gpc); its flag is set when they hold points, a coarser cell's when one
+  // of its 8 children's is; ranks are exclusive counts of set flags.
+  const int nm = (Lb - bl1) < kBkHistLevels ? (Lb - bl1) : kBkHistLevels;  // may be <= 0
+  const int lh = bl1 + (nm > 0 ? nm : 0);
+  const bool deep = Lb > lh;
+  if (tid < kLevels) s_C[tid] = (tid <= Lb && tid <= bl1 && n_j > 0 && d0 <= (uint32_t)tid) ? 1u : 0u;
+  if (nm > 0) {
+    const int gpc = D - 3 * nm;  // group bits below a level-lh cell
+    const uint32_t ncell = 1u << (3 * nm);
+    if (tid < ncell) s_fl[hoff(nm) + tid] = gs[(tid + 1) << gpc] != gs[tid << gpc];
+    __syncthreads();
+    for (int m = nm - 1; m >= 1; --m) {
+      if (tid < (1u << (3 * m)))
+        s_fl[hoff(m) + tid] = *reinterpret_cast<const uint64_t*>(&s_fl[hoff(m + 1) + 8 * tid]) != 0;
+      __syncthreads();
+    }
+    uint64_t c = 0;
+    if (tid < ncell)
+      for (int m = 1; m <= nm; ++m) {
+        const int sh = 3 * (nm - m);
+        if ((tid & ((1u << sh) - 1)) == 0) c += (uint64_t)s_fl[hoff(m) + (tid >> sh)] << (16 * (m - 1));
+      }
+    uint64_t tot;
+    const uint64_t ex = block_scan64<W>(c, s_w, &tot);
+    if (tid < ncell)
+      for (int m = 1; m <= nm; ++m) {
+        const int sh = 3 * (nm - m);
+        if ((tid & ((1u << sh) - 1)) == 0) s_pre[hoff(m) + (tid >> sh)] = (uint16_t)field(ex, m - 1);
+      }
+    if (tid == 0)
+      for (int m = 1; m <= nm; ++m) s_C[bl1 + m] = field(tot, m - 1);
+  }
+  __syncthreads();
+  // the counts of levels <= lh are final: publish them before the sort
+  if (tid <= lh && tid <= Lb)
+    st_relaxed(status + (uint64_t)tid * nsub + u, (u == 0 ? kFlagIncl : kFlagAgg) | s_C[tid]);
+
+  // 4. The sort: the counting sort's scatter, then each point's rank in its
+  // group by the whole item (key bits, index).  A point's place in the
+  // sub-cell is its group's start plus that rank: its permutation entry is
+  // written from there.  The sorted items themselves are kept only where
+  // they are needed (deep levels, tied key bits).
+#pragma unroll
+  for (int k = 0; k < kBkItems; ++k) {
+    if (k * kBkThreads >= (int)n_j) break;
+    const uint32_t p = tid + k * kBkThreads;
+    if (p < n_j) {
+      const uint64_t x = A[p];
+      B[gs[D ? (uint32_t)(x >> gsh) : 0u] + rk[k]] = x;
+    }
+  }
+  __syncthreads();
+  uint32_t* const perm = G.perm;
+  const uint64_t hi = ~imask;
+  const bool keepA = deep;
+  bool tie = false;
+  for (uint32_t p = tid; p < n_j; p += kBkThreads) {
+    const uint64_t x = B[p];
+    const uint32_t g = D ? (uint32_t)(x >> gsh) : 0u;
+    const uint32_t q0 = gs[g], q1 = gs[g + 1];
+    uint32_t r = 0;
+    for (uint32_t q = q0; q < q1; ++q) {
+      const uint64_t y = B[q];
+      r += y < x;
+      tie |= q != p && ((x ^ y) & hi) == 0;
+    }
+    perm[offj + q0 + r] = (uint32_t)(x & imask);
+    if (keepA) A[q0 + r] = x;
+  }
+  if (S.trunc && __syncthreads_or(tie)) {
+    // Points whose kept key bits tie but whose full keys may differ (keys
+    // cut short to make room for the index): the sorted items are formed
+    // again, each tied run is put in (full key, index) order by one thread,
+    // the full keys recomputed from the coordinates, and the permutation is
+    // written again.  Rare: two points in one cell of level about 17.
+    if (!keepA) {
+      for (uint32_t p = tid; p < n_j; p += kBkThreads) {
+        const uint64_t x = B[p];
+        const uint32_t g = D ? (uint32_t)(x >> gsh) : 0u;
+        const uint32_t q0 = gs[g], q1 = gs[g + 1];
+        uint32_t r = 0;
+        for (uint32_t q = q0; q < q1; ++q) r += B[q] < x;
+        A[q0 + r] = x;
+      }
+      __syncthreads();
+    }
+    for (uint32_t p = tid + 1; p < n_j; p += kBkThreads) {
+      if (((A[p] ^ A[p - 1]) & hi) != 0) continue;
+      if (p >= 2 && ((A[p - 1] ^ A[p - 2]) & hi) == 0) continue;  // not the run's second point
+      const uint32_t q0 = p - 1;
+      uint32_t e = p + 1;
+      while (e < n_j && ((A[e] ^ A[q0]) & hi) == 0) ++e;
+      if (e - q0 > kBkTieMax) {
+        atomicOr(G.seg_long, 1u);  // the host redoes this set's order with a full sort
+        atomicExch(&st->seg_long, 1u);
+        continue;
+      }
+      for (uint32_t q = q0; q < e; ++q) {
+        const uint32_t i = (uint32_t)(A[q] & imask);
+        bool ok;
+        B[q] = morton_key(S.xyz[3ull * i], S.xyz[3ull * i + 1], S.xyz[3ull * i + 2], &ok);
+      }
+      // insertion sort by (full key, index); the run starts in index order
+      for (uint32_t q = q0 + 1; q < e; ++q) {
+        const uint64_t kx = B[q], ix = A[q];
+        uint32_t r = q;
+        while (r > q0 && (B[r - 1] > kx || (B[r - 1] == kx && A[r - 1] > ix))) {
+          B[r] = B[r - 1];
+          A[r] = A[r - 1];
+          --r;
+        }
+        B[r] = kx;
+        A[r] = ix;
+      }
+      for (uint32_t q = q0; q < e; ++q) perm[offj + q] = (uint32_t)(A[q] & imask);
+    }
+  }
+  __syncthreads();
+
+  // 5. Levels deeper than lh (only for deep trees): box starts from the
+  // first differing level of every sorted point, counted by groups of three
+  // levels, each with the level above it (for the parents), in 16-bit
+  // fields: thread tid owns the points [tid * ipt, tid * ipt + ipt).
+  const uint32_t ipt = (n_j + kBkThreads - 1) / kBkThreads;
+  const uint32_t p0 = tid * ipt, p1 = p0 + ipt < n_j ? p0 + ipt : n_j;
+  if (deep) {
+    for (uint32_t p = tid; p < n_j; p += kBkThreads)
+      dd[p] = (uint8_t)(p == 0 ? d0 : bk_diff_level(A[p], A[p - 1], keep1, bl1));
+    __syncthreads();
+    for (int g0 = lh + 1; g0 <= Lb; g0 += 3) {
+      const int g1 = g0 + 2 < Lb ? g0 + 2 : Lb;
+      uint64_t c = 0;
+      for (uint32_t p = p0; p < p1; ++p) {
+        const int d = dd[p];
+        if (d <= g1) c += fields((d > g0 - 1 ? d : g0 - 1) - (g0 - 1), g1 - (g0 - 1));
+      }
+      uint64_t tot;
+      block_scan64<W>(c, s_w, &tot);
+      if (tid == 0)
+        for (int l = g0; l <= g1; ++l) {
+          s_C[l] = field(tot, l - (g0 - 1));
+          st_relaxed(status + (uint64_t)l * nsub + u, (u == 0 ? kFlagIncl : kFlagAgg) | s_C[l]);
+        }
+    }
+    __syncthreads();
+  }
+
+  // 6. Box ranks: a decoupled look-back over the set's sub-cells, per level.
+  for (int l = tid >> 5; l <= Lb; l += W) {
+    uint64_t* chain = status + (uint64_t)l * nsub;
+    uint64_t prev = 0;
+    if (u > 0) {
+      prev = lookback_warp(chain, u, 1, st, wait_ns);
+      if (lane == 0) st_relaxed(chain + u, kFlagIncl | (prev + s_C[l]));
+    }
+    if (lane == 0) s_R[l] = (uint32_t)prev;
+  }
+  __syncthreads();
+  if (tid == 0 && u > 0 && ld_relaxed_u32(&st->abort)) s_abort = 1;
+  __syncthreads();
+  if (s_abort) return;  // a wait gave up: ranks may be wrong, write nothing
+
+  // 7. Outputs: the set's totals (last sub-cell slot of the last bucket);
+  // the boxes starting at point 0 at levels <= bl1; the boxes of levels
+  // bl1 + 1 .. lh, one thread per cell; the deeper boxes.
+  if (b == nbk - 1 && j == 7 && tid <= Lb) {
+    const uint32_t tot = s_R[tid] + s_C[tid];
+    G.nbox[tid] = tot;
+    if (tot <= G.lv.cap[tid]) {
+      G.lv.off[tid][tot] = S.n;
+      if (tid < Lb) G.lv.child[tid][tot] = s_R[tid + 1] + s_C[tid + 1];
+    }
+  }
+  if (tid == 0 && n_j > 0) {
+    const int top = Lb < bl1 ? Lb : bl1;
+    for (int l = (int)d0; l <= top; ++l) {
+      const uint32_t rank = s_R[l];
+      if (rank >= G.lv.cap[l]) continue;
+      G.lv.key[l][rank] = (uint64_t)cell1 >> (3 * (bl1 - l));
+      G.lv.off[l][rank] = offj;
+      if (l >= 1) {
+        const bool up = d0 <= (uint32_t)(l - 1);
+        const uint32_t pr = up ? s_R[l - 1] : s_R[l - 1] - 1u;
+        G.lv.parent[l][rank] = pr;
+        if (up && pr < G.lv.cap[l - 1]) G.lv.child[l - 1][pr] = rank;
+      }
+    }
+  }
+  if (nm > 0 && tid < (1u << (3 * nm))) {
+    const int gpc = D - 3 * nm;
+    for (int m = 1; m <= nm; ++m) {
+      const int sh = 3 * (nm - m);
+      if ((tid & ((1u << sh) - 1)) != 0) continue;
+      const uint32_t c = tid >> sh;
+      if (!s_fl[hoff(m) + c]) continue;
+      const int l = bl1 + m;
+      const uint32_t within = s_pre[hoff(m) + c];
+      const uint32_t rank = s_R[l] + within;
+      if (rank >= G.lv.cap[l]) continue;
+      G.lv.key[l][rank] = ((uint64_t)cell1 << (3 * m)) | c;
+      G.lv.off[l][rank] = offj + gs[c << (gpc + 3 * (nm - m))];
+      const uint32_t pr = m == 1 ? s_R[bl1] : s_R[l - 1] + s_pre[hoff(m - 1) + (c >> 3)];
+      G.lv.parent[l][rank] = pr;
+      // the first non-empty child of its parent starts the parent's children
+      const uint32_t first = m == 1 ? 0u : s_pre[hoff(m) + (c & ~7u)];
+      if (within == first && pr < G.lv.cap[l - 1]) G.lv.child[l - 1][pr] = rank;
+    }
+  }
+  if (deep) {
+    for (int g0 = lh + 1; g0 <= Lb; g0 += 3) {
+      const int g1 = g0 + 2 < Lb ? g0 + 2 : Lb;
+      const int f0 = g0 - 1;  // field 0: the level above the group
+      uint64_t c = 0;
+      for (uint32_t p = p0; p < p1; ++p) {
+        const int d = dd[p];
+        if (d <= g1) c += fields((d > f0 ? d : f0) - f0, g1 - f0);
+      }
+      uint64_t tot;
+      uint64_t ex = block_scan64<W>(c, s_w, &tot);  // starts before this thread's first point
+      for (uint32_t p = p0; p < p1; ++p) {
+        const int d = dd[p];
+        if (d > g1) continue;
+        const uint64_t x = A[p];
+        for (int l = d > g0 ? d : g0; l <= g1; ++l) {
+          const uint32_t rank = s_R[l] + field(ex, l - f0);
+          if (rank >= G.lv.cap[l]) continue;
+          G.lv.key[l][rank] = ((uint64_t)cell1 << (3 * (l - bl1))) | (x >> (64 - 3 * (l - bl1)));
+          G.lv.off[l][rank] = offj + p;
+          const bool up = d <= l - 1;
+          const uint32_t pr = s_R[l - 1] + field(ex, l - 1 - f0) - (up ? 0u : 1u);
+          G.lv.parent[l][rank] = pr;
+          if (up && pr < G.lv.cap[l - 1]) G.lv.child[l - 1][pr] = rank;
+        }
+        ex += fields((d > f0 ? d : f0) - f0, g1 - f0);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+void launch_bucket_count(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
+                         int max_bl, DevStatus* st, cudaStream_t s) {
+  if (tiles == 0) return;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(uint32_t) * 8 * kBkMaxCells));
+    return true;
+  }();
+  (void)attr;
+  const size_t smem = sizeof(uint32_t) * 8 * (1u << (3 * max_bl));
+  bucket_count_kernel<<<tiles, kBkTileThreads, smem, s>>>(bsets, slots, nslots, st);
+}
+
+void launch_bucket_plan(const BkSet* bsets, uint32_t nsets, DevStatus* st, cudaStream_t s) {
+  if (nsets == 0) return;
+  bucket_plan_kernel<<<nsets, kBkPlanThreads, 0, s>>>(bsets, st);
+}
+
+void launch_bucket_scatter(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
+                           int max_bl, DevStatus* st, cudaStream_t s) {
+  if (tiles == 0) return;
+  (void)max_bl;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kBkScatterSmem);
+    return true;
+  }();
+  (void)attr;
+  bucket_scatter_kernel<<<tiles, kScThreads, kBkScatterSmem, s>>>(bsets, slots, nslots, st);
+}
+
+void launch_bucket_split(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t units,
+                         DevStatus* st, cudaStream_t s) {
+  if (units == 0) return;
+  bucket_split_kernel<<<units, kSplitThreads, 0, s>>>(bsets, slots, nslots, st);
+}
+
+void launch_bucket_boxes(const BkSet* bsets, const Seg* segs, const Slot* slots, uint32_t nslots,
+                         uint32_t units, int max_lb, uint32_t* ticket, DevStatus* st,
+                         uint64_t wait_ns, cudaStream_t s) {
+  if (units == 0) return;
+  (void)max_lb;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(bucket_boxes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kBkSmem);
+    return true;
+  }();
+  (void)attr;
+  bucket_boxes_kernel<<<units * 8, kBkThreads, kBkSmem, s>>>(bsets, segs, slots, nslots, ticket, st,
+                                                             wait_ns);
+}
+
+}  // namespace fmm

@@ -22,6 +22,11 @@ struct DevStatus {
   uint32_t pad;
 };
 
+// Internal code (never returned by the ABI): a bucket held more points than
+// a block sorts; the build stops and the host builds again with the radix
+// path for the sets concerned.
+constexpr uint32_t kStatusBucketFull = 0x100u;
+
 __device__ __forceinline__ void set_error(DevStatus* st, uint32_t code) {
   atomicCAS(&st->code, 0u, code);
 }
@@ -364,6 +369,37 @@ struct ListLevel {
   uint64_t* total;   // [2] scanned totals of the level (capacity check)
 };
 
+// One point set on the bucket path (bucket.cu): the points are bucketed on
+// the cells of level bl, each bucket is split into its 8 sub-cells (level
+// bl + 1), and each sub-cell is sorted, and its boxes emitted, by one block.
+// Device-resident; built on the host.
+struct BkSet {
+  const float* xyz;  // [n][3]
+  uint32_t n;
+  int bl;            // cell level of the buckets (0..4)
+  int Lb;            // box depth
+  int ib;            // bits of the point index at the bottom of an item
+  int D;             // group bits of a sub-cell's counting sort
+  int trunc;         // items hold fewer key bits than lie below the cell
+  uint64_t keep;     // key bits an item keeps (box-key order: down to Lb only)
+  uint32_t tile;     // points of a count / scatter tile
+  uint32_t ntiles;
+  uint32_t* cnt;     // [8^bl] points per cell (zeroed before the count)
+  uint32_t* sct;     // [8^(bl+1)] points per sub-cell (zeroed before the count)
+  uint32_t* tbase;   // [ntiles][8^bl] a tile's first slot inside each cell
+  uint32_t* coff;    // [8^bl] the cells' first slots (bookmarks)
+  uint32_t* bcell;   // [nslot] non-empty cells, ascending
+  uint32_t* boff;    // [nslot + 1] their bookmarks
+  uint32_t* info;    // [4]: non-empty cells, largest cell
+  uint64_t* items;   // [n] the points, bucketed
+  uint64_t* items2;  // [n] ... and split into sub-cells
+  uint32_t* soff;    // [8 * nslot] sub-cell bookmarks
+  uint32_t* scnt;    // [8 * nslot] sub-cell sizes
+  uint64_t* status;  // [kLevels][8 * nslot] look-back words of the box ranks (zeroed)
+  uint32_t nslot;    // min(8^bl, n): bucket slots
+  uint32_t seg;      // the set's index among the build's sets (its Seg)
+};
+
 // ---------------------------------------------------------------------------
 // Tunables of the kernels.
 constexpr int kSortThreads = 512;
@@ -382,6 +418,18 @@ constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 constexpr int kListThreads = 256;
+
+constexpr int kBkTileThreads = 1024;                // count / scatter blocks
+constexpr int kBkPlanThreads = 1024;
+constexpr int kBkThreads = 512;                     // a sub-cell's block (8 sub-cells a bucket)
+constexpr int kBkItems = 12;
+constexpr int kBkCap = kBkThreads * kBkItems;       // 6144 points sorted by one block
+constexpr int kBkGroupBits = 11;                    // groups of a sub-cell's counting sort
+constexpr int kBkMaxLevel = 4;                      // bucket cells of level 4 at most
+constexpr int kBkMaxCells = 1 << (3 * kBkMaxLevel);  // 4096
+constexpr uint32_t kBkTieMax = 1024;                // longest run of tied items one thread orders
+constexpr size_t kBkSmem =
+    2 * sizeof(uint64_t) * kBkCap + sizeof(uint32_t) * ((1 << kBkGroupBits) + 4);
 
 // Radix passes (8-bit digits) that sort the top 3*Ls key bits.
 __host__ __device__ inline int passes_for(int Ls) { return (3 * Ls + kRadixBits - 1) / kRadixBits; }
@@ -499,6 +547,22 @@ void launch_list_count(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
                        const ListLevel* lvls, DevStatus* st, cudaStream_t s);
 void launch_list_fill(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
                       const ListLevel* lvls, bool codes, DevStatus* st, cudaStream_t s);
+
+// Bucket path (bucket.cu).  count and scatter: units = tiles of the slots'
+// sets (slot seg = BkSet index); plan: one block per set; split: units =
+// bucket slots (slot unit0 = the set's first bucket slot); boxes: units =
+// bucket slots as for split, 8 blocks each (one per sub-cell), taken in
+// order by ticket (slot unit0 = the set's first sub-cell slot).
+void launch_bucket_count(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
+                         int max_bl, DevStatus* st, cudaStream_t s);
+void launch_bucket_plan(const BkSet* bsets, uint32_t nsets, DevStatus* st, cudaStream_t s);
+void launch_bucket_scatter(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
+                           int max_bl, DevStatus* st, cudaStream_t s);
+void launch_bucket_split(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t units,
+                         DevStatus* st, cudaStream_t s);
+void launch_bucket_boxes(const BkSet* bsets, const Seg* segs, const Slot* slots, uint32_t nslots,
+                         uint32_t units, int max_lb, uint32_t* ticket, DevStatus* st,
+                         uint64_t wait_ns, cudaStream_t s);
 
 // Morton keys of n points (public fmm_morton_keys).
 void launch_keys(const float* xyz, uint32_t n, uint64_t* keys, DevStatus* st, cudaStream_t s);

@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(kListThreads, 8) list_count_kernel(const Seg* 
     const uint32_t tot = warp_sum(__popc(q.occ));
     lo = warp_sum(lo);
     hi = warp_sum(hi);
-    const uint32_t c0 = a.rchild_up[p], c1 = a.rchild_up[p + 1];
+    const uint32_t c0 = a.rchild_up[p];
+    const uint32_t c1 = min(a.rchild_up[p + 1], c0 + 8u);  // (at most 8 in a whole tree)
     const uint32_t r = c0 + lane;
     if (r < c1) {
       const uint32_t rho = (uint32_t)(a.rkey[r] & 7u);
@@ -420,7 +421,8 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
     uint32_t* const out4 = J.out4;
     // The receiver children of p (at most 8): lane j fetches child j's octant
     // and list starts up front, so their loads overlap the neighbour loads.
-    const uint32_t c0 = J.a.rchild_up[p], c1 = J.a.rchild_up[p + 1];
+    const uint32_t c0 = J.a.rchild_up[p];
+    const uint32_t c1 = min(J.a.rchild_up[p + 1], c0 + 8u);  // (at most 8 in a whole tree)
     uint32_t my_rho = 0, my_o2 = 0, my_o4 = 0;
     if (c0 + lane < c1) {
       my_rho = (uint32_t)(J.a.rkey[c0 + lane] & 7u);

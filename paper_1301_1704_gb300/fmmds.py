@@ -130,6 +130,7 @@ FMM_NOALLOC_SCAN_MAX = 1 << 26
 FMM_SORT_RTS = 0
 FMM_SORT_ONESWEEP = 1
 FMM_SORT_FIXED_GRID = 2
+FMM_SORT_BUCKET = 3
 
 
 class Tuning(C.Structure):

@@ -100,7 +100,7 @@ def test_batched_workload_full_size(ctx, orc):
         trees = ctx.build_batched(batch, s=64)
         got_all = [t.numpy() for t in trees]
     finally:
-        ctx.set_tuning(fmmds.FMM_SORT_RTS)
+        ctx.set_tuning(fmmds.FMM_SORT_BUCKET)
     for i, p in enumerate(sets):
         got = got_all[i]
         want = orc.build_tree(p, p, L=-1, s=64, parallel=len(p) > 50000)

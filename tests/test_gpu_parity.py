@@ -63,7 +63,7 @@ def test_morton_keys_match_oracle(ctx, orc):
         assert np.array_equal(got, orc.keys(p))
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
 def test_sort_kinds_agree(ctx, orc, kind):
     from paper_1301_1704_gb300 import fmmds
     src = workloads.clumps(150000, 30, nclumps=10, sigma=0.03)
@@ -76,7 +76,7 @@ def test_sort_kinds_agree(ctx, orc, kind):
         got, want = run_both(ctx, orc, p, p[:5000].copy(), 2)
         compare_full(got, want, 2)
     finally:
-        ctx.set_tuning(fmmds.FMM_SORT_RTS)
+        ctx.set_tuning(fmmds.FMM_SORT_BUCKET)
 
 
 def test_config1_full_tree_brute(ctx, orc):
@@ -174,7 +174,7 @@ def test_host_input_flag(ctx, orc):
         compare_full(t, want, 5)
         assert np.array_equal(t["sorted_src"], orc.sorted_points(src, want["src"]["perm"]))
     finally:
-        ctx.set_tuning(fmmds.FMM_SORT_RTS)
+        ctx.set_tuning(fmmds.FMM_SORT_BUCKET)
 
 
 @pytest.mark.parametrize("s", [1, 8, 64, 300])
@@ -291,7 +291,7 @@ def test_full_size_configs(ctx, orc, cfg):
     try:
         got = ctx.build(s, r, L=L).numpy()
     finally:
-        ctx.set_tuning(fmmds.FMM_SORT_RTS)
+        ctx.set_tuning(fmmds.FMM_SORT_BUCKET)
     del s, r
     want = orc.build_tree(src, recv, L=L, mode=orc.MODE_STENCIL, parallel=True)
     compare_full(got, want, L)
@@ -374,7 +374,7 @@ def test_sort_tile_sizes_agree(ctx, orc, items):
         want = orc.build_tree(src, recv, L=-1, s=40)
         compare_full(got, want, want["L"])
     finally:
-        ctx.set_tuning(fmmds.FMM_SORT_RTS, 6)
+        ctx.set_tuning(fmmds.FMM_SORT_BUCKET, 6)
 
 
 def test_autotune_picks_a_candidate(ctx, orc):
@@ -392,7 +392,7 @@ def test_autotune_picks_a_candidate(ctx, orc):
             want = orc.build_tree(p, p, L=-1, s=64)
             compare_full(t.numpy(), want, want["L"])
     finally:
-        ctx.set_tuning(fmmds.FMM_SORT_RTS, 6)
+        ctx.set_tuning(fmmds.FMM_SORT_BUCKET, 6)
     with pytest.raises(fmmds.FmmError):
         ctx.set_tuning(fmmds.FMM_SORT_RTS, 5)
 
@@ -418,3 +418,64 @@ def test_box_types_match_oracle(ctx, orc, lpar):
         want = BT.box_types(want_tree, lpar, owner, node)
         for l in range(2, L + 1):
             assert np.array_equal(got[l].cpu().numpy(), want[l]), (lpar, node, l)
+
+
+# ---------------------------------------------------------------------------
+# The bucket path (the default sort kind): cases that reach its rare branches.
+
+def test_bucket_ties_below_the_kept_key_bits(ctx, orc):
+    """An item keeps the key bits down to about level 18 (the rest of its 64
+    bits hold the point index); points tied there but apart further down are
+    ordered by their full keys recomputed from the coordinates, and runs of
+    more tied points than one thread orders fall back to a full sort."""
+    rng = np.random.default_rng(77)
+    base = workloads.uniform(120000, 78)
+    h = 2.0 ** -21
+    parts = [base]
+    for run in (2, 3, 17, 300):  # tied runs within one level-19 cell
+        c = np.floor(rng.random(3) * 2 ** 19) / 2 ** 19
+        off = rng.integers(0, 4, size=(run, 3)) * h
+        parts.append((c + off).astype(np.float32))
+    src = np.ascontiguousarray(np.concatenate(parts)[rng.permutation(sum(len(p) for p in parts))])
+    recv = workloads.uniform(50000, 79)
+    got, want = run_both(ctx, orc, src, recv, 6)
+    compare_full(got, want, 6)
+    # a run longer than one thread's share: the full-sort fallback
+    c = np.floor(rng.random(3) * 2 ** 19) / 2 ** 19
+    long_run = (c + rng.integers(0, 4, size=(3000, 3)) * h).astype(np.float32)
+    src2 = np.ascontiguousarray(np.concatenate([base, long_run]))
+    got, want = run_both(ctx, orc, src2, recv, 5)
+    compare_full(got, want, 5)
+
+
+def test_bucket_overflow_falls_back_to_radix(ctx, orc):
+    """A cell holding more points than one block sorts sends its set to the
+    radix path (the build is redone), alone or next to a set that fits."""
+    tight = workloads.clumps(60000, 80, nclumps=2, sigma=0.002)
+    loose = workloads.uniform(60000, 81)
+    for src, recv, L in ((tight, loose, 6), (loose, tight, 4), (tight, tight, 8)):
+        got, want = run_both(ctx, orc, src, recv, L)
+        compare_full(got, want, L)
+
+
+@pytest.mark.parametrize("n,L", [(1, 0), (5, 3), (4608, 2), (4609, 5), (36865, 1), (300001, 9),
+                                 (2359297, 6)])
+def test_bucket_cell_levels(ctx, orc, n, L):
+    """Bucket cell levels 0..4 (the level follows n), box depths above and
+    below the cell level, ragged tails of the count and scatter tiles."""
+    src = workloads.uniform(n, 1000 + n)
+    recv = workloads.sphere(max(1, n // 3), 2000 + n)
+    got, want = run_both(ctx, orc, src, recv, L)
+    compare_full(got, want, L)
+
+
+def test_bucket_batched_sets_of_every_size(ctx, orc):
+    """One batched fixed-level build whose sets sit at different bucket cell
+    levels (and one too full for a block, on the radix path), all in the same
+    launches."""
+    pts = [workloads.uniform(n, 3000 + n) for n in (1, 700, 5000, 40000, 330000)]
+    pts.append(workloads.clumps(50000, 3100, nclumps=1, sigma=0.001))
+    devs = [_dev(p) for p in pts]
+    trees = ctx.build_batched([(d, d) for d in devs], L=6)
+    for p, t in zip(pts, trees):
+        compare_full(t.numpy(), orc.build_tree(p, p, L=6), 6)

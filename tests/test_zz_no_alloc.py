@@ -48,7 +48,8 @@ def _scan(fm, counts_np):
 
 
 def _want(counts_np):
-    c = np.concatenate([[0], np.cumsum(counts_np.astype(np.uint64), dtype=np.uint64)])
+    c = np.concatenate([np.zeros(1, np.uint64),
+                        np.cumsum(counts_np.astype(np.uint64), dtype=np.uint64)])
     return (c & np.uint64(0xffffffff)).astype(np.uint32), int(c[-1])
 
 
