@@ -228,9 +228,11 @@ int fmm_query_sizes(uint32_t N, uint32_t M, fmm_params params, fmm_sizes* out);
  *                        their bookmarks -- Alg. 1 and 3 at a coarse level),
  *                        then each bucket is sorted in shared memory by one
  *                        block, which also emits the boxes of every level;
- *                        a set whose bucket is too full for one block, and
- *                        every cluster-size build, takes FMM_SORT_RTS
- *                        (default).
+ *                        a set whose bucket is too full for one block (the
+ *                        build is then redone, and the context builds the
+ *                        same input pointer and size by the radix passes
+ *                        directly until its tuning changes), and every
+ *                        cluster-size build, takes FMM_SORT_RTS (default).
  * All give the same result.  FMM_ERR_ARG for an unknown kind. */
 #define FMM_SORT_RTS 0u
 #define FMM_SORT_ONESWEEP 1u

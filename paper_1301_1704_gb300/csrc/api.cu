@@ -84,6 +84,11 @@ struct fmm_ctx {
   // sets of the build in progress kept off the bucket path (a bucket of
   // theirs was too full for one block)
   std::vector<uint8_t> no_bucket;
+  // Point sets (input pointer, size) whose bucket was too full for one block
+  // in an earlier build on this context: they take the radix path directly,
+  // saving the stopped attempt (resident time-stepped systems keep their
+  // pointer and their clumps).  Cleared when the tuning changes.
+  std::vector<std::pair<const float*, uint32_t>> full_sets;
 };
 
 namespace {
@@ -406,6 +411,7 @@ uint64_t wait_ns_of(const fmm_params& p) {
 
 struct SetPlan {
   const float* xyz = nullptr;
+  const float* orig = nullptr;  // the caller's pointer to the points
   uint32_t n = 0;
   int Lb = 0, Ls = 0;
   bool full = false;      // sort all 63 bits (the order needs no finishing window)
@@ -1411,6 +1417,7 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   auto add_set = [&](const float* p, uint32_t n) {
     SetPlan sp;
     sp.xyz = p;
+    sp.orig = p;
     sp.n = n;
     sets.push_back(sp);
     return (uint32_t)sets.size() - 1;
@@ -1488,7 +1495,10 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
     // can hold; the others, and every set after a bucket overflowed, take
     // the radix passes.
     BkSet probe;
-    sp.bucket = c->tuning.sort_kind == FMM_SORT_BUCKET && !stall && !in_smode[i] &&
+    const bool was_full =
+        std::find(c->full_sets.begin(), c->full_sets.end(), std::make_pair(sp.orig, sp.n)) !=
+        c->full_sets.end();
+    sp.bucket = c->tuning.sort_kind == FMM_SORT_BUCKET && !stall && !in_smode[i] && !was_full &&
                 !(i < c->no_bucket.size() && c->no_bucket[i]) &&
                 bucket_params(sp.n, lb, sp.exact, &probe);
     if (sp.bucket) {
@@ -1609,6 +1619,11 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
       if (rb.seg_long[i] & 2u) {
         c->no_bucket[i] = 1;
         any = true;
+        const auto key = std::make_pair(sets[i].orig, sets[i].n);
+        if (std::find(c->full_sets.begin(), c->full_sets.end(), key) == c->full_sets.end()) {
+          if (c->full_sets.size() >= 1024) c->full_sets.erase(c->full_sets.begin());
+          c->full_sets.push_back(key);
+        }
       }
     if (!any) return FMM_ERR_CUDA;  // (cannot happen: the status comes with the bit)
     cap_abort(c);
@@ -1970,6 +1985,7 @@ int fmm_set_tuning(fmm_ctx* c, const fmm_tuning* t) {
   const uint32_t items = t->sort_items ? t->sort_items : 6;
   if (items != 4 && items != 6 && items != 7 && items != 8) return FMM_ERR_ARG;
   c->tuning = *t;
+  c->full_sets.clear();
   c->tuning.sort_items = items;
   return FMM_OK;
 }
@@ -2002,6 +2018,7 @@ int fmm_autotune(fmm_ctx* c, const fmm_set* sets, uint32_t nsets, fmm_params par
       if (kind == FMM_SORT_ONESWEEP && it != 6) continue;  // onesweep keeps its own tile
       if (kind == FMM_SORT_BUCKET && (it != 6 || !fixed)) continue;  // no radix tile
       c->tuning = fmm_tuning{kind, it};
+      c->full_sets.clear();
       std::vector<double> ms;
       for (uint32_t r = 0; r <= trials && st == FMM_OK; ++r) {
         cudaEventRecord(a, s);
@@ -2027,6 +2044,7 @@ int fmm_autotune(fmm_ctx* c, const fmm_set* sets, uint32_t nsets, fmm_params par
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   c->tuning = st == FMM_OK ? win : saved;
+  c->full_sets.clear();
   if (st != FMM_OK) return st;
   *best = win;
   if (best_ms) *best_ms = win_ms;
