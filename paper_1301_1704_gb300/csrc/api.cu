@@ -825,7 +825,6 @@ struct BucketMem {
   Slot* tile_slots = nullptr;        // count / scatter units of all bucket sets
   uint32_t tiles = 0;
   Slot* one_slots = nullptr;         // per bucket set k: Slot{k, 0} (one-set launches)
-  Slot* split_slots = nullptr;       // bucket slots of all bucket sets
   Slot* box_slots = nullptr;         // sub-cell slots (8 a bucket slot)
   uint32_t units = 0;                // bucket slots
   uint32_t* ticket = nullptr;
@@ -864,7 +863,7 @@ bool bucket_params(uint32_t n, int Lb, bool exact, BkSet* b) {
     b->trunc = 63 - 3 * bl > 64 - ib ? 1 : 0;
   }
   const uint32_t cells = 1u << (3 * bl);
-  b->tile = std::max<uint32_t>(16384u, cells * 64u);
+  b->tile = std::max<uint32_t>(8192u, cells * 32u);
   b->ntiles = (uint32_t)(((uint64_t)n + b->tile - 1) / b->tile);
   b->nslot = std::min<uint32_t>(cells, n);
   return true;
@@ -875,7 +874,7 @@ bool bucket_params(uint32_t n, int Lb, bool exact, BkSet* b) {
 int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
   int err = FMM_OK;
   BucketMem& m = *bm;
-  std::vector<Slot> tile_slots, one, split_slots, box_slots;
+  std::vector<Slot> tile_slots, one, box_slots;
   size_t zero_bytes = align_up(sizeof(uint32_t) * 4);  // the ticket
   std::vector<size_t> zoff;
   for (uint32_t i = 0; i < sets.size(); ++i) {
@@ -888,14 +887,13 @@ int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
     const uint32_t k = (uint32_t)m.host.size();
     tile_slots.push_back(Slot{k, m.tiles, 0, 0});
     one.push_back(Slot{k, 0, 0, 0});
-    split_slots.push_back(Slot{k, m.units, 0, 0});
     box_slots.push_back(Slot{k, 8 * m.units, 0, 0});
     m.tiles += b.ntiles;
     m.units += b.nslot;
     m.max_bl = std::max(m.max_bl, b.bl);
     m.max_lb = std::max(m.max_lb, b.Lb);
     zoff.push_back(zero_bytes);
-    zero_bytes += align_up(sizeof(uint32_t) * 9 * (1u << (3 * b.bl))) + align_up(sizeof(uint32_t) * 4) +
+    zero_bytes += align_up(sizeof(uint32_t) * 8 * (1u << (3 * b.bl))) + align_up(sizeof(uint32_t) * 4) +
                   align_up(sizeof(uint64_t) * kLevels * 8 * b.nslot);
     m.host.push_back(b);
     // the set's Seg fields the later stages read
@@ -911,20 +909,18 @@ int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
   m.ticket = reinterpret_cast<uint32_t*>(zero);
   for (uint32_t k = 0; k < m.count(); ++k) {
     BkSet& b = m.host[k];
-    const uint32_t cells = 1u << (3 * b.bl);
+    const uint32_t subs = 8u << (3 * b.bl);
     char* z = zero + zoff[k];
-    b.cnt = reinterpret_cast<uint32_t*>(z);
-    b.sct = b.cnt + cells;
-    z += align_up(sizeof(uint32_t) * 9 * cells);
+    b.sct = reinterpret_cast<uint32_t*>(z);
+    z += align_up(sizeof(uint32_t) * subs);
     b.info = reinterpret_cast<uint32_t*>(z);
     z += align_up(sizeof(uint32_t) * 4);
     b.status = reinterpret_cast<uint64_t*>(z);
-    b.tbase = arena_get<uint32_t>(c, (size_t)b.ntiles * cells, &err);
-    b.coff = arena_get<uint32_t>(c, cells, &err);
+    b.tbase = arena_get<uint32_t>(c, (size_t)b.ntiles * subs, &err);
+    b.sbase = arena_get<uint32_t>(c, subs, &err);
     b.bcell = arena_get<uint32_t>(c, b.nslot, &err);
     b.boff = arena_get<uint32_t>(c, (size_t)b.nslot + 1, &err);
     b.items = arena_get<uint64_t>(c, b.n, &err);
-    b.items2 = arena_get<uint64_t>(c, b.n, &err);
     b.soff = arena_get<uint32_t>(c, 8ull * b.nslot, &err);
     b.scnt = arena_get<uint32_t>(c, 8ull * b.nslot, &err);
     if (err) return err;
@@ -933,14 +929,12 @@ int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
   const size_t o_b = up.add(m.host.data(), m.host.size());
   const size_t o_t = up.add(tile_slots.data(), tile_slots.size());
   const size_t o_o = up.add(one.data(), one.size());
-  const size_t o_s = up.add(split_slots.data(), split_slots.size());
   const size_t o_x = up.add(box_slots.data(), box_slots.size());
   char* dev = upload(c, up, &err);
   if (err) return err;
   m.bsets = reinterpret_cast<BkSet*>(dev + o_b);
   m.tile_slots = reinterpret_cast<Slot*>(dev + o_t);
   m.one_slots = reinterpret_cast<Slot*>(dev + o_o);
-  m.split_slots = reinterpret_cast<Slot*>(dev + o_s);
   m.box_slots = reinterpret_cast<Slot*>(dev + o_x);
   return dev_zero(c, zero, zero_bytes);
 }
@@ -965,14 +959,6 @@ int bucket_sort(fmm_ctx* c, const BucketMem& m, int k) {
     Launch L(c, "bucket_scatter");
     launch_bucket_scatter(m.bsets, slots, nsl, tiles, max_bl, c->st, s);
   }
-  return cuda_status(cudaGetLastError());
-}
-
-// split of every bucket set's buckets into sub-cells (after their sorts).
-int bucket_split(fmm_ctx* c, const BucketMem& m) {
-  if (!m.units) return FMM_OK;
-  Launch L(c, "bucket_split");
-  launch_bucket_split(m.bsets, m.split_slots, m.count(), m.units, c->st, c->stream);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1165,7 +1151,6 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   if (async_lists) FMM_TRY(dev_zero(c, list_zero, list_zero_bytes));
 
   // ---- boxes, occupancy.
-  FMM_TRY(bucket_split(c, bm));
   if (bm.units) {
     Launch L(c, "bucket_boxes");
     launch_bucket_boxes(bm.bsets, m.segs, bm.box_slots, bm.count(), bm.units, bm.max_lb, bm.ticket,

@@ -3,23 +3,21 @@
 //
 // Alg. 1 orders the points with a histogram of the finest boxes, atomic
 // ranks and one move; Alg. 3 scans that histogram for the bookmarks.  Here
-// the same ideas are applied at coarse levels, where the histograms fit in
+// the same ideas are applied at a coarse level, where the histograms fit in
 // shared memory, and inside each sub-cell, where the rest of the order is
 // finished in shared memory by one block that also emits the boxes:
 //
-//   count    per tile of points: a histogram of the level-bl cells in shared
-//            memory; one atomic per (tile, non-empty cell) reserves the
-//            tile's range inside the cell (Alg. 1's atomic ranks, taken per
-//            tile and cell instead of per point);
-//   plan     per set: the prefix sum of the cell counts -- the cells'
-//            bookmarks (Alg. 3) -- and the list of non-empty cells, the
-//            "buckets";
-//   scatter  per tile, in chunks: each point becomes one 8-byte item -- the
-//            key bits below its cell, left-aligned, over the point index --
-//            the chunk is grouped by cell in shared memory and each cell's
-//            run is stored contiguously after the tile's earlier runs;
-//   split    per bucket: its items go to its 8 sub-cells (level bl + 1) as
-//            coalesced runs, one level down;
+//   count    per tile of points: a histogram of the level-(bl + 1) cells,
+//            the "sub-cells", in shared memory; one atomic per (tile,
+//            non-empty sub-cell) reserves the tile's range inside the
+//            sub-cell (Alg. 1's atomic ranks, taken per tile and sub-cell
+//            instead of per point);
+//   plan     per set: the prefix sum of the sub-cell counts -- their
+//            bookmarks (Alg. 3) -- and the list of non-empty level-bl cells,
+//            the "buckets", each with its 8 sub-cells;
+//   scatter  per tile: each point becomes one 8-byte item -- the key bits
+//            below its sub-cell, left-aligned, over the point index -- and
+//            goes to the next slot of the tile's range in its sub-cell;
 //   boxes    per sub-cell, one block: a counting sort of its items on their
 //            next key bits, whose group counts also give the non-empty boxes
 //            of the next three levels with their ranks and bookmarks (Alg. 3
@@ -30,7 +28,7 @@
 //            if any, come from the first differing level of the sorted items.
 //
 // Traffic per point: coordinates read twice (12 + 12 bytes), the item
-// written and read twice (8 + 8, 8 + 8), the permutation written (4).
+// written and read once (8 + 8), the permutation written (4).
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -45,26 +43,24 @@ __device__ __forceinline__ uint32_t spread5(uint32_t v) {
   return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6) | ((v & 16u) << 8);
 }
 
-// The spread of every 11-bit value (bit i -> bit 3i), built in shared
-// memory by each block that forms full keys: a key is then six table reads.
-constexpr int kLutBits = 11;
-__device__ __forceinline__ void build_lut(uint32_t* lut) {
-  for (uint32_t v = threadIdx.x; v < (1u << kLutBits); v += blockDim.x) {
-    uint32_t s = 0;
-    for (int i = 0; i < kLutBits; ++i) s |= ((v >> i) & 1u) << (3 * i);
-    lut[v] = s;
-  }
-}
-__device__ __forceinline__ uint64_t lut_spread(const uint32_t* lut, uint32_t q) {
-  return (uint64_t)lut[q & 0x7ffu] | ((uint64_t)lut[q >> 11] << 33);
+// Bit i of a 21-bit value moved to bit 3i, by five shift-or-mask steps
+// (each halves the width of the bit groups still to be spread: 16, 8, 4, 2,
+// 1 bits, the masks keeping every group at its place).
+__device__ __forceinline__ uint64_t spread21(uint32_t x) {
+  uint64_t v = x & 0x1fffffu;
+  v = (v | (v << 32)) & 0x001f00000000ffffull;
+  v = (v | (v << 16)) & 0x001f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
 }
 // The same key as morton_key (same quantisation).
-__device__ __forceinline__ uint64_t lut_key(const uint32_t* lut, float x, float y, float z,
-                                            bool* ok) {
+__device__ __forceinline__ uint64_t spread_key(float x, float y, float z, bool* ok) {
   uint32_t qx, qy, qz;
   const bool a = quantize21(x, &qx), b = quantize21(y, &qy), c = quantize21(z, &qz);
   *ok = a && b && c;
-  return lut_spread(lut, qx) | (lut_spread(lut, qy) << 1) | (lut_spread(lut, qz) << 2);
+  return spread21(qx) | (spread21(qy) << 1) | (spread21(qz) << 2);
 }
 
 // Cell of level bl (<= 5) of a point, and whether it lies in [0, 1]^3.
@@ -74,12 +70,6 @@ __device__ __forceinline__ uint32_t cell_of(float x, float y, float z, int bl, b
   *ok = a && b && c;
   const int sh = 21 - bl;
   return spread5(qx >> sh) | (spread5(qy >> sh) << 1) | (spread5(qz >> sh) << 2);
-}
-
-// Item of a point with Morton key `key`: the key bits below its level-bl
-// cell, left-aligned and masked by `keep`, over the point index.
-__device__ __forceinline__ uint64_t bk_item(uint64_t key, int bl, uint64_t keep, uint32_t idx) {
-  return ((key << (1 + 3 * bl)) & keep) | idx;
 }
 
 // First level at which two items of one sub-cell of level bl1 differ (22:
@@ -104,17 +94,20 @@ __device__ __forceinline__ uint32_t field(uint64_t w, int f) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// count: per tile, the histogram of the sub-cells (level bl + 1), the
-// tile's base in every cell (level bl) and the sub-cells' totals.
-__global__ void __launch_bounds__(kBkTileThreads) bucket_count_kernel(
+// count: per tile, the histogram of the sub-cells (level bl + 1) in shared
+// memory, then one atomic per (tile, non-empty sub-cell) on the sub-cell's
+// total: its return value is the tile's first slot inside the sub-cell.
+constexpr int kCountUnroll = 2;  // groups of 4 points a thread loads before it counts
+
+__global__ void __launch_bounds__(kBkTileThreads, 3) bucket_count_kernel(
     const BkSet* __restrict__ bsets, const Slot* __restrict__ slots, uint32_t nslots,
     DevStatus* st) {
   extern __shared__ uint32_t s_h[];
   const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
   const BkSet& S = bsets[sl.seg];
   const uint32_t t = blockIdx.x - sl.unit0;
-  const int bl = S.bl, bl1 = bl + 1;
-  const uint32_t cells = bk_cells(bl), subs = 8 * cells;
+  const int bl1 = S.bl + 1;
+  const uint32_t subs = bk_cells(bl1);
   for (uint32_t c = threadIdx.x; c < subs; c += blockDim.x) s_h[c] = 0;
   __syncthreads();
   const uint64_t base = (uint64_t)t * S.tile;
@@ -123,20 +116,37 @@ __global__ void __launch_bounds__(kBkTileThreads) bucket_count_kernel(
   bool bad = false;
   uint32_t done = 0;
   if ((reinterpret_cast<uintptr_t>(S.xyz) & 15u) == 0) {
-    // 4 points = 3 float4; tiles start at multiples of 4 points
+    // 4 points = 3 float4; tiles start at multiples of 4 points.  Each
+    // thread has kCountUnroll groups' loads in flight before it counts.
     const float4* v = reinterpret_cast<const float4*>(xyz);
-    for (uint32_t g = threadIdx.x; g < cnt / 4; g += blockDim.x) {
-      const float4 a = __ldcs(v + 3 * g), b = __ldcs(v + 3 * g + 1), c = __ldcs(v + 3 * g + 2);
-      bool ok0, ok1, ok2, ok3;
-      const uint32_t c0 = cell_of(a.x, a.y, a.z, bl1, &ok0);
-      const uint32_t c1 = cell_of(a.w, b.x, b.y, bl1, &ok1);
-      const uint32_t c2 = cell_of(b.z, b.w, c.x, bl1, &ok2);
-      const uint32_t c3 = cell_of(c.y, c.z, c.w, bl1, &ok3);
-      atomicAdd(&s_h[c0], 1u);
-      atomicAdd(&s_h[c1], 1u);
-      atomicAdd(&s_h[c2], 1u);
-      atomicAdd(&s_h[c3], 1u);
-      bad |= !(ok0 && ok1 && ok2 && ok3);
+    const uint32_t ng = cnt / 4;
+    for (uint32_t g0 = 0; g0 < ng; g0 += kCountUnroll * blockDim.x) {
+      float4 a[kCountUnroll], b[kCountUnroll], c[kCountUnroll];
+#pragma unroll
+      for (int u = 0; u < kCountUnroll; ++u) {
+        const uint32_t g = g0 + u * blockDim.x + threadIdx.x;
+        if (g < ng) {
+          a[u] = __ldcs(v + 3 * g);
+          b[u] = __ldcs(v + 3 * g + 1);
+          c[u] = __ldcs(v + 3 * g + 2);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kCountUnroll; ++u) {
+        const uint32_t g = g0 + u * blockDim.x + threadIdx.x;
+        if (g < ng) {
+          bool ok0, ok1, ok2, ok3;
+          const uint32_t c0 = cell_of(a[u].x, a[u].y, a[u].z, bl1, &ok0);
+          const uint32_t c1 = cell_of(a[u].w, b[u].x, b[u].y, bl1, &ok1);
+          const uint32_t c2 = cell_of(b[u].z, b[u].w, c[u].x, bl1, &ok2);
+          const uint32_t c3 = cell_of(c[u].y, c[u].z, c[u].w, bl1, &ok3);
+          atomicAdd(&s_h[c0], 1u);
+          atomicAdd(&s_h[c1], 1u);
+          atomicAdd(&s_h[c2], 1u);
+          atomicAdd(&s_h[c3], 1u);
+          bad |= !(ok0 && ok1 && ok2 && ok3);
+        }
+      }
     }
     done = cnt & ~3u;
   }
@@ -146,22 +156,26 @@ __global__ void __launch_bounds__(kBkTileThreads) bucket_count_kernel(
     bad |= !ok;
   }
   __syncthreads();
-  uint32_t* tb = S.tbase + (uint64_t)t * cells;
-  for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) {
-    uint32_t v = 0;
+  // (sub-cells the tile does not touch are never read: no base is stored)
+  uint32_t* tb = S.tbase + (uint64_t)t * subs;
+  for (uint32_t c0 = 0; c0 < subs; c0 += 4 * blockDim.x) {
+    uint32_t h[4], r[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const uint32_t h = s_h[8 * c + q];
-      if (h) atomicAdd(&S.sct[8 * c + q], h);
-      v += h;
+    for (int u = 0; u < 4; ++u) {  // the four atomics in flight together
+      const uint32_t c = c0 + u * blockDim.x + threadIdx.x;
+      h[u] = c < subs ? s_h[c] : 0u;
+      r[u] = h[u] ? atomicAdd(&S.sct[c], h[u]) : 0u;
     }
-    if (v) tb[c] = atomicAdd(&S.cnt[c], v);  // cells the tile does not touch are never read
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (h[u]) tb[c0 + u * blockDim.x + threadIdx.x] = r[u];
   }
   if (bad) set_error(st, FMM_ERR_DOMAIN);
 }
 
 // ---------------------------------------------------------------------------
-// plan: per set (one block each), the cells' bookmarks and the buckets.
+// plan: per set (one block each), the sub-cells' bookmarks and the buckets
+// (the non-empty level-bl cells) with their sub-cells.
 __global__ void __launch_bounds__(kBkPlanThreads) bucket_plan_kernel(const BkSet* __restrict__ bsets,
                                                                     DevStatus* st) {
   constexpr int W = kBkPlanThreads / 32;
@@ -179,7 +193,12 @@ __global__ void __launch_bounds__(kBkPlanThreads) bucket_plan_kernel(const BkSet
   uint32_t mx = 0;
 #pragma unroll
   for (int k = 0; k < kPer; ++k) {
-    v[k] = ((uint32_t)k < per && c0 + k < cells) ? S.cnt[c0 + k] : 0u;
+    v[k] = 0;
+    if ((uint32_t)k < per && c0 + k < cells) {
+      const uint4 lo = *reinterpret_cast<const uint4*>(S.sct + 8 * (c0 + k));
+      const uint4 hi = *reinterpret_cast<const uint4*>(S.sct + 8 * (c0 + k) + 4);
+      v[k] = lo.x + lo.y + lo.z + lo.w + hi.x + hi.y + hi.z + hi.w;
+    }
     sum += (uint64_t)v[k] | ((uint64_t)(v[k] != 0) << 32);
     mx = v[k] > mx ? v[k] : mx;
   }
@@ -217,17 +236,20 @@ __global__ void __launch_bounds__(kBkPlanThreads) bucket_plan_kernel(const BkSet
 #pragma unroll
   for (int k = 0; k < kPer; ++k) {
     if ((uint32_t)k < per && c0 + k < cells) {
-      S.coff[c0 + k] = off;
-      if (v[k]) {
-        S.bcell[b] = c0 + k;
-        S.boff[b] = off;
-        uint32_t so = off;  // the bucket's sub-cells, in octant order
-        for (int q = 0; q < 8; ++q) {
-          const uint32_t n8 = S.sct[8 * (c0 + k) + q];
+      const uint32_t c = c0 + k;
+      uint32_t so = off;  // the cell's sub-cells, in octant order
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t n8 = S.sct[8 * c + q];
+        S.sbase[8 * c + q] = so;
+        if (v[k]) {
           S.soff[8 * b + q] = so;
           S.scnt[8 * b + q] = n8;
-          so += n8;
         }
+        so += n8;
+      }
+      if (v[k]) {
+        S.bcell[b] = c;
+        S.boff[b] = off;
         ++b;
       }
       off += v[k];
@@ -236,222 +258,90 @@ __global__ void __launch_bounds__(kBkPlanThreads) bucket_plan_kernel(const BkSet
 }
 
 // ---------------------------------------------------------------------------
-// scatter: per tile, in chunks of kBkChunk points, every point's item to its
-// place inside its cell, each cell's part of a chunk stored as one run.
-// Shared memory: the key table, per cell the tile's next slot and the
-// chunk's count / first staged slot, the staged items and their cells.
-constexpr int kScThreads = 512;  // two blocks an SM: one loads while the other stores
-constexpr int kBkChunk = kScThreads * 8;
-constexpr size_t kBkScatterSmem = sizeof(uint32_t) * ((1u << kLutBits) + 3 * kBkMaxCells) +
-                                  sizeof(uint64_t) * kBkChunk + sizeof(uint16_t) * kBkChunk;
+// scatter: per tile, every point's item straight to its sub-cell, at the
+// tile's next slot there (a shared-memory atomic per point: Alg. 1's atomic
+// rank, taken inside the tile's reserved range).  The order inside a
+// sub-cell is left to the atomics: the boxes stage orders each sub-cell by
+// whole item.  The stores of a warp land in many sub-cells, each a part of
+// a 32-byte sector that the tile and its neighbours in tile order fill over
+// time; one block an SM (few tiles in flight) and short tiles keep the
+// partly written sectors few, so that most of them fill in L2 before they
+// are evicted.
+constexpr int kScThreads = 1024;
+constexpr int kScGroups = 1;  // groups of 4 points a thread takes per round
 
-__global__ void __launch_bounds__(kScThreads, 2) bucket_scatter_kernel(
+__global__ void __launch_bounds__(kScThreads, 1) bucket_scatter_kernel(
     const BkSet* __restrict__ bsets, const Slot* __restrict__ slots, uint32_t nslots,
     const DevStatus* st) {
-  constexpr int W = kScThreads / 32;
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* s_item = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* lut = reinterpret_cast<uint32_t*>(s_item + kBkChunk);
-  uint32_t* s_at = lut + (1u << kLutBits);  // per cell: the tile's next slot
-  uint32_t* s_cc = s_at + kBkMaxCells;      // per cell: the chunk's count, then first staged slot
-  uint32_t* s_c0 = s_cc + kBkMaxCells;      // ... its first staged slot
-  uint16_t* s_cell = reinterpret_cast<uint16_t*>(s_c0 + kBkMaxCells);
-  __shared__ uint32_t s_wsum[W];
+  extern __shared__ uint32_t s_at[];  // per sub-cell: the tile's next slot
   if (failed(st)) return;
   const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
   const BkSet& S = bsets[sl.seg];
   const uint32_t t = blockIdx.x - sl.unit0;
-  const int bl = S.bl;
-  const uint32_t cells = bk_cells(bl);
-  const int sh = 63 - 3 * bl;
-  const uint64_t keep = S.keep;
-  const uint32_t* tb = S.tbase + (uint64_t)t * cells;
-  build_lut(lut);
-  for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) {
-    s_at[c] = S.coff[c] + tb[c];  // (garbage for cells the tile does not touch: never read)
-    s_cc[c] = 0;
-  }
+  const int bl1 = S.bl + 1;
+  const uint32_t subs = bk_cells(bl1);
+  const int sh = 63 - 3 * bl1, lsh = 1 + 3 * bl1;
+  const uint64_t keep1 = S.keep << 3;
+  const uint32_t n = S.n;
+  const uint32_t* tb = S.tbase + (uint64_t)t * subs;
+  for (uint32_t c = threadIdx.x; c < subs; c += blockDim.x)
+    s_at[c] = S.sbase[c] + tb[c];  // (garbage for sub-cells the tile does not touch: never read)
   __syncthreads();
   const uint64_t base = (uint64_t)t * S.tile;
   const uint32_t cnt = (uint32_t)((S.n - base) < (uint64_t)S.tile ? (S.n - base) : S.tile);
   const float* xyz = S.xyz + 3 * base;
-  const bool vec = (reinterpret_cast<uintptr_t>(S.xyz) & 15u) == 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint64_t* items = S.items;
-  for (uint32_t c0 = 0; c0 < cnt; c0 += kBkChunk) {
-    const uint32_t m = cnt - c0 < (uint32_t)kBkChunk ? cnt - c0 : (uint32_t)kBkChunk;
-    // 1. items and cells of the chunk's points: thread takes points
-    //    4 (tid + kScThreads k) .. + 3, k = 0, 1
-    uint64_t it[8];
-    uint32_t ce[8], rk[8];
+  uint64_t* const items = S.items;
+  uint32_t done = 0;
+  if ((reinterpret_cast<uintptr_t>(S.xyz) & 15u) == 0) {
+    // A round: the loads of kScGroups groups of 4 points, their keys, their
+    // slots (atomics), their stores -- each step for all of them at once.
+    const float4* v = reinterpret_cast<const float4*>(xyz);
+    const uint32_t ng = cnt / 4;
+    for (uint32_t g0 = 0; g0 < ng; g0 += kScGroups * kScThreads) {
+      float p[kScGroups][12];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const uint32_t j0 = 4 * (threadIdx.x + kScThreads * k);  // chunk-local
-      float p[12];
-      if (vec && j0 + 4 <= m) {
-        const float4* v = reinterpret_cast<const float4*>(xyz + 3 * (uint64_t)(c0 + j0));
-        const float4 a = __ldcs(v), b = __ldcs(v + 1), c = __ldcs(v + 2);
-        p[0] = a.x; p[1] = a.y; p[2] = a.z; p[3] = a.w; p[4] = b.x; p[5] = b.y;
-        p[6] = b.z; p[7] = b.w; p[8] = c.x; p[9] = c.y; p[10] = c.z; p[11] = c.w;
-      } else {
-#pragma unroll
-        for (int q = 0; q < 12; ++q)
-          p[q] = (j0 + q / 3 < m) ? xyz[3 * (uint64_t)(c0 + j0) + q] : 0.0f;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = 4 * k + q;
-        bool ok;
-        const uint64_t key = lut_key(lut, p[3 * q], p[3 * q + 1], p[3 * q + 2], &ok);
-        ce[i] = (uint32_t)(key >> sh);
-        it[i] = bk_item(key, bl, keep, (uint32_t)(base + c0 + j0 + q));
-        rk[i] = (j0 + q < m) ? atomicAdd(&s_cc[ce[i]], 1u) : 0u;
-      }
-    }
-    __syncthreads();
-    // 2. first staged slot of each cell: a prefix sum of the chunk's counts
-    {
-      constexpr int kPer = kBkMaxCells / kScThreads;  // 8
-      uint32_t v[kPer], sum = 0;
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        const uint32_t c = threadIdx.x * kPer + k;
-        v[k] = c < cells ? s_cc[c] : 0u;
-        sum += v[k];
-      }
-      uint32_t x = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (lane == 31) s_wsum[warp] = x;
-      __syncthreads();
-      if (threadIdx.x < 32) {
-        const uint32_t w = lane < W ? s_wsum[lane] : 0u;
-        uint32_t y = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
-          if (lane >= o) y += z;
-        }
-        if (lane < W) s_wsum[lane] = y - w;
-      }
-      __syncthreads();
-      uint32_t e = s_wsum[warp] + x - sum;
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        const uint32_t c = threadIdx.x * kPer + k;
-        if (c < cells) s_c0[c] = e;
-        e += v[k];
-      }
-    }
-    __syncthreads();
-    // 3. stage the chunk grouped by cell
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const uint32_t j0 = 4 * (threadIdx.x + kScThreads * k);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = 4 * k + q;
-        if (j0 + q < m) {
-          const uint32_t at = s_c0[ce[i]] + rk[i];
-          s_item[at] = it[i];
-          s_cell[at] = (uint16_t)ce[i];
+      for (int u = 0; u < kScGroups; ++u) {
+        const uint32_t g = g0 + u * kScThreads + threadIdx.x;
+        if (g < ng) {
+          const float4 a = __ldcs(v + 3 * g), b = __ldcs(v + 3 * g + 1), c = __ldcs(v + 3 * g + 2);
+          p[u][0] = a.x; p[u][1] = a.y; p[u][2] = a.z; p[u][3] = a.w;
+          p[u][4] = b.x; p[u][5] = b.y; p[u][6] = b.z; p[u][7] = b.w;
+          p[u][8] = c.x; p[u][9] = c.y; p[u][10] = c.z; p[u][11] = c.w;
         }
       }
+      uint64_t key[4 * kScGroups];
+      uint32_t pos[4 * kScGroups];
+#pragma unroll
+      for (int u = 0; u < kScGroups; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          bool ok;
+          key[4 * u + q] = spread_key(p[u][3 * q], p[u][3 * q + 1], p[u][3 * q + 2], &ok);
+        }
+#pragma unroll
+      for (int u = 0; u < kScGroups; ++u) {
+        const bool in = g0 + u * kScThreads + threadIdx.x < ng;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          pos[4 * u + q] = in ? atomicAdd(&s_at[(uint32_t)(key[4 * u + q] >> sh)], 1u) : n;
+      }
+      // (slots beyond n would mean coordinates that changed since the count)
+#pragma unroll
+      for (int u = 0; u < kScGroups; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t j = 4 * (g0 + u * kScThreads + threadIdx.x) + q;
+          if (pos[4 * u + q] < n)
+            items[pos[4 * u + q]] = ((key[4 * u + q] << lsh) & keep1) | (uint32_t)(base + j);
+        }
     }
-    __syncthreads();
-    // 4. runs out: staged slot a of cell c goes to the tile's next slot of c
-    //    plus its place in the cell's run (slots beyond n would mean
-    //    coordinates that changed since the count)
-    for (uint32_t a = threadIdx.x; a < m; a += kScThreads) {
-      const uint32_t c = s_cell[a];
-      const uint32_t pos = s_at[c] + (a - s_c0[c]);
-      if (pos < S.n) items[pos] = s_item[a];
-    }
-    __syncthreads();
-    for (uint32_t c = threadIdx.x; c < cells; c += kScThreads) {
-      s_at[c] += s_cc[c];
-      s_cc[c] = 0;
-    }
-    __syncthreads();
+    done = cnt & ~3u;
   }
-}
-
-// ---------------------------------------------------------------------------
-// split: one block per bucket.  The bucket's items are read once and stored
-// as the runs of its sub-cells (the next octant, level bl + 1; their sizes
-// come from the count), one level down (the sub-cell's octant shifted out of
-// the key bits): a streaming pass with coalesced runs.
-constexpr int kSplitThreads = 512;  // two or more blocks an SM
-constexpr int kSplitItems = 7;  // a warp's 224 items keep each octant count below 256
-constexpr int kSplitChunk = kSplitThreads * kSplitItems;
-
-__global__ void __launch_bounds__(kSplitThreads) bucket_split_kernel(
-    const BkSet* __restrict__ bsets, const Slot* __restrict__ slots, uint32_t nslots,
-    const DevStatus* st) {
-  constexpr int W = kSplitThreads / 32;
-  __shared__ uint64_t s_wt[W];     // per warp: its octant counts, 8-bit fields
-  __shared__ uint32_t s_wb[W][8];  // per warp and octant: first slot
-  __shared__ uint32_t s_base[8];   // per octant: the next free slot
-  if (failed(st)) return;
-  const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
-  const BkSet& S = bsets[sl.seg];
-  const uint32_t b = blockIdx.x - sl.unit0;
-  if (b >= S.info[0]) return;
-  const uint32_t off0 = S.boff[b], cnt = S.boff[b + 1] - off0;
-  const uint64_t* __restrict__ src = S.items + off0;
-  uint64_t* __restrict__ dst = S.items2 + off0;
-  const uint64_t keep = S.keep, imask = (1ull << S.ib) - 1ull;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  // The sub-cells' first slots, from the plan.
-  if (threadIdx.x < 8) s_base[threadIdx.x] = S.soff[8 * b + threadIdx.x] - off0;
-  __syncthreads();
-
-  // The move, a chunk at a time.  A thread takes kSplitItems consecutive
-  // items; its per-octant counts (8-bit fields of a 64-bit word) are scanned
-  // across the warp and the warps, so that each octant's items of the chunk
-  // land as one run, in chunk order.
-  for (uint32_t c0 = 0; c0 < cnt; c0 += kSplitChunk) {
-    uint64_t it[kSplitItems];
-    const uint32_t i0 = c0 + threadIdx.x * kSplitItems;
-#pragma unroll
-    for (int k = 0; k < kSplitItems; ++k) it[k] = i0 + k < cnt ? src[i0 + k] : 0ull;
-    uint64_t mine = 0;  // this thread's counts
-#pragma unroll
-    for (int k = 0; k < kSplitItems; ++k)
-      if (i0 + k < cnt) mine += 1ull << (8 * (uint32_t)(it[k] >> 61));
-    uint64_t x = mine;  // inclusive scan over the warp (fields stay below 256)
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_wt[warp] = x;
-    __syncthreads();
-    if (threadIdx.x < 8) {
-      const uint32_t q = threadIdx.x;
-      uint32_t at = s_base[q];
-      for (int w = 0; w < W; ++w) {
-        s_wb[w][q] = at;
-        at += (uint32_t)(s_wt[w] >> (8 * q)) & 0xffu;
-      }
-      s_base[q] = at;
-    }
-    __syncthreads();
-    uint64_t run = x - mine;  // items of each octant before this thread's, in the warp
-#pragma unroll
-    for (int k = 0; k < kSplitItems; ++k) {
-      if (i0 + k < cnt) {
-        const uint64_t v = it[k];
-        const uint32_t q = (uint32_t)(v >> 61);
-        dst[s_wb[warp][q] + ((uint32_t)(run >> (8 * q)) & 0xffu)] = ((v & keep) << 3) | (v & imask);
-        run += 1ull << (8 * q);
-      }
-    }
-    __syncthreads();
+  for (uint32_t j = done + threadIdx.x; j < cnt; j += kScThreads) {
+    bool ok;
+    const uint64_t key = spread_key(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], &ok);
+    const uint32_t pos = atomicAdd(&s_at[(uint32_t)(key >> sh)], 1u);
+    if (pos < n) items[pos] = ((key << lsh) & keep1) | (uint32_t)(base + j);
   }
 }
 
@@ -502,7 +392,7 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
   uint64_t* B = A + kBkCap;
   uint32_t* gs = reinterpret_cast<uint32_t*>(B + kBkCap);  // group counts, then starts [2^D + 1]
   uint8_t* dd = reinterpret_cast<uint8_t*>(B);             // first differing levels (deep levels)
-  __shared__ uint32_t s_t, s_abort, s_tie;
+  __shared__ uint32_t s_t, s_abort;
   __shared__ uint64_t s_w[W + 1];
   __shared__ uint32_t s_R[kLevels], s_C[kLevels];
   __shared__ __align__(8) uint8_t s_fl[kBkHistCells];  // non-empty flags
@@ -512,7 +402,6 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
   if (tid == 0) {
     s_t = atomicAdd(ticket, 1u);
     s_abort = failed(st) ? 1u : 0u;
-    s_tie = 0;
   }
   __syncthreads();
   if (s_abort) return;  // an earlier kernel failed: leave the outputs alone
@@ -558,7 +447,7 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
 
   // 1. The sub-cell's items (all loads in flight together).
   {
-    const uint64_t* src = S.items2 + offj;
+    const uint64_t* src = S.items + offj;
     uint64_t v[kBkItems];
 #pragma unroll
     for (int k = 0; k < kBkItems; ++k) {
@@ -870,20 +759,14 @@ void launch_bucket_plan(const BkSet* bsets, uint32_t nsets, DevStatus* st, cudaS
 void launch_bucket_scatter(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
                            int max_bl, DevStatus* st, cudaStream_t s) {
   if (tiles == 0) return;
-  (void)max_bl;
   static const bool attr = [] {
     cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kBkScatterSmem);
+                         (int)(sizeof(uint32_t) * 8 * kBkMaxCells));
     return true;
   }();
   (void)attr;
-  bucket_scatter_kernel<<<tiles, kScThreads, kBkScatterSmem, s>>>(bsets, slots, nslots, st);
-}
-
-void launch_bucket_split(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t units,
-                         DevStatus* st, cudaStream_t s) {
-  if (units == 0) return;
-  bucket_split_kernel<<<units, kSplitThreads, 0, s>>>(bsets, slots, nslots, st);
+  const size_t smem = sizeof(uint32_t) * 8 * (1u << (3 * max_bl));
+  bucket_scatter_kernel<<<tiles, kScThreads, smem, s>>>(bsets, slots, nslots, st);
 }
 
 void launch_bucket_boxes(const BkSet* bsets, const Seg* segs, const Slot* slots, uint32_t nslots,
