@@ -361,14 +361,16 @@ __device__ __forceinline__ uint64_t block_scan64(uint64_t v, uint64_t* s_w, uint
   }
   if (lane == 31) s_w[warp] = x;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t run = 0;
-    for (int w = 0; w < W; ++w) {
-      const uint64_t c = s_w[w];
-      s_w[w] = run;
-      run += c;
+  if (warp == 0) {  // the warps' sums, scanned by one warp
+    const uint64_t w = lane < W ? s_w[lane] : 0ull;
+    uint64_t y = w;
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+      const uint64_t z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
     }
-    s_w[W] = run;
+    if (lane < W) s_w[lane] = y - w;
+    if (lane == W - 1) s_w[W] = y;
   }
   __syncthreads();
   const uint64_t r = s_w[warp] + x - v;
@@ -537,9 +539,8 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
 
   // 4. The sort: the counting sort's scatter, then each point's rank in its
   // group by the whole item (key bits, index).  A point's place in the
-  // sub-cell is its group's start plus that rank: its permutation entry is
-  // written from there.  The sorted items themselves are kept only where
-  // they are needed (deep levels, tied key bits).
+  // sub-cell is its group's start plus that rank: its permutation entry and
+  // its sorted item are written from there.
 #pragma unroll
   for (int k = 0; k < kBkItems; ++k) {
     if (k * kBkThreads >= (int)n_j) break;
@@ -552,38 +553,26 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
   __syncthreads();
   uint32_t* const perm = G.perm;
   const uint64_t hi = ~imask;
-  const bool keepA = deep;
-  bool tie = false;
   for (uint32_t p = tid; p < n_j; p += kBkThreads) {
     const uint64_t x = B[p];
     const uint32_t g = D ? (uint32_t)(x >> gsh) : 0u;
     const uint32_t q0 = gs[g], q1 = gs[g + 1];
     uint32_t r = 0;
-    for (uint32_t q = q0; q < q1; ++q) {
-      const uint64_t y = B[q];
-      r += y < x;
-      tie |= q != p && ((x ^ y) & hi) == 0;
-    }
+    for (uint32_t q = q0; q < q1; ++q) r += B[q] < x;
     perm[offj + q0 + r] = (uint32_t)(x & imask);
-    if (keepA) A[q0 + r] = x;
+    A[q0 + r] = x;  // the sorted items
   }
+  __syncthreads();
+  // Items whose kept key bits tie are neighbours in the sorted order.
+  bool tie = false;
+  if (S.trunc)
+    for (uint32_t p = tid + 1; p < n_j; p += kBkThreads) tie |= ((A[p] ^ A[p - 1]) & hi) == 0;
   if (S.trunc && __syncthreads_or(tie)) {
     // Points whose kept key bits tie but whose full keys may differ (keys
-    // cut short to make room for the index): the sorted items are formed
-    // again, each tied run is put in (full key, index) order by one thread,
-    // the full keys recomputed from the coordinates, and the permutation is
-    // written again.  Rare: two points in one cell of level about 17.
-    if (!keepA) {
-      for (uint32_t p = tid; p < n_j; p += kBkThreads) {
-        const uint64_t x = B[p];
-        const uint32_t g = D ? (uint32_t)(x >> gsh) : 0u;
-        const uint32_t q0 = gs[g], q1 = gs[g + 1];
-        uint32_t r = 0;
-        for (uint32_t q = q0; q < q1; ++q) r += B[q] < x;
-        A[q0 + r] = x;
-      }
-      __syncthreads();
-    }
+    // cut short to make room for the index): each tied run is put in (full
+    // key, index) order by one thread, the full keys recomputed from the
+    // coordinates, and the permutation is written again.  Rare: two points
+    // in one cell of level about 17.
     for (uint32_t p = tid + 1; p < n_j; p += kBkThreads) {
       if (((A[p] ^ A[p - 1]) & hi) != 0) continue;
       if (p >= 2 && ((A[p - 1] ^ A[p - 2]) & hi) == 0) continue;  // not the run's second point
