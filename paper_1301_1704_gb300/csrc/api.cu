@@ -15,6 +15,7 @@
 // first host synchronisation are captured into a CUDA graph, which updates
 // the executable graph kept from the previous build and is launched.
 #include <algorithm>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -827,7 +828,8 @@ struct BucketMem {
   Slot* one_slots = nullptr;         // per bucket set k: Slot{k, 0} (one-set launches)
   Slot* box_slots = nullptr;         // sub-cell slots (8 a bucket slot)
   uint32_t units = 0;                // bucket slots
-  uint32_t* ticket = nullptr;
+  uint32_t* ticket = nullptr;         // sub-cell tickets of an all-sets boxes launch
+  uint32_t* set_tickets = nullptr;    // ... and of one-set launches, one per set
   int max_bl = 0, max_lb = 0;
   uint32_t count() const { return (uint32_t)host.size(); }
 };
@@ -875,7 +877,7 @@ int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
   int err = FMM_OK;
   BucketMem& m = *bm;
   std::vector<Slot> tile_slots, one, box_slots;
-  size_t zero_bytes = align_up(sizeof(uint32_t) * 4);  // the ticket
+  size_t zero_bytes = align_up(sizeof(uint32_t) * (1 + sets.size()));  // the tickets
   std::vector<size_t> zoff;
   for (uint32_t i = 0; i < sets.size(); ++i) {
     SetPlan& sp = sets[i];
@@ -907,6 +909,7 @@ int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
   char* zero = arena_get<char>(c, zero_bytes, &err);
   if (err) return err;
   m.ticket = reinterpret_cast<uint32_t*>(zero);
+  m.set_tickets = m.ticket + 1;
   for (uint32_t k = 0; k < m.count(); ++k) {
     BkSet& b = m.host[k];
     const uint32_t subs = 8u << (3 * b.bl);
@@ -962,10 +965,24 @@ int bucket_sort(fmm_ctx* c, const BucketMem& m, int k) {
   return cuda_status(cudaGetLastError());
 }
 
+// The boxes of bucket set k alone (its own tickets), into the outputs `segs`
+// of the build.
+int bucket_boxes_one(fmm_ctx* c, const BucketMem& bm, const Seg* segs, uint32_t k,
+                     uint64_t wait_ns) {
+  Launch L(c, "bucket_boxes");
+  launch_bucket_boxes(bm.bsets, segs, bm.one_slots + k, 1, bm.host[k].nslot, bm.max_lb,
+                      bm.set_tickets + k, c->st, wait_ns, c->stream);
+  return cuda_status(cudaGetLastError());
+}
+
 // Box and list stages of a build over sorted `sets` (SetPlan::Lb and
 // JobPlan::L fixed).
+// `early`, when given, runs once the outputs are allocated and cleared, in
+// place of the all-sets bucket boxes launch: the pipelined host-input build
+// copies, sorts and boxes its bucket sets one at a time there.
 int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs,
-              const fmm_params& prm, const BucketMem& bm, Readback* rb) {
+              const fmm_params& prm, const BucketMem& bm, Readback* rb,
+              const std::function<int(const Seg*)>* early = nullptr) {
   cudaStream_t s = c->stream;
   int err = FMM_OK;
   const uint64_t wait_ns = wait_ns_of(prm);
@@ -1150,8 +1167,10 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   FMM_TRY(dev_zero(c, zero, zero_bytes));
   if (async_lists) FMM_TRY(dev_zero(c, list_zero, list_zero_bytes));
 
+  if (early) FMM_TRY((*early)(m.segs));
+
   // ---- boxes, occupancy.
-  if (bm.units) {
+  if (bm.units && !early) {
     Launch L(c, "bucket_boxes");
     launch_bucket_boxes(bm.bsets, m.segs, bm.box_slots, bm.count(), bm.units, bm.max_lb, bm.ticket,
                         c->st, wait_ns, s);
@@ -1496,9 +1515,15 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
     if (!sp.bucket) lsd.push_back(&sp);
   BucketMem bm;
   FMM_TRY(bucket_setup(c, sets, &bm));
+  // A pipelined build whose sets all take the bucket path also boxes each
+  // set as soon as it is sorted (inside run_build, once the outputs exist),
+  // so that the sources' box stage runs under the receivers' copy too.
+  const bool early_boxes = pipelined && bm.count() == sets.size();
   {
     SortMem sm;
-    if (pipelined) {
+    if (early_boxes) {
+      // (sorted and boxed in run_build)
+    } else if (pipelined) {
       // set i's copy, then its sort behind an event; copy i+1 is issued after
       // sort i's launches (a pageable copy holds the host meanwhile)
       uint32_t kb = 0;
@@ -1593,7 +1618,20 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   }
 
   Readback rb;
-  const int rs = run_build(c, sets, jobs, prm, bm, &rb);
+  const std::function<int(const Seg*)> copy_sort_box = [&](const Seg* segs) -> int {
+    for (uint32_t k = 0; k < sets.size(); ++k) {
+      SetPlan& sp = sets[k];
+      if (sp.n)
+        FMM_CUDA(cudaMemcpyAsync(const_cast<float*>(sp.xyz), host_xyz[k],
+                                 sizeof(float) * 3 * sp.n, cudaMemcpyHostToDevice, c->cstream));
+      FMM_CUDA(cudaEventRecord(c->cevent, c->cstream));
+      FMM_CUDA(cudaStreamWaitEvent(s, c->cevent, 0));
+      FMM_TRY(bucket_sort(c, bm, (int)k));
+      FMM_TRY(bucket_boxes_one(c, bm, segs, k, wait_ns));
+    }
+    return FMM_OK;
+  };
+  const int rs = run_build(c, sets, jobs, prm, bm, &rb, early_boxes ? &copy_sort_box : nullptr);
   // A bucket too full for one block (status kStatusBucketFull; the sets
   // carry bit 2): the build stopped there; build again with those sets on
   // the radix path.

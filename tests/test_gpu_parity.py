@@ -175,6 +175,18 @@ def test_host_input_flag(ctx, orc):
         assert np.array_equal(t["sorted_src"], orc.sorted_points(src, want["src"]["perm"]))
     finally:
         ctx.set_tuning(fmmds.FMM_SORT_BUCKET)
+    # the bucket path, each set boxed as soon as it has landed: with the
+    # sorted points, and next to a set too dense for one sub-cell's block
+    # (the build is redone on the radix path, copies included)
+    t = ctx.build(hs, hr, L=5, flags=fmmds.FMM_FLAG_HOST_INPUT | fmmds.FMM_FLAG_SORTED_XYZ).numpy()
+    want = orc.build_tree(src, recv, L=5)
+    compare_full(t, want, 5)
+    assert np.array_equal(t["sorted_recv"], orc.sorted_points(recv, want["recv"]["perm"]))
+    tight = workloads.clumps(60000, 80, nclumps=2, sigma=0.002)
+    ht = torch.from_numpy(tight).pin_memory()
+    for a, b, ha, hb, L in ((src, tight, hs, ht, 6), (tight, src, ht, hs, 4)):
+        got = ctx.build(ha, hb, L=L, flags=fmmds.FMM_FLAG_HOST_INPUT).numpy()
+        compare_full(got, orc.build_tree(a, b, L=L), L)
 
 
 @pytest.mark.parametrize("s", [1, 8, 64, 300])
