@@ -399,6 +399,9 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
   __shared__ uint32_t s_R[kLevels], s_C[kLevels];
   __shared__ __align__(8) uint8_t s_fl[kBkHistCells];  // non-empty flags
   __shared__ uint16_t s_pre[kBkHistCells];              // exclusive ranks
+  __shared__ uint64_t* s_lkey[kLevels];                  // the output level arrays
+  __shared__ uint32_t *s_loff[kLevels], *s_lpar[kLevels], *s_lchd[kLevels];
+  __shared__ uint32_t s_lcap[kLevels];
 
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
@@ -447,6 +450,16 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
     return;
   }
 
+  // The output level arrays, read once (their loads overlap the items').
+  if (tid <= Lb) {
+    s_lkey[tid] = G.lv.key[tid];
+    s_loff[tid] = G.lv.off[tid];
+    s_lpar[tid] = G.lv.parent[tid];
+    s_lchd[tid] = G.lv.child[tid];
+    s_lcap[tid] = G.lv.cap[tid];
+  }
+  uint32_t* const perm = G.perm;
+
   // 1. The sub-cell's items (all loads in flight together).
   {
     const uint64_t* src = S.items + offj;
@@ -478,7 +491,7 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
   }
   __syncthreads();
   {
-    constexpr int kPer = (1 << kBkGroupBits) / kBkThreads;  // 4 entries a thread
+    constexpr int kPer = ((1 << kBkGroupBits) + kBkThreads - 1) / kBkThreads;  // entries a thread
     uint32_t v[kPer], sum = 0;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
@@ -551,7 +564,6 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
     }
   }
   __syncthreads();
-  uint32_t* const perm = G.perm;
   const uint64_t hi = ~imask;
   for (uint32_t p = tid; p < n_j; p += kBkThreads) {
     const uint64_t x = B[p];
@@ -655,23 +667,23 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
   if (b == nbk - 1 && j == 7 && tid <= Lb) {
     const uint32_t tot = s_R[tid] + s_C[tid];
     G.nbox[tid] = tot;
-    if (tot <= G.lv.cap[tid]) {
-      G.lv.off[tid][tot] = S.n;
-      if (tid < Lb) G.lv.child[tid][tot] = s_R[tid + 1] + s_C[tid + 1];
+    if (tot <= s_lcap[tid]) {
+      s_loff[tid][tot] = S.n;
+      if (tid < Lb) s_lchd[tid][tot] = s_R[tid + 1] + s_C[tid + 1];
     }
   }
   if (tid == 0 && n_j > 0) {
     const int top = Lb < bl1 ? Lb : bl1;
     for (int l = (int)d0; l <= top; ++l) {
       const uint32_t rank = s_R[l];
-      if (rank >= G.lv.cap[l]) continue;
-      G.lv.key[l][rank] = (uint64_t)cell1 >> (3 * (bl1 - l));
-      G.lv.off[l][rank] = offj;
+      if (rank >= s_lcap[l]) continue;
+      s_lkey[l][rank] = (uint64_t)cell1 >> (3 * (bl1 - l));
+      s_loff[l][rank] = offj;
       if (l >= 1) {
         const bool up = d0 <= (uint32_t)(l - 1);
         const uint32_t pr = up ? s_R[l - 1] : s_R[l - 1] - 1u;
-        G.lv.parent[l][rank] = pr;
-        if (up && pr < G.lv.cap[l - 1]) G.lv.child[l - 1][pr] = rank;
+        s_lpar[l][rank] = pr;
+        if (up && pr < s_lcap[l - 1]) s_lchd[l - 1][pr] = rank;
       }
     }
   }
@@ -685,14 +697,14 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
       const int l = bl1 + m;
       const uint32_t within = s_pre[hoff(m) + c];
       const uint32_t rank = s_R[l] + within;
-      if (rank >= G.lv.cap[l]) continue;
-      G.lv.key[l][rank] = ((uint64_t)cell1 << (3 * m)) | c;
-      G.lv.off[l][rank] = offj + gs[c << (gpc + 3 * (nm - m))];
+      if (rank >= s_lcap[l]) continue;
+      s_lkey[l][rank] = ((uint64_t)cell1 << (3 * m)) | c;
+      s_loff[l][rank] = offj + gs[c << (gpc + 3 * (nm - m))];
       const uint32_t pr = m == 1 ? s_R[bl1] : s_R[l - 1] + s_pre[hoff(m - 1) + (c >> 3)];
-      G.lv.parent[l][rank] = pr;
+      s_lpar[l][rank] = pr;
       // the first non-empty child of its parent starts the parent's children
       const uint32_t first = m == 1 ? 0u : s_pre[hoff(m) + (c & ~7u)];
-      if (within == first && pr < G.lv.cap[l - 1]) G.lv.child[l - 1][pr] = rank;
+      if (within == first && pr < s_lcap[l - 1]) s_lchd[l - 1][pr] = rank;
     }
   }
   if (deep) {
@@ -712,13 +724,13 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
         const uint64_t x = A[p];
         for (int l = d > g0 ? d : g0; l <= g1; ++l) {
           const uint32_t rank = s_R[l] + field(ex, l - f0);
-          if (rank >= G.lv.cap[l]) continue;
-          G.lv.key[l][rank] = ((uint64_t)cell1 << (3 * (l - bl1))) | (x >> (64 - 3 * (l - bl1)));
-          G.lv.off[l][rank] = offj + p;
+          if (rank >= s_lcap[l]) continue;
+          s_lkey[l][rank] = ((uint64_t)cell1 << (3 * (l - bl1))) | (x >> (64 - 3 * (l - bl1)));
+          s_loff[l][rank] = offj + p;
           const bool up = d <= l - 1;
           const uint32_t pr = s_R[l - 1] + field(ex, l - 1 - f0) - (up ? 0u : 1u);
-          G.lv.parent[l][rank] = pr;
-          if (up && pr < G.lv.cap[l - 1]) G.lv.child[l - 1][pr] = rank;
+          s_lpar[l][rank] = pr;
+          if (up && pr < s_lcap[l - 1]) s_lchd[l - 1][pr] = rank;
         }
         ex += fields((d > f0 ? d : f0) - f0, g1 - f0);
       }
