@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(kListThreads, 8) list_count_kernel(const Seg* 
 // Row starts are written rebased to the job's own lists.
 constexpr int kCand = 27 * 8;  // at most 27 neighbours x 8 children
 constexpr int kNear = 64;      // candidates in some sibling's E2: the 4x4x4 block
+constexpr uint32_t kStage = 4 * 189 + 4;  // four E4 lists, and up to 3 entries of alignment
 
 // A warp's current job in the fill kernel.
 struct WarpJob {
@@ -374,6 +375,7 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
   __shared__ uint32_t s_nrank[kListWarps][kNear];
   __shared__ uint16_t s_nsib[kListWarps][kNear];
   __shared__ WarpJob s_job[kListWarps];
+  __shared__ __align__(16) uint32_t s_stage[kListWarps][kStage];  // E4 lists of four siblings
   if (failed(st)) return;  // set before this launch: the same for every thread
   const ListLevel& LV = lvls[l];
   if ((LV.total[0] >> 32) != 0 || (LV.total[1] >> 32) != 0) return;  // capacity error set
@@ -392,6 +394,7 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
   uint16_t* csib = s_sib[warp];
   uint32_t* nrank = s_nrank[warp];
   uint16_t* nsibm = s_nsib[warp];
+  uint32_t* stage = s_stage[warp];
   uint8_t* const code2 = LV.code2;
   const uint32_t npar = jprefix[njobs];
   const BlockRange br = block_range(npar);
@@ -532,19 +535,41 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
           }
         }
       }
-      for (uint32_t c = 0; c < total; c += 32) {
-        const uint32_t i = c + lane;
-        const uint32_t v = i < total ? crank[i] : 0u;
-        const uint32_t sb = i < total ? (csib[i] & 0xffu) : 0xffu;  // past the end: never stored
+      // E4, four siblings at a time: their lists are adjacent in idx4, so
+      // they are gathered in the warp's stage (aligned like idx4) and written
+      // out as whole 16-byte vectors.
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          if (kAll || (uint32_t)jj < nsib) {
-            const uint32_t hit = sb & sbit[jj];
-            const uint32_t b4 = __ballot_sync(0xffffffffu, hit == 0u);
-            st_cs_if_zero(idx4 + w4[jj] + __popc(b4 & lt), v, hit);
-            w4[jj] += __popc(b4);
+      for (int h = 0; h < 2; ++h) {
+        if (!kAll && (uint32_t)(4 * h) >= nsib) break;
+        const uint32_t a0 = w4[4 * h], sb0 = a0 & ~3u;
+        for (uint32_t c = 0; c < total; c += 32) {
+          const uint32_t i = c + lane;
+          const uint32_t v = i < total ? crank[i] : 0u;
+          const uint32_t sb = i < total ? (csib[i] & 0xffu) : 0xffu;  // past the end: never stored
+#pragma unroll
+          for (int jj = 4 * h; jj < 4 * h + 4; ++jj) {
+            if (kAll || (uint32_t)jj < nsib) {
+              const uint32_t hit = sb & sbit[jj];
+              const uint32_t b4 = __ballot_sync(0xffffffffu, hit == 0u);
+              const uint32_t at = w4[jj] + __popc(b4 & lt) - sb0;
+              if (hit == 0u && at < kStage) stage[at] = v;
+              w4[jj] += __popc(b4);
+            }
           }
         }
+        __syncwarp();
+        // the half's entries [a0, a1): head and tail one by one, the rest
+        // as 16-byte vectors
+        uint32_t a1 = a0;  // the end of the half's last list
+#pragma unroll
+        for (int jj = 4 * h; jj < 4 * h + 4; ++jj)
+          if (kAll || (uint32_t)jj < nsib) a1 = w4[jj];
+        const uint32_t v0 = min((a0 + 3u) & ~3u, a1), v1 = max(a1 & ~3u, v0);
+        if ((uint32_t)lane < v0 - a0) __stcs(idx4 + a0 + lane, stage[a0 + lane - sb0]);
+        if ((uint32_t)lane < a1 - v1) __stcs(idx4 + v1 + lane, stage[v1 + lane - sb0]);
+        for (uint32_t e = v0 + 4u * lane; e < v1; e += 128u)
+          __stcs(reinterpret_cast<uint4*>(idx4 + e), *reinterpret_cast<const uint4*>(stage + (e - sb0)));
+        __syncwarp();
       }
     };
     if (nsib == 8)
