@@ -996,18 +996,20 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     for (int l = 0; l <= sp.Lb; ++l) sp.cap[l] = level_cap(sp.n, l);
   }
 
-  // Zero-initialised words per set: look-back words, tickets, box counts and
-  // the long-box flag.
-  size_t zero_bytes = 0;
+  // Zero-initialised words: every set's tickets, box counts and long-box
+  // flag side by side (one read-back copy for all sets), then per set its
+  // look-back words.
+  constexpr size_t kSetWords = 2 + kLevels + 1;
+  size_t zero_bytes = align_up(sizeof(uint32_t) * kSetWords * nsets);
   std::vector<size_t> zoff(nsets);
   for (uint32_t i = 0; i < nsets; ++i) {
     zoff[i] = zero_bytes;
     zero_bytes += align_up(sizeof(uint64_t) * sets[i].dev.btiles) +
-                  align_up(sizeof(uint64_t) * coarse_tiles(sets[i].cap[sets[i].Lb]) * kLevels) +
-                  align_up(sizeof(uint32_t) * (2 + kLevels + 1));
+                  align_up(sizeof(uint64_t) * coarse_tiles(sets[i].cap[sets[i].Lb]) * kLevels);
   }
   char* zero = arena_get<char>(c, std::max<size_t>(zero_bytes, 1), &err);
   if (err) return err;
+  uint32_t* const set_words = reinterpret_cast<uint32_t*>(zero);
 
   // Per-set outputs.
   for (uint32_t i = 0; i < nsets; ++i) {
@@ -1018,7 +1020,7 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     z += align_up(sizeof(uint64_t) * d.btiles);
     d.cstatus = reinterpret_cast<uint64_t*>(z);
     z += align_up(sizeof(uint64_t) * coarse_tiles(sp.cap[sp.Lb]) * kLevels);
-    d.tickets = reinterpret_cast<uint32_t*>(z);
+    d.tickets = set_words + (size_t)i * kSetWords;
     d.nbox = d.tickets + 2;
     d.seg_long = d.nbox + kLevels;
     d.perm = arena_get<uint32_t>(c, sp.n, &err);
@@ -1197,20 +1199,18 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     launch_occupancy(m.segs, m.occ_slots, (uint32_t)occ.size(), m.occ_units, c->st, s);
   }
 
-  const size_t per_set = kLevels + 1;
   auto read_sets = [&](bool lists) -> int {
     const size_t list_words = lists ? 4 * (size_t)njobs * kLevels : 0;
-    const size_t need = 64 + sizeof(uint32_t) * nsets * per_set + 16 + sizeof(uint64_t) * list_words;
+    const size_t need = 64 + sizeof(uint32_t) * nsets * kSetWords + 16 + sizeof(uint64_t) * list_words;
     FMM_TRY(build_sync(c));  // the read-back buffer may be replaced
     FMM_TRY(pinned_reserve(&c->rb_buf, &c->rb_bytes, need));
     char* h = static_cast<char*>(c->rb_buf);
     FMM_CUDA(cudaMemcpyAsync(h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     uint32_t* hn = reinterpret_cast<uint32_t*>(h + 64);
-    for (uint32_t i = 0; i < nsets; ++i)
-      FMM_CUDA(cudaMemcpyAsync(hn + (size_t)i * per_set, sets[i].dev.nbox,
-                               sizeof(uint32_t) * per_set, cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaMemcpyAsync(hn, set_words, sizeof(uint32_t) * nsets * kSetWords,
+                             cudaMemcpyDeviceToHost, s));
     uint64_t* hl = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(hn + (size_t)nsets * per_set) + 15) & ~(uintptr_t)15);
+        (reinterpret_cast<uintptr_t>(hn + (size_t)nsets * kSetWords) + 15) & ~(uintptr_t)15);
     if (lists)
       for (int l = 2; l <= Lmax; ++l) {
         FMM_CUDA(cudaMemcpyAsync(hl + (size_t)l * njobs * 4, lvls[l].base,
@@ -1223,9 +1223,9 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     rb->nbox.assign((size_t)nsets * kLevels, 0);
     rb->seg_long.assign(nsets, 0);
     for (uint32_t i = 0; i < nsets; ++i) {
-      std::memcpy(&rb->nbox[(size_t)i * kLevels], hn + (size_t)i * per_set,
+      std::memcpy(&rb->nbox[(size_t)i * kLevels], hn + (size_t)i * kSetWords + 2,
                   sizeof(uint32_t) * kLevels);
-      rb->seg_long[i] = hn[(size_t)i * per_set + kLevels];
+      rb->seg_long[i] = hn[(size_t)i * kSetWords + 2 + kLevels];
     }
     if (lists) {
       rb->list.assign((size_t)kLevels * njobs * 4, 0);
