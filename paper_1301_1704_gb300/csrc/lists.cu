@@ -351,6 +351,8 @@ __global__ void __launch_bounds__(kListThreads, 8) list_count_kernel(const Seg* 
 constexpr int kCand = 27 * 8;  // at most 27 neighbours x 8 children
 constexpr int kNear = 64;      // candidates in some sibling's E2: the 4x4x4 block
 constexpr uint32_t kStage = 4 * 189 + 4;  // four E4 lists, and up to 3 entries of alignment
+constexpr uint32_t kStageMin = 128;       // candidates of a parent whose E4 lists are staged
+constexpr uint32_t kStageJob = 1u << 25;  // E4 entries of a job's level whose lists are staged
 
 // A warp's current job in the fill kernel.
 struct WarpJob {
@@ -359,6 +361,7 @@ struct WarpJob {
   uint32_t* out4;
   uint32_t G2, G4;  // the job's first entries in the level's lists
   uint32_t j, jstart, jend;
+  uint32_t big;     // the job's E4 lists at this level outgrow L2
 };
 
 // kCodes: also write the E2 entries' offset codes for the next level (every
@@ -414,12 +417,14 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
         J.out4 = jobs[j].out4[l];
         J.G2 = work2[J.a.region];
         J.G4 = work4[J.a.region];
+        J.big = work4[J.a.region + J.a.nrecv] - J.G4 >= kStageJob;
       }
       __syncwarp();
       jend = J.jend;
     }
     const uint32_t p = g - J.jstart;
     const uint32_t region = J.a.region, G2 = J.G2, G4 = J.G4;
+    const bool big = J.big != 0;
     uint32_t* const out2 = J.out2;
     uint32_t* const out4 = J.out4;
     // The receiver children of p (at most 8): lane j fetches child j's octant
@@ -535,20 +540,22 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
           }
         }
       }
-      // E4, four siblings at a time: their lists are adjacent in idx4, so
-      // they are gathered in the warp's stage (aligned like idx4) and written
-      // out as whole 16-byte vectors.
+      // E4.  Where a job's E4 lists of the level outgrow L2, a parent with all eight
+      // children and many candidates gathers its E4 lists four siblings at a
+      // time in the warp's stage (they are adjacent in idx4; the stage is
+      // aligned like idx4) and writes them as whole 16-byte vectors, so that
+      // DRAM sees whole sectors; elsewhere the entries are stored directly
+      // (partial writes merge in L2 there).
+      if (kAll && big && total >= kStageMin) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!kAll && (uint32_t)(4 * h) >= nsib) break;
-        const uint32_t a0 = w4[4 * h], sb0 = a0 & ~3u;
-        for (uint32_t c = 0; c < total; c += 32) {
-          const uint32_t i = c + lane;
-          const uint32_t v = i < total ? crank[i] : 0u;
-          const uint32_t sb = i < total ? (csib[i] & 0xffu) : 0xffu;  // past the end: never stored
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t a0 = w4[4 * h], sb0 = a0 & ~3u;
+          for (uint32_t c = 0; c < total; c += 32) {
+            const uint32_t i = c + lane;
+            const uint32_t v = i < total ? crank[i] : 0u;
+            const uint32_t sb = i < total ? (csib[i] & 0xffu) : 0xffu;  // past the end: never stored
 #pragma unroll
-          for (int jj = 4 * h; jj < 4 * h + 4; ++jj) {
-            if (kAll || (uint32_t)jj < nsib) {
+            for (int jj = 4 * h; jj < 4 * h + 4; ++jj) {
               const uint32_t hit = sb & sbit[jj];
               const uint32_t b4 = __ballot_sync(0xffffffffu, hit == 0u);
               const uint32_t at = w4[jj] + __popc(b4 & lt) - sb0;
@@ -556,20 +563,33 @@ __global__ void __launch_bounds__(kListThreads, 4) list_fill_kernel(const Seg* _
               w4[jj] += __popc(b4);
             }
           }
+          __syncwarp();
+          // the half's entries [a0, a1): head and tail one by one, the rest
+          // as 16-byte vectors
+          const uint32_t a1 = w4[4 * h + 3];
+          const uint32_t v0 = min((a0 + 3u) & ~3u, a1), v1 = max(a1 & ~3u, v0);
+          if ((uint32_t)lane < v0 - a0) __stcs(idx4 + a0 + lane, stage[a0 + lane - sb0]);
+          if ((uint32_t)lane < a1 - v1) __stcs(idx4 + v1 + lane, stage[v1 + lane - sb0]);
+          for (uint32_t e = v0 + 4u * lane; e < v1; e += 128u)
+            __stcs(reinterpret_cast<uint4*>(idx4 + e),
+                   *reinterpret_cast<const uint4*>(stage + (e - sb0)));
+          __syncwarp();
         }
-        __syncwarp();
-        // the half's entries [a0, a1): head and tail one by one, the rest
-        // as 16-byte vectors
-        uint32_t a1 = a0;  // the end of the half's last list
+      } else {
+        for (uint32_t c = 0; c < total; c += 32) {
+          const uint32_t i = c + lane;
+          const uint32_t v = i < total ? crank[i] : 0u;
+          const uint32_t sb = i < total ? (csib[i] & 0xffu) : 0xffu;  // past the end: never stored
 #pragma unroll
-        for (int jj = 4 * h; jj < 4 * h + 4; ++jj)
-          if (kAll || (uint32_t)jj < nsib) a1 = w4[jj];
-        const uint32_t v0 = min((a0 + 3u) & ~3u, a1), v1 = max(a1 & ~3u, v0);
-        if ((uint32_t)lane < v0 - a0) __stcs(idx4 + a0 + lane, stage[a0 + lane - sb0]);
-        if ((uint32_t)lane < a1 - v1) __stcs(idx4 + v1 + lane, stage[v1 + lane - sb0]);
-        for (uint32_t e = v0 + 4u * lane; e < v1; e += 128u)
-          __stcs(reinterpret_cast<uint4*>(idx4 + e), *reinterpret_cast<const uint4*>(stage + (e - sb0)));
-        __syncwarp();
+          for (int jj = 0; jj < 8; ++jj) {
+            if (kAll || (uint32_t)jj < nsib) {
+              const uint32_t hit = sb & sbit[jj];
+              const uint32_t b4 = __ballot_sync(0xffffffffu, hit == 0u);
+              st_cs_if_zero(idx4 + w4[jj] + __popc(b4 & lt), v, hit);
+              w4[jj] += __popc(b4);
+            }
+          }
+        }
       }
     };
     if (nsib == 8)
