@@ -385,15 +385,14 @@ constexpr int kBkHistLevels = 3;
 constexpr int kBkHistCells = 8 + 64 + 512;
 __device__ __forceinline__ int hoff(int m) { return ((1 << (3 * m)) - 8) / 7; }
 
-__global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
+__global__ void __launch_bounds__(kBkThreads, 3) bucket_boxes_kernel(
     const BkSet* __restrict__ bsets, const Seg* __restrict__ segs, const Slot* __restrict__ slots,
     uint32_t nslots, uint32_t* ticket, DevStatus* st, uint64_t wait_ns) {
   constexpr int W = kBkThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* A = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* B = A + kBkCap;
+  uint64_t* B = reinterpret_cast<uint64_t*>(smem);          // the items, by group
   uint32_t* gs = reinterpret_cast<uint32_t*>(B + kBkCap);  // group counts, then starts [2^D + 1]
-  uint8_t* dd = reinterpret_cast<uint8_t*>(B);             // first differing levels (deep levels)
+  uint16_t* ord = reinterpret_cast<uint16_t*>(gs + (1 << kBkGroupBits) + 4);  // sorted k: B[ord[k]]
   __shared__ uint32_t s_t, s_abort;
   __shared__ uint64_t s_w[W + 1];
   __shared__ uint32_t s_R[kLevels], s_C[kLevels];
@@ -460,34 +459,29 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
   }
   uint32_t* const perm = G.perm;
 
-  // 1. The sub-cell's items (all loads in flight together).
+  // 1. The sub-cell's items (all loads in flight together; kept in L2 for
+  // the counting sort's scatter, which reads them again).
+  const uint64_t* src = S.items + offj;
+  const uint32_t ng = 1u << D;
+  const int gsh = 64 - D;
+  uint32_t rk[kBkItems];
   {
-    const uint64_t* src = S.items + offj;
     uint64_t v[kBkItems];
 #pragma unroll
     for (int k = 0; k < kBkItems; ++k) {
       const uint32_t p = tid + k * kBkThreads;
-      v[k] = p < n_j ? __ldcs(src + p) : 0ull;
+      v[k] = p < n_j ? __ldcg(src + p) : 0ull;
     }
+    for (uint32_t q = tid; q <= ng; q += kBkThreads) gs[q] = 0;
+    __syncthreads();
+
+    // 2. Group counts (the top D item bits) with each point's rank in its
+    // group (an unstable counting sort), and the groups' starts.
 #pragma unroll
     for (int k = 0; k < kBkItems; ++k) {
       const uint32_t p = tid + k * kBkThreads;
-      if (p < n_j) A[p] = v[k];
+      if (p < n_j) rk[k] = atomicAdd(&gs[D ? (uint32_t)(v[k] >> gsh) : 0u], 1u);
     }
-  }
-  const uint32_t ng = 1u << D;
-  for (uint32_t q = tid; q <= ng; q += kBkThreads) gs[q] = 0;
-  __syncthreads();
-
-  // 2. Group counts (the top D item bits) with each point's rank in its
-  // group (an unstable counting sort), and the groups' starts.
-  const int gsh = 64 - D;
-  uint32_t rk[kBkItems];
-#pragma unroll
-  for (int k = 0; k < kBkItems; ++k) {
-    if (k * kBkThreads >= (int)n_j) break;
-    const uint32_t p = tid + k * kBkThreads;
-    if (p < n_j) rk[k] = atomicAdd(&gs[D ? (uint32_t)(A[p] >> gsh) : 0u], 1u);
   }
   __syncthreads();
   {
@@ -556,10 +550,9 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
   // its sorted item are written from there.
 #pragma unroll
   for (int k = 0; k < kBkItems; ++k) {
-    if (k * kBkThreads >= (int)n_j) break;
     const uint32_t p = tid + k * kBkThreads;
     if (p < n_j) {
-      const uint64_t x = A[p];
+      const uint64_t x = __ldcs(src + p);
       B[gs[D ? (uint32_t)(x >> gsh) : 0u] + rk[k]] = x;
     }
   }
@@ -572,13 +565,13 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
     uint32_t r = 0;
     for (uint32_t q = q0; q < q1; ++q) r += B[q] < x;
     perm[offj + q0 + r] = (uint32_t)(x & imask);
-    A[q0 + r] = x;  // the sorted items
+    ord[q0 + r] = (uint16_t)p;  // the sorted order
   }
   __syncthreads();
   // Items whose kept key bits tie are neighbours in the sorted order.
   bool tie = false;
   if (S.trunc)
-    for (uint32_t p = tid + 1; p < n_j; p += kBkThreads) tie |= ((A[p] ^ A[p - 1]) & hi) == 0;
+    for (uint32_t p = tid + 1; p < n_j; p += kBkThreads) tie |= ((B[ord[p]] ^ B[ord[p - 1]]) & hi) == 0;
   if (S.trunc && __syncthreads_or(tie)) {
     // Points whose kept key bits tie but whose full keys may differ (keys
     // cut short to make room for the index): each tied run is put in (full
@@ -586,34 +579,35 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
     // coordinates, and the permutation is written again.  Rare: two points
     // in one cell of level about 17.
     for (uint32_t p = tid + 1; p < n_j; p += kBkThreads) {
-      if (((A[p] ^ A[p - 1]) & hi) != 0) continue;
-      if (p >= 2 && ((A[p - 1] ^ A[p - 2]) & hi) == 0) continue;  // not the run's second point
+      const uint64_t xm = B[ord[p - 1]];
+      if (((B[ord[p]] ^ xm) & hi) != 0) continue;
+      if (p >= 2 && ((B[ord[p - 2]] ^ xm) & hi) == 0) continue;  // not the run's second point
       const uint32_t q0 = p - 1;
       uint32_t e = p + 1;
-      while (e < n_j && ((A[e] ^ A[q0]) & hi) == 0) ++e;
-      if (e - q0 > kBkTieMax) {
+      while (e < n_j && ((B[ord[e]] ^ xm) & hi) == 0) ++e;
+      if (e - q0 > kBkTieRun) {
         atomicOr(G.seg_long, 1u);  // the host redoes this set's order with a full sort
         atomicExch(&st->seg_long, 1u);
         continue;
       }
-      for (uint32_t q = q0; q < e; ++q) {
-        const uint32_t i = (uint32_t)(A[q] & imask);
-        bool ok;
-        B[q] = morton_key(S.xyz[3ull * i], S.xyz[3ull * i + 1], S.xyz[3ull * i + 2], &ok);
-      }
       // insertion sort by (full key, index); the run starts in index order
-      for (uint32_t q = q0 + 1; q < e; ++q) {
-        const uint64_t kx = B[q], ix = A[q];
-        uint32_t r = q;
-        while (r > q0 && (B[r - 1] > kx || (B[r - 1] == kx && A[r - 1] > ix))) {
-          B[r] = B[r - 1];
-          A[r] = A[r - 1];
+      uint64_t kk[kBkTieRun];
+      uint32_t ii[kBkTieRun];
+      const uint32_t m = e - q0;
+      for (uint32_t a2 = 0; a2 < m; ++a2) {
+        const uint32_t i = (uint32_t)(B[ord[q0 + a2]] & imask);
+        bool ok;
+        const uint64_t kx = morton_key(S.xyz[3ull * i], S.xyz[3ull * i + 1], S.xyz[3ull * i + 2], &ok);
+        uint32_t r = a2;
+        while (r > 0 && (kk[r - 1] > kx || (kk[r - 1] == kx && ii[r - 1] > i))) {
+          kk[r] = kk[r - 1];
+          ii[r] = ii[r - 1];
           --r;
         }
-        B[r] = kx;
-        A[r] = ix;
+        kk[r] = kx;
+        ii[r] = i;
       }
-      for (uint32_t q = q0; q < e; ++q) perm[offj + q] = (uint32_t)(A[q] & imask);
+      for (uint32_t a2 = 0; a2 < m; ++a2) perm[offj + q0 + a2] = ii[a2];
     }
   }
   __syncthreads();
@@ -624,15 +618,16 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
   // fields: thread tid owns the points [tid * ipt, tid * ipt + ipt).
   const uint32_t ipt = (n_j + kBkThreads - 1) / kBkThreads;
   const uint32_t p0 = tid * ipt, p1 = p0 + ipt < n_j ? p0 + ipt : n_j;
+  // first differing level of sorted point p (the sub-cell's first: d0)
+  auto ddl = [&](uint32_t p) -> int {
+    return p == 0 ? (int)d0 : (int)bk_diff_level(B[ord[p]], B[ord[p - 1]], keep1, bl1);
+  };
   if (deep) {
-    for (uint32_t p = tid; p < n_j; p += kBkThreads)
-      dd[p] = (uint8_t)(p == 0 ? d0 : bk_diff_level(A[p], A[p - 1], keep1, bl1));
-    __syncthreads();
     for (int g0 = lh + 1; g0 <= Lb; g0 += 3) {
       const int g1 = g0 + 2 < Lb ? g0 + 2 : Lb;
       uint64_t c = 0;
       for (uint32_t p = p0; p < p1; ++p) {
-        const int d = dd[p];
+        const int d = ddl(p);
         if (d <= g1) c += fields((d > g0 - 1 ? d : g0 - 1) - (g0 - 1), g1 - (g0 - 1));
       }
       uint64_t tot;
@@ -713,15 +708,15 @@ __global__ void __launch_bounds__(kBkThreads, 2) bucket_boxes_kernel(
       const int f0 = g0 - 1;  // field 0: the level above the group
       uint64_t c = 0;
       for (uint32_t p = p0; p < p1; ++p) {
-        const int d = dd[p];
+        const int d = ddl(p);
         if (d <= g1) c += fields((d > f0 ? d : f0) - f0, g1 - f0);
       }
       uint64_t tot;
       uint64_t ex = block_scan64<W>(c, s_w, &tot);  // starts before this thread's first point
       for (uint32_t p = p0; p < p1; ++p) {
-        const int d = dd[p];
+        const int d = ddl(p);
         if (d > g1) continue;
-        const uint64_t x = A[p];
+        const uint64_t x = B[ord[p]];
         for (int l = d > g0 ? d : g0; l <= g1; ++l) {
           const uint32_t rank = s_R[l] + field(ex, l - f0);
           if (rank >= s_lcap[l]) continue;

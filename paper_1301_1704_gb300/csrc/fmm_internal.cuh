@@ -425,9 +425,9 @@ constexpr int kBkCap = kBkThreads * kBkItems;       // 6144 points sorted by one
 constexpr int kBkGroupBits = 11;                    // groups of a sub-cell's counting sort
 constexpr int kBkMaxLevel = 4;                      // bucket cells of level 4 at most
 constexpr int kBkMaxCells = 1 << (3 * kBkMaxLevel);  // 4096
-constexpr uint32_t kBkTieMax = 1024;                // longest run of tied items one thread orders
-constexpr size_t kBkSmem =
-    2 * sizeof(uint64_t) * kBkCap + sizeof(uint32_t) * ((1 << kBkGroupBits) + 4);
+constexpr uint32_t kBkTieRun = 32;                  // longest run of tied items one thread orders
+constexpr size_t kBkSmem = sizeof(uint64_t) * kBkCap + sizeof(uint32_t) * ((1 << kBkGroupBits) + 4) +
+                           sizeof(uint16_t) * kBkCap;
 
 // Radix passes (8-bit digits) that sort the top 3*Ls key bits.
 __host__ __device__ inline int passes_for(int Ls) { return (3 * Ls + kRadixBits - 1) / kRadixBits; }
