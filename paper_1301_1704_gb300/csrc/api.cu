@@ -319,13 +319,20 @@ struct Launch {
 // Small transfers of a build done by the SMs, not the copy engines: on the
 // copy engines they would queue behind a large host copy of another set's
 // coordinates (a pipelined host-input build) and stall the stage they feed.
-__global__ void __launch_bounds__(256) zero_words_kernel(uint32_t* __restrict__ p, uint64_t words) {
-  const uint64_t n16 = words / 4;
-  uint4* q = reinterpret_cast<uint4*>(p);  // p is 16-byte aligned
+// Zeroes up to two word ranges (16-byte aligned starts) in one launch.
+__global__ void __launch_bounds__(256) zero_words_kernel(uint32_t* __restrict__ p0, uint64_t w0,
+                                                         uint32_t* __restrict__ p1, uint64_t w1) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n16; i += stride)
-    q[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (blockIdx.x == 0 && threadIdx.x < words - 4 * n16) p[4 * n16 + threadIdx.x] = 0u;
+  const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    uint32_t* const p = r ? p1 : p0;
+    const uint64_t words = r ? w1 : w0;
+    const uint64_t n16 = words / 4;
+    uint4* q = reinterpret_cast<uint4*>(p);
+    for (uint64_t i = t0; i < n16; i += stride) q[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (blockIdx.x == 0 && threadIdx.x < words - 4 * n16) p[4 * n16 + threadIdx.x] = 0u;
+  }
 }
 
 __global__ void __launch_bounds__(256) copy_words_kernel(const uint32_t* __restrict__ src,
@@ -341,15 +348,22 @@ uint32_t small_grid(uint64_t items) {
   return (uint32_t)(g == 0 ? 1 : (g > 152u * 4u ? 152u * 4u : g));
 }
 
-// Zeroes `bytes` (a multiple of 4) at p (16-byte aligned) on the build's stream.
-int dev_zero(fmm_ctx* c, void* p, size_t bytes) {
-  if (bytes == 0) return FMM_OK;
-  if (bytes % 4 != 0 || (reinterpret_cast<uintptr_t>(p) & 15) != 0) return FMM_ERR_ARG;
+// Zeroes [p0, p0 + b0) and [p1, p1 + b1) on the build's stream (16-byte
+// aligned starts, whole words).
+int dev_zero2(fmm_ctx* c, void* p0, size_t b0, void* p1, size_t b1) {
+  if (b0 == 0 && b1 == 0) return FMM_OK;
+  if (b0 % 4 != 0 || b1 % 4 != 0 || (reinterpret_cast<uintptr_t>(p0) & 15) != 0 ||
+      (reinterpret_cast<uintptr_t>(p1) & 15) != 0)
+    return FMM_ERR_ARG;
   Launch L(c, "zero");
-  const uint64_t words = bytes / 4;
-  zero_words_kernel<<<small_grid(words / 4), 256, 0, c->stream>>>(static_cast<uint32_t*>(p), words);
+  const uint64_t w0 = b0 / 4, w1 = b1 / 4;
+  zero_words_kernel<<<small_grid(std::max(w0, w1) / 4), 256, 0, c->stream>>>(
+      static_cast<uint32_t*>(p0), w0, static_cast<uint32_t*>(p1), w1);
   return cudaGetLastError() == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
 }
+
+// Zeroes `bytes` (a multiple of 4) at p (16-byte aligned).
+int dev_zero(fmm_ctx* c, void* p, size_t bytes) { return dev_zero2(c, p, bytes, nullptr, 0); }
 
 void collect_times(fmm_ctx* c) {
   for (auto& p : c->pending) {
@@ -919,11 +933,9 @@ int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
     b.info = reinterpret_cast<uint32_t*>(z);
     z += align_up(sizeof(uint32_t) * 4);
     b.status = reinterpret_cast<uint64_t*>(z);
-    b.tbase = arena_get<uint32_t>(c, (size_t)b.ntiles * subs, &err);
-    b.sbase = arena_get<uint32_t>(c, subs, &err);
     b.bcell = arena_get<uint32_t>(c, b.nslot, &err);
     b.boff = arena_get<uint32_t>(c, (size_t)b.nslot + 1, &err);
-    b.items = arena_get<uint64_t>(c, b.n, &err);
+    b.items = arena_get<uint64_t>(c, (size_t)subs * kBkCap, &err);
     b.soff = arena_get<uint32_t>(c, 8ull * b.nslot, &err);
     b.scnt = arena_get<uint32_t>(c, 8ull * b.nslot, &err);
     if (err) return err;
@@ -942,7 +954,7 @@ int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
   return dev_zero(c, zero, zero_bytes);
 }
 
-// count -> plan -> scatter of bucket set k, or of all bucket sets (k < 0).
+// scatter -> plan of bucket set k, or of all bucket sets (k < 0).
 // A one-set launch runs the set's tiles from unit 0 (slot {k, 0}).
 int bucket_sort(fmm_ctx* c, const BucketMem& m, int k) {
   cudaStream_t s = c->stream;
@@ -951,16 +963,12 @@ int bucket_sort(fmm_ctx* c, const BucketMem& m, int k) {
   const uint32_t tiles = k < 0 ? m.tiles : m.host[k].ntiles;
   const int max_bl = k < 0 ? m.max_bl : m.host[k].bl;
   {
-    Launch L(c, "bucket_count");
-    launch_bucket_count(m.bsets, slots, nsl, tiles, max_bl, c->st, s);
+    Launch L(c, "bucket_scatter");
+    launch_bucket_scatter(m.bsets, slots, nsl, tiles, max_bl, c->st, s);
   }
   {
     Launch L(c, "bucket_plan");
     launch_bucket_plan(k < 0 ? m.bsets : m.bsets + k, nsl, c->st, s);
-  }
-  {
-    Launch L(c, "bucket_scatter");
-    launch_bucket_scatter(m.bsets, slots, nsl, tiles, max_bl, c->st, s);
   }
   return cuda_status(cudaGetLastError());
 }
@@ -1166,8 +1174,8 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     FMM_TRY(plan_lists());
   }
   FMM_TRY(upload_all(async_lists));
-  FMM_TRY(dev_zero(c, zero, zero_bytes));
-  if (async_lists) FMM_TRY(dev_zero(c, list_zero, list_zero_bytes));
+  FMM_TRY(dev_zero2(c, zero, zero_bytes, async_lists ? list_zero : nullptr,
+                    async_lists ? list_zero_bytes : 0));
 
   if (early) FMM_TRY((*early)(m.segs));
 

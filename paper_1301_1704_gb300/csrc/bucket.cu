@@ -7,17 +7,16 @@
 // shared memory, and inside each sub-cell, where the rest of the order is
 // finished in shared memory by one block that also emits the boxes:
 //
-//   count    per tile of points: a histogram of the level-(bl + 1) cells,
+//   scatter  per tile of points: a histogram of the level-(bl + 1) cells,
 //            the "sub-cells", in shared memory; one atomic per (tile,
 //            non-empty sub-cell) reserves the tile's range inside the
 //            sub-cell (Alg. 1's atomic ranks, taken per tile and sub-cell
-//            instead of per point);
+//            instead of per point); then each point becomes one 8-byte item
+//            -- the key bits below its sub-cell, left-aligned, over the point
+//            index -- at the next slot of the tile's range in its sub-cell;
 //   plan     per set: the prefix sum of the sub-cell counts -- their
 //            bookmarks (Alg. 3) -- and the list of non-empty level-bl cells,
 //            the "buckets", each with its 8 sub-cells;
-//   scatter  per tile: each point becomes one 8-byte item -- the key bits
-//            below its sub-cell, left-aligned, over the point index -- and
-//            goes to the next slot of the tile's range in its sub-cell;
 //   boxes    per sub-cell, one block: a counting sort of its items on their
 //            next key bits, whose group counts also give the non-empty boxes
 //            of the next three levels with their ranks and bookmarks (Alg. 3
@@ -27,8 +26,9 @@
 //            per level gives the sub-cell's first box ranks; deeper levels,
 //            if any, come from the first differing level of the sorted items.
 //
-// Traffic per point: coordinates read twice (12 + 12 bytes), the item
-// written and read once (8 + 8), the permutation written (4).
+// Traffic per point: coordinates read once (12 bytes; the scatter's second
+// read of a tile comes from L2), the item written and read once (8 + 8), the
+// permutation written (4).
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -92,86 +92,6 @@ __device__ __forceinline__ uint32_t field(uint64_t w, int f) {
 }
 
 }  // namespace
-
-// ---------------------------------------------------------------------------
-// count: per tile, the histogram of the sub-cells (level bl + 1) in shared
-// memory, then one atomic per (tile, non-empty sub-cell) on the sub-cell's
-// total: its return value is the tile's first slot inside the sub-cell.
-constexpr int kCountUnroll = 2;  // groups of 4 points a thread loads before it counts
-
-__global__ void __launch_bounds__(kBkTileThreads, 3) bucket_count_kernel(
-    const BkSet* __restrict__ bsets, const Slot* __restrict__ slots, uint32_t nslots,
-    DevStatus* st) {
-  extern __shared__ uint32_t s_h[];
-  const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
-  const BkSet& S = bsets[sl.seg];
-  const uint32_t t = blockIdx.x - sl.unit0;
-  const int bl1 = S.bl + 1;
-  const uint32_t subs = bk_cells(bl1);
-  for (uint32_t c = threadIdx.x; c < subs; c += blockDim.x) s_h[c] = 0;
-  __syncthreads();
-  const uint64_t base = (uint64_t)t * S.tile;
-  const uint32_t cnt = (uint32_t)((S.n - base) < (uint64_t)S.tile ? (S.n - base) : S.tile);
-  const float* xyz = S.xyz + 3 * base;
-  bool bad = false;
-  uint32_t done = 0;
-  if ((reinterpret_cast<uintptr_t>(S.xyz) & 15u) == 0) {
-    // 4 points = 3 float4; tiles start at multiples of 4 points.  Each
-    // thread has kCountUnroll groups' loads in flight before it counts.
-    const float4* v = reinterpret_cast<const float4*>(xyz);
-    const uint32_t ng = cnt / 4;
-    for (uint32_t g0 = 0; g0 < ng; g0 += kCountUnroll * blockDim.x) {
-      float4 a[kCountUnroll], b[kCountUnroll], c[kCountUnroll];
-#pragma unroll
-      for (int u = 0; u < kCountUnroll; ++u) {
-        const uint32_t g = g0 + u * blockDim.x + threadIdx.x;
-        if (g < ng) {
-          a[u] = __ldcs(v + 3 * g);
-          b[u] = __ldcs(v + 3 * g + 1);
-          c[u] = __ldcs(v + 3 * g + 2);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kCountUnroll; ++u) {
-        const uint32_t g = g0 + u * blockDim.x + threadIdx.x;
-        if (g < ng) {
-          bool ok0, ok1, ok2, ok3;
-          const uint32_t c0 = cell_of(a[u].x, a[u].y, a[u].z, bl1, &ok0);
-          const uint32_t c1 = cell_of(a[u].w, b[u].x, b[u].y, bl1, &ok1);
-          const uint32_t c2 = cell_of(b[u].z, b[u].w, c[u].x, bl1, &ok2);
-          const uint32_t c3 = cell_of(c[u].y, c[u].z, c[u].w, bl1, &ok3);
-          atomicAdd(&s_h[c0], 1u);
-          atomicAdd(&s_h[c1], 1u);
-          atomicAdd(&s_h[c2], 1u);
-          atomicAdd(&s_h[c3], 1u);
-          bad |= !(ok0 && ok1 && ok2 && ok3);
-        }
-      }
-    }
-    done = cnt & ~3u;
-  }
-  for (uint32_t j = done + threadIdx.x; j < cnt; j += blockDim.x) {
-    bool ok;
-    atomicAdd(&s_h[cell_of(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], bl1, &ok)], 1u);
-    bad |= !ok;
-  }
-  __syncthreads();
-  // (sub-cells the tile does not touch are never read: no base is stored)
-  uint32_t* tb = S.tbase + (uint64_t)t * subs;
-  for (uint32_t c0 = 0; c0 < subs; c0 += 4 * blockDim.x) {
-    uint32_t h[4], r[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {  // the four atomics in flight together
-      const uint32_t c = c0 + u * blockDim.x + threadIdx.x;
-      h[u] = c < subs ? s_h[c] : 0u;
-      r[u] = h[u] ? atomicAdd(&S.sct[c], h[u]) : 0u;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (h[u]) tb[c0 + u * blockDim.x + threadIdx.x] = r[u];
-  }
-  if (bad) set_error(st, FMM_ERR_DOMAIN);
-}
 
 // ---------------------------------------------------------------------------
 // plan: per set (one block each), the sub-cells' bookmarks and the buckets
@@ -240,7 +160,6 @@ __global__ void __launch_bounds__(kBkPlanThreads) bucket_plan_kernel(const BkSet
       uint32_t so = off;  // the cell's sub-cells, in octant order
       for (int q = 0; q < 8; ++q) {
         const uint32_t n8 = S.sct[8 * c + q];
-        S.sbase[8 * c + q] = so;
         if (v[k]) {
           S.soff[8 * b + q] = so;
           S.scnt[8 * b + q] = n8;
@@ -258,22 +177,30 @@ __global__ void __launch_bounds__(kBkPlanThreads) bucket_plan_kernel(const BkSet
 }
 
 // ---------------------------------------------------------------------------
-// scatter: per tile, every point's item straight to its sub-cell, at the
-// tile's next slot there (a shared-memory atomic per point: Alg. 1's atomic
-// rank, taken inside the tile's reserved range).  The order inside a
-// sub-cell is left to the atomics: the boxes stage orders each sub-cell by
-// whole item.  The stores of a warp land in many sub-cells, each a part of
-// a 32-byte sector that the tile and its neighbours in tile order fill over
-// time; one block an SM (few tiles in flight) and short tiles keep the
-// partly written sectors few, so that most of them fill in L2 before they
-// are evicted.
+// scatter: per tile of points, in one pass over the tile: the histogram of its
+// sub-cells (level bl + 1) in shared memory; one atomic per (tile, non-empty
+// sub-cell) on the sub-cell's total reserves the tile's range inside the
+// sub-cell (Alg. 1's atomic ranks, taken per tile and sub-cell instead of per
+// point); then each point (its coordinates read again, from L2) becomes one
+// 8-byte item -- the key bits below its sub-cell, left-aligned, over the
+// point index -- at the next slot of that range (a shared-memory atomic per
+// point).  Sub-cell c's items occupy slots [c kBkCap, c kBkCap + count): the
+// totals are not known while the tiles run, so every sub-cell has room for
+// the most points one block sorts; a fuller sub-cell keeps only what fits
+// (the boxes stage then stops the build and the host redoes the set by the
+// radix path).  The order inside a sub-cell is left to the atomics: the
+// boxes stage orders each sub-cell by whole item.  The stores of a warp land
+// in many sub-cells, each a part of a 32-byte sector that the tile and its
+// neighbours in tile order fill over time; one block an SM (few tiles in
+// flight) and short tiles keep the partly written sectors few, so that most
+// of them fill in L2 before they are evicted.
 constexpr int kScThreads = 1024;
-constexpr int kScGroups = 1;  // groups of 4 points a thread takes per round
+constexpr int kScGroups = 2;  // groups of 4 points a thread loads ahead
 
 __global__ void __launch_bounds__(kScThreads, 1) bucket_scatter_kernel(
     const BkSet* __restrict__ bsets, const Slot* __restrict__ slots, uint32_t nslots,
-    const DevStatus* st) {
-  extern __shared__ uint32_t s_at[];  // per sub-cell: the tile's next slot
+    DevStatus* st) {
+  extern __shared__ uint32_t s_at[];  // per sub-cell: the tile's count, then its next slot
   if (failed(st)) return;
   const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
   const BkSet& S = bsets[sl.seg];
@@ -282,67 +209,100 @@ __global__ void __launch_bounds__(kScThreads, 1) bucket_scatter_kernel(
   const uint32_t subs = bk_cells(bl1);
   const int sh = 63 - 3 * bl1, lsh = 1 + 3 * bl1;
   const uint64_t keep1 = S.keep << 3;
-  const uint32_t n = S.n;
-  const uint32_t* tb = S.tbase + (uint64_t)t * subs;
-  for (uint32_t c = threadIdx.x; c < subs; c += blockDim.x)
-    s_at[c] = S.sbase[c] + tb[c];  // (garbage for sub-cells the tile does not touch: never read)
+  for (uint32_t c = threadIdx.x; c < subs; c += blockDim.x) s_at[c] = 0;
   __syncthreads();
   const uint64_t base = (uint64_t)t * S.tile;
   const uint32_t cnt = (uint32_t)((S.n - base) < (uint64_t)S.tile ? (S.n - base) : S.tile);
   const float* xyz = S.xyz + 3 * base;
-  uint64_t* const items = S.items;
-  uint32_t done = 0;
-  if ((reinterpret_cast<uintptr_t>(S.xyz) & 15u) == 0) {
-    // A round: the loads of kScGroups groups of 4 points, their keys, their
-    // slots (atomics), their stores -- each step for all of them at once.
-    const float4* v = reinterpret_cast<const float4*>(xyz);
-    const uint32_t ng = cnt / 4;
-    for (uint32_t g0 = 0; g0 < ng; g0 += kScGroups * kScThreads) {
-      float p[kScGroups][12];
+  const bool vec = (reinterpret_cast<uintptr_t>(S.xyz) & 15u) == 0;
+  const float4* v4 = reinterpret_cast<const float4*>(xyz);  // 4 points = 3 float4
+  const uint32_t ng = vec ? cnt / 4 : 0u, done = 4 * ng;
+  bool bad = false;
+
+  // 1. the tile's histogram
+  for (uint32_t g0 = 0; g0 < ng; g0 += kScGroups * kScThreads) {
+    float4 a[kScGroups], b[kScGroups], c[kScGroups];
 #pragma unroll
-      for (int u = 0; u < kScGroups; ++u) {
-        const uint32_t g = g0 + u * kScThreads + threadIdx.x;
-        if (g < ng) {
-          const float4 a = __ldcs(v + 3 * g), b = __ldcs(v + 3 * g + 1), c = __ldcs(v + 3 * g + 2);
-          p[u][0] = a.x; p[u][1] = a.y; p[u][2] = a.z; p[u][3] = a.w;
-          p[u][4] = b.x; p[u][5] = b.y; p[u][6] = b.z; p[u][7] = b.w;
-          p[u][8] = c.x; p[u][9] = c.y; p[u][10] = c.z; p[u][11] = c.w;
-        }
+    for (int u = 0; u < kScGroups; ++u) {
+      const uint32_t g = g0 + u * kScThreads + threadIdx.x;
+      if (g < ng) {
+        a[u] = __ldcg(v4 + 3 * g);
+        b[u] = __ldcg(v4 + 3 * g + 1);
+        c[u] = __ldcg(v4 + 3 * g + 2);
       }
-      uint64_t key[4 * kScGroups];
-      uint32_t pos[4 * kScGroups];
-#pragma unroll
-      for (int u = 0; u < kScGroups; ++u)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          bool ok;
-          key[4 * u + q] = spread_key(p[u][3 * q], p[u][3 * q + 1], p[u][3 * q + 2], &ok);
-        }
-#pragma unroll
-      for (int u = 0; u < kScGroups; ++u) {
-        const bool in = g0 + u * kScThreads + threadIdx.x < ng;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          pos[4 * u + q] = in ? atomicAdd(&s_at[(uint32_t)(key[4 * u + q] >> sh)], 1u) : n;
-      }
-      // (slots beyond n would mean coordinates that changed since the count)
-#pragma unroll
-      for (int u = 0; u < kScGroups; ++u)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t j = 4 * (g0 + u * kScThreads + threadIdx.x) + q;
-          if (pos[4 * u + q] < n)
-            items[pos[4 * u + q]] = ((key[4 * u + q] << lsh) & keep1) | (uint32_t)(base + j);
-        }
     }
-    done = cnt & ~3u;
+#pragma unroll
+    for (int u = 0; u < kScGroups; ++u) {
+      const uint32_t g = g0 + u * kScThreads + threadIdx.x;
+      if (g < ng) {
+        bool ok0, ok1, ok2, ok3;
+        atomicAdd(&s_at[cell_of(a[u].x, a[u].y, a[u].z, bl1, &ok0)], 1u);
+        atomicAdd(&s_at[cell_of(a[u].w, b[u].x, b[u].y, bl1, &ok1)], 1u);
+        atomicAdd(&s_at[cell_of(b[u].z, b[u].w, c[u].x, bl1, &ok2)], 1u);
+        atomicAdd(&s_at[cell_of(c[u].y, c[u].z, c[u].w, bl1, &ok3)], 1u);
+        bad |= !(ok0 && ok1 && ok2 && ok3);
+      }
+    }
   }
   for (uint32_t j = done + threadIdx.x; j < cnt; j += kScThreads) {
     bool ok;
-    const uint64_t key = spread_key(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], &ok);
-    const uint32_t pos = atomicAdd(&s_at[(uint32_t)(key >> sh)], 1u);
-    if (pos < n) items[pos] = ((key << lsh) & keep1) | (uint32_t)(base + j);
+    atomicAdd(&s_at[cell_of(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], bl1, &ok)], 1u);
+    bad |= !ok;
   }
+  if (bad) set_error(st, FMM_ERR_DOMAIN);
+  __syncthreads();
+
+  // 2. the tile's ranges: four atomics of a thread in flight together
+  for (uint32_t c0 = 0; c0 < subs; c0 += 4 * kScThreads) {
+    uint32_t hh[4], r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t c = c0 + u * kScThreads + threadIdx.x;
+      hh[u] = c < subs ? s_at[c] : 0u;
+      r[u] = hh[u] ? atomicAdd(&S.sct[c], hh[u]) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t c = c0 + u * kScThreads + threadIdx.x;
+      if (hh[u]) s_at[c] = c * (uint32_t)kBkCap + r[u];
+    }
+  }
+  __syncthreads();
+
+  // 3. the items, each at the next slot of its sub-cell's range
+  uint64_t* const items = S.items;
+  auto put = [&](float x, float y, float z, uint32_t j) {
+    bool ok;
+    const uint64_t key = spread_key(x, y, z, &ok);
+    const uint32_t sc = (uint32_t)(key >> sh);
+    const uint32_t pos = atomicAdd(&s_at[sc], 1u);
+    if (pos < (sc + 1u) * (uint32_t)kBkCap)  // (a sub-cell over its room keeps what fits)
+      items[pos] = ((key << lsh) & keep1) | (uint32_t)(base + j);
+  };
+  for (uint32_t g0 = 0; g0 < ng; g0 += kScGroups * kScThreads) {
+    float4 a[kScGroups], b[kScGroups], c[kScGroups];
+#pragma unroll
+    for (int u = 0; u < kScGroups; ++u) {
+      const uint32_t g = g0 + u * kScThreads + threadIdx.x;
+      if (g < ng) {
+        a[u] = __ldcs(v4 + 3 * g);
+        b[u] = __ldcs(v4 + 3 * g + 1);
+        c[u] = __ldcs(v4 + 3 * g + 2);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kScGroups; ++u) {
+      const uint32_t g = g0 + u * kScThreads + threadIdx.x;
+      if (g < ng) {
+        put(a[u].x, a[u].y, a[u].z, 4 * g);
+        put(a[u].w, b[u].x, b[u].y, 4 * g + 1);
+        put(b[u].z, b[u].w, c[u].x, 4 * g + 2);
+        put(c[u].y, c[u].z, c[u].w, 4 * g + 3);
+      }
+    }
+  }
+  for (uint32_t j = done + threadIdx.x; j < cnt; j += kScThreads)
+    put(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], j);
 }
 
 // ---------------------------------------------------------------------------
@@ -461,7 +421,7 @@ __global__ void __launch_bounds__(kBkThreads, 3) bucket_boxes_kernel(
 
   // 1. The sub-cell's items (all loads in flight together; kept in L2 for
   // the counting sort's scatter, which reads them again).
-  const uint64_t* src = S.items + offj;
+  const uint64_t* src = S.items + (uint64_t)cell1 * kBkCap;
   const uint32_t ng = 1u << D;
   const int gsh = 64 - D;
   uint32_t rk[kBkItems];
@@ -734,19 +694,6 @@ __global__ void __launch_bounds__(kBkThreads, 3) bucket_boxes_kernel(
 }
 
 // ---------------------------------------------------------------------------
-void launch_bucket_count(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
-                         int max_bl, DevStatus* st, cudaStream_t s) {
-  if (tiles == 0) return;
-  static const bool attr = [] {
-    cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(uint32_t) * 8 * kBkMaxCells));
-    return true;
-  }();
-  (void)attr;
-  const size_t smem = sizeof(uint32_t) * 8 * (1u << (3 * max_bl));
-  bucket_count_kernel<<<tiles, kBkTileThreads, smem, s>>>(bsets, slots, nslots, st);
-}
-
 void launch_bucket_plan(const BkSet* bsets, uint32_t nsets, DevStatus* st, cudaStream_t s) {
   if (nsets == 0) return;
   bucket_plan_kernel<<<nsets, kBkPlanThreads, 0, s>>>(bsets, st);

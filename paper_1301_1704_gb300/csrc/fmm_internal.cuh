@@ -384,13 +384,11 @@ struct BkSet {
   uint64_t keep;     // key bits an item keeps (box-key order: down to Lb only)
   uint32_t tile;     // points of a count / scatter tile
   uint32_t ntiles;
-  uint32_t* sct;     // [8^(bl+1)] points per sub-cell (zeroed before the count)
-  uint32_t* tbase;   // [ntiles][8^(bl+1)] a tile's first slot inside each sub-cell
-  uint32_t* sbase;   // [8^(bl+1)] the sub-cells' first slots (bookmarks)
+  uint32_t* sct;     // [8^(bl+1)] points per sub-cell (zeroed before the scatter)
   uint32_t* bcell;   // [nslot] non-empty cells, ascending
   uint32_t* boff;    // [nslot + 1] their bookmarks
   uint32_t* info;    // [4]: non-empty cells, largest cell
-  uint64_t* items;   // [n] the points' items, grouped by sub-cell
+  uint64_t* items;   // [8^(bl+1)][kBkCap] the points' items, sub-cell c's from slot c kBkCap
   uint32_t* soff;    // [8 * nslot] sub-cell bookmarks
   uint32_t* scnt;    // [8 * nslot] sub-cell sizes
   uint64_t* status;  // [kLevels][8 * nslot] look-back words of the box ranks (zeroed)
@@ -417,7 +415,6 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 constexpr int kListThreads = 256;
 
-constexpr int kBkTileThreads = 512;                 // count blocks (three an SM)
 constexpr int kBkPlanThreads = 1024;
 constexpr int kBkThreads = 512;                     // a sub-cell's block (8 sub-cells a bucket)
 constexpr int kBkItems = 12;
@@ -551,8 +548,6 @@ void launch_list_fill(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
 // bucket slots (slot unit0 = the set's first bucket slot); boxes: units =
 // bucket slots as for split, 8 blocks each (one per sub-cell), taken in
 // order by ticket (slot unit0 = the set's first sub-cell slot).
-void launch_bucket_count(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
-                         int max_bl, DevStatus* st, cudaStream_t s);
 void launch_bucket_plan(const BkSet* bsets, uint32_t nsets, DevStatus* st, cudaStream_t s);
 void launch_bucket_scatter(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
                            int max_bl, DevStatus* st, cudaStream_t s);
