@@ -223,12 +223,12 @@ int fmm_query_sizes(uint32_t N, uint32_t M, fmm_params params, fmm_sizes* out);
  *                        used when every set's sort depth is at most 8 and
  *                        the histograms hold at most 2^28 cells (else RTS).
  *   FMM_SORT_BUCKET      fixed-depth builds: the points are bucketed on
- *                        coarse cells (a histogram in shared memory and
- *                        atomic ranks per tile, the cells' prefix sum as
- *                        their bookmarks -- Alg. 1 and 3 at a coarse level),
- *                        then each bucket is sorted in shared memory by one
- *                        block, which also emits the boxes of every level;
- *                        a set whose bucket is too full for one block (the
+ *                        coarse cells in one pass (a histogram in shared
+ *                        memory and atomic ranks per tile, the cells' prefix
+ *                        sum as their bookmarks -- Alg. 1 and 3 at a coarse
+ *                        level), then each cell is sorted in shared memory
+ *                        by one block, which also emits the boxes of every
+ *                        level; a set whose cell is too full for one block (the
  *                        build is then redone, and the context builds the
  *                        same input pointer and size by the radix passes
  *                        directly until its tuning changes), and every
