@@ -852,14 +852,20 @@ struct BucketMem {
 // bucket path cannot take it (too many points for level-4 buckets, more box
 // levels below the sub-cells than an item keeps, or a box-key order whose
 // boxes would span several sub-cells).
+// Cell level of the buckets of n points: the mean sub-cell at most 3/4 of
+// what one block sorts; -1 when even level-4 buckets are too few.
+int bucket_level(uint64_t n) {
+  const uint64_t avg = (uint64_t)kBkCap * 3 / 4;
+  int bl = 0;
+  while (bl < kBkMaxLevel && n > (avg << (3 * (bl + 1)))) ++bl;
+  return n > (avg << (3 * (bl + 1))) ? -1 : bl;
+}
+
 bool bucket_params(uint32_t n, int Lb, bool exact, BkSet* b) {
   std::memset(b, 0, sizeof(*b));
   if (n == 0) return false;
-  // the mean sub-cell at most 3/4 of what one block sorts
-  const uint64_t avg = (uint64_t)kBkCap * 3 / 4;
-  int bl = 0;
-  while (bl < kBkMaxLevel && (uint64_t)n > (avg << (3 * (bl + 1)))) ++bl;
-  if ((uint64_t)n > (avg << (3 * (bl + 1)))) return false;
+  const int bl = bucket_level(n);
+  if (bl < 0) return false;
   const int ib = n <= 1 ? 1 : 32 - __builtin_clz(n - 1);
   const int kept = 61 - ib;  // key bits an item keeps below the sub-cell
   const int below = Lb - bl - 1;
@@ -1733,6 +1739,15 @@ void workspace_parts(uint32_t N, uint32_t M, const fmm_params& p, uint64_t* byte
     const uint64_t n = ns[k];
     if (p.flags & FMM_FLAG_HOST_INPUT) total += align_up(12 * n);
     total += 2 * align_up(12 * n + 48) + align_up(4 * n) + (16 << 10);
+    // the bucket path's sub-cells each have room for what one block sorts:
+    // its items can outgrow the radix passes' arrays
+    const int bl = n ? bucket_level(n) : -1;
+    if (bl >= 0) {
+      const uint64_t subs = 8ull << (3 * bl);
+      const uint64_t bk = subs * (8ull * kBkCap + 8ull * kLevels + 64) + (64 << 10);
+      const uint64_t rx = 2 * align_up(12 * n + 48);
+      if (bk > rx) total += bk - rx;
+    }
     const uint64_t tiles = n / (kSortThreads * 4) + 1;  // the smallest tile
     total += tiles * kRadixMax * 4 * 3 + (n / kBoxTile + 1) * 8 * (1 + kLevels);
     total += tiles * sizeof(TileRec) * 8 + 8 * 256;  // tile records, 8 passes

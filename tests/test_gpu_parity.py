@@ -491,3 +491,29 @@ def test_bucket_batched_sets_of_every_size(ctx, orc):
     trees = ctx.build_batched([(d, d) for d in devs], L=6)
     for p, t in zip(pts, trees):
         compare_full(t.numpy(), orc.build_tree(p, p, L=6), 6)
+
+
+def test_workspace_bound_holds():
+    """fmm_query_workspace bounds the arena a build needs: a fresh context's
+    arena, sized from that bound, does not grow during the build -- also
+    where the bucket path's sub-cells (room for one block's points each)
+    outgrow the radix arrays, and where a set overflows and is redone."""
+    from paper_1301_1704_gb300 import fmmds
+    cases = [(workloads.uniform(5, 90), 2), (workloads.uniform(294913, 91), 2),
+             (workloads.uniform(294913, 92), 7), (workloads.uniform(1 << 20, 93), 3),
+             (workloads.clumps(300000, 94, nclumps=2, sigma=0.002), 4)]
+    for pts, L in cases:
+        d = _dev(pts)
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        c = fmmds.Context(0)
+        try:
+            c.build(d, d, L=L, raw=True)
+            torch.cuda.synchronize()
+            used = torch.cuda.memory_allocated() - before
+        finally:
+            c.close()
+        # torch's allocator rounds a block up (to 2 MiB for large ones); an
+        # arena that grew would have added a chunk of 64 MiB or more
+        bound = fmmds.query_workspace(len(pts), len(pts), L=L)
+        assert used <= (bound + (2 << 20) - 1) // (2 << 20) * (2 << 20), (len(pts), L, used, bound)
