@@ -370,8 +370,8 @@ struct ListLevel {
 };
 
 // One point set on the bucket path (bucket.cu): the points are bucketed on
-// the cells of level bl, each bucket is split into its 8 sub-cells (level
-// bl + 1), and each sub-cell is sorted, and its boxes emitted, by one block.
+// the sub-cells (level bl + 1) of the cells of level bl, in one pass, and
+// each sub-cell is sorted, and its boxes emitted, by one block.
 // Device-resident; built on the host.
 struct BkSet {
   const float* xyz;  // [n][3]
@@ -382,7 +382,7 @@ struct BkSet {
   int D;             // group bits of a sub-cell's counting sort
   int trunc;         // items hold fewer key bits than lie below the cell
   uint64_t keep;     // key bits an item keeps (box-key order: down to Lb only)
-  uint32_t tile;     // points of a count / scatter tile
+  uint32_t tile;     // points of a scatter tile
   uint32_t ntiles;
   uint32_t* sct;     // [8^(bl+1)] points per sub-cell (zeroed before the scatter)
   uint32_t* bcell;   // [nslot] non-empty cells, ascending
