@@ -960,23 +960,30 @@ int bucket_setup(fmm_ctx* c, std::vector<SetPlan>& sets, BucketMem* bm) {
   return dev_zero(c, zero, zero_bytes);
 }
 
-// scatter -> plan of bucket set k, or of all bucket sets (k < 0).
-// A one-set launch runs the set's tiles from unit 0 (slot {k, 0}).
-int bucket_sort(fmm_ctx* c, const BucketMem& m, int k) {
-  cudaStream_t s = c->stream;
+// Scatter of tiles [t0, t1) of bucket set k (one-set slot {k, 0}), or of
+// every tile of all bucket sets (k < 0).
+int bucket_scatter(fmm_ctx* c, const BucketMem& m, int k, uint32_t t0, uint32_t t1) {
   const Slot* slots = k < 0 ? m.tile_slots : m.one_slots + k;
   const uint32_t nsl = k < 0 ? m.count() : 1u;
-  const uint32_t tiles = k < 0 ? m.tiles : m.host[k].ntiles;
   const int max_bl = k < 0 ? m.max_bl : m.host[k].bl;
-  {
+  if (t1 > t0) {
     Launch L(c, "bucket_scatter");
-    launch_bucket_scatter(m.bsets, slots, nsl, tiles, max_bl, c->st, s);
-  }
-  {
-    Launch L(c, "bucket_plan");
-    launch_bucket_plan(k < 0 ? m.bsets : m.bsets + k, nsl, c->st, s);
+    launch_bucket_scatter(m.bsets, slots, nsl, t0, t1 - t0, max_bl, c->st, c->stream);
   }
   return cuda_status(cudaGetLastError());
+}
+
+// Plan of bucket set k, or of all bucket sets (k < 0), once scattered.
+int bucket_plan(fmm_ctx* c, const BucketMem& m, int k) {
+  Launch L(c, "bucket_plan");
+  launch_bucket_plan(k < 0 ? m.bsets : m.bsets + k, k < 0 ? m.count() : 1u, c->st, c->stream);
+  return cuda_status(cudaGetLastError());
+}
+
+// scatter -> plan of bucket set k, or of all bucket sets (k < 0).
+int bucket_sort(fmm_ctx* c, const BucketMem& m, int k) {
+  FMM_TRY(bucket_scatter(c, m, k, 0, k < 0 ? m.tiles : m.host[k].ntiles));
+  return bucket_plan(c, m, k);
 }
 
 // The boxes of bucket set k alone (its own tickets), into the outputs `segs`
@@ -1632,15 +1639,27 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   }
 
   Readback rb;
+  // Each set's copy goes in a few tile-aligned chunks: a scatter tile needs
+  // only its own points, so each chunk is scattered as soon as it has landed,
+  // and only the last chunk's scatter, the plan and the boxes follow the
+  // set's copy.
   const std::function<int(const Seg*)> copy_sort_box = [&](const Seg* segs) -> int {
     for (uint32_t k = 0; k < sets.size(); ++k) {
       SetPlan& sp = sets[k];
-      if (sp.n)
-        FMM_CUDA(cudaMemcpyAsync(const_cast<float*>(sp.xyz), host_xyz[k],
-                                 sizeof(float) * 3 * sp.n, cudaMemcpyHostToDevice, c->cstream));
-      FMM_CUDA(cudaEventRecord(c->cevent, c->cstream));
-      FMM_CUDA(cudaStreamWaitEvent(s, c->cevent, 0));
-      FMM_TRY(bucket_sort(c, bm, (int)k));
+      const BkSet& b = bm.host[k];
+      const uint32_t nchunk = std::min<uint32_t>(kCopyChunks, b.ntiles);
+      const uint32_t per = (b.ntiles + nchunk - 1) / nchunk;
+      for (uint32_t t0 = 0; t0 < b.ntiles; t0 += per) {
+        const uint32_t t1 = std::min(b.ntiles, t0 + per);
+        const uint64_t p0 = (uint64_t)t0 * b.tile, p1 = std::min<uint64_t>(sp.n, (uint64_t)t1 * b.tile);
+        FMM_CUDA(cudaMemcpyAsync(const_cast<float*>(sp.xyz) + 3 * p0, host_xyz[k] + 3 * p0,
+                                 sizeof(float) * 3 * (p1 - p0), cudaMemcpyHostToDevice,
+                                 c->cstream));
+        FMM_CUDA(cudaEventRecord(c->cevent, c->cstream));
+        FMM_CUDA(cudaStreamWaitEvent(s, c->cevent, 0));
+        FMM_TRY(bucket_scatter(c, bm, (int)k, t0, t1));
+      }
+      FMM_TRY(bucket_plan(c, bm, (int)k));
       FMM_TRY(bucket_boxes_one(c, bm, segs, k, wait_ns));
     }
     return FMM_OK;

@@ -199,12 +199,13 @@ constexpr int kScGroups = 2;  // groups of 4 points a thread loads ahead
 
 __global__ void __launch_bounds__(kScThreads, 1) bucket_scatter_kernel(
     const BkSet* __restrict__ bsets, const Slot* __restrict__ slots, uint32_t nslots,
-    DevStatus* st) {
+    uint32_t t_first, DevStatus* st) {
   extern __shared__ uint32_t s_at[];  // per sub-cell: the tile's count, then its next slot
   if (failed(st)) return;
-  const Slot sl = slots[find_slot(slots, nslots, blockIdx.x)];
+  const uint32_t unit = blockIdx.x + t_first;  // (a launch may start past unit 0)
+  const Slot sl = slots[find_slot(slots, nslots, unit)];
   const BkSet& S = bsets[sl.seg];
-  const uint32_t t = blockIdx.x - sl.unit0;
+  const uint32_t t = unit - sl.unit0;
   const int bl1 = S.bl + 1;
   const uint32_t subs = bk_cells(bl1);
   const int sh = 63 - 3 * bl1, lsh = 1 + 3 * bl1;
@@ -699,8 +700,8 @@ void launch_bucket_plan(const BkSet* bsets, uint32_t nsets, DevStatus* st, cudaS
   bucket_plan_kernel<<<nsets, kBkPlanThreads, 0, s>>>(bsets, st);
 }
 
-void launch_bucket_scatter(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
-                           int max_bl, DevStatus* st, cudaStream_t s) {
+void launch_bucket_scatter(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t t_first,
+                           uint32_t tiles, int max_bl, DevStatus* st, cudaStream_t s) {
   if (tiles == 0) return;
   static const bool attr = [] {
     cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -709,7 +710,7 @@ void launch_bucket_scatter(const BkSet* bsets, const Slot* slots, uint32_t nslot
   }();
   (void)attr;
   const size_t smem = sizeof(uint32_t) * 8 * (1u << (3 * max_bl));
-  bucket_scatter_kernel<<<tiles, kScThreads, smem, s>>>(bsets, slots, nslots, st);
+  bucket_scatter_kernel<<<tiles, kScThreads, smem, s>>>(bsets, slots, nslots, t_first, st);
 }
 
 void launch_bucket_boxes(const BkSet* bsets, const Seg* segs, const Slot* slots, uint32_t nslots,

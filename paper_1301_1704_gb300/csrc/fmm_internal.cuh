@@ -420,6 +420,7 @@ constexpr int kBkThreads = 512;                     // a sub-cell's block (8 sub
 constexpr int kBkItems = 12;
 constexpr int kBkCap = kBkThreads * kBkItems;       // 6144 points sorted by one block
 constexpr int kBkGroupBits = 11;                    // groups of a sub-cell's counting sort
+constexpr uint32_t kCopyChunks = 8;                 // pieces of a set's host copy (pipelined input)
 constexpr int kBkMaxLevel = 4;                      // bucket cells of level 4 at most
 constexpr int kBkMaxCells = 1 << (3 * kBkMaxLevel);  // 4096
 constexpr uint32_t kBkTieRun = 32;                  // longest run of tied items one thread orders
@@ -549,8 +550,9 @@ void launch_list_fill(const Seg* segs, const Job* jobs, uint32_t njobs, int l,
 // bucket slots as for split, 8 blocks each (one per sub-cell), taken in
 // order by ticket (slot unit0 = the set's first sub-cell slot).
 void launch_bucket_plan(const BkSet* bsets, uint32_t nsets, DevStatus* st, cudaStream_t s);
-void launch_bucket_scatter(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t tiles,
-                           int max_bl, DevStatus* st, cudaStream_t s);
+// Tiles [t_first, t_first + tiles) of the launch's units.
+void launch_bucket_scatter(const BkSet* bsets, const Slot* slots, uint32_t nslots, uint32_t t_first,
+                           uint32_t tiles, int max_bl, DevStatus* st, cudaStream_t s);
 void launch_bucket_boxes(const BkSet* bsets, const Seg* segs, const Slot* slots, uint32_t nslots,
                          uint32_t units, int max_lb, uint32_t* ticket, DevStatus* st,
                          uint64_t wait_ns, cudaStream_t s);
