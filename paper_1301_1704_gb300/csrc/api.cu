@@ -43,6 +43,17 @@ struct TimeAcc {
   double ms;
 };
 
+// Host input of a pipelined build: at most kPipeSets sets, each copied in at
+// most kCopyChunks pieces of whole 2^16-point blocks.
+constexpr uint32_t kPipeSets = 4;
+constexpr uint32_t kCopyChunks = 8;
+constexpr uint64_t kCopyGrain = 1u << 16;
+
+uint64_t copy_chunk_points(uint64_t n) {
+  const uint64_t per = (n + kCopyChunks - 1) / kCopyChunks;
+  return std::max<uint64_t>(kCopyGrain, (per + kCopyGrain - 1) / kCopyGrain * kCopyGrain);
+}
+
 }  // namespace
 
 struct fmm_ctx {
@@ -79,9 +90,12 @@ struct fmm_ctx {
   // earlier work.
   cudaStream_t gstream = nullptr;
   cudaEvent_t gevent = nullptr;
-  // host-input copies of a pipelined build (see do_builds_on)
+  // host-input copies of a pipelined build (see do_builds_on): the copy
+  // stream, the event that orders it behind the build stream, and one event
+  // per copied piece (set k's piece j: k * kCopyChunks + j)
   cudaStream_t cstream = nullptr;
   cudaEvent_t cevent = nullptr;
+  cudaEvent_t chunk_ev[kPipeSets * kCopyChunks] = {};
   // sets of the build in progress kept off the bucket path (a bucket of
   // theirs was too full for one block)
   std::vector<uint8_t> no_bucket;
@@ -999,11 +1013,13 @@ int bucket_boxes_one(fmm_ctx* c, const BucketMem& bm, const Seg* segs, uint32_t 
 // Box and list stages of a build over sorted `sets` (SetPlan::Lb and
 // JobPlan::L fixed).
 // `early`, when given, runs once the outputs are allocated and cleared, in
-// place of the all-sets bucket boxes launch: the pipelined host-input build
-// copies, sorts and boxes its bucket sets one at a time there.
+// place of the all-sets bucket boxes and occupancy launches: the pipelined
+// host-input build copies, sorts and boxes its bucket sets one at a time
+// there, calling its second argument with each set once that set is boxed.
+using EarlyFn = std::function<int(const Seg*, const std::function<int(uint32_t)>&)>;
 int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs,
               const fmm_params& prm, const BucketMem& bm, Readback* rb,
-              const std::function<int(const Seg*)>* early = nullptr) {
+              const EarlyFn* early = nullptr) {
   cudaStream_t s = c->stream;
   int err = FMM_OK;
   const uint64_t wait_ns = wait_ns_of(prm);
@@ -1190,7 +1206,18 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
   FMM_TRY(dev_zero2(c, zero, zero_bytes, async_lists ? list_zero : nullptr,
                     async_lists ? list_zero_bytes : 0));
 
-  if (early) FMM_TRY((*early)(m.segs));
+  if (early) {
+    // a set's child occupancy needs only that set's boxes
+    const std::function<int(uint32_t)> boxed = [&](uint32_t set) -> int {
+      for (const Slot& o : occ)
+        if (o.seg == set) {
+          Launch L(c, "occupancy");
+          launch_occupancy(m.segs, m.occ_slots, (uint32_t)occ.size(), o.aux0, o.unit0, c->st, s);
+        }
+      return FMM_OK;
+    };
+    FMM_TRY((*early)(m.segs, boxed));
+  }
 
   // ---- boxes, occupancy.
   if (bm.units && !early) {
@@ -1215,9 +1242,9 @@ int run_build(fmm_ctx* c, std::vector<SetPlan>& sets, std::vector<JobPlan>& jobs
     launch_coarse_boxes(m.segs, m.crs_slots, (uint32_t)crs.size(), m.crs_units, max_lb, c->st,
                         wait_ns, s);
   }
-  if (m.occ_units) {
+  if (m.occ_units && !early) {
     Launch L(c, "occupancy");
-    launch_occupancy(m.segs, m.occ_slots, (uint32_t)occ.size(), m.occ_units, c->st, s);
+    launch_occupancy(m.segs, m.occ_slots, (uint32_t)occ.size(), m.occ_units, 0, c->st, s);
   }
 
   auto read_sets = [&](bool lists) -> int {
@@ -1459,15 +1486,53 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   // under that sort; otherwise every copy precedes the build.
   bool all_fixed = true;
   for (uint32_t k = 0; k < npairs; ++k) all_fixed &= (pairs[k].L >= 0 ? pairs[k].L : prm.L) >= 0;
-  const bool pipelined = host_in && !stall && all_fixed && sets.size() >= 2 && sets.size() <= 4;
+  const bool pipelined =
+      host_in && !stall && all_fixed && sets.size() >= 2 && sets.size() <= kPipeSets;
   std::vector<const float*> host_xyz(sets.size(), nullptr);
   if (pipelined && !c->cstream) {
-    if (cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->cevent, cudaEventDisableTiming) != cudaSuccess) {
+    bool ok = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->cevent, cudaEventDisableTiming) == cudaSuccess;
+    for (auto& e : c->chunk_ev)
+      ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
       cudaGetLastError();
       return FMM_ERR_CUDA;
     }
   }
+  // Pinned (page-locked or registered) inputs are copied in full at once, in
+  // pieces whose events the sort waits on; a pageable copy holds the host
+  // until it is done, so each piece of one is issued just before the work
+  // that needs it.
+  bool upfront = pipelined;
+  for (size_t i = 0; upfront && i < sets.size(); ++i) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, sets[i].xyz) != cudaSuccess) {
+      cudaGetLastError();
+      upfront = false;
+    } else {
+      upfront = a.type == cudaMemoryTypeHost;
+    }
+  }
+  const auto chunks_of = [&](uint64_t n) -> uint32_t {
+    return (uint32_t)((n + copy_chunk_points(n) - 1) / copy_chunk_points(n));
+  };
+  const auto chunk_end = [&](uint64_t n, uint32_t j) -> uint64_t {
+    return std::min<uint64_t>(n, copy_chunk_points(n) * (j + 1));
+  };
+  const auto copy_chunk = [&](uint32_t k, uint32_t j) -> int {
+    const uint64_t n = sets[k].n, p0 = j ? chunk_end(n, j - 1) : 0, p1 = chunk_end(n, j);
+    FMM_CUDA(cudaMemcpyAsync(const_cast<float*>(sets[k].xyz) + 3 * p0, host_xyz[k] + 3 * p0,
+                             sizeof(float) * 3 * (p1 - p0), cudaMemcpyHostToDevice,
+                             c->cstream));
+    FMM_CUDA(cudaEventRecord(c->chunk_ev[k * kCopyChunks + j], c->cstream));
+    return FMM_OK;
+  };
+  // Piece j of set k is on the device for the build stream's next launches.
+  const auto land = [&](uint32_t k, uint32_t j) -> int {
+    if (!upfront) FMM_TRY(copy_chunk(k, j));
+    FMM_CUDA(cudaStreamWaitEvent(s, c->chunk_ev[k * kCopyChunks + j], 0));
+    return FMM_OK;
+  };
   if (host_in) {
     for (size_t i = 0; i < sets.size(); ++i) {
       SetPlan& sp = sets[i];
@@ -1481,6 +1546,9 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
     if (pipelined) {  // the copies start after the build stream's earlier work
       FMM_CUDA(cudaEventRecord(c->cevent, s));
       FMM_CUDA(cudaStreamWaitEvent(c->cstream, c->cevent, 0));
+      if (upfront)
+        for (uint32_t k = 0; k < sets.size(); ++k)
+          for (uint32_t j = 0; j < chunks_of(sets[k].n); ++j) FMM_TRY(copy_chunk(k, j));
     }
   }
   std::vector<SetPlan*> all;
@@ -1545,16 +1613,12 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
     if (early_boxes) {
       // (sorted and boxed in run_build)
     } else if (pipelined) {
-      // set i's copy, then its sort behind an event; copy i+1 is issued after
-      // sort i's launches (a pageable copy holds the host meanwhile)
+      // set i's copy, then its sort behind its pieces' events; a pageable
+      // set i+1 is copied after sort i's launches
       uint32_t kb = 0;
-      for (size_t i = 0; i < sets.size(); ++i) {
+      for (uint32_t i = 0; i < sets.size(); ++i) {
         SetPlan& sp = sets[i];
-        if (sp.n)
-          FMM_CUDA(cudaMemcpyAsync(const_cast<float*>(sp.xyz), host_xyz[i],
-                                   sizeof(float) * 3 * sp.n, cudaMemcpyHostToDevice, c->cstream));
-        FMM_CUDA(cudaEventRecord(c->cevent, c->cstream));
-        FMM_CUDA(cudaStreamWaitEvent(s, c->cevent, 0));
+        for (uint32_t j = 0; j < chunks_of(sp.n); ++j) FMM_TRY(land(i, j));
         if (sp.bucket) {
           FMM_TRY(bucket_sort(c, bm, (int)kb++));
         } else {
@@ -1639,28 +1703,28 @@ int do_builds_on(fmm_ctx* c, const PairIn* pairs, uint32_t npairs, const fmm_par
   }
 
   Readback rb;
-  // Each set's copy goes in a few tile-aligned chunks: a scatter tile needs
-  // only its own points, so each chunk is scattered as soon as it has landed,
-  // and only the last chunk's scatter, the plan and the boxes follow the
-  // set's copy.
-  const std::function<int(const Seg*)> copy_sort_box = [&](const Seg* segs) -> int {
+  // A scatter tile needs only its own points, so the tiles of each copied
+  // piece are scattered as soon as it has landed, and only the last piece's
+  // scatter, the plan and the boxes follow the set's copy.
+  const EarlyFn copy_sort_box = [&](const Seg* segs,
+                                    const std::function<int(uint32_t)>& boxed) -> int {
     for (uint32_t k = 0; k < sets.size(); ++k) {
-      SetPlan& sp = sets[k];
+      const uint64_t n = sets[k].n;
       const BkSet& b = bm.host[k];
-      const uint32_t nchunk = std::min<uint32_t>(kCopyChunks, b.ntiles);
-      const uint32_t per = (b.ntiles + nchunk - 1) / nchunk;
-      for (uint32_t t0 = 0; t0 < b.ntiles; t0 += per) {
-        const uint32_t t1 = std::min(b.ntiles, t0 + per);
-        const uint64_t p0 = (uint64_t)t0 * b.tile, p1 = std::min<uint64_t>(sp.n, (uint64_t)t1 * b.tile);
-        FMM_CUDA(cudaMemcpyAsync(const_cast<float*>(sp.xyz) + 3 * p0, host_xyz[k] + 3 * p0,
-                                 sizeof(float) * 3 * (p1 - p0), cudaMemcpyHostToDevice,
-                                 c->cstream));
-        FMM_CUDA(cudaEventRecord(c->cevent, c->cstream));
-        FMM_CUDA(cudaStreamWaitEvent(s, c->cevent, 0));
-        FMM_TRY(bucket_scatter(c, bm, (int)k, t0, t1));
+      const uint32_t nch = chunks_of(n);
+      uint32_t t_done = 0;
+      for (uint32_t j = 0; j < nch; ++j) {
+        FMM_TRY(land(k, j));
+        // tiles wholly inside the pieces landed so far
+        const uint32_t t_hi = j + 1 == nch ? b.ntiles : (uint32_t)(chunk_end(n, j) / b.tile);
+        if (t_hi > t_done) {
+          FMM_TRY(bucket_scatter(c, bm, (int)k, t_done, t_hi));
+          t_done = t_hi;
+        }
       }
       FMM_TRY(bucket_plan(c, bm, (int)k));
       FMM_TRY(bucket_boxes_one(c, bm, segs, k, wait_ns));
+      FMM_TRY(boxed(k));
     }
     return FMM_OK;
   };
@@ -1864,6 +1928,8 @@ int fmm_destroy(fmm_ctx* c) {
   if (c->gevent) cudaEventDestroy(c->gevent);
   if (c->gstream) cudaStreamDestroy(c->gstream);
   if (c->cevent) cudaEventDestroy(c->cevent);
+  for (auto e : c->chunk_ev)
+    if (e) cudaEventDestroy(e);
   if (c->cstream) cudaStreamDestroy(c->cstream);
   cudaFree(c->st);
   if (c->up_buf) cudaFreeHost(c->up_buf);

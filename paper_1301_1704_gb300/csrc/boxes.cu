@@ -414,11 +414,13 @@ void launch_coarse_boxes(const Seg* segs, const Slot* slots, uint32_t nslots, ui
 // in proportion to its size; each unit takes a strided share of every level.
 __global__ void __launch_bounds__(256) occupancy_kernel(const Seg* __restrict__ segs,
                                                         const Slot* __restrict__ slots,
-                                                        uint32_t nslots, const DevStatus* st) {
+                                                        uint32_t nslots, uint32_t unit_first,
+                                                        const DevStatus* st) {
   if (failed(st)) return;
-  const uint32_t k = find_slot(slots, nslots, blockIdx.x);
+  const uint32_t unit = blockIdx.x + unit_first;
+  const uint32_t k = find_slot(slots, nslots, unit);
   const Seg& sg = segs[slots[k].seg];
-  const uint32_t u = blockIdx.x - slots[k].unit0, units = slots[k].aux0;
+  const uint32_t u = unit - slots[k].unit0, units = slots[k].aux0;
   for (int l = 0; l < sg.Lb; ++l) {
     const uint32_t nb = sg.nbox[l] < sg.lv.cap[l] ? sg.nbox[l] : sg.lv.cap[l];
     const uint32_t* ch = sg.lv.child[l];
@@ -435,9 +437,9 @@ __global__ void __launch_bounds__(256) occupancy_kernel(const Seg* __restrict__ 
 }
 
 void launch_occupancy(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
-                      DevStatus* st, cudaStream_t s) {
+                      uint32_t unit_first, DevStatus* st, cudaStream_t s) {
   if (units == 0) return;
-  occupancy_kernel<<<units, 256, 0, s>>>(segs, slots, nslots, st);
+  occupancy_kernel<<<units, 256, 0, s>>>(segs, slots, nslots, unit_first, st);
 }
 
 uint32_t occupancy_units(uint32_t n) { return 1u + n / 16384u; }

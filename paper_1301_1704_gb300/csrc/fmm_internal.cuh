@@ -420,7 +420,6 @@ constexpr int kBkThreads = 512;                     // a sub-cell's block (8 sub
 constexpr int kBkItems = 12;
 constexpr int kBkCap = kBkThreads * kBkItems;       // 6144 points sorted by one block
 constexpr int kBkGroupBits = 11;                    // groups of a sub-cell's counting sort
-constexpr uint32_t kCopyChunks = 8;                 // pieces of a set's host copy (pipelined input)
 constexpr int kBkMaxLevel = 4;                      // bucket cells of level 4 at most
 constexpr int kBkMaxCells = 1 << (3 * kBkMaxLevel);  // 4096
 constexpr uint32_t kBkTieRun = 32;                  // longest run of tied items one thread orders
@@ -506,9 +505,10 @@ void launch_child_sides(const uint32_t* child, const uint8_t* on_par, uint32_t n
                         uint8_t* sides, cudaStream_t s);
 void launch_box_type(const uint32_t* e4_off, const uint32_t* e4_idx, const uint8_t* sides,
                      const uint8_t* on, uint32_t nbox, int mode, uint8_t* type, cudaStream_t s);
-// Child-occupancy bytes of the slots' sets (slot aux0 = the set's units).
+// Child-occupancy bytes of the slots' sets (slot aux0 = the set's units):
+// the launch covers units [unit_first, unit_first + units).
 void launch_occupancy(const Seg* segs, const Slot* slots, uint32_t nslots, uint32_t units,
-                      DevStatus* st, cudaStream_t s);
+                      uint32_t unit_first, DevStatus* st, cudaStream_t s);
 uint32_t occupancy_units(uint32_t n);
 // Cluster-size depth per set (units: sort tiles of the slots' sets); out[set]
 // = 1 + deepest level shared by sorted points i and i + s, capped at Ls.

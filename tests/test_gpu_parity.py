@@ -187,6 +187,19 @@ def test_host_input_flag(ctx, orc):
     for a, b, ha, hb, L in ((src, tight, hs, ht, 6), (tight, src, ht, hs, 4)):
         got = ctx.build(ha, hb, L=L, flags=fmmds.FMM_FLAG_HOST_INPUT).numpy()
         compare_full(got, orc.build_tree(a, b, L=L), L)
+    # sets copied in several pieces, the last one ragged: pinned (issued at
+    # once) and pageable (issued piece by piece), bucket and radix paths
+    bs = workloads.uniform(300001, 25)
+    br = workloads.clumps(200003, 26, nclumps=4, sigma=0.05)
+    want = orc.build_tree(bs, br, L=6)
+    pinned = (torch.from_numpy(bs).pin_memory(), torch.from_numpy(br).pin_memory())
+    for a, b in (pinned, (torch.from_numpy(bs), torch.from_numpy(br))):
+        compare_full(ctx.build(a, b, L=6, flags=fmmds.FMM_FLAG_HOST_INPUT).numpy(), want, 6)
+    try:
+        ctx.set_tuning(fmmds.FMM_SORT_RTS)
+        compare_full(ctx.build(*pinned, L=6, flags=fmmds.FMM_FLAG_HOST_INPUT).numpy(), want, 6)
+    finally:
+        ctx.set_tuning(fmmds.FMM_SORT_BUCKET)
 
 
 @pytest.mark.parametrize("s", [1, 8, 64, 300])
