@@ -71,7 +71,11 @@ typedef void (*fmm_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 /* Build flags. */
 #define FMM_FLAG_HOST_INPUT 0x1u   /* src/recv point to host memory (pinned or
                                       pageable); the call copies them to the
-                                      device on its stream */
+                                      device after its stream's earlier work
+                                      (on an internal copy stream that its
+                                      stream then waits on, so that the copies
+                                      overlap the sort of the sets already
+                                      landed) */
 #define FMM_FLAG_BOX_ORDER 0x2u    /* order the points by (level-L box key,
                                       original index) instead of (full key,
                                       original index): the order inside a box
